@@ -1,0 +1,338 @@
+"""FP64 CPU oracle for compressed matrix multiplication (Pagh, "Compressed
+Matrix Multiplication", arXiv 1108.1320).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call or
+execute this module: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.  It shares
+no code with the CUDA library (no kernels, headers, helpers, tables or
+constants); the hash definition and its seeding are implemented here a second
+time, independently, from their published definitions.
+
+Everything is float64 (numpy) unless stated.  Indices are 0-based: the paper
+writes [n] = {1..n} and "for z := 1 to b" in Fig. 1 but maps into {0..b-1}
+in Sec. 2.2; we use 0-based row, column, inner and bucket indices and feed the
+0-based index to the hash polynomial.
+
+What each function follows:
+
+* ``splitmix64`` / ``draw_coefficients`` - seeding of the hash family.  The
+  paper does not say how hash functions are drawn; we use splitmix64 (Steele,
+  Lea, Flood, OOPSLA 2014) and draw, for t = 0..d-1, the (a, c) pairs of
+  h1, s1, h2, s2 in that order, a = 1 + (r mod (p-1)), c = r mod p.
+* ``hash_bucket`` / ``hash_sign`` - the degree-1 polynomial family of Sec. 2.2
+  and the paper's reference [13]: h(x) = ((a x + c) mod p) mod b with
+  p = 2^31 - 1; the sign function (unspecified in Sec. 2.1) is the same family
+  with range 2, mapped to {+1, -1}.
+* ``sketch_fft`` - COMPRESSEDPRODUCT of Fig. 1: per repetition t and inner
+  index k, count-sketch column k of A with (h1, s1) and row k of B with
+  (h2, s2), FFT both, multiply pointwise, accumulate over k, and apply one
+  inverse FFT (Sec. 2.2, the identity p*_{uv}(w^t) = p*_t).  The second
+  scatter in Fig. 1 writes ``pa[h_2(j)] := pb[h_2(j)] + ...``; it is read as
+  ``pb[h_2(j)] := pb[h_2(j)] + s_2(j) B_kj``.
+* ``sketch_definition`` - the same sketch from its definition (Sec. 2.2,
+  polynomial p*_{uv}; abstract: c = (p mod x^b) + (p div x^b)): the count
+  sketch of AB under the decomposed splitting function
+  h(i,j) = (h1(i) + h2(j)) mod b and sign s(i,j) = s1(i) s2(j).
+* ``sketch_convolution`` - the same sketch as an explicit length-b cyclic
+  convolution summed over k (Sec. 2.2, polynomial multiplication), with no
+  FFT: the "2-D sketch" M = sum_k pa_k pb_k^T folded along wrapped
+  anti-diagonals.
+* ``sketch_bucket_values`` - c_t[z] for a few buckets z straight from the
+  definition, one bucket at a time (for full-size spot checks).
+* ``decompress`` / ``decompress_dense`` - DECOMPRESS of Fig. 1:
+  X_t = s1_t(i) s2_t(j) c_t[(h1_t(i) + h2_t(j)) mod b], median over t.  The
+  median of an even number of values is the mean of the two middle ones.
+
+Every function here is pinned by tests under ``-m "not gpu"`` against facts
+that do not come from this module (published splitmix64 outputs, hand-worked
+hash values, the three independent sketch routes, the injective-hash and b=1
+special cases, the AMS identity of Sec. 2.1, Theorem 2's mean and variance,
+Theorem 5's exact recovery).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+P31 = (1 << 31) - 1          # the Mersenne prime p = 2^31 - 1 of the hash family
+_MASK64 = (1 << 64) - 1
+_GOLDEN_GAMMA = 0x9E3779B97F4A7C15
+_MIX1 = 0xBF58476D1CE4E5B9
+_MIX2 = 0x94D049BB133111EB
+
+HASH_NAMES = ("h1", "s1", "h2", "s2")
+
+
+# --------------------------------------------------------------------------
+# Seeding: splitmix64 (Steele, Lea, Flood 2014), plain Python integers.
+# --------------------------------------------------------------------------
+def splitmix64(state: int) -> tuple[int, int]:
+    """One splitmix64 step: returns (next_state, output)."""
+    state = (state + _GOLDEN_GAMMA) & _MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * _MIX1) & _MASK64
+    z = ((z ^ (z >> 27)) * _MIX2) & _MASK64
+    return state, z ^ (z >> 31)
+
+
+def draw_coefficients(seed: int, d: int) -> np.ndarray:
+    """Coefficients (a, c) of h1, s1, h2, s2 for each repetition t.
+
+    Returns an int64 array of shape (d, 4, 2): [t][function][a or c], the
+    functions in the order h1, s1, h2, s2.
+    """
+    out = np.zeros((d, 4, 2), dtype=np.int64)
+    state = seed & _MASK64
+    for t in range(d):
+        for f in range(4):
+            state, r = splitmix64(state)
+            out[t, f, 0] = 1 + r % (P31 - 1)
+            state, r = splitmix64(state)
+            out[t, f, 1] = r % P31
+    return out
+
+
+# --------------------------------------------------------------------------
+# Hash family of Sec. 2.2 / [13]: h(x) = ((a x + c) mod p) mod b.
+# --------------------------------------------------------------------------
+def hash_bucket(a: int, c: int, x: np.ndarray, b: int) -> np.ndarray:
+    """Splitting function value in {0..b-1} for 0-based indices x."""
+    x = np.asarray(x, dtype=np.uint64)
+    v = (np.uint64(a) * x + np.uint64(c)) % np.uint64(P31)
+    return (v % np.uint64(b)).astype(np.int64)
+
+
+def hash_sign(a: int, c: int, x: np.ndarray) -> np.ndarray:
+    """Sign function value in {+1, -1}: 1 - 2 * (((a x + c) mod p) mod 2)."""
+    x = np.asarray(x, dtype=np.uint64)
+    v = (np.uint64(a) * x + np.uint64(c)) % np.uint64(P31)
+    return (1 - 2 * (v % np.uint64(2)).astype(np.int64)).astype(np.int64)
+
+
+class Tables:
+    """Hash tables of d repetitions over the domain {0..n-1}.
+
+    h1[t], s1[t] index rows of A (the i of A_ik); h2[t], s2[t] index columns
+    of B (the j of B_kj).  Shapes (d, n), int64.
+    """
+
+    def __init__(self, h1, s1, h2, s2, b: int):
+        self.h1 = np.asarray(h1, dtype=np.int64)
+        self.s1 = np.asarray(s1, dtype=np.int64)
+        self.h2 = np.asarray(h2, dtype=np.int64)
+        self.s2 = np.asarray(s2, dtype=np.int64)
+        self.b = int(b)
+        self.d = self.h1.shape[0]
+
+    def rep(self, t: int) -> "Tables":
+        return Tables(self.h1[t:t + 1], self.s1[t:t + 1], self.h2[t:t + 1],
+                      self.s2[t:t + 1], self.b)
+
+
+def make_tables(seed: int, n: int, b: int, d: int) -> Tables:
+    """Fig. 1's per-repetition draws of s1, s2, h1, h2, as tables over {0..n-1}."""
+    coef = draw_coefficients(seed, d)
+    x = np.arange(n, dtype=np.int64)
+    h1 = np.stack([hash_bucket(coef[t, 0, 0], coef[t, 0, 1], x, b) for t in range(d)])
+    s1 = np.stack([hash_sign(coef[t, 1, 0], coef[t, 1, 1], x) for t in range(d)])
+    h2 = np.stack([hash_bucket(coef[t, 2, 0], coef[t, 2, 1], x, b) for t in range(d)])
+    s2 = np.stack([hash_sign(coef[t, 3, 0], coef[t, 3, 1], x) for t in range(d)])
+    return Tables(h1, s1, h2, s2, b)
+
+
+# --------------------------------------------------------------------------
+# COMPRESSEDPRODUCT, Fig. 1: sketch -> FFT -> pointwise product -> sum over k
+# -> one inverse FFT.
+# --------------------------------------------------------------------------
+def count_sketch(u: np.ndarray, h: np.ndarray, s: np.ndarray, b: int) -> np.ndarray:
+    """Coefficients of p_u^{h,s}(x) = sum_i s(i) u_i x^{h(i)} (Sec. 2.2)."""
+    return np.bincount(h, weights=s * np.asarray(u, dtype=np.float64), minlength=b)
+
+
+def sketch_fft(A: np.ndarray, B: np.ndarray, tab: Tables, return_imag: bool = False):
+    """COMPRESSEDPRODUCT(A, B, b, d) of Fig. 1, in float64.
+
+    A is n1 x n2, B is n2 x n3 (any memory order).  Returns c of shape (d, b):
+    c[t] = FFT^{-1}( sum_k FFT(pa_k) * FFT(pb_k) ), the real part (the sketch
+    of a real matrix is real; with ``return_imag`` the largest |imag| is also
+    returned as a consistency check).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    n1, n2 = A.shape
+    n2b, n3 = B.shape
+    assert n2 == n2b
+    b = tab.b
+    c = np.zeros((tab.d, b), dtype=np.float64)
+    max_imag = 0.0
+    for t in range(tab.d):
+        h1, s1 = tab.h1[t, :n1], tab.s1[t, :n1]
+        h2, s2 = tab.h2[t, :n3], tab.s2[t, :n3]
+        p = np.zeros(b, dtype=np.complex128)
+        for k in range(n2):
+            pa = count_sketch(A[:, k], h1, s1, b)       # column k of A
+            pb = count_sketch(B[k, :], h2, s2, b)       # row k of B
+            p += np.fft.fft(pa) * np.fft.fft(pb)        # p[t][z] += pa[z] pb[z]
+        q = np.fft.ifft(p)                              # p[t] := FFT^{-1}(p[t])
+        c[t] = q.real
+        max_imag = max(max_imag, float(np.max(np.abs(q.imag))) if b else 0.0)
+    return (c, max_imag) if return_imag else c
+
+
+def sketch_definition(A: np.ndarray, B: np.ndarray, tab: Tables) -> np.ndarray:
+    """Count sketch of AB from its definition (Sec. 2.2).
+
+    c_t[z] = sum over (i, j) with (h1(i) + h2(j)) mod b = z of
+    s1(i) s2(j) (AB)_ij, with AB formed in float64.
+    """
+    AB = np.asarray(A, dtype=np.float64) @ np.asarray(B, dtype=np.float64)
+    n1, n3 = AB.shape
+    b = tab.b
+    c = np.zeros((tab.d, b), dtype=np.float64)
+    for t in range(tab.d):
+        z = (tab.h1[t, :n1, None] + tab.h2[t, None, :n3]) % b
+        w = (tab.s1[t, :n1, None] * tab.s2[t, None, :n3]) * AB
+        c[t] = np.bincount(z.ravel(), weights=w.ravel(), minlength=b)
+    return c
+
+
+def sketch_convolution(A: np.ndarray, B: np.ndarray, tab: Tables) -> np.ndarray:
+    """Sketch as a direct length-b cyclic convolution summed over k (no FFT).
+
+    With PA[x, k] = pa_k[x] and PB[k, y] = pb_k[y], M = PA PB holds
+    sum_k pa_k[x] pb_k[y]; c[z] = sum_x M[x, (z - x) mod b].  This is
+    (p mod x^b) + (p div x^b) for p = sum_k p_{a_k} p_{b_k} (abstract, Sec. 2.2).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    n1, n2 = A.shape
+    n3 = B.shape[1]
+    b = tab.b
+    c = np.zeros((tab.d, b), dtype=np.float64)
+    xs = np.arange(b)
+    for t in range(tab.d):
+        PA = np.zeros((b, n2))
+        np.add.at(PA, tab.h1[t, :n1], tab.s1[t, :n1, None] * A)
+        PB = np.zeros((n2, b))
+        np.add.at(PB.T, tab.h2[t, :n3], tab.s2[t, :n3, None] * B.T)
+        M = PA @ PB
+        for z in range(b):
+            c[t, z] = M[xs, (z - xs) % b].sum()
+    return c
+
+
+def sketch_bucket_values(A: np.ndarray, B: np.ndarray, tab: Tables, t: int,
+                         zs: np.ndarray) -> np.ndarray:
+    """c_t[z] for the listed buckets z only, straight from the definition.
+
+    For each z, every pair (i, j) with (h1(i) + h2(j)) mod b = z contributes
+    s1(i) s2(j) sum_k A_ik B_kj.  Cost ~ (n1 n3 / b) n2 per bucket, so this
+    works at full problem size on a sample of buckets.
+    """
+    A = np.asarray(A)
+    B = np.asarray(B)
+    n1 = A.shape[0]
+    n3 = B.shape[1]
+    b = tab.b
+    h1, s1 = tab.h1[t, :n1], tab.s1[t, :n1]
+    h2, s2 = tab.h2[t, :n3], tab.s2[t, :n3]
+    order = np.argsort(h2, kind="stable")
+    h2_sorted = h2[order]
+    out = np.zeros(len(zs), dtype=np.float64)
+    for q, z in enumerate(np.asarray(zs, dtype=np.int64)):
+        need = (z - h1) % b                      # h2(j) each i needs
+        lo = np.searchsorted(h2_sorted, need, side="left")
+        hi = np.searchsorted(h2_sorted, need, side="right")
+        ii = np.repeat(np.arange(n1), hi - lo)
+        if len(ii) == 0:
+            continue
+        jj = order[np.concatenate([np.arange(l, h) for l, h in zip(lo, hi) if h > l])]
+        ab = np.einsum("pk,kp->p", A[ii, :].astype(np.float64), B[:, jj].astype(np.float64))
+        out[q] = np.sum(s1[ii] * s2[jj] * ab)
+    return out
+
+
+# --------------------------------------------------------------------------
+# DECOMPRESS, Fig. 1.
+# --------------------------------------------------------------------------
+def median(values: np.ndarray, axis: int = 0) -> np.ndarray:
+    """Median over ``axis``; an even count takes the mean of the two middle values."""
+    return np.median(values, axis=axis)
+
+
+def estimates(c: np.ndarray, tab: Tables, i: np.ndarray, j: np.ndarray) -> np.ndarray:
+    """X_t = s1_t(i) s2_t(j) c_t[(h1_t(i) + h2_t(j)) mod b], shape (d, len(i))."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    X = np.empty((tab.d, len(i)), dtype=np.float64)
+    for t in range(tab.d):
+        z = (tab.h1[t, i] + tab.h2[t, j]) % tab.b
+        X[t] = tab.s1[t, i] * tab.s2[t, j] * np.asarray(c[t], dtype=np.float64)[z]
+    return X
+
+
+def decompress(c: np.ndarray, tab: Tables, i: np.ndarray, j: np.ndarray) -> np.ndarray:
+    """DECOMPRESS(i, j) for a list of pairs: median over t of X_t."""
+    return median(estimates(c, tab, i, j), axis=0)
+
+
+def decompress_dense(c: np.ndarray, tab: Tables, n1: int, n3: int) -> np.ndarray:
+    """All n1 x n3 estimates (Sec. 2.2, O(n^2) decoding of every entry)."""
+    ii, jj = np.meshgrid(np.arange(n1), np.arange(n3), indexing="ij")
+    return decompress(c, tab, ii.ravel(), jj.ravel()).reshape(n1, n3)
+
+
+# --------------------------------------------------------------------------
+# Error metric used for parity: relative L2 per repetition, max over t.
+# --------------------------------------------------------------------------
+def rel_l2(x: np.ndarray, ref: np.ndarray) -> float:
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    ref = np.atleast_2d(np.asarray(ref, dtype=np.float64))
+    num = np.linalg.norm(x - ref, axis=-1)
+    den = np.maximum(np.linalg.norm(ref, axis=-1), np.finfo(np.float64).tiny)
+    return float(np.max(num / den))
+
+
+# --------------------------------------------------------------------------
+# Sparse inputs (Sec. 2.2 "sparse or rectangular"; Theorem 5): A given by
+# columns (CSC), B given by rows (CSR).  Exact for integer-valued data.
+# --------------------------------------------------------------------------
+def sketch_definition_sparse(A_csc, B_csr, tab: Tables) -> np.ndarray:
+    """Definition route for sparse A (CSC) and B (CSR) as scipy matrices.
+
+    AB is formed with a sparse product; for integer-valued inputs every
+    bucket is an exact integer (float64 sums of integers below 2^53).
+    """
+    AB = (A_csc @ B_csr).tocoo()
+    b = tab.b
+    c = np.zeros((tab.d, b), dtype=np.float64)
+    i = AB.row.astype(np.int64)
+    j = AB.col.astype(np.int64)
+    v = AB.data.astype(np.float64)
+    for t in range(tab.d):
+        z = (tab.h1[t, i] + tab.h2[t, j]) % b
+        c[t] = np.bincount(z, weights=tab.s1[t, i] * tab.s2[t, j] * v, minlength=b)
+    return c
+
+
+def sketch_fft_sparse(A_csc, B_csr, tab: Tables) -> np.ndarray:
+    """Fig. 1 on sparse inputs: only inner indices k with a nonzero a_k and b_k
+    contribute (Sec. 2.2, time O(N + n2 b lg b) per repetition)."""
+    A_csc = A_csc.tocsc()
+    B_csr = B_csr.tocsr()
+    n2 = A_csc.shape[1]
+    b = tab.b
+    c = np.zeros((tab.d, b), dtype=np.float64)
+    for t in range(tab.d):
+        p = np.zeros(b, dtype=np.complex128)
+        for k in range(n2):
+            a0, a1 = A_csc.indptr[k], A_csc.indptr[k + 1]
+            b0, b1 = B_csr.indptr[k], B_csr.indptr[k + 1]
+            if a0 == a1 or b0 == b1:
+                continue
+            ia = A_csc.indices[a0:a1]
+            jb = B_csr.indices[b0:b1]
+            pa = count_sketch(A_csc.data[a0:a1], tab.h1[t, ia], tab.s1[t, ia], b)
+            pb = count_sketch(B_csr.data[b0:b1], tab.h2[t, jb], tab.s2[t, jb], b)
+            p += np.fft.fft(pa) * np.fft.fft(pb)
+        c[t] = np.fft.ifft(p).real
+    return c

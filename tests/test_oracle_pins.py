@@ -1,0 +1,303 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+Each test names what fixes the expected value: a published generator output,
+a hand-worked hash value, an independent computation route of the paper's
+identities (Sec. 2.2), a special case that reduces to brute force, the AMS
+identity of Sec. 2.1, or Theorems 2 and 5.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import cms_oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- seeding ---
+def test_splitmix64_matches_published_outputs():
+    g = _load("splitmix64_seed0.json")
+    state = g["state"]
+    for hx in g["outputs_hex"]:
+        state, out = O.splitmix64(state)
+        assert out == int(hx, 16)
+
+
+def test_coefficients_in_range_and_ordered():
+    coef = O.draw_coefficients(12345, 7)
+    assert coef.shape == (7, 4, 2)
+    assert np.all(coef[:, :, 0] >= 1) and np.all(coef[:, :, 0] <= O.P31 - 1)
+    assert np.all(coef[:, :, 1] >= 0) and np.all(coef[:, :, 1] <= O.P31 - 1)
+    # draw order: the first published splitmix64 output of state 0 is h1.a of t=0
+    g = _load("splitmix64_seed0.json")
+    r = [int(h, 16) for h in g["outputs_hex"]]
+    c0 = O.draw_coefficients(0, 1)
+    assert c0[0, 0, 0] == 1 + r[0] % (O.P31 - 1)
+    assert c0[0, 0, 1] == r[1] % O.P31
+    assert c0[0, 1, 0] == 1 + r[2] % (O.P31 - 1)
+    # different seeds give different functions
+    assert not np.array_equal(O.draw_coefficients(1, 3), O.draw_coefficients(2, 3))
+
+
+# ------------------------------------------------------------ hash family ---
+def test_hash_hand_worked_values():
+    g = _load("hash_hand.json")
+    for e in g["bucket"]:
+        got = O.hash_bucket(e["a"], e["c"], np.array([e["x"]]), e["b"])[0]
+        assert got == e["h"], e
+    for e in g["sign"]:
+        got = O.hash_sign(e["a"], e["c"], np.array([e["x"]]))[0]
+        assert got == e["s"], e
+
+
+def test_hash_uniform_and_pairwise():
+    # Sec. 2.2 needs Pr[h(x) = h(y)] = 1/b for x != y; check the family gets
+    # close over many draws (chi-square-style bounds, loose).
+    b = 64
+    x = np.arange(4096)
+    hist = np.zeros(b)
+    coll = 0
+    trials = 400
+    for s in range(trials):
+        coef = O.draw_coefficients(s, 1)
+        h = O.hash_bucket(coef[0, 0, 0], coef[0, 0, 1], x, b)
+        hist += np.bincount(h, minlength=b)
+        coll += int(h[3] == h[77])
+    exp = hist.sum() / b
+    chi2 = float(((hist - exp) ** 2 / exp).sum())
+    assert chi2 < 3 * b
+    assert abs(coll / trials - 1 / b) < 5 * math.sqrt((1 / b) / trials)
+    # signs are balanced
+    sg = O.hash_sign(*O.draw_coefficients(9, 1)[0, 1], np.arange(100000))
+    assert abs(sg.mean()) < 0.02
+
+
+# ------------------------------------------------------------ count sketch --
+def test_count_sketch_hand_example():
+    # p_u(x) = sum_i s(i) u_i x^{h(i)}: u = (1, 2, 3), h = (0, 2, 0), s = (+, -, +)
+    # gives 1*x^0 - 2*x^2 + 3*x^0 = 4 - 2 x^2.
+    got = O.count_sketch(np.array([1.0, 2.0, 3.0]), np.array([0, 2, 0]),
+                         np.array([1, -1, 1]), 3)
+    np.testing.assert_array_equal(got, [4.0, 0.0, -2.0])
+
+
+def _random_problem(n1, n2, n3, b, d, seed):
+    A = W.gaussian(n1, n2, seed)
+    B = W.gaussian(n2, n3, seed + 1)
+    tab = O.make_tables(seed + 2, max(n1, n3), b, d)
+    return A, B, tab
+
+
+# ------------------------------------------- three routes of Sec. 2.2 agree --
+@pytest.mark.parametrize("n1,n2,n3,b,d", [
+    (16, 9, 16, 32, 2),       # power-of-two b
+    (23, 17, 11, 64, 3),      # ragged rectangular shapes
+    (40, 12, 40, 100, 1),     # b not a power of two (5-smooth)
+    (10, 5, 10, 7, 2),        # prime b
+    (30, 8, 30, 2000, 1),     # b as in the Fig. 2 demonstration
+])
+def test_fft_route_equals_definition_and_convolution(n1, n2, n3, b, d):
+    A, B, tab = _random_problem(n1, n2, n3, b, d, 100 + b)
+    cf, imag = O.sketch_fft(A, B, tab, return_imag=True)
+    cd = O.sketch_definition(A, B, tab)
+    np.testing.assert_allclose(cf, cd, rtol=0, atol=1e-10 * np.abs(cd).max())
+    assert imag < 1e-9 * np.abs(cd).max()
+    if b <= 256:
+        cc = O.sketch_convolution(A, B, tab)
+        np.testing.assert_allclose(cc, cd, rtol=0, atol=1e-10 * np.abs(cd).max())
+
+
+def test_fft_route_equals_convolution_at_b1024():
+    # the survey's config-1 shape scaled down in n: direct O(b^2) convolution
+    # vs the FFT route at b = 1024
+    A, B, tab = _random_problem(64, 32, 64, 1024, 1, 7)
+    cf = O.sketch_fft(A, B, tab)
+    cc = O.sketch_convolution(A, B, tab)
+    assert O.rel_l2(cf, cc) < 1e-12
+
+
+def test_bucket_values_match_full_definition():
+    A, B, tab = _random_problem(50, 20, 45, 128, 2, 3)
+    cd = O.sketch_definition(A, B, tab)
+    zs = np.array([0, 5, 64, 127, 99])
+    for t in range(2):
+        np.testing.assert_allclose(O.sketch_bucket_values(A, B, tab, t, zs), cd[t, zs],
+                                   rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------- special cases -> brute force ---
+def test_injective_hash_gives_exact_product():
+    # h1(i) = i, h2(j) = n1 j, b = n1 n3: every (i, j) has its own bucket
+    # i + n1 j, so c is vec(AB) with the signs s1(i) s2(j) (Sec. 2.2).
+    n1, n2, n3 = 6, 5, 4
+    A = W.gaussian(n1, n2, 1)
+    B = W.gaussian(n2, n3, 2)
+    n = max(n1, n3)
+    g = W.rng(3)
+    s1 = g.choice([-1, 1], size=(1, n))
+    s2 = g.choice([-1, 1], size=(1, n))
+    h1 = np.arange(n)[None, :]
+    h2 = (n1 * np.arange(n))[None, :]
+    tab = O.Tables(h1, s1, h2, s2, n1 * n3)
+    c = O.sketch_fft(A, B, tab)[0]
+    AB = np.array([[sum(A[i, k] * B[k, j] for k in range(n2)) for j in range(n3)]
+                   for i in range(n1)])
+    for i in range(n1):
+        for j in range(n3):
+            assert abs(c[i + n1 * j] - s1[0, i] * s2[0, j] * AB[i, j]) < 1e-12
+    # and decoding recovers AB exactly
+    est = O.decompress_dense(c[None, :], tab, n1, n3)
+    np.testing.assert_allclose(est, AB, atol=1e-12)
+
+
+def test_b1_is_ams_sketch():
+    # b = 1: every entry in one bucket; c_0 = sum_ij s1(i)s2(j)(AB)_ij
+    # = (sum_i s1(i) a_i)(sum_j s2(j) b_j) summed over k (Sec. 2.1).
+    A, B, tab = _random_problem(20, 7, 13, 1, 3, 11)
+    c = O.sketch_fft(A, B, tab)
+    for t in range(3):
+        lhs = sum((tab.s1[t, :20] @ A[:, k]) * (B[k, :] @ tab.s2[t, :13]) for k in range(7))
+        assert abs(c[t, 0] - lhs) < 1e-10 * max(1.0, abs(lhs))
+
+
+def test_dc_bin_sum_is_ams_sketch():
+    # sum_z c_z = (s1^T A)(B s2) for any b (the t = 0 spectral bin; Sec. 2.1/2.2)
+    A, B, tab = _random_problem(31, 9, 27, 64, 2, 5)
+    c = O.sketch_fft(A, B, tab)
+    for t in range(2):
+        lhs = (tab.s1[t, :31] @ A) @ (B @ tab.s2[t, :27])
+        assert abs(c[t].sum() - lhs) < 1e-10 * max(1.0, abs(lhs))
+
+
+def test_linearity_and_k_permutation():
+    # the sketch is linear in each outer product a_k b_k (eq. (1), Sec. 2.2)
+    A, B, tab = _random_problem(20, 10, 20, 32, 2, 21)
+    A2 = W.gaussian(20, 10, 99)
+    c1 = O.sketch_fft(A, B, tab)
+    c2 = O.sketch_fft(A2, B, tab)
+    c12 = O.sketch_fft(2.0 * A - 3.0 * A2, B, tab)
+    np.testing.assert_allclose(c12, 2.0 * c1 - 3.0 * c2, atol=1e-10)
+    perm = W.rng(4).permutation(10)
+    cp = O.sketch_fft(A[:, perm], B[perm, :], tab)
+    np.testing.assert_allclose(cp, c1, atol=1e-10)
+    # split over k: sketch(A,B) = sketch(A[:, :4], B[:4]) + sketch(A[:, 4:], B[4:])
+    cs = O.sketch_fft(A[:, :4], B[:4], tab) + O.sketch_fft(A[:, 4:], B[4:], tab)
+    np.testing.assert_allclose(cs, c1, atol=1e-10)
+
+
+def test_median_convention():
+    assert O.median(np.array([3.0, 1.0, 2.0])) == 2.0
+    assert O.median(np.array([1.0, 2.0, 3.0, 10.0])) == 2.5
+    assert O.median(np.array([[5.0, -1.0], [4.0, 7.0], [6.0, 0.0]]), axis=0).tolist() == [5.0, 0.0]
+
+
+def test_decompress_formula_on_hand_sketch():
+    # DECOMPRESS of Fig. 1 with hand-chosen tables and sketch.
+    h1 = np.array([[0, 1], [1, 1], [2, 0]])
+    s1 = np.array([[1, -1], [1, 1], [-1, 1]])
+    h2 = np.array([[2, 0], [0, 3], [1, 1]])
+    s2 = np.array([[-1, 1], [1, 1], [1, -1]])
+    tab = O.Tables(h1, s1, h2, s2, 4)
+    c = np.array([[10., 20., 30., 40.], [1., 2., 3., 4.], [-5., 6., -7., 8.]])
+    # (i, j) = (1, 0): t0: s=-1*-1=1, z=(1+2)%4=3 -> 40; t1: 1*1, z=(1+0)=1 -> 2;
+    # t2: 1*1, z=(0+1)=1 -> 6.  median(40, 2, 6) = 6.
+    assert O.decompress(c, tab, [1], [0])[0] == 6.0
+    # (0, 1): t0: 1*1, z=(0+0)=0 -> 10; t1: 1*1, z=(1+3)%4=0 -> 1; t2: -1*-1, z=(2+1)=3 -> 8
+    assert O.decompress(c, tab, [0], [1])[0] == 8.0
+
+
+# ------------------------------------------------------ Theorem 2 (Sec 3.1) --
+def test_theorem2_unbiased_and_variance_bound():
+    # d = 1, many independent hash draws: the estimator C_ij is unbiased and
+    # Var <= ||AB||_F^2 / b.  Data: 64 x 64 N(0,1), b = 256, 2000 seeds.
+    n, b, seeds = 64, 256, 2000
+    A = W.gaussian(n, n, 1)
+    B = W.gaussian(n, n, 2)
+    AB = A @ B
+    fro2 = float((AB ** 2).sum())
+    s = np.zeros((n, n))
+    s2 = np.zeros((n, n))
+    for seed in range(1, seeds + 1):
+        tab = O.make_tables(seed, n, b, 1)
+        c = O.sketch_definition(A, B, tab)
+        est = O.decompress_dense(c, tab, n, n)
+        s += est
+        s2 += est * est
+    mean = s / seeds
+    var = s2 / seeds - mean ** 2
+    sigma = math.sqrt(fro2 / b)
+    assert np.max(np.abs(mean - AB)) < 6.0 * sigma / math.sqrt(seeds)
+    # per-entry exact variance for a collision probability of 1/b is
+    # (||AB||_F^2 - AB_ij^2)/b; check the average against the bound
+    avg_var = float(var.mean())
+    expected = (fro2 - float((AB ** 2).mean())) / b
+    assert avg_var <= 1.08 * fro2 / b
+    assert avg_var >= 0.85 * expected
+
+
+def test_theorem2_fft_route_single_seed_matches_definition():
+    # the statistical test above uses the definition route; it equals the
+    # FFT route seed by seed
+    A = W.gaussian(64, 64, 1)
+    B = W.gaussian(64, 64, 2)
+    tab = O.make_tables(17, 64, 256, 1)
+    assert O.rel_l2(O.sketch_fft(A, B, tab), O.sketch_definition(A, B, tab)) < 1e-12
+
+
+# --------------------------------------------------- Theorem 5 (Sec 3.3.1) --
+def test_theorem5_sparse_product_recovered_exactly():
+    # AB with at most b/8 nonzeros and d >= 6 lg n: median decoding returns AB.
+    n, b = 64, 1024
+    d = 6 * int(math.log2(n))
+    sb = W.sparse_blocks(n, n_blocks=2, inner=3, rows=8, cols=8, seed=5)
+    A, B = sb.scipy()
+    AB = (A @ B).toarray()
+    assert np.count_nonzero(AB) <= b // 8
+    tab = O.make_tables(2024, n, b, d)
+    c = O.sketch_definition(A.toarray(), B.toarray(), tab)
+    est = O.decompress_dense(c, tab, n, n)
+    np.testing.assert_array_equal(np.rint(est), AB)
+
+
+def test_sparse_routes_agree_and_are_integers():
+    sb = W.sparse_blocks(512, n_blocks=8, inner=4, rows=6, cols=5, seed=9)
+    A, B = sb.scipy()
+    tab = O.make_tables(3, 512, 256, 3)
+    cd = O.sketch_definition_sparse(A, B, tab)
+    cf = O.sketch_fft_sparse(A, B, tab)
+    cdense = O.sketch_definition(A.toarray(), B.toarray(), tab)
+    np.testing.assert_array_equal(cd, np.rint(cd))
+    np.testing.assert_allclose(cf, cd, atol=1e-9)
+    np.testing.assert_array_equal(cdense, cd)
+
+
+# ---------------------------------------------------------- Fig. 2 (qual.) --
+def test_fig2_planted_pair_stands_out():
+    # Fig. 2: 100 x 100 uniform[-1, 1] data, rows 21 and 66 positively
+    # correlated, b = 2000; after removing the diagonal's contribution and
+    # thresholding, the planted pair is among the candidates.  Qualitative.
+    n, m, b = 100, 100, 2000
+    X = W.uniform_pm1(n, m, 42)
+    X[66] = 0.9 * X[21] + 0.1 * X[66]
+    tab = O.make_tables(7, n, b, 3)
+    c = O.sketch_definition(X, X.T, tab)
+    # subtract the diagonal's contribution s1(i)s2(i)(AA^T)_ii at its bucket
+    diag = (X * X).sum(axis=1)
+    for t in range(3):
+        z = (tab.h1[t, :n] + tab.h2[t, :n]) % b
+        np.subtract.at(c[t], z, tab.s1[t, :n] * tab.s2[t, :n] * diag)
+    est = O.decompress_dense(c, tab, n, n)
+    np.fill_diagonal(est, 0.0)
+    thr = 0.5 * est[21, 66]
+    cand = set(map(tuple, np.argwhere(est > thr)))
+    assert (21, 66) in cand and (66, 21) in cand
+    assert len(cand) < 0.02 * n * n
