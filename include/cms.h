@@ -1,0 +1,215 @@
+/*
+ * cms.h - C ABI of the GB300 (sm_103a) compressed matrix multiplication
+ * library (Pagh, "Compressed Matrix Multiplication", arXiv 1108.1320).
+ *
+ * The library computes the count sketch c[t][0..b-1], t = 0..d-1, of a matrix
+ * product AB without forming AB (COMPRESSEDPRODUCT, Fig. 1), and decodes
+ * entries as the median over t of s1_t(i) s2_t(j) c_t[(h1_t(i)+h2_t(j)) mod b]
+ * (DECOMPRESS, Fig. 1).
+ *
+ * Conventions shared by every entry point:
+ *  - Indices are 0-based.  A is n1 x n2, B is n2 x n3; k indexes n2.
+ *  - Every matrix, sketch, output and workspace pointer is caller-owned
+ *    DEVICE memory unless the parameter says "host".  The library owns only
+ *    cms_hashes objects (host coefficients plus device tables).
+ *  - Calls that take a stream are asynchronous on that stream (a
+ *    cudaStream_t passed as void*; NULL means the legacy default stream).
+ *    They allocate nothing: scratch comes from the caller's workspace.
+ *  - Every call returns a cms_status; no call throws or aborts.  The text of
+ *    the last error on the calling thread is returned by cms_last_error().
+ *  - Device-side error words (a kernel that detects an impossible internal
+ *    state) are surfaced by cms_check_async().
+ */
+#ifndef CMS_H
+#define CMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CMS_API __attribute__((visibility("default")))
+#else
+#define CMS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CMS_OK = 0,
+    CMS_ERR_INVALID_ARG = 1,   /* bad pointer, size, stride or dtype       */
+    CMS_ERR_UNSUPPORTED = 2,   /* valid but not implemented (e.g. b not 5-smooth) */
+    CMS_ERR_CUDA = 3,          /* a CUDA runtime call failed               */
+    CMS_ERR_WORKSPACE = 4,     /* workspace NULL or smaller than required  */
+    CMS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up       */
+    CMS_ERR_DEVICE = 6         /* a kernel raised its device error word    */
+} cms_status;
+
+typedef enum {
+    CMS_F32 = 0,               /* IEEE binary32                            */
+    CMS_BF16 = 1,              /* bfloat16 storage, computed in FP32       */
+    CMS_F64 = 2                /* IEEE binary64 (rounded to FP32 by the fused path) */
+} cms_dtype;
+
+/* Opaque hash-function set: d repetitions of (h1, s1, h2, s2) over {0..n-1}. */
+typedef struct cms_hashes cms_hashes;
+
+/*
+ * cms_make_hashes - draw d independent repetitions of the splitting and
+ * sign functions (Fig. 1, first lines of COMPRESSEDPRODUCT; Sec. 2.2).
+ *   h1_t, h2_t : {0..n-1} -> {0..b-1},  h(x) = ((a x + c) mod p) mod b,
+ *   s1_t, s2_t : {0..n-1} -> {-1,+1},   s(x) = 1 - 2 (((a x + c) mod p) mod 2),
+ * with p = 2^31 - 1 (the polynomial family of ref. [13], degree 1).  The
+ * coefficients come from splitmix64 over `seed`: for t = 0..d-1, in the
+ * order h1.a, h1.c, s1.a, s1.c, h2.a, h2.c, s2.a, s2.c, a = 1 + (r mod (p-1)),
+ * c = r mod p.
+ *   seed : any 64-bit value.
+ *   n    : domain size, n = max(n1, n3) (h1/s1 index rows of A, h2/s2
+ *          columns of B); 1 <= n <= 2^24.
+ *   b    : sketch length, 1 <= b <= 2^24.  The fused FFT path needs b
+ *          5-smooth (2^x 3^y 5^z); other b still hash and decode.
+ *   d    : repetitions, 1 <= d <= 64.
+ *   out  : host pointer receiving the new object.
+ * Allocates device tables on the current device and fills them
+ * synchronously.  Errors: CMS_ERR_INVALID_ARG, CMS_ERR_CUDA.
+ */
+CMS_API cms_status cms_make_hashes(uint64_t seed, int64_t n, int64_t b, int32_t d,
+                           cms_hashes** out);
+
+/*
+ * cms_reseed_hashes - redraw the functions of an existing object for a new
+ * seed (same n, b, d), on the device, asynchronously on `stream`, without
+ * allocating.  Calls using the object must be ordered after it on the
+ * stream.  Errors: CMS_ERR_INVALID_ARG, CMS_ERR_CUDA.
+ */
+CMS_API cms_status cms_reseed_hashes(cms_hashes* h, uint64_t seed, void* stream);
+
+/*
+ * cms_make_hashes_from_tables - build an object from explicit host tables
+ * (test use: e.g. an injective splitting function, Sec. 2.2 special case).
+ *   h1, h2 : host uint32 [d][n], values < b.   s1, s2 : host int8 [d][n], +-1.
+ * Errors: CMS_ERR_INVALID_ARG, CMS_ERR_CUDA.
+ */
+CMS_API cms_status cms_make_hashes_from_tables(int64_t n, int64_t b, int32_t d,
+                                       const uint32_t* h1, const int8_t* s1,
+                                       const uint32_t* h2, const int8_t* s2,
+                                       cms_hashes** out);
+
+/* Free an object and its device tables (synchronises the device). */
+CMS_API cms_status cms_free_hashes(cms_hashes* h);
+
+/*
+ * cms_hashes_info - n, b, d and the FFT factorisation b = R * C chosen for
+ * the fused path (R = 0, C = 0 when b is not 5-smooth).  Host outputs; any
+ * may be NULL.
+ */
+CMS_API cms_status cms_hashes_info(const cms_hashes* h, int64_t* n, int64_t* b,
+                           int32_t* d, int64_t* R, int64_t* C);
+
+/*
+ * cms_hashes_coeffs - the eight coefficients of repetition t, host out[8] in
+ * the order h1.a, h1.c, s1.a, s1.c, h2.a, h2.c, s2.a, s2.c (all zero for an
+ * object built from tables).
+ */
+CMS_API cms_status cms_hashes_coeffs(const cms_hashes* h, int32_t t, uint32_t out[8]);
+
+/*
+ * cms_hashes_tables - copy the tables to host buffers (synchronous):
+ * h1, h2 uint32 [d][n]; s1, s2 int8 [d][n].  Any pointer may be NULL.
+ */
+CMS_API cms_status cms_hashes_tables(const cms_hashes* h, uint32_t* h1, int8_t* s1,
+                             uint32_t* h2, int8_t* s2);
+
+/*
+ * cms_workspace_size - bytes of device workspace cms_sketch_product needs
+ * for these shapes (A n1 x n2, B n2 x n3, storage dtype dt).  Host output.
+ * Errors: CMS_ERR_INVALID_ARG, CMS_ERR_UNSUPPORTED.
+ */
+CMS_API cms_status cms_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2,
+                              int64_t n3, int32_t dt, size_t* bytes);
+
+/*
+ * cms_sketch_product - COMPRESSEDPRODUCT(A, B, b, d) of Fig. 1 (Lemma 1):
+ *   c[t][z] = sum over (i,j) with (h1_t(i)+h2_t(j)) mod b = z of
+ *             s1_t(i) s2_t(j) (AB)_ij,
+ * computed as in Sec. 2.2: per inner index k, count-sketch column k of A and
+ * row k of B, FFT both, multiply pointwise and accumulate over k
+ * (compensated FP32), then one inverse FFT per repetition.
+ *   A   : n1 x n2, column-major, column k at A + k*lda (lda >= n1), so a
+ *         single pass reads each a_k contiguously (Sec. 2.2, "single pass").
+ *   B   : n2 x n3, row-major, row k at B + k*ldb (ldb >= n3).
+ *   dt  : storage type of A and B (CMS_F32, CMS_BF16 or CMS_F64).
+ *   h   : hashes with n >= max(n1, n3).
+ *   c   : device float [d][b], written (not accumulated).
+ *   ws  : device workspace of at least cms_workspace_size() bytes,
+ *         256-byte aligned.
+ * Errors: CMS_ERR_INVALID_ARG, CMS_ERR_UNSUPPORTED (b not 5-smooth or shape
+ * beyond the kernels' limits), CMS_ERR_WORKSPACE, CMS_ERR_CUDA.
+ */
+CMS_API cms_status cms_sketch_product(const void* A, int64_t lda, const void* B,
+                              int64_t ldb, int64_t n1, int64_t n2, int64_t n3,
+                              int32_t dt, const cms_hashes* h, float* c,
+                              void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * cms_plain_workspace_size / cms_sketch_product_plain_f64 - the same sketch
+ * (Fig. 1) in plain form: FP64 throughout, one instance per call, unfused
+ * passes (scatter, FFT, spectral product, inverse FFT each a separate
+ * kernel; spectra stored in device memory).  Same argument meanings as
+ * cms_sketch_product with A, B double and c double [d][b].
+ */
+CMS_API cms_status cms_plain_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2,
+                                    int64_t n3, size_t* bytes);
+CMS_API cms_status cms_sketch_product_plain_f64(const double* A, int64_t lda,
+                                        const double* B, int64_t ldb,
+                                        int64_t n1, int64_t n2, int64_t n3,
+                                        const cms_hashes* h, double* c,
+                                        void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * cms_decode - DECOMPRESS(i, j) of Fig. 1 for q index pairs:
+ *   out[p] = median_t s1_t(i) s2_t(j) c_t[(h1_t(i) + h2_t(j)) mod b],
+ * (i, j) = (ij[2p], ij[2p+1]).  An even d takes the mean of the two middle
+ * values.
+ *   c  : device float [d][b] from cms_sketch_product.
+ *   ij : device int64 [q][2], 0 <= i < n, 0 <= j < n (out-of-range pairs
+ *        produce NaN and raise the device error word).
+ *   out: device float [q].
+ * Errors: CMS_ERR_INVALID_ARG, CMS_ERR_CUDA.
+ */
+CMS_API cms_status cms_decode(const float* c, const cms_hashes* h, const int64_t* ij,
+                      int64_t q, float* out, void* stream);
+CMS_API cms_status cms_decode_f64(const double* c, const cms_hashes* h,
+                          const int64_t* ij, int64_t q, double* out,
+                          void* stream);
+
+/*
+ * cms_decode_dense - every estimate C_ij, 0 <= i < n1, 0 <= j < n3
+ * (Sec. 2.2: all entries in O(n^2) time): out[i*ldo + j] (row-major,
+ * ldo >= n3), device float.  Errors: CMS_ERR_INVALID_ARG, CMS_ERR_CUDA.
+ */
+CMS_API cms_status cms_decode_dense(const float* c, const cms_hashes* h, int64_t n1,
+                            int64_t n3, float* out, int64_t ldo, void* stream);
+
+/*
+ * cms_merge - c_out[t][z] = sum over the `count` partial sketches (device
+ * float [d][b] each, pointers in a host array) in index order.  The sketch
+ * is linear in the outer products of eq. (1) (Sec. 2.2), so sketches of
+ * disjoint inner-index ranges add up to the sketch of the whole product.
+ */
+CMS_API cms_status cms_merge(const float* const* parts, int32_t count, int32_t d,
+                     int64_t b, float* c_out, void* stream);
+
+/* Surface asynchronous device errors for work queued on `stream`:
+ * synchronises the stream, then reads and clears the device error word. */
+CMS_API cms_status cms_check_async(void* stream);
+
+CMS_API const char* cms_status_string(cms_status s);
+CMS_API const char* cms_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMS_H */

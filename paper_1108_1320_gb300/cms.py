@@ -1,0 +1,290 @@
+"""Python binding of libcms (the C ABI in include/cms.h).
+
+Argument marshalling only: every step of the compressed product runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams.  If
+libcms.so is missing, every call raises: there is no fallback path.
+
+Names mirror the C entry points without the ``cms_`` prefix.  Matrices are
+torch tensors: A (n1 x n2) must be column-major (``A.stride(0) == 1``, e.g.
+``X.T`` of a contiguous X), B (n2 x n3) row-major (``B.stride(1) == 1``), so
+that column k of A and row k of B are contiguous (Sec. 2.2, single pass).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcms.so")
+
+CMS_OK = 0
+STATUS = {0: "CMS_OK", 1: "CMS_ERR_INVALID_ARG", 2: "CMS_ERR_UNSUPPORTED", 3: "CMS_ERR_CUDA",
+          4: "CMS_ERR_WORKSPACE", 5: "CMS_ERR_TIMEOUT", 6: "CMS_ERR_DEVICE"}
+CMS_F32, CMS_BF16, CMS_F64 = 0, 1, 2
+_DTYPES = {torch.float32: CMS_F32, torch.bfloat16: CMS_BF16, torch.float64: CMS_F64}
+
+# Every symbol the header declares, with (restype, argtypes).
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_U64 = ctypes.c_uint64
+_SZ = ctypes.c_size_t
+SIGNATURES = {
+    "cms_make_hashes": (_I32, [_U64, _I64, _I64, _I32, ctypes.POINTER(_P)]),
+    "cms_reseed_hashes": (_I32, [_P, _U64, _P]),
+    "cms_make_hashes_from_tables": (_I32, [_I64, _I64, _I32, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "cms_free_hashes": (_I32, [_P]),
+    "cms_hashes_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I32),
+                               ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "cms_hashes_coeffs": (_I32, [_P, _I32, _P]),
+    "cms_hashes_tables": (_I32, [_P, _P, _P, _P, _P]),
+    "cms_workspace_size": (_I32, [_P, _I64, _I64, _I64, _I32, ctypes.POINTER(_SZ)]),
+    "cms_sketch_product": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P, _SZ, _P]),
+    "cms_plain_workspace_size": (_I32, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
+    "cms_sketch_product_plain_f64": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _P, _P, _P, _SZ,
+                                            _P]),
+    "cms_decode": (_I32, [_P, _P, _P, _I64, _P, _P]),
+    "cms_decode_f64": (_I32, [_P, _P, _P, _I64, _P, _P]),
+    "cms_decode_dense": (_I32, [_P, _P, _I64, _I64, _P, _I64, _P]),
+    "cms_merge": (_I32, [_P, _I32, _I32, _I64, _P, _P]),
+    "cms_check_async": (_I32, [_P]),
+    "cms_status_string": (ctypes.c_char_p, [_I32]),
+    "cms_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class CmsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcms.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1108_1320_gb300.build` (no fallback exists)")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(status: int):
+    if status != CMS_OK:
+        raise CmsError(status, lib().cms_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+class Hashes:
+    """d repetitions of (h1, s1, h2, s2) over {0..n-1} into {0..b-1} (Fig. 1)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @classmethod
+    def make(cls, seed: int, n: int, b: int, d: int) -> "Hashes":
+        out = ctypes.c_void_p()
+        _check(lib().cms_make_hashes(seed & ((1 << 64) - 1), n, b, d, ctypes.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def from_tables(cls, h1, s1, h2, s2, b: int) -> "Hashes":
+        h1 = np.ascontiguousarray(h1, dtype=np.uint32)
+        h2 = np.ascontiguousarray(h2, dtype=np.uint32)
+        s1 = np.ascontiguousarray(s1, dtype=np.int8)
+        s2 = np.ascontiguousarray(s2, dtype=np.int8)
+        d, n = h1.shape
+        out = ctypes.c_void_p()
+        _check(lib().cms_make_hashes_from_tables(n, b, d, h1.ctypes.data, s1.ctypes.data,
+                                                 h2.ctypes.data, s2.ctypes.data, ctypes.byref(out)))
+        return cls(out.value)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise ValueError("hashes already freed")
+        return self._h
+
+    def reseed(self, seed: int, stream=None):
+        _check(lib().cms_reseed_hashes(self.handle, seed & ((1 << 64) - 1), _stream(stream)))
+
+    def info(self) -> dict:
+        n, b, R, C = _I64(), _I64(), _I64(), _I64()
+        d = _I32()
+        _check(lib().cms_hashes_info(self.handle, ctypes.byref(n), ctypes.byref(b), ctypes.byref(d),
+                                     ctypes.byref(R), ctypes.byref(C)))
+        return {"n": n.value, "b": b.value, "d": d.value, "R": R.value, "C": C.value}
+
+    def coeffs(self, t: int) -> np.ndarray:
+        out = np.zeros(8, dtype=np.uint32)
+        _check(lib().cms_hashes_coeffs(self.handle, t, out.ctypes.data))
+        return out
+
+    def tables(self):
+        inf = self.info()
+        d, n = inf["d"], inf["n"]
+        h1 = np.zeros((d, n), np.uint32)
+        h2 = np.zeros((d, n), np.uint32)
+        s1 = np.zeros((d, n), np.int8)
+        s2 = np.zeros((d, n), np.int8)
+        _check(lib().cms_hashes_tables(self.handle, h1.ctypes.data, s1.ctypes.data, h2.ctypes.data,
+                                       s2.ctypes.data))
+        return h1, s1, h2, s2
+
+    def free(self):
+        if self._h:
+            lib().cms_free_hashes(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_hashes(seed: int, n: int, b: int, d: int) -> Hashes:
+    return Hashes.make(seed, n, b, d)
+
+
+def _ab_args(A: torch.Tensor, B: torch.Tensor):
+    if A.dim() != 2 or B.dim() != 2:
+        raise ValueError("A and B must be 2-D")
+    n1, n2 = A.shape
+    n2b, n3 = B.shape
+    if n2 != n2b:
+        raise ValueError(f"inner dimensions differ: {n2} vs {n2b}")
+    if A.dtype != B.dtype or A.dtype not in _DTYPES:
+        raise ValueError("A and B must share a dtype in {float32, bfloat16, float64}")
+    if not (A.is_cuda and B.is_cuda):
+        raise ValueError("A and B must be CUDA tensors")
+    if n1 > 1 and A.stride(0) != 1:
+        raise ValueError("A must be column-major (A.stride(0) == 1), e.g. X.T")
+    if n3 > 1 and B.stride(1) != 1:
+        raise ValueError("B must be row-major (B.stride(1) == 1)")
+    lda = A.stride(1) if n2 > 1 else max(n1, 1)
+    ldb = B.stride(0) if n2 > 1 else max(n3, 1)
+    return n1, n2, n3, lda, ldb
+
+
+def workspace_size(h: Hashes, n1: int, n2: int, n3: int, dtype=torch.float32) -> int:
+    out = _SZ()
+    _check(lib().cms_workspace_size(h.handle, n1, n2, n3, _DTYPES[dtype], ctypes.byref(out)))
+    return out.value
+
+
+def alloc_workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A 256-byte aligned device buffer (torch's caching allocator aligns to 512)."""
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def sketch_product(A: torch.Tensor, B: torch.Tensor, h: Hashes, c: torch.Tensor | None = None,
+                   ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """COMPRESSEDPRODUCT (Fig. 1): returns c, float32 of shape (d, b)."""
+    n1, n2, n3, lda, ldb = _ab_args(A, B)
+    inf = h.info()
+    if c is None:
+        c = torch.empty((inf["d"], inf["b"]), dtype=torch.float32, device=A.device)
+    need = workspace_size(h, n1, n2, n3, A.dtype)
+    if ws is None:
+        ws = alloc_workspace(need, A.device)
+    _check(lib().cms_sketch_product(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype], h.handle,
+                                    _ptr(c), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+    return c
+
+
+def plain_workspace_size(h: Hashes, n1: int, n2: int, n3: int) -> int:
+    out = _SZ()
+    _check(lib().cms_plain_workspace_size(h.handle, n1, n2, n3, ctypes.byref(out)))
+    return out.value
+
+
+def sketch_product_plain_f64(A: torch.Tensor, B: torch.Tensor, h: Hashes,
+                             c: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                             stream=None) -> torch.Tensor:
+    """The plain FP64 form of the same sketch: returns c, float64 (d, b)."""
+    n1, n2, n3, lda, ldb = _ab_args(A, B)
+    if A.dtype != torch.float64:
+        raise ValueError("the plain path takes float64 A and B")
+    inf = h.info()
+    if c is None:
+        c = torch.empty((inf["d"], inf["b"]), dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = alloc_workspace(plain_workspace_size(h, n1, n2, n3), A.device)
+    _check(lib().cms_sketch_product_plain_f64(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, h.handle,
+                                              _ptr(c), _ptr(ws), ws.numel() * ws.element_size(),
+                                              _stream(stream)))
+    return c
+
+
+def decode(c: torch.Tensor, h: Hashes, ij: torch.Tensor, out: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    """DECOMPRESS (Fig. 1) of q index pairs ij (int64, shape (q, 2))."""
+    ij = ij.contiguous()
+    if ij.dtype != torch.int64 or ij.dim() != 2 or ij.shape[1] != 2:
+        raise ValueError("ij must be int64 of shape (q, 2)")
+    q = ij.shape[0]
+    c = c.contiguous()
+    if out is None:
+        out = torch.empty(q, dtype=c.dtype, device=c.device)
+    if c.dtype == torch.float64:
+        _check(lib().cms_decode_f64(_ptr(c), h.handle, _ptr(ij), q, _ptr(out), _stream(stream)))
+    elif c.dtype == torch.float32:
+        _check(lib().cms_decode(_ptr(c), h.handle, _ptr(ij), q, _ptr(out), _stream(stream)))
+    else:
+        raise ValueError("c must be float32 or float64")
+    return out
+
+
+def decode_dense(c: torch.Tensor, h: Hashes, n1: int, n3: int, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """All n1 x n3 estimates, row-major float32."""
+    c = c.contiguous()
+    if c.dtype != torch.float32:
+        raise ValueError("c must be float32")
+    if out is None:
+        out = torch.empty((n1, n3), dtype=torch.float32, device=c.device)
+    _check(lib().cms_decode_dense(_ptr(c), h.handle, n1, n3, _ptr(out), out.stride(0) if n1 else n3,
+                                  _stream(stream)))
+    return out
+
+
+def merge(parts: list[torch.Tensor], out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Sum of partial sketches over disjoint inner-index ranges (linearity, eq. (1))."""
+    d, b = parts[0].shape
+    if out is None:
+        out = torch.empty((d, b), dtype=torch.float32, device=parts[0].device)
+    arr = (ctypes.c_void_p * len(parts))(*[p.data_ptr() for p in parts])
+    _check(lib().cms_merge(arr, len(parts), d, b, _ptr(out), _stream(stream)))
+    return out
+
+
+def check_async(stream=None):
+    _check(lib().cms_check_async(_stream(stream)))
+
+
+def status_string(s: int) -> str:
+    return lib().cms_status_string(s).decode()
+

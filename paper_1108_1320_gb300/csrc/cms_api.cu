@@ -1,0 +1,409 @@
+// cms_api.cu - the C ABI declared in include/cms.h: argument checking,
+// the hash-set object, planning, and the launch sequences.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "cms_internal.h"
+
+namespace cms {
+
+namespace {
+thread_local std::string g_last_error;
+
+// splitmix64 (Steele, Lea, Flood 2014): state += golden gamma, then the
+// variant-13 finaliser.
+uint64_t splitmix64_next(uint64_t* state) {
+  uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Coefficient draw of the hash family: per repetition, (a, c) of h1, s1,
+// h2, s2 in that order, a = 1 + (r mod (p-1)), c = r mod p.
+void draw_coeffs(uint64_t seed, int d, Coeffs* co) {
+  std::memset(co, 0, sizeof(*co));
+  uint64_t st = seed;
+  for (int t = 0; t < d; ++t) {
+    for (int f = 0; f < 4; ++f) {
+      const uint64_t ra = splitmix64_next(&st);
+      const uint64_t rc = splitmix64_next(&st);
+      co->v[t][2 * f + 0] = static_cast<uint32_t>(1 + ra % (kP31 - 1));
+      co->v[t][2 * f + 1] = static_cast<uint32_t>(rc % kP31);
+    }
+  }
+}
+
+struct DeviceProps {
+  int sms = 0;
+  size_t smem_optin = 0;
+};
+
+DeviceProps device_props(int dev) {
+  static std::mutex mu;
+  static std::vector<DeviceProps> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= static_cast<int>(cache.size())) cache.resize(dev + 1);
+  if (cache[dev].sms == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev].sms = v > 0 ? v : 1;
+    v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cache[dev].smem_optin = v > 0 ? static_cast<size_t>(v) : 48 * 1024;
+  }
+  return cache[dev];
+}
+
+cms_status fail(cms_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+cms_status cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return CMS_ERR_CUDA;
+}
+
+cms_status check_device(const cms_hashes* h) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != h->device)
+    return fail(CMS_ERR_INVALID_ARG, "current device differs from the device the hashes were made on");
+  return CMS_OK;
+}
+
+cms_status alloc_tables(cms_hashes* h) {
+  const size_t cells = static_cast<size_t>(h->d) * 2 * static_cast<size_t>(h->n);
+  cudaError_t e = cudaMalloc(&h->d_hs, cells * sizeof(uint32_t));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(hash tables)");
+  if (h->C > 0) {
+    e = cudaMalloc(&h->d_perm, cells * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(bucket lists)");
+    e = cudaMalloc(&h->d_off, static_cast<size_t>(h->d) * 2 * (h->C + 1) * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(bucket offsets)");
+  }
+  return CMS_OK;
+}
+
+void free_tables(cms_hashes* h) {
+  if (h->d_hs) cudaFree(h->d_hs);
+  if (h->d_perm) cudaFree(h->d_perm);
+  if (h->d_off) cudaFree(h->d_off);
+  h->d_hs = h->d_perm = nullptr;
+  h->d_off = nullptr;
+}
+
+cms_status fill_tables(cms_hashes* h, cudaStream_t s, bool hash) {
+  cudaError_t e = cudaSuccess;
+  if (hash) {
+    e = launch_hash_tables(h->coef, h->d, h->n, h->b, h->d_hs, s);
+    if (e != cudaSuccess) return cuda_fail(e, "hash table kernel");
+  }
+  if (h->C > 0) {
+    e = launch_bucket_sort(h->d_hs, h->d, h->n, h->C, h->d_perm, h->d_off, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bucket sort kernel");
+  }
+  return CMS_OK;
+}
+
+bool valid_dtype(int dt) { return dt == CMS_F32 || dt == CMS_BF16 || dt == CMS_F64; }
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace cms
+
+using namespace cms;
+
+extern "C" {
+
+const char* cms_status_string(cms_status s) {
+  switch (s) {
+    case CMS_OK: return "CMS_OK";
+    case CMS_ERR_INVALID_ARG: return "CMS_ERR_INVALID_ARG";
+    case CMS_ERR_UNSUPPORTED: return "CMS_ERR_UNSUPPORTED";
+    case CMS_ERR_CUDA: return "CMS_ERR_CUDA";
+    case CMS_ERR_WORKSPACE: return "CMS_ERR_WORKSPACE";
+    case CMS_ERR_TIMEOUT: return "CMS_ERR_TIMEOUT";
+    case CMS_ERR_DEVICE: return "CMS_ERR_DEVICE";
+  }
+  return "CMS_ERR_UNKNOWN";
+}
+
+const char* cms_last_error(void) { return g_last_error.c_str(); }
+
+cms_status cms_make_hashes(uint64_t seed, int64_t n, int64_t b, int32_t d, cms_hashes** out) {
+  if (!out) return fail(CMS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > (1LL << 24)) return fail(CMS_ERR_INVALID_ARG, "n must be in [1, 2^24]");
+  if (b < 1 || b > (1LL << 24)) return fail(CMS_ERR_INVALID_ARG, "b must be in [1, 2^24]");
+  if (d < 1 || d > kMaxD) return fail(CMS_ERR_INVALID_ARG, "d must be in [1, 64]");
+  cms_hashes* h = new cms_hashes();
+  h->n = n; h->b = b; h->d = d; h->seed = seed;
+  choose_factorisation(b, &h->R, &h->C);
+  cudaGetDevice(&h->device);
+  draw_coeffs(seed, d, &h->coef);
+  cms_status st = alloc_tables(h);
+  if (st == CMS_OK) st = fill_tables(h, nullptr, true);
+  if (st == CMS_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_fail(e, "cms_make_hashes");
+  }
+  if (st != CMS_OK) { free_tables(h); delete h; return st; }
+  *out = h;
+  return CMS_OK;
+}
+
+cms_status cms_reseed_hashes(cms_hashes* h, uint64_t seed, void* stream) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  if (h->from_tables) return fail(CMS_ERR_INVALID_ARG, "hashes built from tables cannot be reseeded");
+  cms_status st = check_device(h);
+  if (st != CMS_OK) return st;
+  h->seed = seed;
+  draw_coeffs(seed, h->d, &h->coef);
+  return fill_tables(h, static_cast<cudaStream_t>(stream), true);
+}
+
+cms_status cms_make_hashes_from_tables(int64_t n, int64_t b, int32_t d, const uint32_t* h1,
+                                       const int8_t* s1, const uint32_t* h2, const int8_t* s2,
+                                       cms_hashes** out) {
+  if (!out) return fail(CMS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!h1 || !s1 || !h2 || !s2) return fail(CMS_ERR_INVALID_ARG, "table pointer is NULL");
+  if (n < 1 || n > (1LL << 24)) return fail(CMS_ERR_INVALID_ARG, "n must be in [1, 2^24]");
+  if (b < 1 || b > (1LL << 24)) return fail(CMS_ERR_INVALID_ARG, "b must be in [1, 2^24]");
+  if (d < 1 || d > kMaxD) return fail(CMS_ERR_INVALID_ARG, "d must be in [1, 64]");
+  std::vector<uint32_t> packed(static_cast<size_t>(d) * 2 * n);
+  for (int t = 0; t < d; ++t) {
+    for (int64_t x = 0; x < n; ++x) {
+      const size_t q = static_cast<size_t>(t) * n + x;
+      if (h1[q] >= b || h2[q] >= b) return fail(CMS_ERR_INVALID_ARG, "table bucket >= b");
+      if ((s1[q] != 1 && s1[q] != -1) || (s2[q] != 1 && s2[q] != -1))
+        return fail(CMS_ERR_INVALID_ARG, "table sign not +-1");
+      packed[(static_cast<size_t>(2 * t) * n) + x] = h1[q] | (s1[q] < 0 ? 0x80000000u : 0u);
+      packed[(static_cast<size_t>(2 * t + 1) * n) + x] = h2[q] | (s2[q] < 0 ? 0x80000000u : 0u);
+    }
+  }
+  cms_hashes* h = new cms_hashes();
+  h->n = n; h->b = b; h->d = d; h->from_tables = true;
+  choose_factorisation(b, &h->R, &h->C);
+  cudaGetDevice(&h->device);
+  cms_status st = alloc_tables(h);
+  if (st == CMS_OK) {
+    cudaError_t e = cudaMemcpy(h->d_hs, packed.data(), packed.size() * sizeof(uint32_t),
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy(tables)");
+  }
+  if (st == CMS_OK) st = fill_tables(h, nullptr, false);
+  if (st == CMS_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_fail(e, "cms_make_hashes_from_tables");
+  }
+  if (st != CMS_OK) { free_tables(h); delete h; return st; }
+  *out = h;
+  return CMS_OK;
+}
+
+cms_status cms_free_hashes(cms_hashes* h) {
+  if (!h) return CMS_OK;
+  cudaDeviceSynchronize();
+  free_tables(h);
+  delete h;
+  return CMS_OK;
+}
+
+cms_status cms_hashes_info(const cms_hashes* h, int64_t* n, int64_t* b, int32_t* d, int64_t* R,
+                           int64_t* C) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  if (n) *n = h->n;
+  if (b) *b = h->b;
+  if (d) *d = h->d;
+  if (R) *R = h->R;
+  if (C) *C = h->C;
+  return CMS_OK;
+}
+
+cms_status cms_hashes_coeffs(const cms_hashes* h, int32_t t, uint32_t out[8]) {
+  if (!h || !out) return fail(CMS_ERR_INVALID_ARG, "NULL argument");
+  if (t < 0 || t >= h->d) return fail(CMS_ERR_INVALID_ARG, "t out of range");
+  for (int q = 0; q < 8; ++q) out[q] = h->coef.v[t][q];
+  return CMS_OK;
+}
+
+cms_status cms_hashes_tables(const cms_hashes* h, uint32_t* h1, int8_t* s1, uint32_t* h2,
+                             int8_t* s2) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  cms_status st = check_device(h);
+  if (st != CMS_OK) return st;
+  std::vector<uint32_t> packed(static_cast<size_t>(h->d) * 2 * h->n);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(packed.data(), h->d_hs, packed.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cms_hashes_tables");
+  for (int t = 0; t < h->d; ++t) {
+    for (int64_t x = 0; x < h->n; ++x) {
+      const size_t q = static_cast<size_t>(t) * h->n + x;
+      const uint32_t wa = packed[static_cast<size_t>(2 * t) * h->n + x];
+      const uint32_t wb = packed[static_cast<size_t>(2 * t + 1) * h->n + x];
+      if (h1) h1[q] = wa & kBucketMask;
+      if (s1) s1[q] = (wa >> 31) ? -1 : 1;
+      if (h2) h2[q] = wb & kBucketMask;
+      if (s2) s2[q] = (wb >> 31) ? -1 : 1;
+    }
+  }
+  return CMS_OK;
+}
+
+static cms_status check_shapes(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
+                               int64_t lda, int64_t ldb) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  if (n1 < 0 || n2 < 0 || n3 < 0) return fail(CMS_ERR_INVALID_ARG, "negative dimension");
+  if (n1 > h->n || n3 > h->n) return fail(CMS_ERR_INVALID_ARG, "n1 and n3 must be <= the hash domain n");
+  if (n2 > (1LL << 31) - 1) return fail(CMS_ERR_INVALID_ARG, "n2 too large");
+  if (lda < std::max<int64_t>(n1, 1)) return fail(CMS_ERR_INVALID_ARG, "lda < n1");
+  if (ldb < std::max<int64_t>(n3, 1)) return fail(CMS_ERR_INVALID_ARG, "ldb < n3");
+  return CMS_OK;
+}
+
+cms_status cms_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int32_t dt,
+                              size_t* bytes) {
+  if (!bytes) return fail(CMS_ERR_INVALID_ARG, "bytes is NULL");
+  cms_status st = check_shapes(h, n1, n2, n3, std::max<int64_t>(n1, 1), std::max<int64_t>(n3, 1));
+  if (st != CMS_OK) return st;
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  DeviceProps dp = device_props(h->device);
+  SketchPlan plan;
+  std::string why;
+  int r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &plan, &why);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  *bytes = plan.ws_bytes;
+  return CMS_OK;
+}
+
+cms_status cms_sketch_product(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
+                              int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h, float* c,
+                              void* ws, size_t ws_bytes, void* stream) {
+  cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
+  if (st != CMS_OK) return st;
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  if (!c) return fail(CMS_ERR_INVALID_ARG, "c is NULL");
+  if (n2 > 0 && ((n1 > 0 && !A) || (n3 > 0 && !B))) return fail(CMS_ERR_INVALID_ARG, "A or B is NULL");
+  st = check_device(h);
+  if (st != CMS_OK) return st;
+  DeviceProps dp = device_props(h->device);
+  SketchPlan plan;
+  std::string why;
+  int r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &plan, &why);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  if (!ws || ws_bytes < plan.ws_bytes)
+    return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_workspace_size()");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+    return fail(CMS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaError_t e = launch_sketch(plan, h, A, lda, B, ldb, n1, n2, n3, dt, c, static_cast<char*>(ws),
+                                static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product");
+  return CMS_OK;
+}
+
+cms_status cms_plain_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
+                                    size_t* bytes) {
+  if (!bytes) return fail(CMS_ERR_INVALID_ARG, "bytes is NULL");
+  cms_status st = check_shapes(h, n1, n2, n3, std::max<int64_t>(n1, 1), std::max<int64_t>(n3, 1));
+  if (st != CMS_OK) return st;
+  PlainPlan plan;
+  std::string why;
+  int r = make_plain_plan(h, n2, &plan, &why);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  *bytes = plan.ws_bytes;
+  return CMS_OK;
+}
+
+cms_status cms_sketch_product_plain_f64(const double* A, int64_t lda, const double* B, int64_t ldb,
+                                        int64_t n1, int64_t n2, int64_t n3, const cms_hashes* h,
+                                        double* c, void* ws, size_t ws_bytes, void* stream) {
+  cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
+  if (st != CMS_OK) return st;
+  if (!c) return fail(CMS_ERR_INVALID_ARG, "c is NULL");
+  if (n2 > 0 && ((n1 > 0 && !A) || (n3 > 0 && !B))) return fail(CMS_ERR_INVALID_ARG, "A or B is NULL");
+  st = check_device(h);
+  if (st != CMS_OK) return st;
+  PlainPlan plan;
+  std::string why;
+  int r = make_plain_plan(h, n2, &plan, &why);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  if (!ws || ws_bytes < plan.ws_bytes)
+    return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_plain_workspace_size()");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+    return fail(CMS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaError_t e = launch_plain(plan, h, A, lda, B, ldb, n1, n2, n3, c, static_cast<char*>(ws),
+                               static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_plain_f64");
+  return CMS_OK;
+}
+
+cms_status cms_decode(const float* c, const cms_hashes* h, const int64_t* ij, int64_t q, float* out,
+                      void* stream) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  if (q < 0) return fail(CMS_ERR_INVALID_ARG, "q < 0");
+  if (q > 0 && (!c || !ij || !out)) return fail(CMS_ERR_INVALID_ARG, "NULL pointer");
+  cms_status st = check_device(h);
+  if (st != CMS_OK) return st;
+  cudaError_t e = launch_decode_pairs_f32(c, h, ij, q, out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_decode");
+  return CMS_OK;
+}
+
+cms_status cms_decode_f64(const double* c, const cms_hashes* h, const int64_t* ij, int64_t q,
+                          double* out, void* stream) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  if (q < 0) return fail(CMS_ERR_INVALID_ARG, "q < 0");
+  if (q > 0 && (!c || !ij || !out)) return fail(CMS_ERR_INVALID_ARG, "NULL pointer");
+  cms_status st = check_device(h);
+  if (st != CMS_OK) return st;
+  cudaError_t e = launch_decode_pairs_f64(c, h, ij, q, out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_decode_f64");
+  return CMS_OK;
+}
+
+cms_status cms_decode_dense(const float* c, const cms_hashes* h, int64_t n1, int64_t n3, float* out,
+                            int64_t ldo, void* stream) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  if (n1 < 0 || n3 < 0 || n1 > h->n || n3 > h->n) return fail(CMS_ERR_INVALID_ARG, "bad n1 or n3");
+  if (ldo < n3) return fail(CMS_ERR_INVALID_ARG, "ldo < n3");
+  if (n1 > 0 && n3 > 0 && (!c || !out)) return fail(CMS_ERR_INVALID_ARG, "NULL pointer");
+  cms_status st = check_device(h);
+  if (st != CMS_OK) return st;
+  cudaError_t e = launch_decode_dense_f32(c, h, n1, n3, out, ldo, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_decode_dense");
+  return CMS_OK;
+}
+
+cms_status cms_merge(const float* const* parts, int32_t count, int32_t d, int64_t b, float* c_out,
+                     void* stream) {
+  if (count < 0 || d < 1 || b < 1) return fail(CMS_ERR_INVALID_ARG, "bad count, d or b");
+  if (!c_out || (count > 0 && !parts)) return fail(CMS_ERR_INVALID_ARG, "NULL pointer");
+  for (int q = 0; q < count; ++q)
+    if (!parts[q]) return fail(CMS_ERR_INVALID_ARG, "NULL part");
+  cudaError_t e = launch_merge(parts, count, static_cast<int64_t>(d) * b, c_out,
+                               static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_merge");
+  return CMS_OK;
+}
+
+cms_status cms_check_async(void* stream) {
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_check_async");
+  const uint32_t w = read_clear_error_decode();
+  if (w == 0xFFFFFFFFu) return fail(CMS_ERR_CUDA, "could not read the device error word");
+  if (w) return fail(CMS_ERR_DEVICE, "decode saw an index pair outside the hash domain");
+  return CMS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// cms_internal.h - host-side declarations shared by the library's
+// translation units (kernel launchers, the hash-set object, the plan).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "cms_common.cuh"
+
+struct cms_hashes {
+  int64_t n = 0;            // hash domain {0..n-1}
+  int64_t b = 0;            // sketch length
+  int32_t d = 0;            // repetitions
+  uint64_t seed = 0;
+  bool from_tables = false;
+  cms::Coeffs coef{};       // host copy of the coefficients
+  // factorisation b = R * C of the fused path (C = 0: b not 5-smooth)
+  int64_t R = 0, C = 0;
+  int device = 0;
+  uint32_t* d_hs = nullptr;     // [d][2][n] packed bucket | sign
+  uint32_t* d_perm = nullptr;   // [d][2][n] indices sorted by (bucket mod C), stable
+  uint32_t* d_off = nullptr;    // [d][2][C+1] bucket-class offsets into d_perm
+};
+
+namespace cms {
+
+// Thread-local error text (set by the C entry points).
+void set_error(const std::string& msg);
+
+// Device error words: one per translation unit that owns kernels which can
+// raise it.  Each reader returns the word and clears it.
+uint32_t read_clear_error_decode();
+
+// ------------------------------------------------------------- launchers --
+// Fill d_hs from coefficients (hash evaluation on the device).
+cudaError_t launch_hash_tables(const Coeffs& co, int d, int64_t n, int64_t b,
+                               uint32_t* hs, cudaStream_t s);
+// Stable counting sort of each [t][side] table by (bucket mod C).
+cudaError_t launch_bucket_sort(const uint32_t* hs, int d, int64_t n, int64_t C,
+                               uint32_t* perm, uint32_t* off, cudaStream_t s);
+
+// Plan of the fused sketch path for one call.
+struct SketchPlan {
+  int64_t b = 0, R = 0, C = 0;
+  int nrows = 0;            // rows f1 = 0..floor(R/2) of the b = R*C grid
+  int d = 0;
+  int nradC = 0;
+  int radC[16] = {0};
+  int G = 1;                // inner indices per group in the fused kernel
+  int64_t kchunk = 0;       // inner indices per task
+  int nkc = 0;              // number of inner-index chunks
+  int threads = 256;
+  size_t smem = 0;          // dynamic shared memory of the fused kernel
+  // workspace layout (byte offsets)
+  size_t off_partial = 0, off_V = 0, off_twfe = 0, off_twC = 0, off_twR = 0;
+  size_t ws_bytes = 0;
+};
+
+bool choose_factorisation(int64_t b, int64_t* R, int64_t* C);
+int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
+                     int dt, int num_sms, size_t smem_optin, SketchPlan* plan,
+                     std::string* why);
+
+cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h,
+                          const void* A, int64_t lda, const void* B, int64_t ldb,
+                          int64_t n1, int64_t n2, int64_t n3, int dt, float* c,
+                          char* ws, cudaStream_t s);
+
+cudaError_t launch_decode_pairs_f32(const float* c, const cms_hashes* h,
+                                    const int64_t* ij, int64_t q, float* out,
+                                    cudaStream_t s);
+cudaError_t launch_decode_pairs_f64(const double* c, const cms_hashes* h,
+                                    const int64_t* ij, int64_t q, double* out,
+                                    cudaStream_t s);
+cudaError_t launch_decode_dense_f32(const float* c, const cms_hashes* h,
+                                    int64_t n1, int64_t n3, float* out,
+                                    int64_t ldo, cudaStream_t s);
+cudaError_t launch_merge(const float* const* parts, int count, int64_t len,
+                         float* out, cudaStream_t s);
+
+// Plain FP64 path.
+struct PlainPlan {
+  int64_t b = 0;
+  int nrad = 0;
+  int rad[24] = {0};
+  int64_t kc = 0;           // inner indices per scatter/FFT batch
+  size_t off_Z = 0, off_Z2 = 0, off_S = 0, off_tw = 0;
+  size_t ws_bytes = 0;
+};
+int make_plain_plan(const cms_hashes* h, int64_t n2, PlainPlan* plan, std::string* why);
+cudaError_t launch_plain(const PlainPlan& plan, const cms_hashes* h,
+                         const double* A, int64_t lda, const double* B, int64_t ldb,
+                         int64_t n1, int64_t n2, int64_t n3, double* c, char* ws,
+                         cudaStream_t s);
+
+}  // namespace cms

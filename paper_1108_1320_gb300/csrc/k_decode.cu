@@ -1,0 +1,134 @@
+// k_decode.cu - DECOMPRESS of Fig. 1: X_t = s1_t(i) s2_t(j) c_t[(h1_t(i) +
+// h2_t(j)) mod b], estimate = median over t (even d: mean of the two middle
+// values).  Also the element-wise merge of partial sketches (linearity of
+// the sketch in the outer products of eq. (1)).
+#include <algorithm>
+#include <cmath>
+
+#include "cms_internal.h"
+
+namespace cms {
+namespace {
+
+__device__ uint32_t g_decode_error = 0;   // set when a pair index is out of range
+
+// Median of x[0..d) (d <= kMaxD): insertion sort in a per-thread array.
+template <typename T>
+__device__ __forceinline__ T median_of(T* x, int d) {
+  for (int a = 1; a < d; ++a) {
+    const T v = x[a];
+    int q = a - 1;
+    while (q >= 0 && x[q] > v) { x[q + 1] = x[q]; --q; }
+    x[q + 1] = v;
+  }
+  const int mid = d >> 1;
+  return (d & 1) ? x[mid] : static_cast<T>(0.5) * (x[mid - 1] + x[mid]);
+}
+
+template <typename T>
+__device__ __forceinline__ T estimate(const T* __restrict__ c, const uint32_t* __restrict__ hs,
+                                      int64_t n, uint32_t b, int d, int64_t i, int64_t j) {
+  T x[kMaxD];
+  for (int t = 0; t < d; ++t) {
+    const uint32_t wa = __ldg(hs + (static_cast<size_t>(2 * t) * n + i));
+    const uint32_t wb = __ldg(hs + (static_cast<size_t>(2 * t + 1) * n + j));
+    uint32_t z = (wa & kBucketMask) + (wb & kBucketMask);
+    if (z >= b) z -= b;
+    T v = __ldg(c + static_cast<size_t>(t) * b + z);
+    if ((wa ^ wb) >> 31) v = -v;
+    x[t] = v;
+  }
+  return median_of(x, d);
+}
+
+template <typename T>
+__global__ void k_decode_pairs(const T* __restrict__ c, const uint32_t* __restrict__ hs,
+                               int64_t n, uint32_t b, int d, const int64_t* __restrict__ ij,
+                               int64_t q, T* __restrict__ out) {
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= q) return;
+  const int64_t i = ij[2 * p], j = ij[2 * p + 1];
+  if (i < 0 || i >= n || j < 0 || j >= n) {
+    out[p] = static_cast<T>(NAN);
+    atomicOr(&g_decode_error, 1u);
+    return;
+  }
+  out[p] = estimate(c, hs, n, b, d, i, j);
+}
+
+template <typename T>
+__global__ void k_decode_dense(const T* __restrict__ c, const uint32_t* __restrict__ hs,
+                               int64_t n, uint32_t b, int d, int64_t n1, int64_t n3,
+                               T* __restrict__ out, int64_t ldo) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int64_t i = blockIdx.y; i < n1; i += gridDim.y) {
+    if (j < n3) out[i * ldo + j] = estimate(c, hs, n, b, d, i, j);
+  }
+}
+
+struct PartPtrs {
+  const float* p[32];
+};
+
+__global__ void k_merge(PartPtrs parts, int count, int64_t len, int accumulate,
+                        float* __restrict__ out) {
+  for (int64_t z = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; z < len;
+       z += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float s = accumulate ? out[z] : 0.f;
+    for (int q = 0; q < count; ++q) s += parts.p[q][z];
+    out[z] = s;
+  }
+}
+
+}  // namespace
+
+uint32_t read_clear_error_decode() {
+  uint32_t v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_decode_error, sizeof(v)) != cudaSuccess) return 0xFFFFFFFFu;
+  if (v) cudaMemcpyToSymbol(g_decode_error, &zero, sizeof(zero));
+  return v;
+}
+
+cudaError_t launch_decode_pairs_f32(const float* c, const cms_hashes* h, const int64_t* ij,
+                                    int64_t q, float* out, cudaStream_t s) {
+  if (q == 0) return cudaSuccess;
+  k_decode_pairs<float><<<static_cast<unsigned>((q + 255) / 256), 256, 0, s>>>(
+      c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d, ij, q, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_pairs_f64(const double* c, const cms_hashes* h, const int64_t* ij,
+                                    int64_t q, double* out, cudaStream_t s) {
+  if (q == 0) return cudaSuccess;
+  k_decode_pairs<double><<<static_cast<unsigned>((q + 255) / 256), 256, 0, s>>>(
+      c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d, ij, q, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_dense_f32(const float* c, const cms_hashes* h, int64_t n1, int64_t n3,
+                                    float* out, int64_t ldo, cudaStream_t s) {
+  if (n1 == 0 || n3 == 0) return cudaSuccess;
+  dim3 grid(static_cast<unsigned>((n3 + 255) / 256),
+            static_cast<unsigned>(std::min<int64_t>(n1, 65535)));
+  k_decode_dense<float><<<grid, 256, 0, s>>>(c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d,
+                                             n1, n3, out, ldo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const float* const* parts, int count, int64_t len, float* out,
+                         cudaStream_t s) {
+  if (len == 0) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((len + 255) / 256, 4096));
+  if (count == 0) return cudaMemsetAsync(out, 0, static_cast<size_t>(len) * sizeof(float), s);
+  for (int base = 0; base < count; base += 32) {
+    PartPtrs pp{};
+    const int m = std::min(32, count - base);
+    for (int q = 0; q < m; ++q) pp.p[q] = parts[base + q];
+    k_merge<<<blocks, 256, 0, s>>>(pp, m, len, base > 0 ? 1 : 0, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace cms

@@ -1,0 +1,409 @@
+// k_sketch.cu - the fused FP32 path of COMPRESSEDPRODUCT (Fig. 1, Sec. 2.2).
+//
+// For one repetition t the sketch spectrum is
+//   S_t[f] = sum_k PA_k[f] PB_k[f],  PA_k = DFT_b(pa_k), PB_k = DFT_b(pb_k),
+// with pa_k[z] = sum_{h1(i)=z} s1(i) A_ik and pb_k likewise from row k of B
+// (Fig. 1; Sec. 2.2 "p*_t = p_u(w^t) p_v(w^t)").  The length-b DFT is split
+// as b = R * C (Cooley-Tukey four-step, input index z = C z1 + z2, output
+// f = f1 + R f2):
+//   PA_k[f1 + R f2] = sum_{z2} w_C^{f2 z2} Y_k[f1][z2],
+//   Y_k[f1][z2]     = sum_{i : h1(i) mod C = z2} s1(i) A_ik w_b^{f1 h1(i)}.
+// The first step is evaluated directly from the <= n nonzeros of the sketch
+// (a pruned first stage), so a thread block owning row f1 needs nothing but
+// column k of A and row k of B: no length-b vector is ever formed, and rows
+// are independent.  Because pa, pb are real, row R - f1 is the conjugate
+// mirror of row f1 and only rows f1 = 0..floor(R/2) are computed.
+//
+// K0  twiddle tables (front-end twiddles per (t, f1, side, entry); w_C; w_R)
+// K1  per task (t, f1, k-range): gather front end -> 2G length-C FFTs in
+//     shared memory -> spectral products summed over the group -> Kahan
+//     compensated accumulation over k -> one partial row written out
+// K2a per (t, f1): fixed-order sum of the k-range partials, inverse
+//     length-C FFT, twiddle w_b^{-f1 z2}
+// K2b per output z = C z1 + z2: real inverse length-R DFT over f1 using the
+//     conjugate symmetry, scaled by 1/b (Fig. 1, p[t] := FFT^{-1}(p[t])).
+#include <algorithm>
+
+#include "cms_internal.h"
+
+namespace cms {
+namespace {
+
+constexpr int kMaxG = 4;
+
+struct SketchArgs {
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  int n1, n2, n3, n;
+  int64_t b;
+  int R, C, nrows, d;
+  int nradC;
+  int radC[16];
+  int G;
+  int kchunk, nkc;
+  const uint32_t* perm;
+  const uint32_t* off;
+  const float2* twfe;
+  const float2* twC;
+  float2* partial;
+};
+
+template <typename T> __device__ __forceinline__ float load_val(const T* p);
+template <> __device__ __forceinline__ float load_val<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float load_val<double>(const double* p) {
+  return static_cast<float>(__ldg(p));
+}
+template <> __device__ __forceinline__ float load_val<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
+// w_M^m = exp(-2 pi i m / M) for m < M, rounded from double.
+__global__ void k_twiddle_table(float2* __restrict__ tw, int M) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * static_cast<double>(m) / static_cast<double>(M), &s, &c);
+    tw[m] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+  }
+}
+
+// Front-end twiddle of sorted entry e of table (t, side) for row f1:
+// s(x) w_b^{(h(x) f1) mod b}, x = perm[e].
+__global__ void k_frontend_twiddles(const uint32_t* __restrict__ hs,
+                                    const uint32_t* __restrict__ perm, int n, int64_t b,
+                                    int nrows, float2* __restrict__ twfe) {
+  const int f1 = blockIdx.y;
+  const int ts = blockIdx.z;  // t * 2 + side
+  const int t = ts >> 1, side = ts & 1;
+  const uint32_t* pm = perm + static_cast<size_t>(ts) * n;
+  const uint32_t* tab = hs + static_cast<size_t>(ts) * n;
+  float2* out = twfe + ((static_cast<size_t>(t) * nrows + f1) * 2 + side) * n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const uint32_t w = tab[pm[e]];
+    const uint64_t m = (static_cast<uint64_t>(w & kBucketMask) * static_cast<uint64_t>(f1)) %
+                       static_cast<uint64_t>(b);
+    double s, c;
+    sincospi(2.0 * static_cast<double>(m) / static_cast<double>(b), &s, &c);
+    float2 v = make_float2(static_cast<float>(c), static_cast<float>(-s));
+    if (w >> 31) { v.x = -v.x; v.y = -v.y; }
+    out[e] = v;
+  }
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sketch_fused(SketchArgs p) {
+  extern __shared__ float4 smem4[];
+  const int C = p.C, G = p.G, n = p.n;
+  float2* twC = reinterpret_cast<float2*>(smem4);              // C
+  float4* acc = smem4 + (C + 1) / 2;                            // C (sum re, im, comp re, im)
+  float2* P = reinterpret_cast<float2*>(acc + C);               // 2 G C
+  float2* Q = P + 2 * G * C;                                    // >= 2 G C, staging aliases it
+  float* val = reinterpret_cast<float*>(Q);                     // [2][G][n]
+
+  const int task = blockIdx.x;
+  const int kc = task % p.nkc;
+  const int row = (task / p.nkc) % p.nrows;
+  const int t = task / (p.nkc * p.nrows);
+
+  for (int i = threadIdx.x; i < C; i += blockDim.x) {
+    twC[i] = p.twC[i];
+    acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+
+  const T* A = static_cast<const T*>(p.A);
+  const T* B = static_cast<const T*>(p.B);
+  const int k_begin = kc * p.kchunk;
+  const int k_end = min(p.n2, k_begin + p.kchunk);
+  const uint32_t* pmA = p.perm + static_cast<size_t>(t * 2 + 0) * n;
+  const uint32_t* pmB = p.perm + static_cast<size_t>(t * 2 + 1) * n;
+  const uint32_t* ofA = p.off + static_cast<size_t>(t * 2 + 0) * (C + 1);
+  const uint32_t* ofB = p.off + static_cast<size_t>(t * 2 + 1) * (C + 1);
+  const float2* twA = p.twfe + ((static_cast<size_t>(t) * p.nrows + row) * 2 + 0) * n;
+  const float2* twB = twA + n;
+
+  for (int k0 = k_begin; k0 < k_end; k0 += G) {
+    const int gcnt = min(G, k_end - k0);
+    __syncthreads();
+    // stage a_k (column k of A) and b_k (row k of B), zero-filled to n
+    for (int g = 0; g < G; ++g) {
+      float* va = val + (0 * G + g) * n;
+      float* vb = val + (1 * G + g) * n;
+      const bool live = g < gcnt;
+      const T* colA = A + static_cast<size_t>(k0 + g) * p.lda;
+      const T* rowB = B + static_cast<size_t>(k0 + g) * p.ldb;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        va[i] = (live && i < p.n1) ? load_val<T>(colA + i) : 0.f;
+        vb[i] = (live && i < p.n3) ? load_val<T>(rowB + i) : 0.f;
+      }
+    }
+    __syncthreads();
+    // gather front end: Y[side][g][z2] = sum over the bucket class z2
+    for (int task2 = threadIdx.x; task2 < 2 * C; task2 += blockDim.x) {
+      const int side = task2 >= C;
+      const int z2 = task2 - side * C;
+      const uint32_t* pm = side ? pmB : pmA;
+      const uint32_t* of = side ? ofB : ofA;
+      const float2* tw = side ? twB : twA;
+      const float* v = val + side * G * n;
+      float2 s[kMaxG];
+#pragma unroll
+      for (int g = 0; g < kMaxG; ++g) s[g] = make_float2(0.f, 0.f);
+      const uint32_t e1 = of[z2 + 1];
+      for (uint32_t e = of[z2]; e < e1; ++e) {
+        const uint32_t x = pm[e];
+        const float2 w = tw[e];
+#pragma unroll
+        for (int g = 0; g < kMaxG; ++g) {
+          if (g < G) {
+            const float a = v[g * n + x];
+            s[g].x = fmaf(a, w.x, s[g].x);
+            s[g].y = fmaf(a, w.y, s[g].y);
+          }
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < kMaxG; ++g)
+        if (g < G) P[(side * G + g) * C + z2] = s[g];
+    }
+    __syncthreads();
+    float2* X = fft_block<false>(P, Q, C, 2 * G, p.radC, p.nradC, twC);
+    // spectral products, summed over the group, Kahan-accumulated over k
+    for (int f2 = threadIdx.x; f2 < C; f2 += blockDim.x) {
+      float2 prod = make_float2(0.f, 0.f);
+      for (int g = 0; g < gcnt; ++g) {
+        const float2 a = X[g * C + f2];
+        const float2 bb = X[(G + g) * C + f2];
+        prod.x = fmaf(a.x, bb.x, prod.x);
+        prod.x = fmaf(-a.y, bb.y, prod.x);
+        prod.y = fmaf(a.x, bb.y, prod.y);
+        prod.y = fmaf(a.y, bb.x, prod.y);
+      }
+      float4 ac = acc[f2];
+      kahan_add(ac.x, ac.z, prod.x);
+      kahan_add(ac.y, ac.w, prod.y);
+      acc[f2] = ac;
+    }
+  }
+  __syncthreads();
+  float2* out = p.partial + static_cast<size_t>(task) * C;
+  for (int f2 = threadIdx.x; f2 < C; f2 += blockDim.x) {
+    const float4 ac = acc[f2];
+    out[f2] = make_float2(ac.x - ac.z, ac.y - ac.w);
+  }
+}
+
+struct InvArgs {
+  int64_t b;
+  int R, C, nrows, d, nkc;
+  int nradC;
+  int radC[16];
+  const float2* partial;
+  const float2* twC;
+  float2* V;
+};
+
+// K2a: one block per (t, f1).
+__global__ void __launch_bounds__(256) k_rows_inverse(InvArgs p) {
+  extern __shared__ float2 sm2[];
+  const int C = p.C;
+  float2* twC = sm2;
+  float2* P = twC + C;
+  float2* Q = P + C;
+  const int tr = blockIdx.x;   // t * nrows + f1
+  const int f1 = tr % p.nrows;
+  for (int i = threadIdx.x; i < C; i += blockDim.x) twC[i] = p.twC[i];
+  const float2* part = p.partial + static_cast<size_t>(tr) * p.nkc * C;
+  for (int f2 = threadIdx.x; f2 < C; f2 += blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int kc = 0; kc < p.nkc; ++kc) {
+      const float2 v = part[static_cast<size_t>(kc) * C + f2];
+      sx += v.x;
+      sy += v.y;
+    }
+    P[f2] = make_float2(static_cast<float>(sx), static_cast<float>(sy));
+  }
+  __syncthreads();
+  float2* X = fft_block<true>(P, Q, C, 1, p.radC, p.nradC, twC);
+  float2* out = p.V + static_cast<size_t>(tr) * C;
+  for (int z2 = threadIdx.x; z2 < C; z2 += blockDim.x) {
+    const uint64_t m = (static_cast<uint64_t>(f1) * static_cast<uint64_t>(z2)) %
+                       static_cast<uint64_t>(p.b);
+    double s, c;
+    sincospi(2.0 * static_cast<double>(m) / static_cast<double>(p.b), &s, &c);
+    const float2 w = make_float2(static_cast<float>(c), static_cast<float>(s));  // w_b^{-m}
+    out[z2] = cmul(X[z2], w);
+  }
+}
+
+// K2b: c[t][C z1 + z2] = (1/b) Re sum_{f1=0}^{R-1} V[f1][z2] w_R^{-f1 z1}, rows
+// above R/2 taken as conjugates of rows below it.
+__global__ void __launch_bounds__(256)
+k_cols_inverse(const float2* __restrict__ V, const float2* __restrict__ twR, int64_t b,
+               int R, int C, int nrows, float* __restrict__ c) {
+  const int t = blockIdx.y;
+  const int64_t z = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (z >= b) return;
+  const int z1 = static_cast<int>(z / C);
+  const int z2 = static_cast<int>(z - static_cast<int64_t>(z1) * C);
+  const float2* Vt = V + static_cast<size_t>(t) * nrows * C + z2;
+  float sum = Vt[0].x;
+  const bool even = (R % 2) == 0;
+  for (int f1 = 1; f1 < nrows; ++f1) {
+    const float2 v = Vt[static_cast<size_t>(f1) * C];
+    const float2 w = twR[(static_cast<int64_t>(f1) * z1) % R];   // w_R^{f1 z1}
+    const float term = v.x * w.x + v.y * w.y;                    // Re(v conj(w))
+    sum += (even && 2 * f1 == R) ? term : 2.f * term;
+  }
+  c[static_cast<size_t>(t) * b + z] = sum / static_cast<float>(b);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+size_t fused_smem_bytes(int C, int G, int n) {
+  const size_t tw = static_cast<size_t>((C + 1) / 2) * 16;
+  const size_t acc = static_cast<size_t>(C) * 16;
+  const size_t Pb = static_cast<size_t>(2 * G) * C * 8;
+  const size_t Qb = std::max(static_cast<size_t>(2 * G) * C * 8, static_cast<size_t>(2 * G) * n * 4);
+  return tw + acc + Pb + Qb;
+}
+
+}  // namespace
+
+bool choose_factorisation(int64_t b, int64_t* R, int64_t* C) {
+  int rad[64];
+  if (b < 1 || factor_radices(b, rad, 64) < 0) { *R = 0; *C = 0; return false; }
+  int64_t best = 1;
+  for (int64_t c = 1; c <= std::min<int64_t>(b, 1024); ++c)
+    if (b % c == 0) best = c;
+  *C = best;
+  *R = b / best;
+  return true;
+}
+
+int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int dt,
+                     int num_sms, size_t smem_optin, SketchPlan* plan, std::string* why) {
+  (void)dt;
+  SketchPlan p;
+  p.b = h->b;
+  p.d = h->d;
+  if (h->C <= 0) { *why = "b is not 5-smooth (2^x 3^y 5^z): the fused FFT path needs it"; return CMS_ERR_UNSUPPORTED; }
+  p.R = h->R;
+  p.C = h->C;
+  p.nrows = static_cast<int>(p.R / 2 + 1);
+  p.nradC = factor_radices(p.C, p.radC, 16);
+  if (p.nradC < 0) { *why = "internal: C not factorable"; return CMS_ERR_UNSUPPORTED; }
+  if (p.R > 65536) { *why = "R = b / C too large"; return CMS_ERR_UNSUPPORTED; }
+  const int n = static_cast<int>(h->n);
+  int G = 0;
+  for (int g = kMaxG; g >= 1; --g) {
+    if (fused_smem_bytes(static_cast<int>(p.C), g, n) <= 112 * 1024) { G = g; break; }
+  }
+  if (G == 0) {
+    for (int g = kMaxG; g >= 1; --g)
+      if (fused_smem_bytes(static_cast<int>(p.C), g, n) <= smem_optin) { G = g; break; }
+  }
+  if (G == 0) {
+    *why = "hash domain n too large for the shared-memory staging of the fused kernel";
+    return CMS_ERR_UNSUPPORTED;
+  }
+  p.G = G;
+  p.smem = fused_smem_bytes(static_cast<int>(p.C), G, n);
+  const int per_sm = std::max<int>(1, static_cast<int>(std::min<size_t>(4, (228 * 1024) / (p.smem + 1024))));
+  const int64_t units = static_cast<int64_t>(p.d) * p.nrows;
+  const int64_t target = 2LL * num_sms * per_sm;
+  int64_t nkc = std::max<int64_t>(1, (target + units - 1) / units);
+  const int64_t max_chunks = std::max<int64_t>(1, (n2 + G - 1) / G);
+  nkc = std::min(nkc, max_chunks);
+  int64_t kchunk = n2 > 0 ? (n2 + nkc - 1) / nkc : G;
+  kchunk = ((kchunk + G - 1) / G) * G;
+  nkc = n2 > 0 ? (n2 + kchunk - 1) / kchunk : 1;
+  p.kchunk = kchunk;
+  p.nkc = static_cast<int>(nkc);
+  (void)n1; (void)n3;
+  size_t off = 0;
+  p.off_partial = off; off = align256(off + static_cast<size_t>(units) * p.nkc * p.C * 8);
+  p.off_V = off;       off = align256(off + static_cast<size_t>(units) * p.C * 8);
+  p.off_twfe = off;    off = align256(off + static_cast<size_t>(units) * 2 * h->n * 8);
+  p.off_twC = off;     off = align256(off + static_cast<size_t>(p.C) * 8);
+  p.off_twR = off;     off = align256(off + static_cast<size_t>(p.R) * 8);
+  p.ws_bytes = off;
+  *plan = p;
+  return CMS_OK;
+}
+
+cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const void* A,
+                          int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
+                          int64_t n3, int dt, float* c, char* ws, cudaStream_t s) {
+  float2* partial = reinterpret_cast<float2*>(ws + plan.off_partial);
+  float2* V = reinterpret_cast<float2*>(ws + plan.off_V);
+  float2* twfe = reinterpret_cast<float2*>(ws + plan.off_twfe);
+  float2* twC = reinterpret_cast<float2*>(ws + plan.off_twC);
+  float2* twR = reinterpret_cast<float2*>(ws + plan.off_twR);
+  const int n = static_cast<int>(h->n);
+
+  k_twiddle_table<<<static_cast<unsigned>((plan.C + 255) / 256), 256, 0, s>>>(twC, static_cast<int>(plan.C));
+  k_twiddle_table<<<static_cast<unsigned>((plan.R + 255) / 256), 256, 0, s>>>(twR, static_cast<int>(plan.R));
+  {
+    dim3 grid(static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 64)), plan.nrows, 2 * plan.d);
+    k_frontend_twiddles<<<grid, 256, 0, s>>>(h->d_hs, h->d_perm, n, plan.b, plan.nrows, twfe);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  SketchArgs a{};
+  a.A = A; a.lda = lda; a.B = B; a.ldb = ldb;
+  a.n1 = static_cast<int>(n1); a.n2 = static_cast<int>(n2); a.n3 = static_cast<int>(n3); a.n = n;
+  a.b = plan.b; a.R = static_cast<int>(plan.R); a.C = static_cast<int>(plan.C);
+  a.nrows = plan.nrows; a.d = plan.d;
+  a.nradC = plan.nradC;
+  for (int i = 0; i < 16; ++i) a.radC[i] = plan.radC[i];
+  a.G = plan.G; a.kchunk = static_cast<int>(plan.kchunk); a.nkc = plan.nkc;
+  a.perm = h->d_perm; a.off = h->d_off; a.twfe = twfe; a.twC = twC; a.partial = partial;
+  const unsigned ntask = static_cast<unsigned>(static_cast<int64_t>(plan.d) * plan.nrows * plan.nkc);
+  const int smem = static_cast<int>(plan.smem);
+  switch (dt) {
+    case CMS_F32:
+      e = cudaFuncSetAttribute(k_sketch_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) k_sketch_fused<float><<<ntask, plan.threads, smem, s>>>(a);
+      break;
+    case CMS_BF16:
+      e = cudaFuncSetAttribute(k_sketch_fused<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) k_sketch_fused<__nv_bfloat16><<<ntask, plan.threads, smem, s>>>(a);
+      break;
+    default:
+      e = cudaFuncSetAttribute(k_sketch_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) k_sketch_fused<double><<<ntask, plan.threads, smem, s>>>(a);
+      break;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  InvArgs ia{};
+  ia.b = plan.b; ia.R = static_cast<int>(plan.R); ia.C = static_cast<int>(plan.C);
+  ia.nrows = plan.nrows; ia.d = plan.d; ia.nkc = plan.nkc;
+  ia.nradC = plan.nradC;
+  for (int i = 0; i < 16; ++i) ia.radC[i] = plan.radC[i];
+  ia.partial = partial; ia.twC = twC; ia.V = V;
+  const int smem2 = static_cast<int>(3 * plan.C * 8);
+  if (smem2 > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_rows_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
+    if (e != cudaSuccess) return e;
+  }
+  k_rows_inverse<<<static_cast<unsigned>(plan.d * plan.nrows), 256, smem2, s>>>(ia);
+  dim3 g2(static_cast<unsigned>((plan.b + 255) / 256), plan.d);
+  k_cols_inverse<<<g2, 256, 0, s>>>(V, twR, plan.b, static_cast<int>(plan.R), static_cast<int>(plan.C),
+                                    plan.nrows, c);
+  return cudaGetLastError();
+}
+
+}  // namespace cms

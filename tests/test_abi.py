@@ -1,0 +1,65 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every
+symbol include/cms.h declares; host-only calls behave.  No compute calls."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1108_1320_gb300 import build as b
+    b.build()
+    from paper_1108_1320_gb300 import cms
+    return cms.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cms.h")).read()
+    return sorted(set(re.findall(r"CMS_API\s+[\w\s\*]+?\b(cms_\w+)\s*\(", src)))
+
+
+def test_header_declares_expected_entry_points():
+    names = _declared()
+    for must in ("cms_make_hashes", "cms_sketch_product", "cms_decode", "cms_decode_dense",
+                 "cms_sketch_product_plain_f64", "cms_workspace_size", "cms_check_async"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1108_1320_gb300 import cms
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in cms.SIGNATURES, f"binding lacks {name}"
+
+
+def test_binding_declares_nothing_extra():
+    from paper_1108_1320_gb300 import cms
+    assert set(cms.SIGNATURES) == set(_declared())
+
+
+def test_status_strings(lib):
+    from paper_1108_1320_gb300 import cms
+    for code, name in cms.STATUS.items():
+        assert cms.status_string(code) == name
+
+
+def test_null_arguments_are_rejected_without_cuda(lib):
+    # argument checks run before any CUDA call
+    assert lib.cms_make_hashes(1, 10, 16, 1, None) == 1
+    out = ctypes.c_void_p()
+    assert lib.cms_make_hashes(1, 0, 16, 1, ctypes.byref(out)) == 1
+    assert lib.cms_make_hashes(1, 10, 16, 0, ctypes.byref(out)) == 1
+    assert lib.cms_make_hashes(1, 10, 16, 65, ctypes.byref(out)) == 1
+    assert b"d must be" in lib.cms_last_error()
+    assert lib.cms_workspace_size(None, 1, 1, 1, 0, None) == 1
+    assert lib.cms_decode(None, None, None, 0, None, None) == 1
+    assert lib.cms_merge(None, -1, 1, 1, None, None) == 1
+
+
+def test_build_flags_target_sm103a():
+    from paper_1108_1320_gb300 import build as b
+    assert "arch=compute_103a,code=sm_103a" in b.ARCH

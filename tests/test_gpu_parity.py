@@ -1,0 +1,331 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: hash tables and bucket indices bit-exact; the sketch c within
+relative L2 1e-5 per repetition for FP32 (and FP64-stored) inputs, 3e-3 for
+BF16 storage against the unrounded data and 1e-5 against the BF16 values
+themselves; the plain FP64 path within 1e-10; decoding exact when fed the
+oracle's own sketch.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import cms_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_BF16 = 3e-3
+
+
+@pytest.fixture(scope="module")
+def cms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1108_1320_gb300 import build as b
+    b.build()
+    import paper_1108_1320_gb300 as m
+    m.lib()
+    return m
+
+
+def dev():
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def colmajor(A: np.ndarray, dtype=torch.float32) -> torch.Tensor:
+    """Device copy of A (n1 x n2) in column-major order."""
+    return torch.from_numpy(np.ascontiguousarray(A.T)).to(dev(), dtype).T
+
+
+def rowmajor(B: np.ndarray, dtype=torch.float32) -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(B)).to(dev(), dtype)
+
+
+# ------------------------------------------------------------ hash tables --
+@pytest.mark.parametrize("seed,n,b,d", [(1, 256, 1024, 1), (2, 2048, 65536, 5), (3, 1000, 2000, 3),
+                                        (4, 37, 7, 2), (5, 5000, 1, 1), (6, 70000, 1 << 20, 3),
+                                        (2**64 - 1, 64, 16384, 64)])
+def test_hash_tables_bit_exact(cms, seed, n, b, d):
+    h = cms.make_hashes(seed, n, b, d)
+    h1, s1, h2, s2 = h.tables()
+    tab = O.make_tables(seed, n, b, d)
+    np.testing.assert_array_equal(h1, tab.h1)
+    np.testing.assert_array_equal(s1, tab.s1)
+    np.testing.assert_array_equal(h2, tab.h2)
+    np.testing.assert_array_equal(s2, tab.s2)
+    coef = O.draw_coefficients(seed, d)
+    for t in range(d):
+        np.testing.assert_array_equal(h.coeffs(t), coef[t].reshape(-1))
+    h.free()
+
+
+def test_reseed_matches_fresh_tables(cms):
+    h = cms.make_hashes(10, 3000, 4096, 3)
+    h.reseed(11)
+    torch.cuda.synchronize()
+    h1, s1, h2, s2 = h.tables()
+    tab = O.make_tables(11, 3000, 4096, 3)
+    np.testing.assert_array_equal(h1, tab.h1)
+    np.testing.assert_array_equal(s2, tab.s2)
+    h.free()
+
+
+# ------------------------------------------------------- sketch parity -----
+CASES = [
+    # n1, n2, n3, b, d  (A n1 x n2, B n2 x n3)
+    (256, 256, 256, 1024, 1),      # the plain-method configuration, b = 1024
+    (100, 37, 77, 4096, 3),        # ragged shapes, R = 4 rows of C = 1024
+    (2048, 40, 2048, 65536, 5),    # the covariance configuration's n and b, few k
+    (500, 64, 300, 2000, 2),       # b = 2000 as in Fig. 2 (5-smooth, C = 1000)
+    (64, 10, 64, 1, 2),            # b = 1: the AMS sketch
+    (33, 5, 17, 12, 3),            # tiny mixed-radix b
+    (300, 129, 301, 3 * 1024, 4),  # R = 3 (odd), ragged k tail
+    (1, 9, 1, 8, 1),               # single row / column
+]
+
+
+@pytest.mark.parametrize("n1,n2,n3,b,d", CASES)
+def test_sketch_f32_matches_oracle(cms, n1, n2, n3, b, d):
+    A = W.gaussian(n1, n2, 1000 + n1)
+    B = W.gaussian(n2, n3, 2000 + n3)
+    Af = A.astype(np.float32)
+    Bf = B.astype(np.float32)
+    n = max(n1, n3)
+    h = cms.make_hashes(77 + b, n, b, d)
+    c = cms.sketch_product(colmajor(Af), rowmajor(Bf), h).cpu().numpy()
+    cms.check_async()
+    tab = O.make_tables(77 + b, n, b, d)
+    ref = O.sketch_definition(Af.astype(np.float64), Bf.astype(np.float64), tab)
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
+def test_sketch_empty_inner_dimension_is_zero(cms):
+    h = cms.make_hashes(1, 50, 1024, 2)
+    A = torch.zeros((50, 0), device=dev())
+    B = torch.zeros((0, 40), device=dev())
+    c = cms.sketch_product(A, B, h)
+    assert torch.count_nonzero(c).item() == 0
+    h.free()
+
+
+def test_sketch_is_deterministic(cms):
+    A = W.gaussian(700, 90, 5).astype(np.float32)
+    h = cms.make_hashes(3, 700, 8192, 3)
+    a = colmajor(A)
+    bm = rowmajor(A.T)
+    c1 = cms.sketch_product(a, bm, h)
+    c2 = cms.sketch_product(a, bm, h)
+    assert torch.equal(c1, c2)
+    h.free()
+
+
+def test_sketch_bf16_storage(cms):
+    n, m, b, d = 600, 200, 8192, 3
+    X = W.gaussian(m, n, 31).astype(np.float32)
+    Xb, _ = W.bf16_round(X)
+    h = cms.make_hashes(4, n, b, d)
+    xt = torch.from_numpy(X).to(dev(), torch.bfloat16)
+    c = cms.sketch_product(xt.T, xt, h).cpu().numpy()
+    tab = O.make_tables(4, n, b, d)
+    ref_bf16 = O.sketch_definition(Xb.T.astype(np.float64), Xb.astype(np.float64), tab)
+    ref_f32 = O.sketch_definition(X.T.astype(np.float64), X.astype(np.float64), tab)
+    assert O.rel_l2(c, ref_bf16) < TOL_F32
+    assert O.rel_l2(c, ref_f32) < TOL_BF16
+    h.free()
+
+
+def test_sketch_f64_storage_fused(cms):
+    A = W.gaussian(128, 50, 8)
+    B = W.gaussian(50, 96, 9)
+    h = cms.make_hashes(6, 128, 2048, 2)
+    c = cms.sketch_product(colmajor(A, torch.float64), rowmajor(B, torch.float64), h).cpu().numpy()
+    ref = O.sketch_definition(A, B, O.make_tables(6, 128, 2048, 2))
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
+def test_sketch_strided_leading_dimensions(cms):
+    # lda > n1 and ldb > n3: slices of larger buffers
+    big_a = W.gaussian(70, 200, 3).astype(np.float32)      # stored as (n2, lda) rows
+    big_b = W.gaussian(70, 150, 4).astype(np.float32)      # (n2, ldb)
+    ta = torch.from_numpy(big_a).to(dev())
+    tb = torch.from_numpy(big_b).to(dev())
+    A = ta[:, :120].T            # n1 = 120, n2 = 70, lda = 200
+    B = tb[:, :100]              # n3 = 100, ldb = 150
+    h = cms.make_hashes(8, 120, 4096, 2)
+    c = cms.sketch_product(A, B, h).cpu().numpy()
+    ref = O.sketch_definition(big_a[:, :120].T.astype(np.float64), big_b[:, :100].astype(np.float64),
+                              O.make_tables(8, 120, 4096, 2))
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
+def test_sketch_on_side_stream_and_merge(cms):
+    # linearity over k (eq. (1)): sketches of two k-ranges merge to the whole
+    A = W.gaussian(300, 80, 12).astype(np.float32)
+    B = W.gaussian(80, 260, 13).astype(np.float32)
+    h = cms.make_hashes(9, 300, 16384, 3)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = colmajor(A)
+        bm = rowmajor(B)
+        c_all = cms.sketch_product(a, bm, h, stream=s)
+        c1 = cms.sketch_product(a[:, :33], bm[:33], h, stream=s)
+        c2 = cms.sketch_product(a[:, 33:], bm[33:], h, stream=s)
+        cm = cms.merge([c1, c2], stream=s)
+    s.synchronize()
+    ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), O.make_tables(9, 300, 16384, 3))
+    assert O.rel_l2(c_all.cpu().numpy(), ref) < TOL_F32
+    assert O.rel_l2(cm.cpu().numpy(), ref) < TOL_F32
+    h.free()
+
+
+def test_injective_hash_recovers_product(cms):
+    # h1(i) = i, h2(j) = n1 j, b = n1 n3: c = vec(AB) with signs (Sec. 2.2)
+    n1, n2, n3 = 16, 20, 8
+    A = W.gaussian(n1, n2, 1).astype(np.float32)
+    B = W.gaussian(n2, n3, 2).astype(np.float32)
+    n = n1
+    g = W.rng(3)
+    s1 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    s2 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    h1 = np.arange(n, dtype=np.uint32)[None, :]
+    h2 = (n1 * np.arange(n, dtype=np.uint32))[None, :]
+    h2 = np.minimum(h2, n1 * n3 - 1).astype(np.uint32)   # columns >= n3 are never used
+    h = cms.Hashes.from_tables(h1, s1, h2, s2, n1 * n3)
+    c = cms.sketch_product(colmajor(A), rowmajor(B), h)
+    ii, jj = np.meshgrid(np.arange(n1), np.arange(n3), indexing="ij")
+    ij = torch.from_numpy(np.stack([ii.ravel(), jj.ravel()], 1).astype(np.int64)).to(dev())
+    est = cms.decode(c, h, ij).cpu().numpy().reshape(n1, n3)
+    AB = A.astype(np.float64) @ B.astype(np.float64)
+    np.testing.assert_allclose(est, AB, atol=2e-5 * np.abs(AB).max())
+    h.free()
+
+
+# ------------------------------------------------------------ plain FP64 --
+@pytest.mark.parametrize("n1,n2,n3,b,d", [(256, 256, 256, 1024, 1), (100, 37, 77, 4096, 3),
+                                          (500, 64, 300, 2000, 2), (64, 10, 64, 1, 2)])
+def test_plain_f64_matches_oracle(cms, n1, n2, n3, b, d):
+    A = W.gaussian(n1, n2, 10 + n1)
+    B = W.gaussian(n2, n3, 20 + n3)
+    n = max(n1, n3)
+    h = cms.make_hashes(55, n, b, d)
+    c = cms.sketch_product_plain_f64(colmajor(A, torch.float64), rowmajor(B, torch.float64), h)
+    ref = O.sketch_definition(A, B, O.make_tables(55, n, b, d))
+    assert O.rel_l2(c.cpu().numpy(), ref) < 1e-10
+    h.free()
+
+
+# ----------------------------------------------------------------- decode --
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 7, 8, 36])
+def test_decode_exact_on_oracle_sketch(cms, d):
+    # feed the oracle's sketch (rounded to FP32) to both decoders: median is a
+    # selection, so odd d matches exactly; even d averages in FP32
+    n1, n3, b = 300, 200, 4096
+    rng = W.rng(d)
+    c_ref = rng.standard_normal((d, b)).astype(np.float32)
+    h = cms.make_hashes(100 + d, max(n1, n3), b, d)
+    tab = O.make_tables(100 + d, max(n1, n3), b, d)
+    ij = W.sample_pairs(n1, n3, 5000, 4)
+    got = cms.decode(torch.from_numpy(c_ref).to(dev()), h, torch.from_numpy(ij).to(dev())).cpu().numpy()
+    want = O.decompress(c_ref.astype(np.float64), tab, ij[:, 0], ij[:, 1])
+    if d % 2:
+        np.testing.assert_array_equal(got, want.astype(np.float32))
+    else:
+        np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-6)
+    dense = cms.decode_dense(torch.from_numpy(c_ref).to(dev()), h, n1, n3).cpu().numpy()
+    want_dense = O.decompress_dense(c_ref.astype(np.float64), tab, n1, n3)
+    np.testing.assert_allclose(dense, want_dense, rtol=1e-6, atol=1e-6)
+    h.free()
+
+
+def test_decode_f64(cms):
+    d, b = 5, 2048
+    c_ref = W.rng(1).standard_normal((d, b))
+    h = cms.make_hashes(3, 100, b, d)
+    tab = O.make_tables(3, 100, b, d)
+    ij = W.sample_pairs(100, 100, 1000, 2)
+    got = cms.decode(torch.from_numpy(c_ref).to(dev()), h, torch.from_numpy(ij).to(dev())).cpu().numpy()
+    np.testing.assert_array_equal(got, O.decompress(c_ref, tab, ij[:, 0], ij[:, 1]))
+    h.free()
+
+
+def test_decode_out_of_range_pair_raises(cms):
+    h = cms.make_hashes(3, 10, 64, 1)
+    c = torch.zeros((1, 64), device=dev())
+    ij = torch.tensor([[0, 0], [10, 0]], dtype=torch.int64, device=dev())
+    out = cms.decode(c, h, ij)
+    with pytest.raises(cms.CmsError) as e:
+        cms.check_async()
+    assert e.value.status == 6
+    assert math.isnan(out[1].item())
+    cms.check_async()   # the word was cleared
+    h.free()
+
+
+# ---------------------------------------------------- argument checking ----
+def test_invalid_arguments(cms):
+    h = cms.make_hashes(1, 64, 1024, 1)
+    A = torch.zeros((64, 8), device=dev()).T.contiguous().T  # column-major
+    B = torch.zeros((8, 64), device=dev())
+    with pytest.raises(ValueError):
+        cms.sketch_product(A.contiguous(), B, h)            # row-major A rejected by binding
+    ws = torch.empty(16, dtype=torch.uint8, device=dev())
+    with pytest.raises(cms.CmsError) as e:
+        cms.sketch_product(A, B, h, ws=ws)
+    assert e.value.status == 4
+    h7 = cms.make_hashes(1, 64, 7, 1)                       # prime b: no FFT factorisation
+    with pytest.raises(cms.CmsError) as e:
+        cms.sketch_product(A, B, h7)
+    assert e.value.status == 2
+    big = torch.zeros((65, 8), device=dev()).T.contiguous().T
+    with pytest.raises(cms.CmsError) as e:
+        cms.sketch_product(big, B, h)                        # n1 > n
+    assert e.value.status == 1
+    h.free()
+    h7.free()
+
+
+# ------------------------------------------------- Theorem 5, on the GPU ---
+def test_theorem5_exact_sparse_on_gpu(cms):
+    n, b = 64, 1024
+    d = 6 * int(math.log2(n))
+    sb = W.sparse_blocks(n, n_blocks=2, inner=3, rows=8, cols=8, seed=5)
+    A, B = sb.scipy()
+    Ad = A.toarray()
+    Bd = B.toarray()
+    h = cms.make_hashes(2024, n, b, d)
+    c = cms.sketch_product(colmajor(Ad), rowmajor(Bd), h)
+    tab = O.make_tables(2024, n, b, d)
+    ref = O.sketch_definition(Ad, Bd, tab)
+    np.testing.assert_array_equal(np.rint(c.cpu().numpy()), ref)
+    est = cms.decode_dense(c, h, n, n).cpu().numpy()
+    np.testing.assert_array_equal(np.rint(est), Ad @ Bd)
+    h.free()
+
+
+# ------------------------------------------ full-size covariance workload --
+def test_covariance_full_size_sampled(cms):
+    # X 4096 samples x 2048 variables FP32, 32 planted pairs rho = 0.5,
+    # A = X^T, B = X, b = 65536, d = 5 (the benchmarked configuration).
+    m, n, b, d = 4096, 2048, 65536, 5
+    cov = W.covariance(m, n, 32, 0.5, seed=2, dtype=np.float32)
+    X = torch.from_numpy(cov.X).to(dev())
+    h = cms.make_hashes(2, n, b, d)
+    c = cms.sketch_product(X.T, X, h).cpu().numpy().astype(np.float64)
+    tab = O.make_tables(2, n, b, d)
+    Xd = cov.X.astype(np.float64)
+    zs = W.rng(22).choice(b, 128, replace=False)
+    for t in range(d):
+        want = O.sketch_bucket_values(Xd.T, Xd, tab, t, zs)
+        err = np.linalg.norm(c[t, zs] - want) / np.linalg.norm(want)
+        assert err < TOL_F32, (t, err)
+        # the DC bin: sum_z c_z = (s1^T X^T)(X s2)  (Sec. 2.1)
+        dc = (tab.s1[t] @ Xd.T) @ (Xd @ tab.s2[t])
+        assert abs(c[t].sum() - dc) < 1e-5 * np.abs(c[t]).sum()
+    h.free()
