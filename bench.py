@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Throughput of the compressed matrix product (COMPRESSEDPRODUCT + DECOMPRESS,
+Fig. 1 of Pagh, arXiv 1108.1320) on the sample-covariance workload.
+
+Workload (Sec. 3.2 use): X = 4096 samples x 2048 variables, FP32, i.i.d.
+N(0, 1) with 32 disjoint planted pairs of correlation 0.5; A = X^T, B = X;
+b = 65536, d = 5.  One step = one product: redraw the hash functions on the
+device (new seed), sketch (hash -> FFT -> spectral product summed over k ->
+inverse FFT), and decode all 2048 x 2048 estimates (median of 5).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
+(on a bounded sample of the same workload, scaled to products/s).
+"""
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A,B GB/s as % of HBM roofline; products/s fused FP32 vs plain FP64, same error"
+WORKLOAD = dict(name="covariance", m=4096, n=2048, pairs=32, rho=0.5, b=65536, d=5, seed=2)
+FLUSH_BYTES = 256 << 20            # > 129 MB L2: written between timed steps
+FP32_LANES_PER_SM = 128            # Blackwell SM: 4 partitions x 32 FP32 lanes
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_sketch_fused_covariance.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1108_1320_gb300", "csrc", f)
+                  for f in ("k_sketch.cu", "cms_common.cuh")]
+
+
+def workload_label(w=WORKLOAD) -> str:
+    return (f"covariance X {w['m']}x{w['n']} fp32, {w['pairs']} planted pairs rho={w['rho']}, "
+            f"A=X^T B=X, b={w['b']}, d={w['d']}")
+
+
+def sketch_flops(d: int, K: int, b: int) -> float:
+    """Algorithmic flops of the fused kernel: per repetition and inner index,
+    two real length-b FFTs packed as one complex FFT (5 b log2 b) plus the
+    spectral complex multiply-accumulate (8 flops x b/2 bins)."""
+    return d * K * (5.0 * b * math.log2(b) + 4.0 * b)
+
+
+def total_flops(d: int, K: int, b: int) -> float:
+    return sketch_flops(d, K, b) + d * 2.5 * b * math.log2(b)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, or None when absent or taken on a different kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch_full")
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.6)      # let nvidia-smi attach before the timed region
+
+    def mark_begin(self):
+        self.t0 = _dt.datetime.now()
+
+    def mark_end(self):
+        self.t1 = _dt.datetime.now()
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = _dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                continue
+            rows.append((ts, parts))
+        inside = [p for ts, p in rows if self.t0 and self.t1 and self.t0 <= ts <= self.t1]
+        used = inside if inside else [p for _, p in rows]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in used if num(p[1]) is not None]
+        mx = [num(p[2]) for p in used if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for p in used for k in range(4) if p[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons,
+                "samples": len(inside),
+                "samples_total": len(rows),
+                "power_w_max": max((num(p[3]) or 0.0) for p in used) if used else None}
+
+
+# --------------------------------------------------------- CPU oracle leg --
+def oracle_sample(X: np.ndarray, w: dict, k_count: int, seed: int, rows: int = 16):
+    """Time the FP64 oracle (Route F of Fig. 1 plus DECOMPRESS) on the first
+    k_count inner indices and `rows` rows of the dense decode; returns
+    (seconds, extrapolated seconds per full product)."""
+    from oracle import cms_oracle as O
+    n, b, d = w["n"], w["b"], w["d"]
+    Xs = X[:k_count].astype(np.float64)
+    tab = O.make_tables(seed, n, b, d)
+    t0 = time.perf_counter()
+    c = O.sketch_fft(Xs.T, Xs, tab)
+    t1 = time.perf_counter()
+    O.decompress_dense(c, tab, rows, n)
+    t2 = time.perf_counter()
+    per_product = (t1 - t0) * (w["m"] / k_count) + (t2 - t1) * (n / rows)
+    return t2 - t0, per_product
+
+
+def cpu_baseline(X: np.ndarray, w: dict, budget_s: float = 12.0) -> dict:
+    # calibrate on a small sample, then one run sized to the budget
+    _, per = oracle_sample(X, w, 4, 1)
+    k_count = int(max(4, min(w["m"], budget_s / max(per, 1e-9) * w["m"])))
+    took, per = oracle_sample(X, w, k_count, 2)
+    return {"value": 1.0 / per, "unit": "products/s", "cores": 1, "kind": "oracle",
+            "sample": f"Route F (per-k numpy FFT, FP64) over {k_count} of {w['m']} inner "
+                      f"indices and 16 of {w['n']} decode rows, scaled to one product; "
+                      f"{took:.1f} s of CPU work, single-threaded numpy"}
+
+
+def reference_arm(args):
+    """--impl reference: the oracle on the host cores, rank 0 only."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import workloads as W
+    w = WORKLOAD
+    cov = W.covariance(w["m"], w["n"], w["pairs"], w["rho"], w["seed"], dtype=np.float32)
+    k_count = 16
+    times = []
+    for i in range(args.warmup + args.steps):
+        _, per = oracle_sample(cov.X, w, k_count, 100 + i)
+        if i >= args.warmup:
+            times.append(per)
+    per = statistics.mean(times)
+    value = 1.0 / per
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "products/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_label(), "m": w["m"], "n": w["n"], "b": w["b"], "d": w["d"],
+                   "l2": "host run"},
+        "cpu_baseline": {"value": value, "unit": "products/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: Route F over {k_count} of {w['m']} inner indices "
+                                   f"+ 16 decode rows, scaled to one product"},
+        "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------- GPU arm -----
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    import workloads as W
+    from paper_1108_1320_gb300 import build as B
+    B.build()
+    import paper_1108_1320_gb300 as cms
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOAD
+    m, n, b, d = w["m"], w["n"], w["b"], w["d"]
+
+    cov = W.covariance(m, n, w["pairs"], w["rho"], w["seed"], dtype=np.float32)
+    X_host = torch.from_numpy(cov.X).pin_memory()
+    X = X_host.to(dev)
+    h = cms.make_hashes(w["seed"], n, b, d)
+    ws = cms.alloc_workspace(cms.workspace_size(h, n, m, n, torch.float32), dev)
+    c = torch.empty((d, b), dtype=torch.float32, device=dev)
+    est = torch.empty((n, n), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    seed_base = 1000 * (rank + 1)
+
+    def step(i):
+        h.reseed(seed_base + i, stream)
+        cms.sketch_product(X.T, X, h, c=c, ws=ws, stream=stream)
+        cms.decode_dense(c, h, n, n, out=est, stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    cms.check_async()
+
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    sampler = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
+    sampler.start()
+    cms.profile_enable(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.mark_begin()
+    for i in range(args.steps):
+        flush.zero_()                                  # evict X and c from L2
+        starts[i].record(stream)
+        step(args.warmup + i)
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    sampler.mark_end()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = cms.profile_summary()
+    cms.profile_enable(False)
+    cms.check_async()
+    step_ms = [a.elapsed_time(z) for a, z in zip(starts, stops)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    launches = int(sum(v["launches"] for v in prof.values()))
+
+    # ---- roofline of the dominant kernel (the fused sketch kernel) --------
+    fused = prof.get("k_sketch_fused", {"launches": 0, "ms": float("nan")})
+    fused_ms = fused["ms"] / max(fused["launches"], 1)
+    props = torch.cuda.get_device_properties(dev)
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    alg_flops = sketch_flops(d, m, b)
+    achieved = alg_flops / (fused_ms * 1e-3) / 1e12
+    traffic = load_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "kernel": "k_sketch_fused", "kernel_ms": fused_ms,
+                "alg_flops_per_launch": alg_flops,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
+                               f"lanes x 2 flop/FMA x {max_mhz:.0f} MHz (FP32 FMA pipe, not tensor)"}
+    ms_step = total_ms / args.steps
+    ab_bytes = 2 * m * n * 4                       # A and B each read once (same bytes here)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ab_gbs = ab_bytes / (ms_step * 1e-3) / 1e9
+    extra = {
+        "ab_gbs": ab_gbs, "ab_hbm_frac": ab_gbs / hbm,
+        "hbm_peak_gbs": hbm, "hbm_peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+        "roofline_time_ms": max(ab_bytes / (hbm * 1e9), total_flops(d, m, b) / (peak_tflops * 1e12)) * 1e3,
+        "kernel_ms": {k: v["ms"] / max(v["launches"], 1) for k, v in prof.items()},
+    }
+    extra["step_frac_of_roofline"] = extra["roofline_time_ms"] / ms_step
+    sketch_kernels = ("k_twiddle_table", "k_frontend_twiddles", "k_sketch_fused", "k_rows_inverse",
+                      "k_cols_inverse")
+    extra["sketch_only_ms"] = sum(prof[k]["ms"] for k in sketch_kernels if k in prof) / args.steps
+
+    # ---- end to end through the public API with host buffers --------------
+    c_host = torch.empty((d, b), dtype=torch.float32).pin_memory()
+    pairs = torch.from_numpy(cov.pairs).to(dev)
+    pair_host = torch.empty(len(cov.pairs), dtype=torch.float32).pin_memory()
+    pair_est = torch.empty(len(cov.pairs), dtype=torch.float32, device=dev)
+    Xe = torch.empty_like(X)
+    e2e_steps = max(3, min(args.steps, 50))
+
+    def e2e_step(i):
+        Xe.copy_(X_host, non_blocking=True)
+        h.reseed(seed_base + 50000 + i, stream)
+        cms.sketch_product(Xe.T, Xe, h, c=c, ws=ws, stream=stream)
+        cms.decode_dense(c, h, n, n, out=est, stream=stream)
+        cms.decode(c, h, pairs, out=pair_est, stream=stream)
+        c_host.copy_(c, non_blocking=True)
+        pair_host.copy_(pair_est, non_blocking=True)
+
+    e2e_step(0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(e2e_steps):
+        e2e_step(1 + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * e2e_steps / (e2e_ms / 1e3), "unit": "products/s",
+           "h2d_bytes_per_step": m * n * 4,
+           "d2h_bytes_per_step": d * b * 4 + len(cov.pairs) * 4,
+           "steps": e2e_steps}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_label(), "m": m, "n": n, "b": b, "d": d,
+                   "pairs": w["pairs"], "rho": w["rho"],
+                   "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write, outside the step events)",
+                   "parallelism": f"independent products per GPU x{world}"},
+        "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+    }
+    line.update(extra)
+
+    if rank == 0 and not args.no_context:
+        line["context"] = context_numbers(cms, torch, X, h, c, cov, w, dev, stream)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cov.X, w, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line))
+    h.free()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def context_numbers(cms, torch, X, h, c, cov, w, dev, stream):
+    """Plain FP64 form (same product, same seed) and cuBLAS SGEMM for context,
+    plus the 'same error' comparison of the two forms."""
+    m, n, b, d = w["m"], w["n"], w["b"], w["d"]
+    out = {}
+    h.reseed(w["seed"], stream)
+    c32 = cms.sketch_product(X.T, X, h, stream=stream)
+    Xd = X.double()
+    wsp = cms.alloc_workspace(cms.plain_workspace_size(h, n, m, n), dev)
+    c64 = torch.empty((d, b), dtype=torch.float64, device=dev)
+    cms.sketch_product_plain_f64(Xd.T, Xd, h, c=c64, ws=wsp, stream=stream)   # warm-up
+    torch.cuda.synchronize()
+    reps = 2
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        cms.sketch_product_plain_f64(Xd.T, Xd, h, c=c64, ws=wsp, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / reps
+    out["plain_f64"] = {"value": 1e3 / plain_ms, "unit": "products/s", "ms_per_product": plain_ms,
+                        "note": "sketch only (no decode), FP64, unfused passes, one instance per call"}
+    # same error: decoded estimates of both forms against the exact product
+    AB = Xd.T @ Xd
+    fro = float(torch.linalg.norm(AB))
+    idx = torch.from_numpy(np.stack(np.meshgrid(np.arange(0, n, 7), np.arange(0, n, 5),
+                                                indexing="ij"), -1).reshape(-1, 2)).to(dev)
+    e32 = cms.decode(c32, h, idx).double()
+    e64 = cms.decode(c64, h, idx)
+    ref = AB[idx[:, 0], idx[:, 1]]
+    rms = lambda v: float(torch.sqrt(torch.mean(v * v)))          # noqa: E731
+    out["same_error"] = {
+        "sketch_std": fro / math.sqrt(b),
+        "fused_rms_err_vs_AB": rms(e32 - ref), "plain_rms_err_vs_AB": rms(e64 - ref),
+        "c_rel_l2_fused_vs_plain": float(torch.max(torch.linalg.norm(c32.double() - c64, dim=1) /
+                                                    torch.linalg.norm(c64, dim=1))),
+        "pairs_sampled": int(idx.shape[0])}
+    planted = torch.from_numpy(cov.pairs).to(dev)
+    pe = cms.decode(c32, h, planted)
+    out["planted_pairs"] = {"count": int(planted.shape[0]), "median_estimate": float(pe.median()),
+                            "expected": w["rho"] * m,
+                            "recovered_above_half": int((pe > 0.5 * w["rho"] * m).sum())}
+    # cuBLAS SGEMM of the same shapes (A^T A), context only
+    torch.matmul(X.T, X)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        torch.matmul(X.T, X)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sg = e0.elapsed_time(e1) / 5
+    out["sgemm"] = {"ms": sg, "tflops": 2.0 * n * n * m / (sg * 1e-3) / 1e12,
+                    "note": "torch.matmul fp32 (cuBLAS, TF32 off by default) of X^T X"}
+    del Xd, wsp, c64, AB
+    torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["cms", "reference"], default="cms")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-context", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -205,6 +205,23 @@ CMS_API cms_status cms_merge(const float* const* parts, int32_t count, int32_t d
  * synchronises the stream, then reads and clears the device error word. */
 CMS_API cms_status cms_check_async(void* stream);
 
+/*
+ * cms_profile_enable - per-kernel device timing (no counterpart in the
+ * paper).  While on, every kernel the library launches is bracketed by CUDA
+ * events recorded on the stream it runs on.  Switching on or off clears the
+ * records (waiting for pending events).  Not for use during graph capture.
+ */
+CMS_API cms_status cms_profile_enable(int32_t on);
+
+/*
+ * cms_profile_summary - the records so far as a JSON object
+ * {"kernel": {"launches": L, "ms": T}, ...} in the host buffer buf[len]
+ * (waits for the recorded events).  *needed (if not NULL) receives the
+ * size including the terminating NUL.  Errors: CMS_ERR_INVALID_ARG when
+ * the buffer is too small, CMS_ERR_CUDA.
+ */
+CMS_API cms_status cms_profile_summary(char* buf, size_t len, size_t* needed);
+
 CMS_API const char* cms_status_string(cms_status s);
 CMS_API const char* cms_last_error(void);
 

@@ -51,6 +51,8 @@ SIGNATURES = {
     "cms_decode_dense": (_I32, [_P, _P, _I64, _I64, _P, _I64, _P]),
     "cms_merge": (_I32, [_P, _I32, _I32, _I64, _P, _P]),
     "cms_check_async": (_I32, [_P]),
+    "cms_profile_enable": (_I32, [_I32]),
+    "cms_profile_summary": (_I32, [_P, _SZ, ctypes.POINTER(_SZ)]),
     "cms_status_string": (ctypes.c_char_p, [_I32]),
     "cms_last_error": (ctypes.c_char_p, []),
 }
@@ -283,6 +285,21 @@ def merge(parts: list[torch.Tensor], out: torch.Tensor | None = None, stream=Non
 
 def check_async(stream=None):
     _check(lib().cms_check_async(_stream(stream)))
+
+
+def profile_enable(on: bool = True):
+    """Per-kernel CUDA-event timing of the library's launches (clears records)."""
+    _check(lib().cms_profile_enable(1 if on else 0))
+
+
+def profile_summary() -> dict:
+    """{kernel: {"launches": L, "ms": total}} of the launches recorded so far."""
+    import json
+    need = _SZ()
+    _check(lib().cms_profile_summary(None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value + 64)
+    _check(lib().cms_profile_summary(buf, len(buf), None))
+    return json.loads(buf.value.decode())
 
 
 def status_string(s: int) -> str:

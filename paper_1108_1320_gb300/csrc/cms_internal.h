@@ -28,6 +28,21 @@ namespace cms {
 // Thread-local error text (set by the C entry points).
 void set_error(const std::string& msg);
 
+// Brackets the launches in its scope with CUDA events on stream s while
+// profiling is enabled (cms_profile_enable); a no-op otherwise.
+class ProfScope {
+ public:
+  ProfScope(const char* name, cudaStream_t s);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
 // Device error words: one per translation unit that owns kernels which can
 // raise it.  Each reader returns the word and clears it.
 uint32_t read_clear_error_decode();

@@ -92,16 +92,22 @@ uint32_t read_clear_error_decode() {
 cudaError_t launch_decode_pairs_f32(const float* c, const cms_hashes* h, const int64_t* ij,
                                     int64_t q, float* out, cudaStream_t s) {
   if (q == 0) return cudaSuccess;
-  k_decode_pairs<float><<<static_cast<unsigned>((q + 255) / 256), 256, 0, s>>>(
-      c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d, ij, q, out);
+  {
+    ProfScope prof_scope("k_decode_pairs", s);
+    k_decode_pairs<float><<<static_cast<unsigned>((q + 255) / 256), 256, 0, s>>>(
+        c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d, ij, q, out);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_decode_pairs_f64(const double* c, const cms_hashes* h, const int64_t* ij,
                                     int64_t q, double* out, cudaStream_t s) {
   if (q == 0) return cudaSuccess;
-  k_decode_pairs<double><<<static_cast<unsigned>((q + 255) / 256), 256, 0, s>>>(
-      c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d, ij, q, out);
+  {
+    ProfScope prof_scope("k_decode_pairs_f64", s);
+    k_decode_pairs<double><<<static_cast<unsigned>((q + 255) / 256), 256, 0, s>>>(
+        c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d, ij, q, out);
+  }
   return cudaGetLastError();
 }
 
@@ -110,8 +116,11 @@ cudaError_t launch_decode_dense_f32(const float* c, const cms_hashes* h, int64_t
   if (n1 == 0 || n3 == 0) return cudaSuccess;
   dim3 grid(static_cast<unsigned>((n3 + 255) / 256),
             static_cast<unsigned>(std::min<int64_t>(n1, 65535)));
-  k_decode_dense<float><<<grid, 256, 0, s>>>(c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d,
-                                             n1, n3, out, ldo);
+  {
+    ProfScope prof_scope("k_decode_dense", s);
+    k_decode_dense<float><<<grid, 256, 0, s>>>(c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d,
+                                               n1, n3, out, ldo);
+  }
   return cudaGetLastError();
 }
 
@@ -124,7 +133,10 @@ cudaError_t launch_merge(const float* const* parts, int count, int64_t len, floa
     PartPtrs pp{};
     const int m = std::min(32, count - base);
     for (int q = 0; q < m; ++q) pp.p[q] = parts[base + q];
-    k_merge<<<blocks, 256, 0, s>>>(pp, m, len, base > 0 ? 1 : 0, out);
+    {
+      ProfScope prof_scope("k_merge", s);
+      k_merge<<<blocks, 256, 0, s>>>(pp, m, len, base > 0 ? 1 : 0, out);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

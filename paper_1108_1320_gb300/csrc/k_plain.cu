@@ -119,6 +119,7 @@ cudaError_t run_fft(const PlainPlan& p, double2* a, double2* bbuf, int64_t nvec,
     const int r = p.rad[q];
     const int64_t work = nvec * (N / r);
     const unsigned g = static_cast<unsigned>((work + 255) / 256);
+    ProfScope prof_scope("k_plain_pass", s);
     switch (r) {
       case 2: k_plain_pass<2, INV><<<g, 256, 0, s>>>(src, dst, N, L, nvec, tw); break;
       case 3: k_plain_pass<3, INV><<<g, 256, 0, s>>>(src, dst, N, L, nvec, tw); break;
@@ -163,7 +164,10 @@ cudaError_t launch_plain(const PlainPlan& p, const cms_hashes* h, const double* 
   double2* S = reinterpret_cast<double2*>(ws + p.off_S);
   double2* tw = reinterpret_cast<double2*>(ws + p.off_tw);
   const int64_t b = p.b;
-  k_plain_twiddles<<<grid_for(b), 256, 0, s>>>(tw, b);
+  {
+    ProfScope prof_scope("k_plain_twiddles", s);
+    k_plain_twiddles<<<grid_for(b), 256, 0, s>>>(tw, b);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t nmax = std::max<int64_t>(std::max<int64_t>(n1, n3), 1);
@@ -178,20 +182,29 @@ cudaError_t launch_plain(const PlainPlan& p, const cms_hashes* h, const double* 
       if (e != cudaSuccess) return e;
       dim3 g(static_cast<unsigned>(std::min<int64_t>((nmax + 255) / 256, 1024)),
              static_cast<unsigned>(nk));
-      k_plain_scatter<<<g, 256, 0, s>>>(A, lda, B, ldb, n1, n3, k0, hsA, hsB, b, Z);
+      {
+        ProfScope prof_scope("k_plain_scatter", s);
+        k_plain_scatter<<<g, 256, 0, s>>>(A, lda, B, ldb, n1, n3, k0, hsA, hsB, b, Z);
+      }
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       double2* F = nullptr;
       e = run_fft<false>(p, Z, Z2, nk, tw, &F, s);
       if (e != cudaSuccess) return e;
-      k_plain_product<<<grid_for(b), 256, 0, s>>>(F, nk, b, S);
+      {
+        ProfScope prof_scope("k_plain_product", s);
+        k_plain_product<<<grid_for(b), 256, 0, s>>>(F, nk, b, S);
+      }
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
     double2* X = nullptr;
     e = run_fft<true>(p, S, Z, 1, tw, &X, s);
     if (e != cudaSuccess) return e;
-    k_plain_finish<<<grid_for(b), 256, 0, s>>>(X, b, c + static_cast<size_t>(t) * b);
+    {
+      ProfScope prof_scope("k_plain_finish", s);
+      k_plain_finish<<<grid_for(b), 256, 0, s>>>(X, b, c + static_cast<size_t>(t) * b);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

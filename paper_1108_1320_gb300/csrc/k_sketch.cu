@@ -350,11 +350,20 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   float2* twR = reinterpret_cast<float2*>(ws + plan.off_twR);
   const int n = static_cast<int>(h->n);
 
-  k_twiddle_table<<<static_cast<unsigned>((plan.C + 255) / 256), 256, 0, s>>>(twC, static_cast<int>(plan.C));
-  k_twiddle_table<<<static_cast<unsigned>((plan.R + 255) / 256), 256, 0, s>>>(twR, static_cast<int>(plan.R));
+  {
+    ProfScope prof_scope("k_twiddle_table", s);
+    k_twiddle_table<<<static_cast<unsigned>((plan.C + 255) / 256), 256, 0, s>>>(twC, static_cast<int>(plan.C));
+  }
+  {
+    ProfScope prof_scope("k_twiddle_table", s);
+    k_twiddle_table<<<static_cast<unsigned>((plan.R + 255) / 256), 256, 0, s>>>(twR, static_cast<int>(plan.R));
+  }
   {
     dim3 grid(static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 64)), plan.nrows, 2 * plan.d);
-    k_frontend_twiddles<<<grid, 256, 0, s>>>(h->d_hs, h->d_perm, n, plan.b, plan.nrows, twfe);
+    {
+      ProfScope prof_scope("k_frontend_twiddles", s);
+      k_frontend_twiddles<<<grid, 256, 0, s>>>(h->d_hs, h->d_perm, n, plan.b, plan.nrows, twfe);
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -373,15 +382,24 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   switch (dt) {
     case CMS_F32:
       e = cudaFuncSetAttribute(k_sketch_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e == cudaSuccess) k_sketch_fused<float><<<ntask, plan.threads, smem, s>>>(a);
+      if (e == cudaSuccess) {
+        ProfScope prof_scope("k_sketch_fused", s);
+        k_sketch_fused<float><<<ntask, plan.threads, smem, s>>>(a);
+      }
       break;
     case CMS_BF16:
       e = cudaFuncSetAttribute(k_sketch_fused<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e == cudaSuccess) k_sketch_fused<__nv_bfloat16><<<ntask, plan.threads, smem, s>>>(a);
+      if (e == cudaSuccess) {
+        ProfScope prof_scope("k_sketch_fused", s);
+        k_sketch_fused<__nv_bfloat16><<<ntask, plan.threads, smem, s>>>(a);
+      }
       break;
     default:
       e = cudaFuncSetAttribute(k_sketch_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e == cudaSuccess) k_sketch_fused<double><<<ntask, plan.threads, smem, s>>>(a);
+      if (e == cudaSuccess) {
+        ProfScope prof_scope("k_sketch_fused", s);
+        k_sketch_fused<double><<<ntask, plan.threads, smem, s>>>(a);
+      }
       break;
   }
   if (e != cudaSuccess) return e;
@@ -399,10 +417,16 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
     e = cudaFuncSetAttribute(k_rows_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
     if (e != cudaSuccess) return e;
   }
-  k_rows_inverse<<<static_cast<unsigned>(plan.d * plan.nrows), 256, smem2, s>>>(ia);
+  {
+    ProfScope prof_scope("k_rows_inverse", s);
+    k_rows_inverse<<<static_cast<unsigned>(plan.d * plan.nrows), 256, smem2, s>>>(ia);
+  }
   dim3 g2(static_cast<unsigned>((plan.b + 255) / 256), plan.d);
-  k_cols_inverse<<<g2, 256, 0, s>>>(V, twR, plan.b, static_cast<int>(plan.R), static_cast<int>(plan.C),
-                                    plan.nrows, c);
+  {
+    ProfScope prof_scope("k_cols_inverse", s);
+    k_cols_inverse<<<g2, 256, 0, s>>>(V, twR, plan.b, static_cast<int>(plan.R), static_cast<int>(plan.C),
+                                      plan.nrows, c);
+  }
   return cudaGetLastError();
 }
 

@@ -77,8 +77,11 @@ k_bucket_sort(const uint32_t* __restrict__ hs, uint32_t n, uint32_t C,
 cudaError_t launch_hash_tables(const Coeffs& co, int d, int64_t n, int64_t b,
                                uint32_t* hs, cudaStream_t s) {
   dim3 grid(static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 4096)), 2 * d);
-  k_hash_tables<<<grid, 256, 0, s>>>(co, d, static_cast<uint32_t>(n),
-                                     static_cast<uint32_t>(b), hs);
+  {
+    ProfScope prof_scope("k_hash_tables", s);
+    k_hash_tables<<<grid, 256, 0, s>>>(co, d, static_cast<uint32_t>(n),
+                                       static_cast<uint32_t>(b), hs);
+  }
   return cudaGetLastError();
 }
 
@@ -90,8 +93,11 @@ cudaError_t launch_bucket_sort(const uint32_t* hs, int d, int64_t n, int64_t C,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
   }
-  k_bucket_sort<<<2 * d, kSortThreads, smem, s>>>(hs, static_cast<uint32_t>(n),
-                                                  static_cast<uint32_t>(C), perm, off);
+  {
+    ProfScope prof_scope("k_bucket_sort", s);
+    k_bucket_sort<<<2 * d, kSortThreads, smem, s>>>(hs, static_cast<uint32_t>(n),
+                                                    static_cast<uint32_t>(C), perm, off);
+  }
   return cudaGetLastError();
 }
 
