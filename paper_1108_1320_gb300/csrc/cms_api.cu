@@ -88,6 +88,17 @@ cms_status alloc_tables(cms_hashes* h) {
     e = cudaMalloc(&h->d_off, static_cast<size_t>(h->d) * 2 * (h->C + 1) * sizeof(uint32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(bucket offsets)");
   }
+  if (h->C == kFeC && h->n <= 65535) {
+    h->fe_ecap = static_cast<uint32_t>(h->n + 32 * kFeCap);
+    const size_t ts = static_cast<size_t>(h->d) * 2;
+    if ((e = cudaMalloc(&h->d_fe_x, ts * h->fe_ecap * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_hs, ts * h->fe_ecap * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_grp, ts * (kFeC / 32) * 2 * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_dest, ts * kFeC * 2)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_ovf_off, ts * (kFeC + 1) * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_ovf_x, ts * h->n * 4)) != cudaSuccess)
+      return cuda_fail(e, "cudaMalloc(front-end records)");
+  }
   return CMS_OK;
 }
 
@@ -97,6 +108,13 @@ void free_tables(cms_hashes* h) {
   if (h->d_off) cudaFree(h->d_off);
   h->d_hs = h->d_perm = nullptr;
   h->d_off = nullptr;
+  for (uint32_t** q : {&h->d_fe_x, &h->d_fe_hs, &h->d_fe_grp, &h->d_fe_ovf_off, &h->d_fe_ovf_x}) {
+    if (*q) cudaFree(*q);
+    *q = nullptr;
+  }
+  if (h->d_fe_dest) cudaFree(h->d_fe_dest);
+  h->d_fe_dest = nullptr;
+  h->fe_ecap = 0;
 }
 
 cms_status fill_tables(cms_hashes* h, cudaStream_t s, bool hash) {
@@ -108,6 +126,11 @@ cms_status fill_tables(cms_hashes* h, cudaStream_t s, bool hash) {
   if (h->C > 0) {
     e = launch_bucket_sort(h->d_hs, h->d, h->n, h->C, h->d_perm, h->d_off, s);
     if (e != cudaSuccess) return cuda_fail(e, "bucket sort kernel");
+  }
+  if (h->fe_ecap > 0) {
+    e = launch_frontend_tables(h->d_hs, h->d, h->n, h->fe_ecap, h->d_fe_x, h->d_fe_hs, h->d_fe_grp,
+                               h->d_fe_dest, h->d_fe_ovf_off, h->d_fe_ovf_x, s);
+    if (e != cudaSuccess) return cuda_fail(e, "front-end table kernel");
   }
   return CMS_OK;
 }
@@ -300,7 +323,7 @@ cms_status cms_sketch_product(const void* A, int64_t lda, const void* B, int64_t
   DeviceProps dp = device_props(h->device);
   SketchPlan plan;
   std::string why;
-  int r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &plan, &why);
+  int r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &plan, &why, A, lda, B, ldb);
   if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
   if (!ws || ws_bytes < plan.ws_bytes)
     return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_workspace_size()");
@@ -401,7 +424,10 @@ cms_status cms_check_async(void* stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cms_check_async");
   const uint32_t w = read_clear_error_decode();
-  if (w == 0xFFFFFFFFu) return fail(CMS_ERR_CUDA, "could not read the device error word");
+  const uint32_t ws = read_clear_error_sketch();
+  if (w == 0xFFFFFFFFu || ws == 0xFFFFFFFFu)
+    return fail(CMS_ERR_CUDA, "could not read the device error words");
+  if (ws) return fail(CMS_ERR_TIMEOUT, "a fused-kernel wait for its TMA copies gave up");
   if (w) return fail(CMS_ERR_DEVICE, "decode saw an index pair outside the hash domain");
   return CMS_OK;
 }

@@ -21,6 +21,14 @@ struct cms_hashes {
   uint32_t* d_hs = nullptr;     // [d][2][n] packed bucket | sign
   uint32_t* d_perm = nullptr;   // [d][2][n] indices sorted by (bucket mod C), stable
   uint32_t* d_off = nullptr;    // [d][2][C+1] bucket-class offsets into d_perm
+  // front-end records of the C = 1024 fused kernel (present when fe_ecap > 0)
+  uint32_t fe_ecap = 0;
+  uint32_t* d_fe_x = nullptr;      // [d][2][fe_ecap]
+  uint32_t* d_fe_hs = nullptr;     // [d][2][fe_ecap]
+  uint32_t* d_fe_grp = nullptr;    // [d][2][C/32][2] (base, count)
+  uint16_t* d_fe_dest = nullptr;   // [d][2][C]
+  uint32_t* d_fe_ovf_off = nullptr;  // [d][2][C+1]
+  uint32_t* d_fe_ovf_x = nullptr;    // [d][2][n]
 };
 
 namespace cms {
@@ -55,6 +63,15 @@ cudaError_t launch_hash_tables(const Coeffs& co, int d, int64_t n, int64_t b,
 cudaError_t launch_bucket_sort(const uint32_t* hs, int d, int64_t n, int64_t C,
                                uint32_t* perm, uint32_t* off, cudaStream_t s);
 
+// Front-end record tables of the C = 1024 fused kernel.
+constexpr int kFeC = 1024;        // FFT length of the specialised kernel
+constexpr int kFeCap = 16;        // bucket entries kept in the padded layout
+cudaError_t launch_frontend_tables(const uint32_t* hs, int d, int64_t n, uint32_t ecap,
+                                   uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
+                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,
+                                   cudaStream_t s);
+uint32_t read_clear_error_sketch();
+
 // Plan of the fused sketch path for one call.
 struct SketchPlan {
   int64_t b = 0, R = 0, C = 0;
@@ -67,6 +84,10 @@ struct SketchPlan {
   int nkc = 0;              // number of inner-index chunks
   int threads = 256;
   size_t smem = 0;          // dynamic shared memory of the fused kernel
+  bool fast = false;        // the C = 1024 register-FFT kernel applies
+  bool alias = false;       // A and B are the same bytes (stage once)
+  int npad = 0;             // staging row length of the fast kernel (floats)
+  int tw_shift = 0, nhi = 0;  // two-level w_b table: S = 2^tw_shift, nhi high entries
   // workspace layout (byte offsets)
   size_t off_partial = 0, off_V = 0, off_twfe = 0, off_twC = 0, off_twR = 0;
   size_t ws_bytes = 0;
@@ -75,7 +96,12 @@ struct SketchPlan {
 bool choose_factorisation(int64_t b, int64_t* R, int64_t* C);
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
                      int dt, int num_sms, size_t smem_optin, SketchPlan* plan,
-                     std::string* why);
+                     std::string* why, const void* A = nullptr, int64_t lda = 0,
+                     const void* B = nullptr, int64_t ldb = 0);
+size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi);
+cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, const void* A,
+                               int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
+                               int64_t n3, float2* partial, cudaStream_t s);
 
 cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h,
                           const void* A, int64_t lda, const void* B, int64_t ldb,

@@ -289,9 +289,30 @@ bool choose_factorisation(int64_t b, int64_t* R, int64_t* C) {
   return true;
 }
 
+namespace {
+
+// Inner-index chunks per (t, f1) unit so that the task count fills whole
+// waves of `slots` concurrent blocks as evenly as possible.
+int64_t choose_chunks(int64_t units, int64_t n2, int G, int64_t slots, int64_t lo, int64_t hi) {
+  const int64_t max_chunks = std::max<int64_t>(1, (n2 + G - 1) / G);
+  hi = std::min(hi, max_chunks);
+  lo = std::min(lo, hi);
+  int64_t best = lo;
+  double best_eff = -1.0;
+  for (int64_t c = lo; c <= hi; ++c) {
+    const int64_t tasks = units * c;
+    const int64_t waves = (tasks + slots - 1) / slots;
+    const double eff = static_cast<double>(tasks) / static_cast<double>(waves * slots);
+    if (eff > best_eff + 1e-9) { best_eff = eff; best = c; }
+  }
+  return best;
+}
+
+}  // namespace
+
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int dt,
-                     int num_sms, size_t smem_optin, SketchPlan* plan, std::string* why) {
-  (void)dt;
+                     int num_sms, size_t smem_optin, SketchPlan* plan, std::string* why,
+                     const void* A, int64_t lda, const void* B, int64_t ldb) {
   SketchPlan p;
   p.b = h->b;
   p.d = h->d;
@@ -303,36 +324,57 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   if (p.nradC < 0) { *why = "internal: C not factorable"; return CMS_ERR_UNSUPPORTED; }
   if (p.R > 65536) { *why = "R = b / C too large"; return CMS_ERR_UNSUPPORTED; }
   const int n = static_cast<int>(h->n);
-  int G = 0;
-  for (int g = kMaxG; g >= 1; --g) {
-    if (fused_smem_bytes(static_cast<int>(p.C), g, n) <= 112 * 1024) { G = g; break; }
-  }
-  if (G == 0) {
-    for (int g = kMaxG; g >= 1; --g)
-      if (fused_smem_bytes(static_cast<int>(p.C), g, n) <= smem_optin) { G = g; break; }
-  }
-  if (G == 0) {
-    *why = "hash domain n too large for the shared-memory staging of the fused kernel";
-    return CMS_ERR_UNSUPPORTED;
-  }
-  p.G = G;
-  p.smem = fused_smem_bytes(static_cast<int>(p.C), G, n);
-  const int per_sm = std::max<int>(1, static_cast<int>(std::min<size_t>(4, (228 * 1024) / (p.smem + 1024))));
   const int64_t units = static_cast<int64_t>(p.d) * p.nrows;
-  const int64_t target = 2LL * num_sms * per_sm;
-  int64_t nkc = std::max<int64_t>(1, (target + units - 1) / units);
-  const int64_t max_chunks = std::max<int64_t>(1, (n2 + G - 1) / G);
-  nkc = std::min(nkc, max_chunks);
+
+  // the C = 1024 register-FFT kernel: FP32 rows that TMA can copy
+  const bool aligned = (A == nullptr || reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
+                       (B == nullptr || reinterpret_cast<uintptr_t>(B) % 16 == 0) &&
+                       lda % 4 == 0 && ldb % 4 == 0 && n1 % 4 == 0 && n3 % 4 == 0;
+  if (dt == CMS_F32 && p.C == kFeC && h->fe_ecap > 0 && aligned) {
+    p.alias = A != nullptr && A == B && lda == ldb && n1 == n3;
+    p.npad = static_cast<int>(((h->n + 1) + 3) / 4 * 4);
+    int sh = 0;
+    while ((static_cast<int64_t>(1) << (2 * sh)) < p.b) ++sh;
+    p.tw_shift = sh;
+    p.nhi = static_cast<int>((p.b + (static_cast<int64_t>(1) << sh) - 1) >> sh);
+    const size_t sm = fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi);
+    if (sm <= smem_optin) {
+      p.fast = true;
+      p.G = 4;
+      p.threads = 256;
+      p.smem = sm;
+    }
+  }
+  if (!p.fast) {
+    int G = 0;
+    for (int g = kMaxG; g >= 1; --g) {
+      if (fused_smem_bytes(static_cast<int>(p.C), g, n) <= 112 * 1024) { G = g; break; }
+    }
+    if (G == 0) {
+      for (int g = kMaxG; g >= 1; --g)
+        if (fused_smem_bytes(static_cast<int>(p.C), g, n) <= smem_optin) { G = g; break; }
+    }
+    if (G == 0) {
+      *why = "hash domain n too large for the shared-memory staging of the fused kernel";
+      return CMS_ERR_UNSUPPORTED;
+    }
+    p.G = G;
+    p.smem = fused_smem_bytes(static_cast<int>(p.C), G, n);
+  }
+  const int G = p.G;
+  const int per_sm = p.fast ? 1 : std::max<int>(1, static_cast<int>(std::min<size_t>(4, (228 * 1024) / (p.smem + 1024))));
+  const int64_t slots = static_cast<int64_t>(num_sms) * per_sm;
+  const int64_t lo = std::max<int64_t>(1, (2 * slots + units - 1) / units);
+  int64_t nkc = choose_chunks(units, n2, G, slots, lo, std::max<int64_t>(lo, 4 * lo));
   int64_t kchunk = n2 > 0 ? (n2 + nkc - 1) / nkc : G;
   kchunk = ((kchunk + G - 1) / G) * G;
   nkc = n2 > 0 ? (n2 + kchunk - 1) / kchunk : 1;
   p.kchunk = kchunk;
   p.nkc = static_cast<int>(nkc);
-  (void)n1; (void)n3;
   size_t off = 0;
   p.off_partial = off; off = align256(off + static_cast<size_t>(units) * p.nkc * p.C * 8);
   p.off_V = off;       off = align256(off + static_cast<size_t>(units) * p.C * 8);
-  p.off_twfe = off;    off = align256(off + static_cast<size_t>(units) * 2 * h->n * 8);
+  p.off_twfe = off;    off = align256(off + static_cast<size_t>(units) * 2 * h->n * 8);  // both kernels: same size
   p.off_twC = off;     off = align256(off + static_cast<size_t>(p.C) * 8);
   p.off_twR = off;     off = align256(off + static_cast<size_t>(p.R) * 8);
   p.ws_bytes = off;
@@ -358,7 +400,7 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
     ProfScope prof_scope("k_twiddle_table", s);
     k_twiddle_table<<<static_cast<unsigned>((plan.R + 255) / 256), 256, 0, s>>>(twR, static_cast<int>(plan.R));
   }
-  {
+  if (!plan.fast) {
     dim3 grid(static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 64)), plan.nrows, 2 * plan.d);
     {
       ProfScope prof_scope("k_frontend_twiddles", s);
@@ -368,6 +410,10 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
+  if (plan.fast) {
+    e = launch_sketch_fast(plan, h, A, lda, B, ldb, n1, n2, n3, partial, s);
+    if (e != cudaSuccess) return e;
+  } else {
   SketchArgs a{};
   a.A = A; a.lda = lda; a.B = B; a.ldb = ldb;
   a.n1 = static_cast<int>(n1); a.n2 = static_cast<int>(n2); a.n3 = static_cast<int>(n3); a.n = n;
@@ -405,6 +451,7 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  }
 
   InvArgs ia{};
   ia.b = plan.b; ia.R = static_cast<int>(plan.R); ia.C = static_cast<int>(plan.C);

@@ -1,0 +1,511 @@
+// k_sketch_fast.cu - the fused FP32 kernel for C = 1024 (b = R * 1024),
+// the same computation as k_sketch_fused in k_sketch.cu (see there for the
+// four-step split of the length-b DFT and the pruned first stage) with a
+// GB300-specific layout:
+//
+//  * a_k (column k of A) and b_k (row k of B) for a group of G = 4 inner
+//    indices are staged into shared memory by TMA bulk copies
+//    (cp.async.bulk + mbarrier), issued as soon as the previous group's
+//    front end has consumed the buffer, so the copy overlaps the FFTs;
+//  * the gather front end Y[f1][z2] = sum s(x) A_xk w_b^{f1 h(x)} walks
+//    per-(t, side) records (x, twiddle) kept in shared memory for the whole
+//    task; 32 buckets of equal (capped) occupancy form a group whose lanes
+//    run in lock step, so warps do not diverge on bucket sizes;
+//  * each of the 8 warps runs one length-1024 FFT (one (side, k) pair):
+//    radix-32 in registers, twiddle, one XOR-swizzled (conflict-free)
+//    transpose through shared memory, radix-32 in registers; lane l ends
+//    holding bins l + 32 m, m = 0..31;
+//  * the side-b warps publish their spectra, the side-a warps multiply and
+//    accumulate PA PB in registers; every kFlush groups the four partial
+//    sums are added (fixed order) and folded into Kahan-compensated
+//    accumulators held in registers by all threads (4 bins per thread).
+#include <algorithm>
+
+#include "cms_internal.h"
+
+namespace cms {
+namespace {
+
+constexpr int kC = kFeC;       // 1024
+constexpr int kG = 4;          // inner indices per group
+constexpr int kThreads = 256;  // 8 warps = 2 sides x kG FFTs
+constexpr int kFlush = 8;      // groups between Kahan folds
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
+
+__device__ uint32_t g_sketch_error = 0;   // 1: a TMA wait gave up
+
+struct FastArgs {
+  const float* A;
+  int64_t lda;
+  const float* B;
+  int64_t ldb;
+  int n1, n2, n3, n, npad;
+  int64_t b;
+  int nrows;
+  int kchunk, nkc;
+  int alias;
+  uint32_t ecap;
+  int tw_shift, nhi;
+  const uint32_t* rec_x;
+  const uint32_t* rec_hs;
+  const uint32_t* grp;
+  const uint16_t* dest;
+  const uint32_t* ovf_off;
+  const uint32_t* ovf_x;
+  const uint32_t* hs;
+  float2* partial;
+};
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: true when it completed, false after
+// kWaitLimitNs (the caller then reports the timeout and leaves).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// ------------------------------------------------------ radix-32 codelet --
+// w_32^e = exp(-2 pi i e / 32): cos and sin of 2 pi e / 32 for e = 0..8.
+__device__ __forceinline__ float c32(int e) {
+  constexpr float t[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
+                          0.83146961230254523708f, 0.70710678118654752440f,
+                          0.55557023301960222474f, 0.38268343236508977173f,
+                          0.19509032201612826785f, 0.0f};
+  return t[e];
+}
+
+// v * w_32^e (forward) or v * w_32^{-e} (inverse), e a compile-time constant
+// after unrolling; the trivial angles cost no multiplies.
+template <bool INV>
+__device__ __forceinline__ float2 tw32(float2 v, int e) {
+  e &= 31;
+  if (e == 0) return v;
+  if (e == 8) return mul_mi<INV>(v);
+  if (e == 16) return make_float2(-v.x, -v.y);
+  if (e == 24) return mul_mi<!INV>(v);
+  // cos(2 pi e/32), sin(2 pi e/32) from the first-octant table
+  const int q = e >> 3, r = e & 7;
+  float c, s;
+  if (q == 0) { c = c32(r);     s = c32(8 - r); }
+  else if (q == 1) { c = -c32(8 - r); s = c32(r); }
+  else if (q == 2) { c = -c32(r); s = -c32(8 - r); }
+  else { c = c32(8 - r); s = -c32(r); }
+  // forward multiplies by c - i s, inverse by c + i s
+  const float si = INV ? -s : s;
+  return make_float2(v.x * c + v.y * si, v.y * c - v.x * si);
+}
+
+// In-register DFT of length 32 as 8 x DFT4 (stride 8), twiddles w_32^{n2 k1},
+// 4 x DFT8: x[k] = sum_j x[j] w_32^{jk} on return.
+template <bool INV>
+__device__ __forceinline__ void dft32(float2 (&x)[32]) {
+  float2 y[32];
+#pragma unroll
+  for (int n2 = 0; n2 < 8; ++n2) {
+    float2 u[4] = {x[n2], x[8 + n2], x[16 + n2], x[24 + n2]};
+    Dft<4, INV, float2>::run(u);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[n2 * 4 + k1] = tw32<INV>(u[k1], n2 * k1);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 v[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) v[n2] = y[n2 * 4 + k1];
+    Dft<8, INV, float2>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) x[k1 + 4 * k2] = v[k2];
+  }
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// w_b^m from the two-level table: T_lo[m mod S] * T_hi[m div S].
+__device__ __forceinline__ float2 wb(const float2* tlo, const float2* thi, uint32_t m, int sh) {
+  return cmul(thi[m >> sh], tlo[m & ((1u << sh) - 1u)]);
+}
+
+__device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, int64_t b) {
+  return static_cast<uint32_t>((static_cast<uint64_t>(h) * f1) % static_cast<uint64_t>(b));
+}
+
+struct SmemLayout {
+  size_t stage, rec_tw, rec_x, work, tlo, thi, grp, dest, ovf, bar, total;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
+
+__host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int alias, int tw_shift, int nhi) {
+  SmemLayout L{};
+  size_t o = 0;
+  const int nstage = alias ? 1 : 2;
+  L.stage = o;  o = al16(o + static_cast<size_t>(nstage) * kG * npad * 4);
+  L.rec_tw = o; o = al16(o + static_cast<size_t>(2) * ecap * 8);
+  L.rec_x = o;  o = al16(o + static_cast<size_t>(2) * ecap * 2);
+  L.work = o;   o = al16(o + static_cast<size_t>(2 * kG) * kC * 8);
+  L.tlo = o;    o = al16(o + (static_cast<size_t>(1) << tw_shift) * 8);
+  L.thi = o;    o = al16(o + static_cast<size_t>(nhi) * 8);
+  L.grp = o;    o = al16(o + static_cast<size_t>(2) * (kC / 32) * 2 * 4);
+  L.dest = o;   o = al16(o + static_cast<size_t>(2) * kC * 2);
+  L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 4);
+  L.bar = o;    o = al16(o + 8);
+  L.total = o;
+  return L;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const SmemLayout L = fast_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi);
+  float* stage = reinterpret_cast<float*>(sm + L.stage);
+  float2* rec_tw = reinterpret_cast<float2*>(sm + L.rec_tw);
+  uint16_t* rec_x = reinterpret_cast<uint16_t*>(sm + L.rec_x);
+  float2* work = reinterpret_cast<float2*>(sm + L.work);
+  float2* tlo = reinterpret_cast<float2*>(sm + L.tlo);
+  float2* thi = reinterpret_cast<float2*>(sm + L.thi);
+  uint32_t* grp = reinterpret_cast<uint32_t*>(sm + L.grp);
+  uint16_t* dest = reinterpret_cast<uint16_t*>(sm + L.dest);
+  uint32_t* ovf = reinterpret_cast<uint32_t*>(sm + L.ovf);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int task = blockIdx.x;
+  const int kc = task % p.nkc;
+  const int row = (task / p.nkc) % p.nrows;
+  const int t = task / (p.nkc * p.nrows);
+  const uint32_t f1 = static_cast<uint32_t>(row);
+  const int n = p.n;
+  const int S = 1 << p.tw_shift;
+  const int nstage = p.alias ? 1 : 2;
+  const int k_begin = kc * p.kchunk;
+  const int k_end = min(p.n2, k_begin + p.kchunk);
+
+  // ---- prologue: tables, records, staging tails, barrier ----------------
+  for (int i = tid; i < S; i += kThreads) {
+    float s, c;
+    sincospif(2.0f * static_cast<float>(i) / static_cast<float>(p.b), &s, &c);
+    tlo[i] = make_float2(c, -s);
+  }
+  for (int i = tid; i < p.nhi; i += kThreads) {
+    const double a = 2.0 * static_cast<double>(static_cast<int64_t>(i) * S) / static_cast<double>(p.b);
+    double s, c;
+    sincospi(a, &s, &c);
+    thi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+  }
+  for (int side = 0; side < 2; ++side) {
+    const size_t ts = static_cast<size_t>(t) * 2 + side;
+    for (int i = tid; i < (kC / 32) * 2; i += kThreads) grp[side * (kC / 32) * 2 + i] = p.grp[ts * (kC / 32) * 2 + i];
+    for (int i = tid; i < kC; i += kThreads) dest[side * kC + i] = p.dest[ts * kC + i];
+    for (int i = tid; i <= kC; i += kThreads) ovf[side * (kC + 1) + i] = p.ovf_off[ts * (kC + 1) + i];
+  }
+  // zero the staging tails [n_side, npad): entries x >= n_side read zeros
+  for (int s2 = 0; s2 < nstage; ++s2) {
+    const int nside = s2 == 0 ? p.n1 : p.n3;
+    for (int g = 0; g < kG; ++g)
+      for (int i = nside + tid; i < p.npad; i += kThreads) stage[(s2 * kG + g) * p.npad + i] = 0.f;
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  // records: x and s(x) w_b^{(h(x) f1) mod b}, padding x = n with weight 0
+  for (int side = 0; side < 2; ++side) {
+    const size_t ts = static_cast<size_t>(t) * 2 + side;
+    const uint32_t* gsrc = grp + side * (kC / 32) * 2;
+    const uint32_t epad = gsrc[(kC / 32 - 1) * 2] + 32u * gsrc[(kC / 32 - 1) * 2 + 1];
+    for (uint32_t e = tid; e < epad; e += kThreads) {
+      const uint32_t x = p.rec_x[ts * p.ecap + e];
+      const uint32_t w = p.rec_hs[ts * p.ecap + e];
+      float2 tw = make_float2(0.f, 0.f);
+      if (x < static_cast<uint32_t>(n)) {
+        tw = wb(tlo, thi, mulmod(w & kBucketMask, f1, p.b), p.tw_shift);
+        if (w >> 31) { tw.x = -tw.x; tw.y = -tw.y; }
+      }
+      rec_tw[side * p.ecap + e] = tw;
+      rec_x[side * p.ecap + e] = static_cast<uint16_t>(min(x, static_cast<uint32_t>(n)));
+    }
+  }
+  // lane twiddle anchors w_1024^{lane * 8 q}, q = 0..3, and the step w_1024^lane
+  float2 anchor[4];
+  float2 step;
+  {
+    float s, c;
+    sincospif(2.0f * static_cast<float>(lane) / static_cast<float>(kC), &s, &c);
+    step = make_float2(c, -s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sincospif(2.0f * static_cast<float>((lane * 8 * q) & (kC - 1)) / static_cast<float>(kC), &s, &c);
+      anchor[q] = make_float2(c, -s);
+    }
+  }
+
+  // issue the TMA copies of group starting at k0 (thread 0 only)
+  auto issue = [&](int k0) {
+    uint32_t bytes = 0;
+    const int gl = min(kG, k_end - k0);
+    for (int g = 0; g < gl; ++g) bytes += static_cast<uint32_t>(p.n1) * 4u;
+    if (!p.alias)
+      for (int g = 0; g < gl; ++g) bytes += static_cast<uint32_t>(p.n3) * 4u;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, bytes);
+    for (int g = 0; g < gl; ++g) {
+      if (p.n1 > 0)
+        bulk_g2s(stage + (0 * kG + g) * p.npad, p.A + static_cast<size_t>(k0 + g) * p.lda,
+                 static_cast<uint32_t>(p.n1) * 4u, bar);
+      if (!p.alias && p.n3 > 0)
+        bulk_g2s(stage + (1 * kG + g) * p.npad, p.B + static_cast<size_t>(k0 + g) * p.ldb,
+                 static_cast<uint32_t>(p.n3) * 4u, bar);
+    }
+  };
+
+  float2 part[32];
+#pragma unroll
+  for (int m = 0; m < 32; ++m) part[m] = make_float2(0.f, 0.f);
+  float acc_s[8], acc_c[8];   // Kahan sum and compensation of bins tid + 256 u (re, im)
+#pragma unroll
+  for (int u = 0; u < 8; ++u) { acc_s[u] = 0.f; acc_c[u] = 0.f; }
+
+  if (tid == 0 && k_begin < k_end) issue(k_begin);
+  __syncthreads();
+
+  const int side_w = warp / kG;          // FFT side of this warp
+  const int g_w = warp % kG;             // inner index of the group
+  float2* region = work + warp * kC;
+  uint32_t phase = 0;
+  int group = 0;
+  bool timed_out = false;
+
+  for (int k0 = k_begin; k0 < k_end; k0 += kG, ++group) {
+    const int gcnt = min(kG, k_end - k0);
+    // ---- wait for this group's staging ----------------------------------
+    const bool ok = mbar_wait_bounded(bar, phase);
+    if (__syncthreads_or(!ok)) { timed_out = true; break; }
+    phase ^= 1u;
+    // ---- gather front end -------------------------------------------------
+    for (int item = warp; item < 2 * (kC / 32); item += kThreads / 32) {
+      const int side = item / (kC / 32);
+      const int gi = item % (kC / 32);
+      const uint32_t base = grp[(side * (kC / 32) + gi) * 2];
+      const uint32_t cnt = grp[(side * (kC / 32) + gi) * 2 + 1];
+      const int z2 = dest[side * kC + gi * 32 + lane];
+      const float* st = stage + (p.alias ? 0 : side) * kG * p.npad;
+      const float2* tw = rec_tw + side * p.ecap + base + lane;
+      const uint16_t* xs = rec_x + side * p.ecap + base + lane;
+      float2 a[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) a[g] = make_float2(0.f, 0.f);
+      for (uint32_t e = 0; e < cnt; ++e) {
+        const int x = xs[32 * e];
+        const float2 w = tw[32 * e];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          const float v = st[g * p.npad + x];
+          a[g].x = fmaf(v, w.x, a[g].x);
+          a[g].y = fmaf(v, w.y, a[g].y);
+        }
+      }
+      // entries past the capped count of this bucket (rare): on-the-fly twiddles
+      const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
+      for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
+        const uint32_t x = p.ovf_x[(static_cast<size_t>(t) * 2 + side) * n + o];
+        const uint32_t wv = p.hs[(static_cast<size_t>(t) * 2 + side) * n + x];
+        float2 w = wb(tlo, thi, mulmod(wv & kBucketMask, f1, p.b), p.tw_shift);
+        if (wv >> 31) { w.x = -w.x; w.y = -w.y; }
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          const float v = st[g * p.npad + x];
+          a[g].x = fmaf(v, w.x, a[g].x);
+          a[g].y = fmaf(v, w.y, a[g].y);
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < kG; ++g) work[(side * kG + g) * kC + z2] = a[g];
+    }
+    __syncthreads();
+    // staging consumed: fetch the next group while the FFTs run
+    if (tid == 0 && k0 + kG < k_end) issue(k0 + kG);
+    // ---- FFT of length 1024, one per warp --------------------------------
+    float2 x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
+    dft32<false>(x);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 w = anchor[q];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (q + r > 0) x[8 * q + r] = cmul(x[8 * q + r], w);
+        w = cmul(w, step);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < 32; ++f) region[f * 32 + (lane ^ f)] = x[f];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = region[lane * 32 + (j ^ lane)];
+    dft32<false>(x);
+    __syncwarp();
+    if (side_w == 1) {
+#pragma unroll
+      for (int m = 0; m < 32; ++m) region[lane + 32 * m] = x[m];
+    }
+    __syncthreads();
+    // ---- spectral products (side-a warps) --------------------------------
+    if (side_w == 0 && g_w < gcnt) {
+      const float2* pb = work + (kG + g_w) * kC;
+#pragma unroll
+      for (int m = 0; m < 32; ++m) {
+        const float2 q = pb[lane + 32 * m];
+        part[m].x = fmaf(x[m].x, q.x, part[m].x);
+        part[m].x = fmaf(-x[m].y, q.y, part[m].x);
+        part[m].y = fmaf(x[m].x, q.y, part[m].y);
+        part[m].y = fmaf(x[m].y, q.x, part[m].y);
+      }
+    }
+    // ---- fold the partial sums into the Kahan accumulators ---------------
+    const bool last = k0 + kG >= k_end;
+    if ((group % kFlush) == kFlush - 1 || last) {
+      __syncthreads();
+      if (side_w == 0) {
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+          region[lane + 32 * m] = part[m];
+          part[m] = make_float2(0.f, 0.f);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = tid + kThreads * u;
+        float2 s = work[f];
+#pragma unroll
+        for (int g = 1; g < kG; ++g) {
+          const float2 v = work[g * kC + f];
+          s.x += v.x;
+          s.y += v.y;
+        }
+        kahan_add(acc_s[2 * u], acc_c[2 * u], s.x);
+        kahan_add(acc_s[2 * u + 1], acc_c[2 * u + 1], s.y);
+      }
+    }
+    __syncthreads();
+  }
+
+  if (timed_out) {
+    if (tid == 0) atomicOr(&g_sketch_error, 1u);
+    return;
+  }
+  float2* out = p.partial + static_cast<size_t>(task) * kC;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int f = tid + kThreads * u;
+    out[f] = make_float2(acc_s[2 * u] - acc_c[2 * u], acc_s[2 * u + 1] - acc_c[2 * u + 1]);
+  }
+}
+
+}  // namespace
+
+uint32_t read_clear_error_sketch() {
+  uint32_t v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_sketch_error, sizeof(v)) != cudaSuccess) return 0xFFFFFFFFu;
+  if (v) cudaMemcpyToSymbol(g_sketch_error, &zero, sizeof(zero));
+  return v;
+}
+
+size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi) {
+  return fast_layout(npad, ecap, alias, tw_shift, nhi).total;
+}
+
+cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, const void* A,
+                               int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
+                               int64_t n3, float2* partial, cudaStream_t s) {
+  FastArgs a{};
+  a.A = static_cast<const float*>(A);
+  a.lda = lda;
+  a.B = static_cast<const float*>(B);
+  a.ldb = ldb;
+  a.n1 = static_cast<int>(n1); a.n2 = static_cast<int>(n2); a.n3 = static_cast<int>(n3);
+  a.n = static_cast<int>(h->n);
+  a.npad = plan.npad;
+  a.b = plan.b;
+  a.nrows = plan.nrows;
+  a.kchunk = static_cast<int>(plan.kchunk);
+  a.nkc = plan.nkc;
+  a.alias = plan.alias ? 1 : 0;
+  a.ecap = h->fe_ecap;
+  a.tw_shift = plan.tw_shift;
+  a.nhi = plan.nhi;
+  a.rec_x = h->d_fe_x;
+  a.rec_hs = h->d_fe_hs;
+  a.grp = h->d_fe_grp;
+  a.dest = h->d_fe_dest;
+  a.ovf_off = h->d_fe_ovf_off;
+  a.ovf_x = h->d_fe_ovf_x;
+  a.hs = h->d_hs;
+  a.partial = partial;
+  const int smem = static_cast<int>(plan.smem);
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned ntask = static_cast<unsigned>(static_cast<int64_t>(plan.d) * plan.nrows * plan.nkc);
+  {
+    ProfScope prof_scope("k_sketch_fused", s);
+    k_sketch_fast<<<ntask, kThreads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cms

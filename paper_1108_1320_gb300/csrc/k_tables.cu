@@ -102,3 +102,122 @@ cudaError_t launch_bucket_sort(const uint32_t* hs, int d, int64_t n, int64_t C,
 }
 
 }  // namespace cms
+
+namespace cms {
+namespace {
+
+// Front-end records for the C = 1024 fused kernel, one block per (t, side).
+// Buckets z2 = h mod C are ordered by capped count (<= kFeCap) descending,
+// ties by z2; consecutive runs of 32 buckets form a group whose lanes walk
+// their buckets in lock step: entry r of the bucket at group position l sits
+// at base[group] + 32 r + l (padding entries point at x = n).  Entries past
+// the kFeCap-th of a bucket go, in x order, to a per-bucket overflow list.
+__global__ void __launch_bounds__(1024)
+k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
+                  uint32_t* __restrict__ rec_x, uint32_t* __restrict__ rec_hs,
+                  uint32_t* __restrict__ grp, uint16_t* __restrict__ dest,
+                  uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x) {
+  constexpr int C = kFeC;
+  __shared__ uint32_t cnt[C];
+  __shared__ uint32_t key[C];
+  __shared__ uint32_t lanepos[C];
+  __shared__ uint32_t cursor[C];
+  __shared__ uint32_t gbase[C / 32];
+  __shared__ uint32_t oof[C + 1];
+  const int ts = blockIdx.x;
+  const uint32_t* tab = hs + static_cast<size_t>(ts) * n;
+  uint32_t* rx = rec_x + static_cast<size_t>(ts) * ecap;
+  uint32_t* rh = rec_hs + static_cast<size_t>(ts) * ecap;
+  uint32_t* gp = grp + static_cast<size_t>(ts) * (C / 32) * 2;
+  uint16_t* ds = dest + static_cast<size_t>(ts) * C;
+  uint32_t* of = ovf_off + static_cast<size_t>(ts) * (C + 1);
+  uint32_t* ox = ovf_x + static_cast<size_t>(ts) * n;
+  const int tid = threadIdx.x;
+  cnt[tid] = 0;
+  cursor[tid] = 0;
+  __syncthreads();
+  for (uint32_t x = tid; x < n; x += blockDim.x) atomicAdd(&cnt[(tab[x] & kBucketMask) % C], 1u);
+  __syncthreads();
+  // bitonic sort (ascending) of (kFeCap - capped count) << 16 | z2
+  key[tid] = (static_cast<uint32_t>(kFeCap - min(cnt[tid], static_cast<uint32_t>(kFeCap))) << 16) | tid;
+  __syncthreads();
+  for (int size = 2; size <= C; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const int partner = tid ^ stride;
+      if (partner > tid) {
+        const bool up = (tid & size) == 0;
+        const uint32_t a = key[tid], b2 = key[partner];
+        if ((a > b2) == up) { key[tid] = b2; key[partner] = a; }
+      }
+      __syncthreads();
+    }
+  }
+  const uint32_t zsorted = key[tid] & 0xFFFFu;
+  lanepos[zsorted] = tid;
+  ds[tid] = static_cast<uint16_t>(zsorted);
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = 0;
+    for (int g = 0; g < C / 32; ++g) {
+      const uint32_t m = min(cnt[key[32 * g] & 0xFFFFu], static_cast<uint32_t>(kFeCap));
+      gbase[g] = run;
+      gp[2 * g] = run;
+      gp[2 * g + 1] = m;
+      run += 32u * m;
+    }
+    uint32_t o = 0;
+    for (int z = 0; z < C; ++z) {
+      oof[z] = o;
+      of[z] = o;
+      o += cnt[z] > static_cast<uint32_t>(kFeCap) ? cnt[z] - kFeCap : 0u;
+    }
+    oof[C] = o;
+    of[C] = o;
+  }
+  __syncthreads();
+  for (uint32_t e = tid; e < ecap; e += blockDim.x) { rx[e] = n; rh[e] = 0u; }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (uint32_t base = 0; base < n; base += blockDim.x) {
+    const uint32_t x = base + tid;
+    const bool valid = x < n;
+    const uint32_t w = valid ? tab[x] : 0u;
+    const uint32_t z = valid ? (w & kBucketMask) % C : 0xFFFFFFFFu;
+    for (int wv = 0; wv < 32; ++wv) {
+      __syncthreads();
+      if (warp == wv) {
+        const uint32_t grpmask = __match_any_sync(0xFFFFFFFFu, z);
+        if (valid) {
+          const uint32_t r = cursor[z] + __popc(grpmask & lt_mask);
+          if (r < static_cast<uint32_t>(kFeCap)) {
+            const uint32_t p = lanepos[z];
+            const uint32_t pos = gbase[p >> 5] + 32u * r + (p & 31u);
+            rx[pos] = x;
+            rh[pos] = w;
+          } else {
+            ox[oof[z] + (r - kFeCap)] = x;
+          }
+        }
+        __syncwarp();
+        if (valid && lane == __ffs(grpmask) - 1) cursor[z] += __popc(grpmask);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_frontend_tables(const uint32_t* hs, int d, int64_t n, uint32_t ecap,
+                                   uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
+                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,
+                                   cudaStream_t s) {
+  {
+    ProfScope prof_scope("k_frontend_tables", s);
+    k_frontend_tables<<<2 * d, 1024, 0, s>>>(hs, static_cast<uint32_t>(n), ecap, rec_x, rec_hs,
+                                             grp, dest, ovf_off, ovf_x);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cms

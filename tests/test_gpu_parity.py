@@ -329,3 +329,69 @@ def test_covariance_full_size_sampled(cms):
         dc = (tab.s1[t] @ Xd.T) @ (Xd @ tab.s2[t])
         assert abs(c[t].sum() - dc) < 1e-5 * np.abs(c[t]).sum()
     h.free()
+
+
+# ------------------------------------- C = 1024 register-FFT kernel cases --
+@pytest.mark.parametrize("n1,n2,n3,b,d", [
+    (300, 130, 304, 3 * 1024, 3),     # R = 3 (odd), ragged inner tail (130 = 4*32 + 2)
+    (256, 7, 256, 1024, 2),           # R = 1, fewer k than one group
+    (1024, 64, 512, 65536, 2),        # R = 64, rectangular
+    (2044, 33, 2044, 1 << 20, 1),     # R = 1024 rows
+])
+def test_fast_kernel_cases_match_oracle(cms, n1, n2, n3, b, d):
+    A = W.gaussian(n1, n2, 7 + n1).astype(np.float32)
+    B = W.gaussian(n2, n3, 9 + n3).astype(np.float32)
+    n = max(n1, n3)
+    h = cms.make_hashes(31 + b, n, b, d)
+    c = cms.sketch_product(colmajor(A), rowmajor(B), h).cpu().numpy()
+    ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), O.make_tables(31 + b, n, b, d))
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
+def test_fast_kernel_overflow_buckets(cms):
+    # 32 entries per occupied bucket class: half of each goes through the
+    # overflow list of the gather front end
+    n, n2, b = 256, 40, 1024
+    A = W.gaussian(n, n2, 1).astype(np.float32)
+    B = W.gaussian(n2, n, 2).astype(np.float32)
+    g = W.rng(5)
+    h1 = (np.arange(n) % 8)[None, :].astype(np.uint32)
+    h2 = g.integers(0, b, size=(1, n)).astype(np.uint32)
+    s1 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    s2 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    h = cms.Hashes.from_tables(h1, s1, h2, s2, b)
+    c = cms.sketch_product(colmajor(A), rowmajor(B), h).cpu().numpy()
+    tab = O.Tables(h1.astype(np.int64), s1.astype(np.int64), h2.astype(np.int64), s2.astype(np.int64), b)
+    ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), tab)
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
+def test_fast_and_generic_kernels_agree(cms):
+    # same product through the TMA kernel (aligned rows) and the generic
+    # kernel (leading dimension not a multiple of 4 floats)
+    n1, n2, n3, b, d = 512, 96, 512, 16384, 3
+    A = W.gaussian(n1, n2, 3).astype(np.float32)
+    B = W.gaussian(n2, n3, 4).astype(np.float32)
+    h = cms.make_hashes(12, 512, b, d)
+    c_fast = cms.sketch_product(colmajor(A), rowmajor(B), h).cpu().numpy()
+    pad_a = torch.zeros((n2, n1 + 1), device=dev())
+    pad_a[:, :n1] = torch.from_numpy(A.T)
+    c_gen = cms.sketch_product(pad_a[:, :n1].T, rowmajor(B), h).cpu().numpy()
+    ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), O.make_tables(12, 512, b, d))
+    assert O.rel_l2(c_fast, ref) < TOL_F32
+    assert O.rel_l2(c_gen, ref) < TOL_F32
+    h.free()
+
+
+def test_reseeded_fast_path(cms):
+    # reseed rebuilds the front-end records on the device
+    X = W.gaussian(96, 1024, 8).astype(np.float32)
+    h = cms.make_hashes(1, 1024, 65536, 2)
+    xt = torch.from_numpy(X).to(dev())
+    h.reseed(99)
+    c = cms.sketch_product(xt.T, xt, h).cpu().numpy()
+    ref = O.sketch_definition(X.T.astype(np.float64), X.astype(np.float64), O.make_tables(99, 1024, 65536, 2))
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
