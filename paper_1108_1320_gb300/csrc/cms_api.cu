@@ -304,9 +304,14 @@ cms_status cms_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64
   DeviceProps dp = device_props(h->device);
   SketchPlan plan;
   std::string why;
+  // the kernel is chosen per call (pointer alignment); cover both plans
   int r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &plan, &why);
   if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
-  *bytes = plan.ws_bytes;
+  SketchPlan generic;
+  r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &generic, &why, nullptr, 0, nullptr, 0,
+                       false);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  *bytes = std::max(plan.ws_bytes, generic.ws_bytes);
   return CMS_OK;
 }
 

@@ -97,7 +97,7 @@ bool choose_factorisation(int64_t b, int64_t* R, int64_t* C);
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
                      int dt, int num_sms, size_t smem_optin, SketchPlan* plan,
                      std::string* why, const void* A = nullptr, int64_t lda = 0,
-                     const void* B = nullptr, int64_t ldb = 0);
+                     const void* B = nullptr, int64_t ldb = 0, bool allow_fast = true);
 size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi);
 cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, const void* A,
                                int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,

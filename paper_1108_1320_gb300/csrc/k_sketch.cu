@@ -312,7 +312,7 @@ int64_t choose_chunks(int64_t units, int64_t n2, int G, int64_t slots, int64_t l
 
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int dt,
                      int num_sms, size_t smem_optin, SketchPlan* plan, std::string* why,
-                     const void* A, int64_t lda, const void* B, int64_t ldb) {
+                     const void* A, int64_t lda, const void* B, int64_t ldb, bool allow_fast) {
   SketchPlan p;
   p.b = h->b;
   p.d = h->d;
@@ -330,7 +330,7 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   const bool aligned = (A == nullptr || reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                        (B == nullptr || reinterpret_cast<uintptr_t>(B) % 16 == 0) &&
                        lda % 4 == 0 && ldb % 4 == 0 && n1 % 4 == 0 && n3 % 4 == 0;
-  if (dt == CMS_F32 && p.C == kFeC && h->fe_ecap > 0 && aligned) {
+  if (allow_fast && dt == CMS_F32 && p.C == kFeC && h->fe_ecap > 0 && aligned) {
     p.alias = A != nullptr && A == B && lda == ldb && n1 == n3;
     p.npad = static_cast<int>(((h->n + 1) + 3) / 4 * 4);
     int sh = 0;
