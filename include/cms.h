@@ -153,6 +153,33 @@ CMS_API cms_status cms_sketch_product(const void* A, int64_t lda, const void* B,
                               void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * cms_sketch_product_noalloc - the same sketch as cms_sketch_product, for
+ * callers that cannot allocate device memory or pass a workspace (for
+ * example code running inside another application whose allocator owns all
+ * device memory, or a path that must not call cudaMalloc/cudaFree because
+ * they can synchronise the device).  The paper has no counterpart: this is a
+ * memory-management variant of COMPRESSEDPRODUCT, not a different method.
+ *   Arguments are those of cms_sketch_product without ws / ws_bytes; the
+ *   caller still passes A, B, the hashes and the output c.
+ *   Scratch: a fixed 32 MiB device array owned by the library (held on every
+ *   GPU that loads it until the process exits).  Shapes whose
+ *   cms_workspace_size() exceeds 32 MiB are rejected with CMS_ERR_WORKSPACE
+ *   (the covariance shape n = 2048, b = 65536, d = 5 needs about 18 MiB).
+ *   The call allocates nothing.  Its first call on a device looks up the
+ *   array's device address (cudaGetSymbolAddress) with that device current;
+ *   make that first call before any stream capture.
+ *   All calls on a device share the array, which keeps the previous call's
+ *   contents (no part of it needs to start at zero): calls that overlap on
+ *   the GPU (other streams or host threads) race and must be serialised by
+ *   the caller.
+ * Errors: those of cms_sketch_product, CMS_ERR_WORKSPACE above the limit.
+ */
+CMS_API cms_status cms_sketch_product_noalloc(const void* A, int64_t lda, const void* B,
+                                              int64_t ldb, int64_t n1, int64_t n2, int64_t n3,
+                                              int32_t dt, const cms_hashes* h, float* c,
+                                              void* stream);
+
+/*
  * cms_plain_workspace_size / cms_sketch_product_plain_f64 - the same sketch
  * (Fig. 1) in plain form: FP64 throughout, one instance per call, unfused
  * passes (scatter, FFT, spectral product, inverse FFT each a separate

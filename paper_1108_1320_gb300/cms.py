@@ -43,6 +43,7 @@ SIGNATURES = {
     "cms_hashes_tables": (_I32, [_P, _P, _P, _P, _P]),
     "cms_workspace_size": (_I32, [_P, _I64, _I64, _I64, _I32, ctypes.POINTER(_SZ)]),
     "cms_sketch_product": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P, _SZ, _P]),
+    "cms_sketch_product_noalloc": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P]),
     "cms_plain_workspace_size": (_I32, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
     "cms_sketch_product_plain_f64": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _P, _P, _P, _SZ,
                                             _P]),
@@ -214,6 +215,21 @@ def sketch_product(A: torch.Tensor, B: torch.Tensor, h: Hashes, c: torch.Tensor 
         ws = alloc_workspace(need, A.device)
     _check(lib().cms_sketch_product(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype], h.handle,
                                     _ptr(c), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+    return c
+
+
+def sketch_product_noalloc(A: torch.Tensor, B: torch.Tensor, h: Hashes,
+                           c: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """COMPRESSEDPRODUCT without a workspace, for callers that cannot
+    allocate device memory: the library's fixed 32 MiB scratch array is used
+    (shared by all calls on the device; calls overlapping on the GPU race).
+    Returns c, float32 (d, b)."""
+    n1, n2, n3, lda, ldb = _ab_args(A, B)
+    inf = h.info()
+    if c is None:
+        c = torch.empty((inf["d"], inf["b"]), dtype=torch.float32, device=A.device)
+    _check(lib().cms_sketch_product_noalloc(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype],
+                                            h.handle, _ptr(c), _stream(stream)))
     return c
 
 
