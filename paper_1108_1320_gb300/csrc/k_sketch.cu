@@ -340,7 +340,7 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
     const size_t sm = fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi);
     if (sm <= smem_optin) {
       p.fast = true;
-      p.G = 4;
+      p.G = 2;
       p.threads = 256;
       p.smem = sm;
     }
@@ -364,8 +364,10 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   const int G = p.G;
   const int per_sm = p.fast ? 1 : std::max<int>(1, static_cast<int>(std::min<size_t>(4, (228 * 1024) / (p.smem + 1024))));
   const int64_t slots = static_cast<int64_t>(num_sms) * per_sm;
-  const int64_t lo = std::max<int64_t>(1, (2 * slots + units - 1) / units);
-  int64_t nkc = choose_chunks(units, n2, G, slots, lo, std::max<int64_t>(lo, 4 * lo));
+  // the fast kernel's blocks own two rows each
+  const int64_t blocks_per_chunk = p.fast ? static_cast<int64_t>(p.d) * ((p.nrows + 1) / 2) : units;
+  const int64_t lo = std::max<int64_t>(1, (2 * slots + blocks_per_chunk - 1) / blocks_per_chunk);
+  int64_t nkc = choose_chunks(blocks_per_chunk, n2, G, slots, lo, std::max<int64_t>(lo, 4 * lo));
   int64_t kchunk = n2 > 0 ? (n2 + nkc - 1) / nkc : G;
   kchunk = ((kchunk + G - 1) / G) * G;
   nkc = n2 > 0 ? (n2 + kchunk - 1) / kchunk : 1;

@@ -3,22 +3,27 @@
 // four-step split of the length-b DFT and the pruned first stage) with a
 // GB300-specific layout:
 //
-//  * a_k (column k of A) and b_k (row k of B) for a group of G = 4 inner
+//  * a thread block owns TWO rows f1 of the R x C output grid (one
+//    repetition t, a range of inner indices k), so every value of a_k / b_k
+//    it gathers serves both rows;
+//  * a_k (column k of A) and b_k (row k of B) for a group of G = 2 inner
 //    indices are staged into shared memory by TMA bulk copies
 //    (cp.async.bulk + mbarrier), issued as soon as the previous group's
 //    front end has consumed the buffer, so the copy overlaps the FFTs;
+//    when A = X^T and B = X are the same bytes the rows are staged once;
 //  * the gather front end Y[f1][z2] = sum s(x) A_xk w_b^{f1 h(x)} walks
-//    per-(t, side) records (x, twiddle) kept in shared memory for the whole
-//    task; 32 buckets of equal (capped) occupancy form a group whose lanes
-//    run in lock step, so warps do not diverge on bucket sizes;
-//  * each of the 8 warps runs one length-1024 FFT (one (side, k) pair):
+//    per-(t, side) records (x and the two rows' twiddles) kept in shared
+//    memory for the whole task; 32 buckets of equal (capped) occupancy form
+//    a group whose lanes run in lock step, placed so that the stores to Y
+//    are free of bank conflicts;
+//  * each of the 8 warps runs one length-1024 FFT (one (row, side, k)):
 //    radix-32 in registers, twiddle, one XOR-swizzled (conflict-free)
 //    transpose through shared memory, radix-32 in registers; lane l ends
 //    holding bins l + 32 m, m = 0..31;
 //  * the side-b warps publish their spectra, the side-a warps multiply and
-//    accumulate PA PB in registers; every kFlush groups the four partial
-//    sums are added (fixed order) and folded into Kahan-compensated
-//    accumulators held in registers by all threads (4 bins per thread).
+//    accumulate PA PB in registers; every kFlush groups the two inner
+//    indices' partial sums are added (fixed order) and folded into
+//    Kahan-compensated accumulators in shared memory.
 #include <algorithm>
 
 #include "cms_internal.h"
@@ -27,9 +32,10 @@ namespace cms {
 namespace {
 
 constexpr int kC = kFeC;       // 1024
-constexpr int kG = 4;          // inner indices per group
-constexpr int kThreads = 256;  // 8 warps = 2 sides x kG FFTs
-constexpr int kFlush = 8;      // groups between Kahan folds
+constexpr int kG = 2;          // inner indices per group
+constexpr int kRows = 2;       // rows f1 per block
+constexpr int kThreads = 256;  // 8 warps = kRows x 2 sides x kG FFTs
+constexpr int kFlush = 16;     // groups between Kahan folds
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
 
 __device__ uint32_t g_sketch_error = 0;   // 1: a TMA wait gave up
@@ -41,7 +47,7 @@ struct FastArgs {
   int64_t ldb;
   int n1, n2, n3, n, npad;
   int64_t b;
-  int nrows;
+  int nrows, nunits;
   int kchunk, nkc;
   int alias;
   uint32_t ecap;
@@ -183,7 +189,7 @@ __device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, int64_t b) {
 }
 
 struct SmemLayout {
-  size_t stage, rec_tw, rec_x, work, tlo, thi, grp, dest, ovf, bar, total;
+  size_t stage, rec_tw, rec_x, work, acc, tlo, thi, grp, dest, ovf, bar, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
@@ -193,14 +199,15 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   size_t o = 0;
   const int nstage = alias ? 1 : 2;
   L.stage = o;  o = al16(o + static_cast<size_t>(nstage) * kG * npad * 4);
-  L.rec_tw = o; o = al16(o + static_cast<size_t>(2) * ecap * 8);
+  L.rec_tw = o; o = al16(o + static_cast<size_t>(kRows) * 2 * ecap * 8);
   L.rec_x = o;  o = al16(o + static_cast<size_t>(2) * ecap * 2);
-  L.work = o;   o = al16(o + static_cast<size_t>(2 * kG) * kC * 8);
+  L.work = o;   o = al16(o + static_cast<size_t>(kRows * 2 * kG) * kC * 8);
+  L.acc = o;    o = al16(o + static_cast<size_t>(kRows) * kC * 16);
   L.tlo = o;    o = al16(o + (static_cast<size_t>(1) << tw_shift) * 8);
   L.thi = o;    o = al16(o + static_cast<size_t>(nhi) * 8);
   L.grp = o;    o = al16(o + static_cast<size_t>(2) * (kC / 32) * 2 * 4);
   L.dest = o;   o = al16(o + static_cast<size_t>(2) * kC * 2);
-  L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 4);
+  L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
   L.bar = o;    o = al16(o + 8);
   L.total = o;
   return L;
@@ -213,26 +220,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   float2* rec_tw = reinterpret_cast<float2*>(sm + L.rec_tw);
   uint16_t* rec_x = reinterpret_cast<uint16_t*>(sm + L.rec_x);
   float2* work = reinterpret_cast<float2*>(sm + L.work);
+  float4* acc = reinterpret_cast<float4*>(sm + L.acc);
   float2* tlo = reinterpret_cast<float2*>(sm + L.tlo);
   float2* thi = reinterpret_cast<float2*>(sm + L.thi);
   uint32_t* grp = reinterpret_cast<uint32_t*>(sm + L.grp);
   uint16_t* dest = reinterpret_cast<uint16_t*>(sm + L.dest);
-  uint32_t* ovf = reinterpret_cast<uint32_t*>(sm + L.ovf);
+  uint16_t* ovf = reinterpret_cast<uint16_t*>(sm + L.ovf);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int task = blockIdx.x;
   const int kc = task % p.nkc;
-  const int row = (task / p.nkc) % p.nrows;
-  const int t = task / (p.nkc * p.nrows);
-  const uint32_t f1 = static_cast<uint32_t>(row);
+  const int unit = (task / p.nkc) % p.nunits;
+  const int t = task / (p.nkc * p.nunits);
+  // rows of this block: 2 unit, 2 unit + 1 (the odd last unit repeats its row)
+  uint32_t f1r[kRows];
+  f1r[0] = static_cast<uint32_t>(2 * unit);
+  f1r[1] = static_cast<uint32_t>(min(2 * unit + 1, p.nrows - 1));
+  const bool row1_live = 2 * unit + 1 < p.nrows;
   const int n = p.n;
   const int S = 1 << p.tw_shift;
   const int nstage = p.alias ? 1 : 2;
   const int k_begin = kc * p.kchunk;
   const int k_end = min(p.n2, k_begin + p.kchunk);
 
-  // ---- prologue: tables, records, staging tails, barrier ----------------
+  // ---- prologue: tables, records, staging tails, accumulators, barrier ----
   for (int i = tid; i < S; i += kThreads) {
     float s, c;
     sincospif(2.0f * static_cast<float>(i) / static_cast<float>(p.b), &s, &c);
@@ -248,8 +260,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     const size_t ts = static_cast<size_t>(t) * 2 + side;
     for (int i = tid; i < (kC / 32) * 2; i += kThreads) grp[side * (kC / 32) * 2 + i] = p.grp[ts * (kC / 32) * 2 + i];
     for (int i = tid; i < kC; i += kThreads) dest[side * kC + i] = p.dest[ts * kC + i];
-    for (int i = tid; i <= kC; i += kThreads) ovf[side * (kC + 1) + i] = p.ovf_off[ts * (kC + 1) + i];
+    for (int i = tid; i <= kC; i += kThreads)
+      ovf[side * (kC + 1) + i] = static_cast<uint16_t>(p.ovf_off[ts * (kC + 1) + i]);
   }
+  for (int i = tid; i < kRows * kC; i += kThreads) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   // zero the staging tails [n_side, npad): entries x >= n_side read zeros
   for (int s2 = 0; s2 < nstage; ++s2) {
     const int nside = s2 == 0 ? p.n1 : p.n3;
@@ -261,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     fence_proxy_async();
   }
   __syncthreads();
-  // records: x and s(x) w_b^{(h(x) f1) mod b}, padding x = n with weight 0
+  // records: x and s(x) w_b^{(h(x) f1) mod b} for both rows, padding x = n
   for (int side = 0; side < 2; ++side) {
     const size_t ts = static_cast<size_t>(t) * 2 + side;
     const uint32_t* gsrc = grp + side * (kC / 32) * 2;
@@ -269,12 +283,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     for (uint32_t e = tid; e < epad; e += kThreads) {
       const uint32_t x = p.rec_x[ts * p.ecap + e];
       const uint32_t w = p.rec_hs[ts * p.ecap + e];
-      float2 tw = make_float2(0.f, 0.f);
-      if (x < static_cast<uint32_t>(n)) {
-        tw = wb(tlo, thi, mulmod(w & kBucketMask, f1, p.b), p.tw_shift);
-        if (w >> 31) { tw.x = -tw.x; tw.y = -tw.y; }
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        float2 tw = make_float2(0.f, 0.f);
+        if (x < static_cast<uint32_t>(n)) {
+          tw = wb(tlo, thi, mulmod(w & kBucketMask, f1r[r], p.b), p.tw_shift);
+          if (w >> 31) { tw.x = -tw.x; tw.y = -tw.y; }
+        }
+        rec_tw[(r * 2 + side) * p.ecap + e] = tw;
       }
-      rec_tw[side * p.ecap + e] = tw;
       rec_x[side * p.ecap + e] = static_cast<uint16_t>(min(x, static_cast<uint32_t>(n)));
     }
   }
@@ -292,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     }
   }
 
-  // issue the TMA copies of group starting at k0 (thread 0 only)
+  // issue the TMA copies of the group starting at k0 (thread 0 only)
   auto issue = [&](int k0) {
     uint32_t bytes = 0;
     const int gl = min(kG, k_end - k0);
@@ -314,15 +331,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   float2 part[32];
 #pragma unroll
   for (int m = 0; m < 32; ++m) part[m] = make_float2(0.f, 0.f);
-  float acc_s[8], acc_c[8];   // Kahan sum and compensation of bins tid + 256 u (re, im)
-#pragma unroll
-  for (int u = 0; u < 8; ++u) { acc_s[u] = 0.f; acc_c[u] = 0.f; }
 
   if (tid == 0 && k_begin < k_end) issue(k_begin);
   __syncthreads();
 
-  const int side_w = warp / kG;          // FFT side of this warp
-  const int g_w = warp % kG;             // inner index of the group
+  // warp -> (row, side, inner index of the group); region = warp
+  const int row_w = warp >> 2;
+  const int side_w = (warp >> 1) & 1;
+  const int g_w = warp & 1;
   float2* region = work + warp * kC;
   uint32_t phase = 0;
   int group = 0;
@@ -334,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     const bool ok = mbar_wait_bounded(bar, phase);
     if (__syncthreads_or(!ok)) { timed_out = true; break; }
     phase ^= 1u;
-    // ---- gather front end -------------------------------------------------
+    // ---- gather front end (both rows, both inner indices) ----------------
     for (int item = warp; item < 2 * (kC / 32); item += kThreads / 32) {
       const int side = item / (kC / 32);
       const int gi = item % (kC / 32);
@@ -342,37 +358,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
       const uint32_t cnt = grp[(side * (kC / 32) + gi) * 2 + 1];
       const int z2 = dest[side * kC + gi * 32 + lane];
       const float* st = stage + (p.alias ? 0 : side) * kG * p.npad;
-      const float2* tw = rec_tw + side * p.ecap + base + lane;
+      const float2* tw0 = rec_tw + (0 * 2 + side) * p.ecap + base + lane;
+      const float2* tw1 = rec_tw + (1 * 2 + side) * p.ecap + base + lane;
       const uint16_t* xs = rec_x + side * p.ecap + base + lane;
-      float2 a[kG];
-#pragma unroll
-      for (int g = 0; g < kG; ++g) a[g] = make_float2(0.f, 0.f);
+      float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
       for (uint32_t e = 0; e < cnt; ++e) {
         const int x = xs[32 * e];
-        const float2 w = tw[32 * e];
-#pragma unroll
-        for (int g = 0; g < kG; ++g) {
-          const float v = st[g * p.npad + x];
-          a[g].x = fmaf(v, w.x, a[g].x);
-          a[g].y = fmaf(v, w.y, a[g].y);
-        }
+        const float2 w0 = tw0[32 * e];
+        const float2 w1 = tw1[32 * e];
+        const float v0 = st[x];
+        const float v1 = st[p.npad + x];
+        a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
+        a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
+        a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
+        a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
       }
       // entries past the capped count of this bucket (rare): on-the-fly twiddles
       const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
       for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
         const uint32_t x = p.ovf_x[(static_cast<size_t>(t) * 2 + side) * n + o];
         const uint32_t wv = p.hs[(static_cast<size_t>(t) * 2 + side) * n + x];
-        float2 w = wb(tlo, thi, mulmod(wv & kBucketMask, f1, p.b), p.tw_shift);
-        if (wv >> 31) { w.x = -w.x; w.y = -w.y; }
-#pragma unroll
-        for (int g = 0; g < kG; ++g) {
-          const float v = st[g * p.npad + x];
-          a[g].x = fmaf(v, w.x, a[g].x);
-          a[g].y = fmaf(v, w.y, a[g].y);
-        }
+        float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], p.b), p.tw_shift);
+        float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], p.b), p.tw_shift);
+        if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
+        const float v0 = st[x];
+        const float v1 = st[p.npad + x];
+        a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
+        a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
+        a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
+        a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
       }
-#pragma unroll
-      for (int g = 0; g < kG; ++g) work[(side * kG + g) * kC + z2] = a[g];
+      work[((0 * 2 + side) * kG + 0) * kC + z2] = a00;
+      work[((0 * 2 + side) * kG + 1) * kC + z2] = a01;
+      work[((1 * 2 + side) * kG + 0) * kC + z2] = a10;
+      work[((1 * 2 + side) * kG + 1) * kC + z2] = a11;
     }
     __syncthreads();
     // staging consumed: fetch the next group while the FFTs run
@@ -406,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     __syncthreads();
     // ---- spectral products (side-a warps) --------------------------------
     if (side_w == 0 && g_w < gcnt) {
-      const float2* pb = work + (kG + g_w) * kC;
+      const float2* pb = work + ((row_w * 2 + 1) * kG + g_w) * kC;
 #pragma unroll
       for (int m = 0; m < 32; ++m) {
         const float2 q = pb[lane + 32 * m];
@@ -429,17 +448,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
       }
       __syncthreads();
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int f = tid + kThreads * u;
-        float2 s = work[f];
+      for (int u = 0; u < (kRows * kC) / kThreads; ++u) {
+        const int idx = tid + kThreads * u;
+        const int r = idx / kC, f = idx % kC;
+        float2 s = work[((r * 2 + 0) * kG + 0) * kC + f];
 #pragma unroll
         for (int g = 1; g < kG; ++g) {
-          const float2 v = work[g * kC + f];
+          const float2 v = work[((r * 2 + 0) * kG + g) * kC + f];
           s.x += v.x;
           s.y += v.y;
         }
-        kahan_add(acc_s[2 * u], acc_c[2 * u], s.x);
-        kahan_add(acc_s[2 * u + 1], acc_c[2 * u + 1], s.y);
+        float4 a = acc[idx];
+        kahan_add(a.x, a.z, s.x);
+        kahan_add(a.y, a.w, s.y);
+        acc[idx] = a;
       }
     }
     __syncthreads();
@@ -449,11 +471,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     if (tid == 0) atomicOr(&g_sketch_error, 1u);
     return;
   }
-  float2* out = p.partial + static_cast<size_t>(task) * kC;
+  __syncthreads();
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int f = tid + kThreads * u;
-    out[f] = make_float2(acc_s[2 * u] - acc_c[2 * u], acc_s[2 * u + 1] - acc_c[2 * u + 1]);
+  for (int u = 0; u < (kRows * kC) / kThreads; ++u) {
+    const int idx = tid + kThreads * u;
+    const int r = idx / kC, f = idx % kC;
+    if (r == 1 && !row1_live) continue;
+    const float4 a = acc[idx];
+    float2* out = p.partial + ((static_cast<size_t>(t) * p.nrows + f1r[r]) * p.nkc + kc) * kC;
+    out[f] = make_float2(a.x - a.z, a.y - a.w);
   }
 }
 
@@ -483,6 +509,7 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
   a.npad = plan.npad;
   a.b = plan.b;
   a.nrows = plan.nrows;
+  a.nunits = (plan.nrows + 1) / 2;
   a.kchunk = static_cast<int>(plan.kchunk);
   a.nkc = plan.nkc;
   a.alias = plan.alias ? 1 : 0;
@@ -500,7 +527,7 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
   const int smem = static_cast<int>(plan.smem);
   cudaError_t e = cudaFuncSetAttribute(k_sketch_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const unsigned ntask = static_cast<unsigned>(static_cast<int64_t>(plan.d) * plan.nrows * plan.nkc);
+  const unsigned ntask = static_cast<unsigned>(static_cast<int64_t>(plan.d) * a.nunits * plan.nkc);
   {
     ProfScope prof_scope("k_sketch_fused", s);
     k_sketch_fast<<<ntask, kThreads, smem, s>>>(a);

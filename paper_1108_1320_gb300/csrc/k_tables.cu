@@ -152,6 +152,29 @@ k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
       __syncthreads();
     }
   }
+  // Within each group of 32 buckets, place buckets so that each half-warp
+  // holds distinct z2 mod 16 where possible: the front end's 8-byte stores
+  // to Y[z2] are then free of bank conflicts.  The group's bucket set (and
+  // so its padded length) is unchanged.
+  if (tid < C / 32) {
+    uint32_t* grpkey = key + 32 * tid;
+    uint32_t in[32], half0[16], half1[16], pool[32];
+    int n0 = 0, n1 = 0, np = 0;
+    uint32_t used0 = 0, used1 = 0;
+    for (int i = 0; i < 32; ++i) in[i] = grpkey[i];
+    for (int i = 0; i < 32; ++i) {
+      const uint32_t r = (in[i] & 0xFFFFu) & 15u;
+      if (!(used0 >> r & 1u)) { used0 |= 1u << r; half0[n0++] = in[i]; }
+      else if (!(used1 >> r & 1u)) { used1 |= 1u << r; half1[n1++] = in[i]; }
+      else { pool[np++] = in[i]; }
+    }
+    for (int i = 0; i < np; ++i) {
+      if (n0 < 16) half0[n0++] = pool[i];
+      else half1[n1++] = pool[i];
+    }
+    for (int i = 0; i < 16; ++i) { grpkey[i] = half0[i]; grpkey[16 + i] = half1[i]; }
+  }
+  __syncthreads();
   const uint32_t zsorted = key[tid] & 0xFFFFu;
   lanepos[zsorted] = tid;
   ds[tid] = static_cast<uint16_t>(zsorted);
@@ -159,7 +182,9 @@ k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
   if (tid == 0) {
     uint32_t run = 0;
     for (int g = 0; g < C / 32; ++g) {
-      const uint32_t m = min(cnt[key[32 * g] & 0xFFFFu], static_cast<uint32_t>(kFeCap));
+      uint32_t m = 0;
+      for (int i = 0; i < 32; ++i)
+        m = max(m, min(cnt[key[32 * g + i] & 0xFFFFu], static_cast<uint32_t>(kFeCap)));
       gbase[g] = run;
       gp[2 * g] = run;
       gp[2 * g + 1] = m;
