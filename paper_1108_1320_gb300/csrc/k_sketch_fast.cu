@@ -36,6 +36,8 @@ constexpr int kG = 2;          // inner indices per group
 constexpr int kRows = 2;       // rows f1 per block
 constexpr int kThreads = 256;  // 8 warps = kRows x 2 sides x kG FFTs
 constexpr int kFlush = 16;     // groups between Kahan folds
+constexpr int kPitch = 33;     // transpose row pitch (float2): conflict-free both ways
+constexpr int kRegion = 32 * kPitch;   // float2 per warp region (>= kC)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
 
 __device__ uint32_t g_sketch_error = 0;   // 1: a TMA wait gave up
@@ -199,9 +201,9 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   size_t o = 0;
   const int nstage = alias ? 1 : 2;
   L.stage = o;  o = al16(o + static_cast<size_t>(nstage) * kG * npad * 4);
-  L.rec_tw = o; o = al16(o + static_cast<size_t>(kRows) * 2 * ecap * 8);
+  L.rec_tw = o; o = al16(o + static_cast<size_t>(2) * ecap * 16);
   L.rec_x = o;  o = al16(o + static_cast<size_t>(2) * ecap * 2);
-  L.work = o;   o = al16(o + static_cast<size_t>(kRows * 2 * kG) * kC * 8);
+  L.work = o;   o = al16(o + static_cast<size_t>(kRows * 2 * kG) * kRegion * 8);
   L.acc = o;    o = al16(o + static_cast<size_t>(kRows) * kC * 16);
   L.tlo = o;    o = al16(o + (static_cast<size_t>(1) << tw_shift) * 8);
   L.thi = o;    o = al16(o + static_cast<size_t>(nhi) * 8);
@@ -217,13 +219,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout L = fast_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi);
   float* stage = reinterpret_cast<float*>(sm + L.stage);
-  float2* rec_tw = reinterpret_cast<float2*>(sm + L.rec_tw);
+  float4* rec_tw = reinterpret_cast<float4*>(sm + L.rec_tw);     // [side][e]: row 0 tw, row 1 tw
   uint16_t* rec_x = reinterpret_cast<uint16_t*>(sm + L.rec_x);
   float2* work = reinterpret_cast<float2*>(sm + L.work);
   float4* acc = reinterpret_cast<float4*>(sm + L.acc);
   float2* tlo = reinterpret_cast<float2*>(sm + L.tlo);
   float2* thi = reinterpret_cast<float2*>(sm + L.thi);
-  uint32_t* grp = reinterpret_cast<uint32_t*>(sm + L.grp);
+  uint2* grp = reinterpret_cast<uint2*>(sm + L.grp);
   uint16_t* dest = reinterpret_cast<uint16_t*>(sm + L.dest);
   uint16_t* ovf = reinterpret_cast<uint16_t*>(sm + L.ovf);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
@@ -258,7 +260,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   }
   for (int side = 0; side < 2; ++side) {
     const size_t ts = static_cast<size_t>(t) * 2 + side;
-    for (int i = tid; i < (kC / 32) * 2; i += kThreads) grp[side * (kC / 32) * 2 + i] = p.grp[ts * (kC / 32) * 2 + i];
+    for (int i = tid; i < kC / 32; i += kThreads)
+      grp[side * (kC / 32) + i] = make_uint2(p.grp[(ts * (kC / 32) + i) * 2], p.grp[(ts * (kC / 32) + i) * 2 + 1]);
     for (int i = tid; i < kC; i += kThreads) dest[side * kC + i] = p.dest[ts * kC + i];
     for (int i = tid; i <= kC; i += kThreads)
       ovf[side * (kC + 1) + i] = static_cast<uint16_t>(p.ovf_off[ts * (kC + 1) + i]);
@@ -278,20 +281,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   // records: x and s(x) w_b^{(h(x) f1) mod b} for both rows, padding x = n
   for (int side = 0; side < 2; ++side) {
     const size_t ts = static_cast<size_t>(t) * 2 + side;
-    const uint32_t* gsrc = grp + side * (kC / 32) * 2;
-    const uint32_t epad = gsrc[(kC / 32 - 1) * 2] + 32u * gsrc[(kC / 32 - 1) * 2 + 1];
+    const uint2 lastg = grp[side * (kC / 32) + kC / 32 - 1];
+    const uint32_t epad = lastg.x + 32u * (lastg.y & 0xFFFFu);
     for (uint32_t e = tid; e < epad; e += kThreads) {
       const uint32_t x = p.rec_x[ts * p.ecap + e];
       const uint32_t w = p.rec_hs[ts * p.ecap + e];
+      float2 tw[kRows];
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
-        float2 tw = make_float2(0.f, 0.f);
+        tw[r] = make_float2(0.f, 0.f);
         if (x < static_cast<uint32_t>(n)) {
-          tw = wb(tlo, thi, mulmod(w & kBucketMask, f1r[r], p.b), p.tw_shift);
-          if (w >> 31) { tw.x = -tw.x; tw.y = -tw.y; }
+          tw[r] = wb(tlo, thi, mulmod(w & kBucketMask, f1r[r], p.b), p.tw_shift);
+          if (w >> 31) { tw[r].x = -tw[r].x; tw[r].y = -tw[r].y; }
         }
-        rec_tw[(r * 2 + side) * p.ecap + e] = tw;
       }
+      rec_tw[side * p.ecap + e] = make_float4(tw[0].x, tw[0].y, tw[1].x, tw[1].y);
       rec_x[side * p.ecap + e] = static_cast<uint16_t>(min(x, static_cast<uint32_t>(n)));
     }
   }
@@ -328,9 +332,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     }
   };
 
-  float2 part[32];
+  // Each warp accumulates the spectral product of its (row, k-slot) pair for
+  // 16 of its 32 bins: side-a warps own m = 0..15, side-b warps m = 16..31.
+  float2 part[16];
 #pragma unroll
-  for (int m = 0; m < 32; ++m) part[m] = make_float2(0.f, 0.f);
+  for (int m = 0; m < 16; ++m) part[m] = make_float2(0.f, 0.f);
 
   if (tid == 0 && k_begin < k_end) issue(k_begin);
   __syncthreads();
@@ -339,7 +345,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   const int row_w = warp >> 2;
   const int side_w = (warp >> 1) & 1;
   const int g_w = warp & 1;
-  float2* region = work + warp * kC;
+  float2* region = work + warp * kRegion;
+  // partner: same row and k slot, other side
+  const float2* partner = work + (warp ^ 2) * kRegion;
+  const int own_m0 = side_w * 16;       // bins this warp accumulates: m in [own_m0, own_m0 + 16)
   uint32_t phase = 0;
   int group = 0;
   bool timed_out = false;
@@ -351,47 +360,54 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     if (__syncthreads_or(!ok)) { timed_out = true; break; }
     phase ^= 1u;
     // ---- gather front end (both rows, both inner indices) ----------------
-    for (int item = warp; item < 2 * (kC / 32); item += kThreads / 32) {
-      const int side = item / (kC / 32);
-      const int gi = item % (kC / 32);
-      const uint32_t base = grp[(side * (kC / 32) + gi) * 2];
-      const uint32_t cnt = grp[(side * (kC / 32) + gi) * 2 + 1];
+    // items (side, bucket group) dealt to warps in snake order so that the
+    // heavy (first) groups of each side spread over all warps
+#pragma unroll 1
+    for (int j = 0; j < 2 * (kC / 32) / (kThreads / 32); ++j) {
+      const int slot = (j & 1) ? (kThreads / 32 - 1 - warp) : warp;
+      const int item = j * (kThreads / 32) + slot;
+      const int side = item & 1;
+      const int gi = item >> 1;
+      const uint2 gd = grp[side * (kC / 32) + gi];
+      const uint32_t base = gd.x;
+      const uint32_t cnt = gd.y & 0xFFFFu;
       const int z2 = dest[side * kC + gi * 32 + lane];
       const float* st = stage + (p.alias ? 0 : side) * kG * p.npad;
-      const float2* tw0 = rec_tw + (0 * 2 + side) * p.ecap + base + lane;
-      const float2* tw1 = rec_tw + (1 * 2 + side) * p.ecap + base + lane;
+      const float4* tw = rec_tw + side * p.ecap + base + lane;
       const uint16_t* xs = rec_x + side * p.ecap + base + lane;
       float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
+#pragma unroll 2
       for (uint32_t e = 0; e < cnt; ++e) {
         const int x = xs[32 * e];
-        const float2 w0 = tw0[32 * e];
-        const float2 w1 = tw1[32 * e];
+        const float4 w = tw[32 * e];
         const float v0 = st[x];
         const float v1 = st[p.npad + x];
-        a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
-        a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
-        a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
-        a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
+        a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
+        a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
+        a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
+        a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
       }
-      // entries past the capped count of this bucket (rare): on-the-fly twiddles
-      const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
-      for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
-        const uint32_t x = p.ovf_x[(static_cast<size_t>(t) * 2 + side) * n + o];
-        const uint32_t wv = p.hs[(static_cast<size_t>(t) * 2 + side) * n + x];
-        float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], p.b), p.tw_shift);
-        float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], p.b), p.tw_shift);
-        if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
-        const float v0 = st[x];
-        const float v1 = st[p.npad + x];
-        a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
-        a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
-        a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
-        a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
+      if (gd.y >> 31) {
+        // entries past the capped count of some bucket: on-the-fly twiddles
+        const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
+        for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
+          const uint32_t x = p.ovf_x[(static_cast<size_t>(t) * 2 + side) * n + o];
+          const uint32_t wv = p.hs[(static_cast<size_t>(t) * 2 + side) * n + x];
+          float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], p.b), p.tw_shift);
+          float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], p.b), p.tw_shift);
+          if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
+          const float v0 = st[x];
+          const float v1 = st[p.npad + x];
+          a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
+          a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
+          a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
+          a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
+        }
       }
-      work[((0 * 2 + side) * kG + 0) * kC + z2] = a00;
-      work[((0 * 2 + side) * kG + 1) * kC + z2] = a01;
-      work[((1 * 2 + side) * kG + 0) * kC + z2] = a10;
-      work[((1 * 2 + side) * kG + 1) * kC + z2] = a11;
+      work[((0 * 2 + side) * kG + 0) * kRegion + z2] = a00;
+      work[((0 * 2 + side) * kG + 1) * kRegion + z2] = a01;
+      work[((1 * 2 + side) * kG + 0) * kRegion + z2] = a10;
+      work[((1 * 2 + side) * kG + 1) * kRegion + z2] = a11;
     }
     __syncthreads();
     // staging consumed: fetch the next group while the FFTs run
@@ -411,50 +427,65 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
       }
     }
     __syncwarp();
+    // transpose through the padded region: T[f][lane] at f * 33 + lane
 #pragma unroll
-    for (int f = 0; f < 32; ++f) region[f * 32 + (lane ^ f)] = x[f];
+    for (int f = 0; f < 32; ++f) region[f * kPitch + lane] = x[f];
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = region[lane * 32 + (j ^ lane)];
+    for (int j = 0; j < 32; ++j) x[j] = region[lane * kPitch + j];
     dft32<false>(x);
     __syncwarp();
-    if (side_w == 1) {
+    // hand the partner the half of the bins it accumulates (register indices
+    // must stay compile-time constants: one branch per side)
+    if (side_w == 0) {
 #pragma unroll
-      for (int m = 0; m < 32; ++m) region[lane + 32 * m] = x[m];
+      for (int m = 16; m < 32; ++m) region[lane + 32 * m] = x[m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) region[lane + 32 * m] = x[m];
     }
     __syncthreads();
-    // ---- spectral products (side-a warps) --------------------------------
-    if (side_w == 0 && g_w < gcnt) {
-      const float2* pb = work + ((row_w * 2 + 1) * kG + g_w) * kC;
+    // ---- spectral products: own half of the bins -------------------------
+    if (g_w < gcnt) {
+      if (side_w == 0) {
 #pragma unroll
-      for (int m = 0; m < 32; ++m) {
-        const float2 q = pb[lane + 32 * m];
-        part[m].x = fmaf(x[m].x, q.x, part[m].x);
-        part[m].x = fmaf(-x[m].y, q.y, part[m].x);
-        part[m].y = fmaf(x[m].x, q.y, part[m].y);
-        part[m].y = fmaf(x[m].y, q.x, part[m].y);
+        for (int m = 0; m < 16; ++m) {
+          const float2 q = partner[lane + 32 * m];
+          part[m].x = fmaf(x[m].x, q.x, part[m].x);
+          part[m].x = fmaf(-x[m].y, q.y, part[m].x);
+          part[m].y = fmaf(x[m].x, q.y, part[m].y);
+          part[m].y = fmaf(x[m].y, q.x, part[m].y);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const float2 q = partner[lane + 32 * (16 + m)];
+          part[m].x = fmaf(x[16 + m].x, q.x, part[m].x);
+          part[m].x = fmaf(-x[16 + m].y, q.y, part[m].x);
+          part[m].y = fmaf(x[16 + m].x, q.y, part[m].y);
+          part[m].y = fmaf(x[16 + m].y, q.x, part[m].y);
+        }
       }
     }
     // ---- fold the partial sums into the Kahan accumulators ---------------
     const bool last = k0 + kG >= k_end;
     if ((group % kFlush) == kFlush - 1 || last) {
       __syncthreads();
-      if (side_w == 0) {
 #pragma unroll
-        for (int m = 0; m < 32; ++m) {
-          region[lane + 32 * m] = part[m];
-          part[m] = make_float2(0.f, 0.f);
-        }
+      for (int m = 0; m < 16; ++m) {
+        region[lane + 32 * (own_m0 + m)] = part[m];
+        part[m] = make_float2(0.f, 0.f);
       }
       __syncthreads();
 #pragma unroll
       for (int u = 0; u < (kRows * kC) / kThreads; ++u) {
         const int idx = tid + kThreads * u;
         const int r = idx / kC, f = idx % kC;
-        float2 s = work[((r * 2 + 0) * kG + 0) * kC + f];
+        const int sd = f >> 9;            // bins f < 512 live with side a, the rest with side b
+        float2 s = work[((r * 2 + sd) * kG + 0) * kRegion + f];
 #pragma unroll
         for (int g = 1; g < kG; ++g) {
-          const float2 v = work[((r * 2 + 0) * kG + g) * kC + f];
+          const float2 v = work[((r * 2 + sd) * kG + g) * kRegion + f];
           s.x += v.x;
           s.y += v.y;
         }

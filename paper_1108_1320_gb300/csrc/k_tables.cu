@@ -185,9 +185,11 @@ k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
       uint32_t m = 0;
       for (int i = 0; i < 32; ++i)
         m = max(m, min(cnt[key[32 * g + i] & 0xFFFFu], static_cast<uint32_t>(kFeCap)));
+      uint32_t any_ovf = 0;
+      for (int i = 0; i < 32; ++i) any_ovf |= cnt[key[32 * g + i] & 0xFFFFu] > static_cast<uint32_t>(kFeCap);
       gbase[g] = run;
       gp[2 * g] = run;
-      gp[2 * g + 1] = m;
+      gp[2 * g + 1] = m | (any_ovf << 31);   // bit 31: some bucket of the group overflows
       run += 32u * m;
     }
     uint32_t o = 0;
