@@ -186,6 +186,13 @@ __device__ __forceinline__ float2 wb(const float2* tlo, const float2* thi, uint3
   return cmul(thi[m >> sh], tlo[m & ((1u << sh) - 1u)]);
 }
 
+// w_b^m directly (rare overflow entries, after the tables are recycled).
+__device__ __forceinline__ float2 wb_direct(uint32_t m, int64_t b) {
+  double s, c;
+  sincospi(2.0 * static_cast<double>(m) / static_cast<double>(b), &s, &c);
+  return make_float2(static_cast<float>(c), static_cast<float>(-s));
+}
+
 __device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, int64_t b) {
   return static_cast<uint32_t>((static_cast<uint64_t>(h) * f1) % static_cast<uint64_t>(b));
 }
@@ -193,6 +200,7 @@ __device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, int64_t b) {
 struct SmemLayout {
   size_t stage, rec_tw, rec_x, work, acc, tlo, thi, grp, dest, ovf, bar, total;
 };
+// (tlo, thi) and the FFT twiddle table share one region; see fast_layout.
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
@@ -205,8 +213,12 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   L.rec_x = o;  o = al16(o + static_cast<size_t>(2) * ecap * 2);
   L.work = o;   o = al16(o + static_cast<size_t>(kRows * 2 * kG) * kRegion * 8);
   L.acc = o;    o = al16(o + static_cast<size_t>(kRows) * kC * 16);
-  L.tlo = o;    o = al16(o + (static_cast<size_t>(1) << tw_shift) * 8);
-  L.thi = o;    o = al16(o + static_cast<size_t>(nhi) * 8);
+  // the two-level w_b tables are needed only while the records are built;
+  // afterwards the same bytes hold the w_1024^{lane f} table of the FFT
+  const size_t tables = (static_cast<size_t>(1) << tw_shift) * 8 + static_cast<size_t>(nhi) * 8;
+  L.tlo = o;
+  L.thi = o + (static_cast<size_t>(1) << tw_shift) * 8;
+  o = al16(o + (tables > static_cast<size_t>(kC) * 8 ? tables : static_cast<size_t>(kC) * 8));
   L.grp = o;    o = al16(o + static_cast<size_t>(2) * (kC / 32) * 2 * 4);
   L.dest = o;   o = al16(o + static_cast<size_t>(2) * kC * 2);
   L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
@@ -299,18 +311,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
       rec_x[side * p.ecap + e] = static_cast<uint16_t>(min(x, static_cast<uint32_t>(n)));
     }
   }
-  // lane twiddle anchors w_1024^{lane * 8 q}, q = 0..3, and the step w_1024^lane
-  float2 anchor[4];
-  float2 step;
-  {
+  __syncthreads();
+  // the w_b tables are no longer needed: build the FFT twiddle table
+  // twtab[f * 32 + l] = w_1024^{l f} in their place (conflict-free reads)
+  float2* twtab = tlo;
+  for (int i = tid; i < kC; i += kThreads) {
+    const int f = i >> 5, l = i & 31;
     float s, c;
-    sincospif(2.0f * static_cast<float>(lane) / static_cast<float>(kC), &s, &c);
-    step = make_float2(c, -s);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      sincospif(2.0f * static_cast<float>((lane * 8 * q) & (kC - 1)) / static_cast<float>(kC), &s, &c);
-      anchor[q] = make_float2(c, -s);
-    }
+    sincospif(2.0f * static_cast<float>((l * f) & (kC - 1)) / static_cast<float>(kC), &s, &c);
+    twtab[i] = make_float2(c, -s);
   }
 
   // issue the TMA copies of the group starting at k0 (thread 0 only)
@@ -376,16 +385,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
       const float4* tw = rec_tw + side * p.ecap + base + lane;
       const uint16_t* xs = rec_x + side * p.ecap + base + lane;
       float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
-#pragma unroll 2
-      for (uint32_t e = 0; e < cnt; ++e) {
-        const int x = xs[32 * e];
-        const float4 w = tw[32 * e];
-        const float v0 = st[x];
-        const float v1 = st[p.npad + x];
-        a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
-        a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
-        a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
-        a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
+      // all loads of the bucket's (at most kFeCap) entries first, then the math
+      int xv[kFeCap];
+      float4 wrec[kFeCap];
+#pragma unroll
+      for (int e = 0; e < kFeCap; ++e) {
+        if (e < static_cast<int>(cnt)) {
+          xv[e] = xs[32 * e];
+          wrec[e] = tw[32 * e];
+        }
+      }
+      float v0[kFeCap], v1[kFeCap];
+#pragma unroll
+      for (int e = 0; e < kFeCap; ++e) {
+        if (e < static_cast<int>(cnt)) {
+          v0[e] = st[xv[e]];
+          v1[e] = st[p.npad + xv[e]];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < kFeCap; ++e) {
+        if (e < static_cast<int>(cnt)) {
+          const float4 w = wrec[e];
+          a00.x = fmaf(v0[e], w.x, a00.x); a00.y = fmaf(v0[e], w.y, a00.y);
+          a01.x = fmaf(v1[e], w.x, a01.x); a01.y = fmaf(v1[e], w.y, a01.y);
+          a10.x = fmaf(v0[e], w.z, a10.x); a10.y = fmaf(v0[e], w.w, a10.y);
+          a11.x = fmaf(v1[e], w.z, a11.x); a11.y = fmaf(v1[e], w.w, a11.y);
+        }
       }
       if (gd.y >> 31) {
         // entries past the capped count of some bucket: on-the-fly twiddles
@@ -393,8 +419,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
         for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
           const uint32_t x = p.ovf_x[(static_cast<size_t>(t) * 2 + side) * n + o];
           const uint32_t wv = p.hs[(static_cast<size_t>(t) * 2 + side) * n + x];
-          float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], p.b), p.tw_shift);
-          float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], p.b), p.tw_shift);
+          float2 w0 = wb_direct(mulmod(wv & kBucketMask, f1r[0], p.b), p.b);
+          float2 w1 = wb_direct(mulmod(wv & kBucketMask, f1r[1], p.b), p.b);
           if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
           const float v0 = st[x];
           const float v1 = st[p.npad + x];
@@ -418,14 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
     dft32<false>(x);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float2 w = anchor[q];
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        if (q + r > 0) x[8 * q + r] = cmul(x[8 * q + r], w);
-        w = cmul(w, step);
-      }
-    }
+    for (int f = 1; f < 32; ++f) x[f] = cmul(x[f], twtab[f * 32 + lane]);
     __syncwarp();
     // transpose through the padded region: T[f][lane] at f * 33 + lane
 #pragma unroll
