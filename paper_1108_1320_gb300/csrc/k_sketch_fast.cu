@@ -186,11 +186,14 @@ __device__ __forceinline__ float2 wb(const float2* tlo, const float2* thi, uint3
   return cmul(thi[m >> sh], tlo[m & ((1u << sh) - 1u)]);
 }
 
-// w_b^m directly (rare overflow entries, after the tables are recycled).
+// w_b^m directly in FP32 (overflow entries, after the tables are recycled):
+// the argument 2m/b is reduced to (-1, 1] first and is exact for power-of-two
+// b; sincospif keeps the result within a few ulp.
 __device__ __forceinline__ float2 wb_direct(uint32_t m, int64_t b) {
-  double s, c;
-  sincospi(2.0 * static_cast<double>(m) / static_cast<double>(b), &s, &c);
-  return make_float2(static_cast<float>(c), static_cast<float>(-s));
+  const int64_t mm = 2 * static_cast<int64_t>(m) > b ? static_cast<int64_t>(m) - b : static_cast<int64_t>(m);
+  float s, c;
+  sincospif(2.0f * static_cast<float>(mm) / static_cast<float>(b), &s, &c);
+  return make_float2(c, -s);
 }
 
 __device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, int64_t b) {
