@@ -65,7 +65,7 @@ cudaError_t launch_bucket_sort(const uint32_t* hs, int d, int64_t n, int64_t C,
 
 // Front-end record tables of the C = 1024 fused kernel.
 constexpr int kFeC = 1024;        // FFT length of the specialised kernel
-constexpr int kFeCap = 6;         // bucket entries kept in the padded layout
+constexpr int kFeCap = 8;         // bucket entries kept in the padded layout
 cudaError_t launch_frontend_tables(const uint32_t* hs, int d, int64_t n, uint32_t ecap,
                                    uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
                                    uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,

@@ -186,16 +186,6 @@ __device__ __forceinline__ float2 wb(const float2* tlo, const float2* thi, uint3
   return cmul(thi[m >> sh], tlo[m & ((1u << sh) - 1u)]);
 }
 
-// w_b^m directly in FP32 (overflow entries, after the tables are recycled):
-// the argument 2m/b is reduced to (-1, 1] first and is exact for power-of-two
-// b; sincospif keeps the result within a few ulp.
-__device__ __forceinline__ float2 wb_direct(uint32_t m, int64_t b) {
-  const int64_t mm = 2 * static_cast<int64_t>(m) > b ? static_cast<int64_t>(m) - b : static_cast<int64_t>(m);
-  float s, c;
-  sincospif(2.0f * static_cast<float>(mm) / static_cast<float>(b), &s, &c);
-  return make_float2(c, -s);
-}
-
 __device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, int64_t b) {
   return static_cast<uint32_t>((static_cast<uint64_t>(h) * f1) % static_cast<uint64_t>(b));
 }
@@ -203,7 +193,6 @@ __device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, int64_t b) {
 struct SmemLayout {
   size_t stage, rec_tw, rec_x, work, acc, tlo, thi, grp, dest, ovf, bar, total;
 };
-// (tlo, thi) and the FFT twiddle table share one region; see fast_layout.
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
@@ -216,12 +205,8 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   L.rec_x = o;  o = al16(o + static_cast<size_t>(2) * ecap * 2);
   L.work = o;   o = al16(o + static_cast<size_t>(kRows * 2 * kG) * kRegion * 8);
   L.acc = o;    o = al16(o + static_cast<size_t>(kRows) * kC * 16);
-  // the two-level w_b tables are needed only while the records are built;
-  // afterwards the same bytes hold the w_1024^{lane f} table of the FFT
-  const size_t tables = (static_cast<size_t>(1) << tw_shift) * 8 + static_cast<size_t>(nhi) * 8;
-  L.tlo = o;
-  L.thi = o + (static_cast<size_t>(1) << tw_shift) * 8;
-  o = al16(o + (tables > static_cast<size_t>(kC) * 8 ? tables : static_cast<size_t>(kC) * 8));
+  L.tlo = o;    o = al16(o + (static_cast<size_t>(1) << tw_shift) * 8);
+  L.thi = o;    o = al16(o + static_cast<size_t>(nhi) * 8);
   L.grp = o;    o = al16(o + static_cast<size_t>(2) * (kC / 32) * 2 * 4);
   L.dest = o;   o = al16(o + static_cast<size_t>(2) * kC * 2);
   L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
@@ -314,15 +299,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
       rec_x[side * p.ecap + e] = static_cast<uint16_t>(min(x, static_cast<uint32_t>(n)));
     }
   }
-  __syncthreads();
-  // the w_b tables are no longer needed: build the FFT twiddle table
-  // twtab[f * 32 + l] = w_1024^{l f} in their place (conflict-free reads)
-  float2* twtab = tlo;
-  for (int i = tid; i < kC; i += kThreads) {
-    const int f = i >> 5, l = i & 31;
+  // lane twiddle anchors w_1024^{lane * 8 q}, q = 0..3, and the step w_1024^lane
+  float2 anchor[4];
+  float2 step;
+  {
     float s, c;
-    sincospif(2.0f * static_cast<float>((l * f) & (kC - 1)) / static_cast<float>(kC), &s, &c);
-    twtab[i] = make_float2(c, -s);
+    sincospif(2.0f * static_cast<float>(lane) / static_cast<float>(kC), &s, &c);
+    step = make_float2(c, -s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sincospif(2.0f * static_cast<float>((lane * 8 * q) & (kC - 1)) / static_cast<float>(kC), &s, &c);
+      anchor[q] = make_float2(c, -s);
+    }
   }
 
   // issue the TMA copies of the group starting at k0 (thread 0 only)
@@ -422,8 +410,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
         for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
           const uint32_t x = p.ovf_x[(static_cast<size_t>(t) * 2 + side) * n + o];
           const uint32_t wv = p.hs[(static_cast<size_t>(t) * 2 + side) * n + x];
-          float2 w0 = wb_direct(mulmod(wv & kBucketMask, f1r[0], p.b), p.b);
-          float2 w1 = wb_direct(mulmod(wv & kBucketMask, f1r[1], p.b), p.b);
+          float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], p.b), p.tw_shift);
+          float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], p.b), p.tw_shift);
           if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
           const float v0 = st[x];
           const float v1 = st[p.npad + x];
@@ -447,7 +435,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
     dft32<false>(x);
 #pragma unroll
-    for (int f = 1; f < 32; ++f) x[f] = cmul(x[f], twtab[f * 32 + lane]);
+    for (int q = 0; q < 4; ++q) {
+      float2 w = anchor[q];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (q + r > 0) x[8 * q + r] = cmul(x[8 * q + r], w);
+        w = cmul(w, step);
+      }
+    }
     __syncwarp();
     // transpose through the padded region: T[f][lane] at f * 33 + lane
 #pragma unroll
