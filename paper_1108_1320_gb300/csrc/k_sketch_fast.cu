@@ -376,33 +376,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
       const float4* tw = rec_tw + side * p.ecap + base + lane;
       const uint16_t* xs = rec_x + side * p.ecap + base + lane;
       float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
-      // all loads of the bucket's (at most kFeCap) entries first, then the math
-      int xv[kFeCap];
-      float4 wrec[kFeCap];
-#pragma unroll
-      for (int e = 0; e < kFeCap; ++e) {
-        if (e < static_cast<int>(cnt)) {
-          xv[e] = xs[32 * e];
-          wrec[e] = tw[32 * e];
-        }
-      }
-      float v0[kFeCap], v1[kFeCap];
-#pragma unroll
-      for (int e = 0; e < kFeCap; ++e) {
-        if (e < static_cast<int>(cnt)) {
-          v0[e] = st[xv[e]];
-          v1[e] = st[p.npad + xv[e]];
-        }
-      }
-#pragma unroll
-      for (int e = 0; e < kFeCap; ++e) {
-        if (e < static_cast<int>(cnt)) {
-          const float4 w = wrec[e];
-          a00.x = fmaf(v0[e], w.x, a00.x); a00.y = fmaf(v0[e], w.y, a00.y);
-          a01.x = fmaf(v1[e], w.x, a01.x); a01.y = fmaf(v1[e], w.y, a01.y);
-          a10.x = fmaf(v0[e], w.z, a10.x); a10.y = fmaf(v0[e], w.w, a10.y);
-          a11.x = fmaf(v1[e], w.z, a11.x); a11.y = fmaf(v1[e], w.w, a11.y);
-        }
+#pragma unroll 2
+      for (uint32_t e = 0; e < cnt; ++e) {
+        const int x = xs[32 * e];
+        const float4 w = tw[32 * e];
+        const float v0 = st[x];
+        const float v1 = st[p.npad + x];
+        a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
+        a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
+        a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
+        a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
       }
       if (gd.y >> 31) {
         // entries past the capped count of some bucket: on-the-fly twiddles
