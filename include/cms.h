@@ -180,6 +180,32 @@ CMS_API cms_status cms_sketch_product_noalloc(const void* A, int64_t lda, const 
                                               void* stream);
 
 /*
+ * cms_sparse_workspace_size / cms_sketch_product_csr - COMPRESSEDPRODUCT for
+ * sparse inputs (Sec. 2.2: time O(N + n2 b lg b) when the nonzeros of a
+ * column of A and of a row of B can be listed in linear time; Theorem 5's
+ * exact recovery of sparse products).  Only inner indices k whose column
+ * a_k and row b_k both have nonzeros contribute; they are compacted on the
+ * device in increasing k.  Result as cms_sketch_product.
+ *   a_colptr : device int64 [n2 + 1], CSC column pointers of A (n1 x n2).
+ *   a_rowidx : device int32, row index of each nonzero of A (< n1).
+ *   a_val    : device values of A, storage type dt.
+ *   b_rowptr : device int64 [n2 + 1], CSR row pointers of B (n2 x n3).
+ *   b_colidx : device int32, column index of each nonzero of B (< n3).
+ *   b_val    : device values of B, storage type dt.
+ *   Indices outside [0, n1) / [0, n3) contribute nothing.
+ *   b must be a multiple of 1024 (CMS_ERR_UNSUPPORTED otherwise).
+ *   The call waits once for the stream (to read the number of nonempty k).
+ */
+CMS_API cms_status cms_sparse_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2,
+                                             int64_t n3, size_t* bytes);
+CMS_API cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t* a_rowidx,
+                                          const void* a_val, const int64_t* b_rowptr,
+                                          const int32_t* b_colidx, const void* b_val,
+                                          int64_t n1, int64_t n2, int64_t n3, int32_t dt,
+                                          const cms_hashes* h, float* c, void* ws,
+                                          size_t ws_bytes, void* stream);
+
+/*
  * cms_plain_workspace_size / cms_sketch_product_plain_f64 - the same sketch
  * (Fig. 1) in plain form: FP64 throughout, one instance per call, unfused
  * passes (scatter, FFT, spectral product, inverse FFT each a separate

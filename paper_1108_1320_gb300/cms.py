@@ -44,6 +44,9 @@ SIGNATURES = {
     "cms_workspace_size": (_I32, [_P, _I64, _I64, _I64, _I32, ctypes.POINTER(_SZ)]),
     "cms_sketch_product": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P, _SZ, _P]),
     "cms_sketch_product_noalloc": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P]),
+    "cms_sparse_workspace_size": (_I32, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
+    "cms_sketch_product_csr": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _P, _P, _SZ,
+                                      _P]),
     "cms_plain_workspace_size": (_I32, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
     "cms_sketch_product_plain_f64": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _P, _P, _P, _SZ,
                                             _P]),
@@ -230,6 +233,39 @@ def sketch_product_noalloc(A: torch.Tensor, B: torch.Tensor, h: Hashes,
         c = torch.empty((inf["d"], inf["b"]), dtype=torch.float32, device=A.device)
     _check(lib().cms_sketch_product_noalloc(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype],
                                             h.handle, _ptr(c), _stream(stream)))
+    return c
+
+
+def sparse_workspace_size(h: Hashes, n1: int, n2: int, n3: int) -> int:
+    out = _SZ()
+    _check(lib().cms_sparse_workspace_size(h.handle, n1, n2, n3, ctypes.byref(out)))
+    return out.value
+
+
+def sketch_product_csr(a_colptr: torch.Tensor, a_rowidx: torch.Tensor, a_val: torch.Tensor,
+                       b_rowptr: torch.Tensor, b_colidx: torch.Tensor, b_val: torch.Tensor,
+                       n1: int, n3: int, h: Hashes, c: torch.Tensor | None = None,
+                       ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """COMPRESSEDPRODUCT of sparse A (CSC: colptr int64, rowidx int32) and B
+    (CSR: rowptr int64, colidx int32); returns c float32 (d, b)."""
+    n2 = a_colptr.numel() - 1
+    if b_rowptr.numel() - 1 != n2:
+        raise ValueError("A and B disagree on the inner dimension")
+    for t_, dt_ in ((a_colptr, torch.int64), (b_rowptr, torch.int64), (a_rowidx, torch.int32),
+                    (b_colidx, torch.int32)):
+        if t_.dtype != dt_ or not t_.is_cuda or not t_.is_contiguous():
+            raise ValueError("pointer arrays must be contiguous CUDA int64, index arrays int32")
+    if a_val.dtype != b_val.dtype or a_val.dtype not in _DTYPES:
+        raise ValueError("values must share a dtype in {float32, bfloat16, float64}")
+    inf = h.info()
+    if c is None:
+        c = torch.empty((inf["d"], inf["b"]), dtype=torch.float32, device=a_colptr.device)
+    if ws is None:
+        ws = alloc_workspace(sparse_workspace_size(h, n1, n2, n3), a_colptr.device)
+    _check(lib().cms_sketch_product_csr(_ptr(a_colptr), _ptr(a_rowidx), _ptr(a_val), _ptr(b_rowptr),
+                                        _ptr(b_colidx), _ptr(b_val), n1, n2, n3, _DTYPES[a_val.dtype],
+                                        h.handle, _ptr(c), _ptr(ws), ws.numel() * ws.element_size(),
+                                        _stream(stream)))
     return c
 
 

@@ -340,6 +340,69 @@ cms_status cms_sketch_product(const void* A, int64_t lda, const void* B, int64_t
   return CMS_OK;
 }
 
+cms_status cms_sparse_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
+                                     size_t* bytes) {
+  if (!bytes) return fail(CMS_ERR_INVALID_ARG, "bytes is NULL");
+  cms_status st = check_shapes(h, n1, n2, n3, std::max<int64_t>(n1, 1), std::max<int64_t>(n3, 1));
+  if (st != CMS_OK) return st;
+  DeviceProps dp = device_props(h->device);
+  SketchPlan plan;
+  size_t off_klist = 0;
+  std::string why;
+  int r = make_sparse_plan(h, n2, -1, dp.sms, &plan, &off_klist, &why);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  *bytes = plan.ws_bytes;
+  return CMS_OK;
+}
+
+cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t* a_rowidx, const void* a_val,
+                                  const int64_t* b_rowptr, const int32_t* b_colidx, const void* b_val,
+                                  int64_t n1, int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h,
+                                  float* c, void* ws, size_t ws_bytes, void* stream) {
+  cms_status st = check_shapes(h, n1, n2, n3, std::max<int64_t>(n1, 1), std::max<int64_t>(n3, 1));
+  if (st != CMS_OK) return st;
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  if (!c) return fail(CMS_ERR_INVALID_ARG, "c is NULL");
+  if (n2 > 0 && (!a_colptr || !b_rowptr)) return fail(CMS_ERR_INVALID_ARG, "pointer array is NULL");
+  if (n2 >= (1LL << 31) - 1) return fail(CMS_ERR_INVALID_ARG, "n2 too large for int32 inner indices");
+  st = check_device(h);
+  if (st != CMS_OK) return st;
+  DeviceProps dp = device_props(h->device);
+  SketchPlan worst;
+  size_t off_klist = 0;
+  std::string why;
+  int r = make_sparse_plan(h, n2, -1, dp.sms, &worst, &off_klist, &why);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  if (!ws || ws_bytes < worst.ws_bytes)
+    return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_sparse_workspace_size()");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(CMS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  int32_t* klist = reinterpret_cast<int32_t*>(w + off_klist);
+  int32_t K = 0;
+  cudaError_t e = cudaSuccess;
+  if (n2 > 0) {
+    e = launch_nonempty(a_colptr, b_rowptr, n2, klist, klist + n2, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&K, klist + n2, sizeof(K), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr (nonempty inner indices)");
+  }
+  SketchPlan plan;
+  r = make_sparse_plan(h, n2, K, dp.sms, &plan, &off_klist, &why);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  float2* partial = reinterpret_cast<float2*>(w + plan.off_partial);
+  float2* V = reinterpret_cast<float2*>(w + plan.off_V);
+  float2* twC = reinterpret_cast<float2*>(w + plan.off_twC);
+  float2* twR = reinterpret_cast<float2*>(w + plan.off_twR);
+  SparseArgsHost in{a_colptr, a_rowidx, a_val, b_rowptr, b_colidx, b_val, static_cast<int>(n1),
+                    static_cast<int>(n3)};
+  e = launch_twiddle_tables(twC, static_cast<int>(plan.C), twR, static_cast<int>(plan.R), s);
+  if (e == cudaSuccess) e = launch_sketch_sparse(plan, h, in, dt, klist, K, partial, s);
+  if (e == cudaSuccess) e = launch_inverse(plan, partial, V, twC, twR, c, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr");
+  return CMS_OK;
+}
+
 cms_status cms_plain_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
                                     size_t* bytes) {
   if (!bytes) return fail(CMS_ERR_INVALID_ARG, "bytes is NULL");

@@ -108,6 +108,25 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h,
                           int64_t n1, int64_t n2, int64_t n3, int dt, float* c,
                           char* ws, cudaStream_t s);
 
+// Fixed-order reduction of the k-range partials, inverse FFT, 1/b (K2a, K2b);
+// twC / twR must hold w_C^m and w_R^m (launch_twiddle_tables).
+cudaError_t launch_inverse(const SketchPlan& plan, const float2* partial, float2* V, const float2* twC,
+                           const float2* twR, float* c, cudaStream_t s);
+cudaError_t launch_twiddle_tables(float2* twC, int C, float2* twR, int R, cudaStream_t s);
+
+// Sparse inputs (A by columns, B by rows).
+struct SparseArgsHost {
+  const int64_t* a_ptr; const int32_t* a_idx; const void* a_val;
+  const int64_t* b_ptr; const int32_t* b_idx; const void* b_val;
+  int n1, n3;
+};
+int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, SketchPlan* plan,
+                     size_t* off_klist, std::string* why);
+cudaError_t launch_nonempty(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int32_t* klist,
+                            int32_t* kcount, cudaStream_t s);
+cudaError_t launch_sketch_sparse(const SketchPlan& plan, const cms_hashes* h, const SparseArgsHost& in,
+                                 int dt, const int32_t* klist, int K, float2* partial, cudaStream_t s);
+
 cudaError_t launch_decode_pairs_f32(const float* c, const cms_hashes* h,
                                     const int64_t* ij, int64_t q, float* out,
                                     cudaStream_t s);

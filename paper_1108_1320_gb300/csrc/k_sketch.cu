@@ -455,6 +455,24 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   if (e != cudaSuccess) return e;
   }
 
+  return launch_inverse(plan, partial, V, twC, twR, c, s);
+}
+
+cudaError_t launch_twiddle_tables(float2* twC, int C, float2* twR, int R, cudaStream_t s) {
+  {
+    ProfScope prof_scope("k_twiddle_table", s);
+    k_twiddle_table<<<static_cast<unsigned>((C + 255) / 256), 256, 0, s>>>(twC, C);
+  }
+  {
+    ProfScope prof_scope("k_twiddle_table", s);
+    k_twiddle_table<<<static_cast<unsigned>((R + 255) / 256), 256, 0, s>>>(twR, R);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inverse(const SketchPlan& plan, const float2* partial, float2* V, const float2* twC,
+                           const float2* twR, float* c, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   InvArgs ia{};
   ia.b = plan.b; ia.R = static_cast<int>(plan.R); ia.C = static_cast<int>(plan.C);
   ia.nrows = plan.nrows; ia.d = plan.d; ia.nkc = plan.nkc;

@@ -27,9 +27,12 @@
 #include <algorithm>
 
 #include "cms_internal.h"
+#include "warp_fft.cuh"
 
 namespace cms {
 namespace {
+
+using namespace wfft;
 
 constexpr int kC = kFeC;       // 1024
 constexpr int kG = 2;          // inner indices per group
@@ -38,7 +41,6 @@ constexpr int kThreads = 256;  // 8 warps = kRows x 2 sides x kG FFTs
 constexpr int kFlush = 16;     // groups between Kahan folds
 constexpr int kPitch = 33;     // transpose row pitch (float2): conflict-free both ways
 constexpr int kRegion = 32 * kPitch;   // float2 per warp region (>= kC)
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
 
 __device__ uint32_t g_sketch_error = 0;   // 1: a TMA wait gave up
 
@@ -63,132 +65,6 @@ struct FastArgs {
   const uint32_t* hs;
   float2* partial;
 };
-
-// ------------------------------------------------------------ PTX helpers --
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait on an mbarrier phase: true when it completed, false after
-// kWaitLimitNs (the caller then reports the timeout and leaves).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  for (;;) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
-  }
-}
-
-// ------------------------------------------------------ radix-32 codelet --
-// w_32^e = exp(-2 pi i e / 32): cos and sin of 2 pi e / 32 for e = 0..8.
-__device__ __forceinline__ float c32(int e) {
-  constexpr float t[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
-                          0.83146961230254523708f, 0.70710678118654752440f,
-                          0.55557023301960222474f, 0.38268343236508977173f,
-                          0.19509032201612826785f, 0.0f};
-  return t[e];
-}
-
-// v * w_32^e (forward) or v * w_32^{-e} (inverse), e a compile-time constant
-// after unrolling; the trivial angles cost no multiplies.
-template <bool INV>
-__device__ __forceinline__ float2 tw32(float2 v, int e) {
-  e &= 31;
-  if (e == 0) return v;
-  if (e == 8) return mul_mi<INV>(v);
-  if (e == 16) return make_float2(-v.x, -v.y);
-  if (e == 24) return mul_mi<!INV>(v);
-  // cos(2 pi e/32), sin(2 pi e/32) from the first-octant table
-  const int q = e >> 3, r = e & 7;
-  float c, s;
-  if (q == 0) { c = c32(r);     s = c32(8 - r); }
-  else if (q == 1) { c = -c32(8 - r); s = c32(r); }
-  else if (q == 2) { c = -c32(r); s = -c32(8 - r); }
-  else { c = c32(8 - r); s = -c32(r); }
-  // forward multiplies by c - i s, inverse by c + i s
-  const float si = INV ? -s : s;
-  return make_float2(v.x * c + v.y * si, v.y * c - v.x * si);
-}
-
-// In-register DFT of length 32 as 8 x DFT4 (stride 8), twiddles w_32^{n2 k1},
-// 4 x DFT8: x[k] = sum_j x[j] w_32^{jk} on return.
-template <bool INV>
-__device__ __forceinline__ void dft32(float2 (&x)[32]) {
-  float2 y[32];
-#pragma unroll
-  for (int n2 = 0; n2 < 8; ++n2) {
-    float2 u[4] = {x[n2], x[8 + n2], x[16 + n2], x[24 + n2]};
-    Dft<4, INV, float2>::run(u);
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) y[n2 * 4 + k1] = tw32<INV>(u[k1], n2 * k1);
-  }
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) {
-    float2 v[8];
-#pragma unroll
-    for (int n2 = 0; n2 < 8; ++n2) v[n2] = y[n2 * 4 + k1];
-    Dft<8, INV, float2>::run(v);
-#pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) x[k1 + 4 * k2] = v[k2];
-  }
-}
-
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
-// w_b^m from the two-level table: T_lo[m mod S] * T_hi[m div S].
-__device__ __forceinline__ float2 wb(const float2* tlo, const float2* thi, uint32_t m, int sh) {
-  return cmul(thi[m >> sh], tlo[m & ((1u << sh) - 1u)]);
-}
-
-__device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, int64_t b) {
-  return static_cast<uint32_t>((static_cast<uint64_t>(h) * f1) % static_cast<uint64_t>(b));
-}
 
 struct SmemLayout {
   size_t stage, rec_tw, rec_x, work, acc, tlo, thi, grp, dest, ovf, bar, total;

@@ -1,0 +1,405 @@
+// k_sketch_sparse.cu - COMPRESSEDPRODUCT for sparse inputs (Sec. 2.2, "A and
+// B sparse ... nonzeros of a column (row) retrieved in linear time";
+// Theorem 5's setting): A given by columns (CSC: colptr, rowidx, val), B by
+// rows (CSR: rowptr, colidx, val).  Only inner indices k with a nonzero
+// column a_k AND a nonzero row b_k contribute; they are compacted first, in
+// increasing k, by a deterministic scan.
+//
+// The per-k work is the same four-step split as the dense kernels
+// (b = R * 1024, a block owns one row f1 for one repetition and a range of
+// nonempty k): the pruned first stage scatters the few nonzeros of a_k / b_k
+// into Y[f1][z2] = sum s(x) v_x w_b^{f1 h(x)}, one warp per (side, k), in a
+// fixed order (lanes with distinct buckets add in parallel, colliding lanes
+// in lane order), then the radix-32 x radix-32 warp FFT, the spectral
+// product (split across the two sides' warps) and Kahan-compensated
+// accumulation, exactly as in k_sketch_fast.cu.
+#include <algorithm>
+
+#include "cms_internal.h"
+#include "warp_fft.cuh"
+
+namespace cms {
+namespace {
+
+using namespace wfft;
+
+constexpr int kC = kFeC;       // 1024
+constexpr int kG = 4;          // nonempty inner indices per group
+constexpr int kThreads = 256;  // 8 warps = 2 sides x kG
+constexpr int kFlush = 8;      // groups between Kahan folds
+constexpr int kPitch = 33;
+constexpr int kRegion = 32 * kPitch;
+
+struct SparseArgs {
+  const int64_t* ptr0;         // colptr of A (side 0)
+  const int64_t* ptr1;         // rowptr of B (side 1)
+  const int32_t* idx0;         // row indices of A
+  const int32_t* idx1;         // column indices of B
+  const void* val0;
+  const void* val1;
+  int nside0, nside1;          // n1, n3
+  int n;
+  int64_t b;
+  int nrows;
+  int kchunk, nkc;
+  const int32_t* klist;
+  int K;
+  const uint32_t* hs;
+  int tw_shift, nhi;
+  float2* partial;
+};
+
+template <typename T> __device__ __forceinline__ float ld_val(const void* p, int64_t e);
+template <> __device__ __forceinline__ float ld_val<float>(const void* p, int64_t e) {
+  return __ldg(static_cast<const float*>(p) + e);
+}
+template <> __device__ __forceinline__ float ld_val<double>(const void* p, int64_t e) {
+  return static_cast<float>(__ldg(static_cast<const double*>(p) + e));
+}
+template <> __device__ __forceinline__ float ld_val<__nv_bfloat16>(const void* p, int64_t e) {
+  return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[e]);
+}
+
+size_t sparse_smem_bytes(int tw_shift, int nhi) {
+  return static_cast<size_t>(2 * kG) * kRegion * 8 + static_cast<size_t>(kC) * 16 +
+         (static_cast<size_t>(1) << tw_shift) * 8 + static_cast<size_t>(nhi) * 8;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  float2* work = reinterpret_cast<float2*>(sm);
+  float4* acc = reinterpret_cast<float4*>(sm + static_cast<size_t>(2 * kG) * kRegion * 8);
+  float2* tlo = reinterpret_cast<float2*>(acc + kC);
+  float2* thi = tlo + (1 << p.tw_shift);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int task = blockIdx.x;
+  const int kc = task % p.nkc;
+  const int row = (task / p.nkc) % p.nrows;
+  const int t = task / (p.nkc * p.nrows);
+  const uint32_t f1 = static_cast<uint32_t>(row);
+  const int S = 1 << p.tw_shift;
+  const int l_begin = kc * p.kchunk;
+  const int l_end = min(p.K, l_begin + p.kchunk);
+
+  for (int i = tid; i < S; i += kThreads) {
+    float s, c;
+    sincospif(2.0f * static_cast<float>(i) / static_cast<float>(p.b), &s, &c);
+    tlo[i] = make_float2(c, -s);
+  }
+  for (int i = tid; i < p.nhi; i += kThreads) {
+    const double a = 2.0 * static_cast<double>(static_cast<int64_t>(i) * S) / static_cast<double>(p.b);
+    double s, c;
+    sincospi(a, &s, &c);
+    thi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+  }
+  for (int i = tid; i < kC; i += kThreads) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 anchor[4];
+  float2 step;
+  {
+    float s, c;
+    sincospif(2.0f * static_cast<float>(lane) / static_cast<float>(kC), &s, &c);
+    step = make_float2(c, -s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sincospif(2.0f * static_cast<float>((lane * 8 * q) & (kC - 1)) / static_cast<float>(kC), &s, &c);
+      anchor[q] = make_float2(c, -s);
+    }
+  }
+  __syncthreads();
+
+  const int side_w = warp / kG;
+  const int g_w = warp % kG;
+  float2* region = work + warp * kRegion;
+  const float2* partner = work + (warp ^ kG) * kRegion;   // same k slot, other side
+  const uint32_t* tab = p.hs + (static_cast<size_t>(t) * 2 + side_w) * p.n;
+  const int64_t* ptr = side_w ? p.ptr1 : p.ptr0;
+  const int32_t* idx = side_w ? p.idx1 : p.idx0;
+  const void* val = side_w ? p.val1 : p.val0;
+  const int nside = side_w ? p.nside1 : p.nside0;
+
+  float2 part[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) part[m] = make_float2(0.f, 0.f);
+
+  int group = 0;
+  for (int l0 = l_begin; l0 < l_end; l0 += kG, ++group) {
+    const int gcnt = min(kG, l_end - l0);
+    // ---- zero this warp's Y and scatter the nonzeros of its (side, k) ----
+    float4* r4 = reinterpret_cast<float4*>(region);
+#pragma unroll
+    for (int i = 0; i < kC / 2 / 32; ++i) r4[lane + 32 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    if (g_w < gcnt) {
+      const int k = p.klist[l0 + g_w];
+      const int64_t e0 = ptr[k], e1 = ptr[k + 1];
+      for (int64_t base = e0; base < e1; base += 32) {
+        const int64_t e = base + lane;
+        const bool valid = e < e1;
+        uint32_t z2 = 0x80000000u | static_cast<uint32_t>(lane);   // unique sentinel
+        float2 contrib = make_float2(0.f, 0.f);
+        if (valid) {
+          const int32_t x = idx[e];
+          const float v = ld_val<T>(val, e);
+          if (x >= 0 && x < nside) {
+            const uint32_t w = __ldg(tab + x);
+            const uint32_t h = w & kBucketMask;
+            float2 tw = wb(tlo, thi, mulmod(h, f1, p.b), p.tw_shift);
+            if (w >> 31) { tw.x = -tw.x; tw.y = -tw.y; }
+            contrib = make_float2(v * tw.x, v * tw.y);
+            z2 = h & (kC - 1);
+          }
+        }
+        const uint32_t same = __match_any_sync(0xFFFFFFFFu, z2);
+        const bool collide = __any_sync(0xFFFFFFFFu, __popc(same) > 1);
+        if (!collide) {
+          if (!(z2 >> 31)) {
+            float2 y = region[z2];
+            y.x += contrib.x;
+            y.y += contrib.y;
+            region[z2] = y;
+          }
+        } else {
+          for (int l = 0; l < 32; ++l) {
+            if (lane == l && !(z2 >> 31)) {
+              float2 y = region[z2];
+              y.x += contrib.x;
+              y.y += contrib.y;
+              region[z2] = y;
+            }
+            __syncwarp();
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    // ---- FFT of length 1024 ----------------------------------------------
+    float2 x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
+    dft32<false>(x);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 w = anchor[q];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (q + r > 0) x[8 * q + r] = cmul(x[8 * q + r], w);
+        w = cmul(w, step);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < 32; ++f) region[f * kPitch + lane] = x[f];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = region[lane * kPitch + j];
+    dft32<false>(x);
+    __syncwarp();
+    if (side_w == 0) {
+#pragma unroll
+      for (int m = 16; m < 32; ++m) region[lane + 32 * m] = x[m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) region[lane + 32 * m] = x[m];
+    }
+    __syncthreads();
+    if (g_w < gcnt) {
+      if (side_w == 0) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const float2 q = partner[lane + 32 * m];
+          part[m].x = fmaf(x[m].x, q.x, part[m].x);
+          part[m].x = fmaf(-x[m].y, q.y, part[m].x);
+          part[m].y = fmaf(x[m].x, q.y, part[m].y);
+          part[m].y = fmaf(x[m].y, q.x, part[m].y);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const float2 q = partner[lane + 32 * (16 + m)];
+          part[m].x = fmaf(x[16 + m].x, q.x, part[m].x);
+          part[m].x = fmaf(-x[16 + m].y, q.y, part[m].x);
+          part[m].y = fmaf(x[16 + m].x, q.y, part[m].y);
+          part[m].y = fmaf(x[16 + m].y, q.x, part[m].y);
+        }
+      }
+    }
+    const bool last = l0 + kG >= l_end;
+    if ((group % kFlush) == kFlush - 1 || last) {
+      __syncthreads();
+      const int own = side_w * 16;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        region[lane + 32 * (own + m)] = part[m];
+        part[m] = make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < kC / kThreads; ++u) {
+        const int f = tid + kThreads * u;
+        const int sd = f >> 9;          // bins f < 512 live with side a
+        float2 s = work[(sd * kG + 0) * kRegion + f];
+#pragma unroll
+        for (int g = 1; g < kG; ++g) {
+          const float2 v = work[(sd * kG + g) * kRegion + f];
+          s.x += v.x;
+          s.y += v.y;
+        }
+        float4 a = acc[f];
+        kahan_add(a.x, a.z, s.x);
+        kahan_add(a.y, a.w, s.y);
+        acc[f] = a;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  float2* out = p.partial + ((static_cast<size_t>(t) * p.nrows + f1) * p.nkc + kc) * kC;
+  for (int f = tid; f < kC; f += kThreads) {
+    const float4 a = acc[f];
+    out[f] = make_float2(a.x - a.z, a.y - a.w);
+  }
+}
+
+// Compaction of the inner indices with a nonzero column of A and row of B,
+// in increasing k (one block; exclusive scan per chunk of 1024).
+__global__ void __launch_bounds__(1024)
+k_nonempty(const int64_t* __restrict__ a_ptr, const int64_t* __restrict__ b_ptr, int64_t n2,
+           int32_t* __restrict__ klist, int32_t* __restrict__ kcount) {
+  __shared__ int32_t warp_tot[32];
+  __shared__ int32_t running;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) running = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n2; base += 1024) {
+    const int64_t k = base + tid;
+    const int flag = (k < n2 && a_ptr[k + 1] > a_ptr[k] && b_ptr[k + 1] > b_ptr[k]) ? 1 : 0;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, flag);
+    const int in_warp = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_tot[w];
+    if (flag) klist[running + before + in_warp] = static_cast<int32_t>(k);
+    __syncthreads();
+    if (tid == 0) {
+      int tot = 0;
+      for (int w = 0; w < 32; ++w) tot += warp_tot[w];
+      running += tot;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *kcount = running;
+}
+
+}  // namespace
+
+int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, SketchPlan* plan,
+                     size_t* off_klist, std::string* why) {
+  SketchPlan p;
+  p.b = h->b;
+  p.d = h->d;
+  if (h->C != kFeC) {
+    *why = "the sparse path needs b to be a multiple of 1024 (b = R * 1024)";
+    return CMS_ERR_UNSUPPORTED;
+  }
+  p.R = h->R;
+  p.C = h->C;
+  p.nrows = static_cast<int>(p.R / 2 + 1);
+  p.nradC = factor_radices(p.C, p.radC, 16);
+  int sh = 0;
+  while ((static_cast<int64_t>(1) << (2 * sh)) < p.b) ++sh;
+  p.tw_shift = sh;
+  p.nhi = static_cast<int>((p.b + (static_cast<int64_t>(1) << sh) - 1) >> sh);
+  p.smem = sparse_smem_bytes(p.tw_shift, p.nhi);
+  p.G = kG;
+  p.threads = kThreads;
+  const int64_t units = static_cast<int64_t>(p.d) * p.nrows;
+  const int64_t slots = num_sms;
+  const int64_t lo = std::max<int64_t>(1, (2 * slots + units - 1) / units);
+  const int64_t hi = std::max<int64_t>(lo, 4 * lo);
+  // chunks over the list of nonempty k; the workspace covers the largest count
+  int64_t nkc;
+  if (K < 0) {
+    nkc = hi;
+  } else {
+    nkc = 1;
+    double best = -1.0;
+    const int64_t maxc = std::max<int64_t>(1, (K + kG - 1) / kG);
+    for (int64_t c2 = std::min(lo, maxc); c2 <= std::min(hi, maxc); ++c2) {
+      const int64_t tasks = units * c2;
+      const int64_t waves = (tasks + slots - 1) / slots;
+      const double eff = static_cast<double>(tasks) / static_cast<double>(waves * slots);
+      if (eff > best + 1e-9) { best = eff; nkc = c2; }
+    }
+  }
+  const int64_t KK = K < 0 ? n2 : K;
+  int64_t kchunk = KK > 0 ? (KK + nkc - 1) / nkc : kG;
+  kchunk = ((kchunk + kG - 1) / kG) * kG;
+  if (K >= 0) nkc = KK > 0 ? (KK + kchunk - 1) / kchunk : 1;
+  p.kchunk = kchunk;
+  p.nkc = static_cast<int>(nkc);
+  auto align256 = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+  size_t off = 0;
+  p.off_partial = off; off = align256(off + static_cast<size_t>(units) * hi * p.C * 8);
+  p.off_V = off;       off = align256(off + static_cast<size_t>(units) * p.C * 8);
+  p.off_twC = off;     off = align256(off + static_cast<size_t>(p.C) * 8);
+  p.off_twR = off;     off = align256(off + static_cast<size_t>(p.R) * 8);
+  *off_klist = off;    off = align256(off + static_cast<size_t>(std::max<int64_t>(n2, 1) + 1) * 4);
+  p.ws_bytes = off;
+  (void)why;
+  *plan = p;
+  return CMS_OK;
+}
+
+cudaError_t launch_nonempty(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int32_t* klist,
+                            int32_t* kcount, cudaStream_t s) {
+  {
+    ProfScope prof_scope("k_nonempty", s);
+    k_nonempty<<<1, 1024, 0, s>>>(a_ptr, b_ptr, n2, klist, kcount);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_sparse(const SketchPlan& plan, const cms_hashes* h, const SparseArgsHost& in,
+                                 int dt, const int32_t* klist, int K, float2* partial, cudaStream_t s) {
+  SparseArgs a{};
+  a.ptr0 = in.a_ptr; a.ptr1 = in.b_ptr;
+  a.idx0 = in.a_idx; a.idx1 = in.b_idx;
+  a.val0 = in.a_val; a.val1 = in.b_val;
+  a.n = static_cast<int>(h->n);
+  a.nside0 = in.n1; a.nside1 = in.n3;
+  a.b = plan.b;
+  a.nrows = plan.nrows;
+  a.kchunk = static_cast<int>(plan.kchunk);
+  a.nkc = plan.nkc;
+  a.klist = klist;
+  a.K = K;
+  a.hs = h->d_hs;
+  a.tw_shift = plan.tw_shift;
+  a.nhi = plan.nhi;
+  a.partial = partial;
+  const int smem = static_cast<int>(plan.smem);
+  const unsigned ntask = static_cast<unsigned>(static_cast<int64_t>(plan.d) * plan.nrows * plan.nkc);
+  cudaError_t e = cudaSuccess;
+  switch (dt) {
+    case CMS_F32:
+      e = cudaFuncSetAttribute(k_sketch_sparse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) { ProfScope ps("k_sketch_sparse", s); k_sketch_sparse<float><<<ntask, kThreads, smem, s>>>(a); }
+      break;
+    case CMS_BF16:
+      e = cudaFuncSetAttribute(k_sketch_sparse<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) { ProfScope ps("k_sketch_sparse", s); k_sketch_sparse<__nv_bfloat16><<<ntask, kThreads, smem, s>>>(a); }
+      break;
+    default:
+      e = cudaFuncSetAttribute(k_sketch_sparse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) { ProfScope ps("k_sketch_sparse", s); k_sketch_sparse<double><<<ntask, kThreads, smem, s>>>(a); }
+      break;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace cms

@@ -1,0 +1,120 @@
+"""GPU parity of the sparse-input path (A by columns, B by rows) against the
+FP64 oracle: integer-valued block-sparse products (Theorem 5's setting) must
+come out exact after rounding; real-valued inputs within relative L2 1e-5."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import cms_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1108_1320_gb300 import build as b
+    b.build()
+    import paper_1108_1320_gb300 as m
+    m.lib()
+    return m
+
+
+def dev():
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def to_dev(sb: W.SparseBlocks, dtype=torch.float32):
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev(), dt)   # noqa: E731
+    return (t(sb.a_colptr, torch.int64), t(sb.a_rowidx, torch.int32), t(sb.a_val, dtype),
+            t(sb.b_rowptr, torch.int64), t(sb.b_colidx, torch.int32), t(sb.b_val, dtype))
+
+
+@pytest.mark.parametrize("n,blocks,b,d", [(1 << 16, 64, 1 << 16, 3), (5000, 10, 4096, 2), (3000, 4, 1024, 5)])
+def test_sparse_blocks_exact(cms, n, blocks, b, d):
+    sb = W.sparse_blocks(n, n_blocks=blocks, inner=8, rows=32, cols=32, seed=n + blocks)
+    A, B = sb.scipy()
+    h = cms.make_hashes(7 + b, n, b, d)
+    c = cms.sketch_product_csr(*to_dev(sb), n, n, h).cpu().numpy()
+    ref = O.sketch_definition_sparse(A, B, O.make_tables(7 + b, n, b, d))
+    np.testing.assert_array_equal(np.rint(c), ref)
+    assert O.rel_l2(c, ref) < 1e-5
+    h.free()
+
+
+def test_sparse_real_values_match_dense_path(cms):
+    n, n2, b, d = 700, 300, 8192, 3
+    g = W.rng(4)
+    A = np.where(g.random((n, n2)) < 0.05, g.standard_normal((n, n2)), 0.0).astype(np.float32)
+    B = np.where(g.random((n2, n)) < 0.05, g.standard_normal((n2, n)), 0.0).astype(np.float32)
+    import scipy.sparse as sp
+    Ac = sp.csc_matrix(A)
+    Br = sp.csr_matrix(B)
+    h = cms.make_hashes(5, n, b, d)
+    T = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev(), dt)   # noqa: E731
+    c_sp = cms.sketch_product_csr(T(Ac.indptr, torch.int64), T(Ac.indices, torch.int32),
+                                  T(Ac.data, torch.float32), T(Br.indptr, torch.int64),
+                                  T(Br.indices, torch.int32), T(Br.data, torch.float32), n, n, h)
+    c_dn = cms.sketch_product(T(A.T, torch.float32).T, T(B, torch.float32), h)
+    ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), O.make_tables(5, n, b, d))
+    assert O.rel_l2(c_sp.cpu().numpy(), ref) < 1e-5
+    assert O.rel_l2(c_dn.cpu().numpy(), ref) < 1e-5
+    h.free()
+
+
+def test_sparse_without_common_inner_index_is_zero(cms):
+    n, b = 200, 2048
+    colptr = np.zeros(11, np.int64)
+    colptr[1:] = np.arange(1, 11)            # A: one nonzero in each column k = 0..9
+    rowptr = np.zeros(11, np.int64)          # B: all rows empty
+    T = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev(), dt)   # noqa: E731
+    h = cms.make_hashes(1, n, b, 2)
+    c = cms.sketch_product_csr(T(colptr, torch.int64), T(np.arange(10), torch.int32),
+                               T(np.ones(10), torch.float32), T(rowptr, torch.int64),
+                               T(np.zeros(1), torch.int32), T(np.zeros(1), torch.float32), n, n, h)
+    assert torch.count_nonzero(c).item() == 0
+    h.free()
+
+
+def test_sparse_bf16_values_exact(cms):
+    n, b, d = 4096, 4096, 3
+    sb = W.sparse_blocks(n, n_blocks=16, inner=4, rows=16, cols=16, seed=12)
+    A, B = sb.scipy()
+    h = cms.make_hashes(3, n, b, d)
+    c = cms.sketch_product_csr(*to_dev(sb, torch.bfloat16), n, n, h).cpu().numpy()
+    ref = O.sketch_definition_sparse(A, B, O.make_tables(3, n, b, d))
+    np.testing.assert_array_equal(np.rint(c), ref)   # small integers are exact in BF16
+    h.free()
+
+
+def test_exact_sparse_full_size(cms):
+    # n = 2^20; 256 disjoint blocks of 8 inner indices x 32 rows of A x 32
+    # columns of B, integer values in [-8, 8] \ {0}; b = 2^20, d = 3.
+    n, b, d = 1 << 20, 1 << 20, 3
+    sb = W.sparse_blocks(n, n_blocks=256, inner=8, rows=32, cols=32, seed=3)
+    A, B = sb.scipy()
+    h = cms.make_hashes(3, n, b, d)
+    c = cms.sketch_product_csr(*to_dev(sb), n, n, h)
+    tab = O.make_tables(3, n, b, d)
+    ref = O.sketch_definition_sparse(A, B, tab)
+    np.testing.assert_array_equal(np.rint(c.cpu().numpy()), ref)      # c bit-exact after rounding
+    # decode at every nonzero of AB and at as many random positions: the GPU's
+    # medians equal the oracle's medians exactly (both decode integer sketches)
+    AB = (A @ B).tocoo()
+    g = W.rng(33)
+    zi = g.integers(0, n, AB.nnz)
+    zj = g.integers(0, n, AB.nnz)
+    ii = np.concatenate([AB.row, zi]).astype(np.int64)
+    jj = np.concatenate([AB.col, zj]).astype(np.int64)
+    ij = torch.from_numpy(np.stack([ii, jj], 1)).to(dev())
+    est = cms.decode(c, h, ij).cpu().numpy()
+    want = O.decompress(ref, tab, ii, jj)
+    np.testing.assert_array_equal(np.rint(est), want)
+    # how often the median equals AB (Theorem 5 regime needs d >= 6 lg n; d = 3 here)
+    exact = np.mean(np.rint(est[:AB.nnz]) == AB.data)
+    assert exact > 0.8
+    h.free()
