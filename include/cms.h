@@ -206,6 +206,70 @@ CMS_API cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t
                                           size_t ws_bytes, void* stream);
 
 /*
+ * Batches: the paper treats one product; a batch runs COMPRESSEDPRODUCT on
+ * many independent (A, B) pairs in one persistent launch.
+ *
+ * cms_instance - one product of a batch: the arguments of
+ * cms_sketch_product (A column-major, B row-major, device pointers) plus its
+ * hashes and its output c (device float [d][b]).
+ */
+typedef struct {
+    const void* A;
+    int64_t lda;
+    const void* B;
+    int64_t ldb;
+    int64_t n1, n2, n3;
+    int32_t dt;
+    int32_t reserved;
+    const cms_hashes* h;
+    float* c;
+} cms_instance;
+
+typedef struct cms_batch cms_batch;
+
+#define CMS_BATCH_AUTOTUNE 1
+
+/*
+ * cms_batch_create - plan a batch of `count` instances (Fig. 1 for each):
+ * allocates one device workspace for all of them, computes their constant
+ * twiddle tables and uploads one task descriptor per instance (synchronous
+ * on `stream`).  With flags & CMS_BATCH_AUTOTUNE, shapes not found in the
+ * cache file `tune_cache` (may be NULL) are tuned by timing candidate
+ * inner-index chunkings (and group sizes of the generic kernel) on the
+ * instance's own data; results are written back to the file, one line per
+ * key "b,n1,n2,n3,dt,d,SM count,kernel".
+ * The instances' pointers are captured: the same buffers are used by every
+ * run.  Errors: CMS_ERR_INVALID_ARG, CMS_ERR_UNSUPPORTED, CMS_ERR_CUDA.
+ */
+CMS_API cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t flags,
+                                    const char* tune_cache, void* stream, cms_batch** out);
+
+/*
+ * cms_batch_run - compute every instance's sketch c: one persistent kernel
+ * over all instances' tasks (longest first, taken from an atomic work
+ * counter; each task writes only its own partial row, so results do not
+ * depend on scheduling), then per instance the fixed-order reduction and
+ * inverse FFT.  Asynchronous, allocates nothing.
+ */
+CMS_API cms_status cms_batch_run(cms_batch* b, void* stream);
+
+/*
+ * cms_batch_run_graph - the same, through a CUDA graph captured on the
+ * first call (stream must not be the legacy default stream) and replayed
+ * afterwards.  Hash tables reseeded after the capture are picked up (the
+ * graph reads them at replay).
+ */
+CMS_API cms_status cms_batch_run_graph(cms_batch* b, void* stream);
+
+/* Counts of instances, persistent-kernel tasks, kernel launches per run,
+ * workspace bytes and instances served by the C = 1024 kernel (any NULL). */
+CMS_API cms_status cms_batch_info(const cms_batch* b, int32_t* instances, int32_t* tasks,
+                                  int32_t* launches, size_t* ws_bytes, int32_t* fast_instances);
+
+/* Free a batch (synchronises the device). */
+CMS_API cms_status cms_batch_free(cms_batch* b);
+
+/*
  * cms_plain_workspace_size / cms_sketch_product_plain_f64 - the same sketch
  * (Fig. 1) in plain form: FP64 throughout, one instance per call, unfused
  * passes (scatter, FFT, spectral product, inverse FFT each a separate

@@ -47,6 +47,12 @@ SIGNATURES = {
     "cms_sparse_workspace_size": (_I32, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
     "cms_sketch_product_csr": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _P, _P, _SZ,
                                       _P]),
+    "cms_batch_create": (_I32, [_P, _I32, _I32, ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
+    "cms_batch_run": (_I32, [_P, _P]),
+    "cms_batch_run_graph": (_I32, [_P, _P]),
+    "cms_batch_info": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                              ctypes.POINTER(_SZ), ctypes.POINTER(_I32)]),
+    "cms_batch_free": (_I32, [_P]),
     "cms_plain_workspace_size": (_I32, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
     "cms_sketch_product_plain_f64": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _P, _P, _P, _SZ,
                                             _P]),
@@ -267,6 +273,64 @@ def sketch_product_csr(a_colptr: torch.Tensor, a_rowidx: torch.Tensor, a_val: to
                                         h.handle, _ptr(c), _ptr(ws), ws.numel() * ws.element_size(),
                                         _stream(stream)))
     return c
+
+
+class _Instance(ctypes.Structure):
+    _fields_ = [("A", _P), ("lda", _I64), ("B", _P), ("ldb", _I64), ("n1", _I64), ("n2", _I64),
+                ("n3", _I64), ("dt", _I32), ("reserved", _I32), ("h", _P), ("c", _P)]
+
+
+class Batch:
+    """Many products (A_q, B_q, hashes_q) -> c_q in one persistent launch.
+
+    ``items`` is a list of (A, B, hashes) with A column-major and B row-major
+    device tensors; outputs are allocated here (``self.c[q]``, float32 (d, b)).
+    The tensors must stay alive and in place while the batch exists."""
+
+    def __init__(self, items, autotune: bool = False, tune_cache: str | None = None, stream=None):
+        self._keep = []
+        self.c = []
+        arr = (_Instance * len(items))()
+        for q, (A, B, h) in enumerate(items):
+            n1, n2, n3, lda, ldb = _ab_args(A, B)
+            inf = h.info()
+            c = torch.empty((inf["d"], inf["b"]), dtype=torch.float32, device=A.device)
+            self.c.append(c)
+            self._keep += [A, B, h]
+            arr[q] = _Instance(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype], 0,
+                               h.handle.value, _ptr(c))
+        out = ctypes.c_void_p()
+        _check(lib().cms_batch_create(arr, len(items), 1 if autotune else 0,
+                                      tune_cache.encode() if tune_cache else None, _stream(stream),
+                                      ctypes.byref(out)))
+        self._b = out
+
+    def run(self, stream=None):
+        _check(lib().cms_batch_run(self._b, _stream(stream)))
+        return self.c
+
+    def run_graph(self, stream):
+        _check(lib().cms_batch_run_graph(self._b, _stream(stream)))
+        return self.c
+
+    def info(self) -> dict:
+        inst, tasks, launches, fast = _I32(), _I32(), _I32(), _I32()
+        ws = _SZ()
+        _check(lib().cms_batch_info(self._b, ctypes.byref(inst), ctypes.byref(tasks),
+                                    ctypes.byref(launches), ctypes.byref(ws), ctypes.byref(fast)))
+        return {"instances": inst.value, "tasks": tasks.value, "launches": launches.value,
+                "ws_bytes": ws.value, "fast_instances": fast.value}
+
+    def free(self):
+        if self._b:
+            lib().cms_batch_free(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def plain_workspace_size(h: Hashes, n1: int, n2: int, n3: int) -> int:

@@ -97,7 +97,8 @@ bool choose_factorisation(int64_t b, int64_t* R, int64_t* C);
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
                      int dt, int num_sms, size_t smem_optin, SketchPlan* plan,
                      std::string* why, const void* A = nullptr, int64_t lda = 0,
-                     const void* B = nullptr, int64_t ldb = 0, bool allow_fast = true);
+                     const void* B = nullptr, int64_t ldb = 0, bool allow_fast = true,
+                     int nkc_override = 0, int G_override = 0);
 size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi);
 cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, const void* A,
                                int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
@@ -113,6 +114,15 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h,
 cudaError_t launch_inverse(const SketchPlan& plan, const float2* partial, float2* V, const float2* twC,
                            const float2* twR, float* c, cudaStream_t s);
 cudaError_t launch_twiddle_tables(float2* twC, int C, float2* twR, int R, cudaStream_t s);
+cudaError_t launch_frontend_twiddles(const SketchPlan& plan, const cms_hashes* h, char* ws, cudaStream_t s);
+
+// Batched persistent launch (descriptors built on the host, copied to the device).
+size_t batch_desc_bytes();
+void fill_batch_desc(void* dst, const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,
+                     const void* B, int64_t ldb, int64_t n1, int64_t n2, int64_t n3, int dt, char* ws);
+int batch_tasks(const SketchPlan& plan);
+cudaError_t launch_sketch_batched(const void* d_desc, const int* d_start, int ninst, int total,
+                                  int* d_next, size_t smem, int grid, cudaStream_t s);
 
 // Sparse inputs (A by columns, B by rows).
 struct SparseArgsHost {

@@ -25,39 +25,14 @@
 #include <algorithm>
 
 #include "cms_internal.h"
+#include "sketch_generic.cuh"
 
 namespace cms {
 namespace {
 
-constexpr int kMaxG = 4;
+using namespace generic;
 
-struct SketchArgs {
-  const void* A;
-  int64_t lda;
-  const void* B;
-  int64_t ldb;
-  int n1, n2, n3, n;
-  int64_t b;
-  int R, C, nrows, d;
-  int nradC;
-  int radC[16];
-  int G;
-  int kchunk, nkc;
-  const uint32_t* perm;
-  const uint32_t* off;
-  const float2* twfe;
-  const float2* twC;
-  float2* partial;
-};
 
-template <typename T> __device__ __forceinline__ float load_val(const T* p);
-template <> __device__ __forceinline__ float load_val<float>(const float* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float load_val<double>(const double* p) {
-  return static_cast<float>(__ldg(p));
-}
-template <> __device__ __forceinline__ float load_val<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(*p);
-}
 
 // w_M^m = exp(-2 pi i m / M) for m < M, rounded from double.
 __global__ void k_twiddle_table(float2* __restrict__ tw, int M) {
@@ -91,114 +66,10 @@ __global__ void k_frontend_twiddles(const uint32_t* __restrict__ hs,
   }
 }
 
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_sketch_fused(SketchArgs p) {
+__global__ void __launch_bounds__(256) k_sketch_fused(SketchArgs p) {
   extern __shared__ float4 smem4[];
-  const int C = p.C, G = p.G, n = p.n;
-  float2* twC = reinterpret_cast<float2*>(smem4);              // C
-  float4* acc = smem4 + (C + 1) / 2;                            // C (sum re, im, comp re, im)
-  float2* P = reinterpret_cast<float2*>(acc + C);               // 2 G C
-  float2* Q = P + 2 * G * C;                                    // >= 2 G C, staging aliases it
-  float* val = reinterpret_cast<float*>(Q);                     // [2][G][n]
-
-  const int task = blockIdx.x;
-  const int kc = task % p.nkc;
-  const int row = (task / p.nkc) % p.nrows;
-  const int t = task / (p.nkc * p.nrows);
-
-  for (int i = threadIdx.x; i < C; i += blockDim.x) {
-    twC[i] = p.twC[i];
-    acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-
-  const T* A = static_cast<const T*>(p.A);
-  const T* B = static_cast<const T*>(p.B);
-  const int k_begin = kc * p.kchunk;
-  const int k_end = min(p.n2, k_begin + p.kchunk);
-  const uint32_t* pmA = p.perm + static_cast<size_t>(t * 2 + 0) * n;
-  const uint32_t* pmB = p.perm + static_cast<size_t>(t * 2 + 1) * n;
-  const uint32_t* ofA = p.off + static_cast<size_t>(t * 2 + 0) * (C + 1);
-  const uint32_t* ofB = p.off + static_cast<size_t>(t * 2 + 1) * (C + 1);
-  const float2* twA = p.twfe + ((static_cast<size_t>(t) * p.nrows + row) * 2 + 0) * n;
-  const float2* twB = twA + n;
-
-  for (int k0 = k_begin; k0 < k_end; k0 += G) {
-    const int gcnt = min(G, k_end - k0);
-    __syncthreads();
-    // stage a_k (column k of A) and b_k (row k of B), zero-filled to n
-    for (int g = 0; g < G; ++g) {
-      float* va = val + (0 * G + g) * n;
-      float* vb = val + (1 * G + g) * n;
-      const bool live = g < gcnt;
-      const T* colA = A + static_cast<size_t>(k0 + g) * p.lda;
-      const T* rowB = B + static_cast<size_t>(k0 + g) * p.ldb;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        va[i] = (live && i < p.n1) ? load_val<T>(colA + i) : 0.f;
-        vb[i] = (live && i < p.n3) ? load_val<T>(rowB + i) : 0.f;
-      }
-    }
-    __syncthreads();
-    // gather front end: Y[side][g][z2] = sum over the bucket class z2
-    for (int task2 = threadIdx.x; task2 < 2 * C; task2 += blockDim.x) {
-      const int side = task2 >= C;
-      const int z2 = task2 - side * C;
-      const uint32_t* pm = side ? pmB : pmA;
-      const uint32_t* of = side ? ofB : ofA;
-      const float2* tw = side ? twB : twA;
-      const float* v = val + side * G * n;
-      float2 s[kMaxG];
-#pragma unroll
-      for (int g = 0; g < kMaxG; ++g) s[g] = make_float2(0.f, 0.f);
-      const uint32_t e1 = of[z2 + 1];
-      for (uint32_t e = of[z2]; e < e1; ++e) {
-        const uint32_t x = pm[e];
-        const float2 w = tw[e];
-#pragma unroll
-        for (int g = 0; g < kMaxG; ++g) {
-          if (g < G) {
-            const float a = v[g * n + x];
-            s[g].x = fmaf(a, w.x, s[g].x);
-            s[g].y = fmaf(a, w.y, s[g].y);
-          }
-        }
-      }
-#pragma unroll
-      for (int g = 0; g < kMaxG; ++g)
-        if (g < G) P[(side * G + g) * C + z2] = s[g];
-    }
-    __syncthreads();
-    float2* X = fft_block<false>(P, Q, C, 2 * G, p.radC, p.nradC, twC);
-    // spectral products, summed over the group, Kahan-accumulated over k
-    for (int f2 = threadIdx.x; f2 < C; f2 += blockDim.x) {
-      float2 prod = make_float2(0.f, 0.f);
-      for (int g = 0; g < gcnt; ++g) {
-        const float2 a = X[g * C + f2];
-        const float2 bb = X[(G + g) * C + f2];
-        prod.x = fmaf(a.x, bb.x, prod.x);
-        prod.x = fmaf(-a.y, bb.y, prod.x);
-        prod.y = fmaf(a.x, bb.y, prod.y);
-        prod.y = fmaf(a.y, bb.x, prod.y);
-      }
-      float4 ac = acc[f2];
-      kahan_add(ac.x, ac.z, prod.x);
-      kahan_add(ac.y, ac.w, prod.y);
-      acc[f2] = ac;
-    }
-  }
-  __syncthreads();
-  float2* out = p.partial + static_cast<size_t>(task) * C;
-  for (int f2 = threadIdx.x; f2 < C; f2 += blockDim.x) {
-    const float4 ac = acc[f2];
-    out[f2] = make_float2(ac.x - ac.z, ac.y - ac.w);
-  }
+  generic_task<T>(p, blockIdx.x, smem4);
 }
 
 struct InvArgs {
@@ -312,7 +183,8 @@ int64_t choose_chunks(int64_t units, int64_t n2, int G, int64_t slots, int64_t l
 
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int dt,
                      int num_sms, size_t smem_optin, SketchPlan* plan, std::string* why,
-                     const void* A, int64_t lda, const void* B, int64_t ldb, bool allow_fast) {
+                     const void* A, int64_t lda, const void* B, int64_t ldb, bool allow_fast,
+                     int nkc_override, int G_override) {
   SketchPlan p;
   p.b = h->b;
   p.d = h->d;
@@ -358,6 +230,9 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
       *why = "hash domain n too large for the shared-memory staging of the fused kernel";
       return CMS_ERR_UNSUPPORTED;
     }
+    if (G_override > 0 && G_override <= kMaxG &&
+        fused_smem_bytes(static_cast<int>(p.C), G_override, n) <= smem_optin)
+      G = G_override;
     p.G = G;
     p.smem = fused_smem_bytes(static_cast<int>(p.C), G, n);
   }
@@ -368,6 +243,7 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   const int64_t blocks_per_chunk = p.fast ? static_cast<int64_t>(p.d) * ((p.nrows + 1) / 2) : units;
   const int64_t lo = std::max<int64_t>(1, (2 * slots + blocks_per_chunk - 1) / blocks_per_chunk);
   int64_t nkc = choose_chunks(blocks_per_chunk, n2, G, slots, lo, std::max<int64_t>(lo, 4 * lo));
+  if (nkc_override > 0) nkc = std::min<int64_t>(nkc_override, std::max<int64_t>(1, (n2 + G - 1) / G));
   int64_t kchunk = n2 > 0 ? (n2 + nkc - 1) / nkc : G;
   kchunk = ((kchunk + G - 1) / G) * G;
   nkc = n2 > 0 ? (n2 + kchunk - 1) / kchunk : 1;
@@ -456,6 +332,17 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   }
 
   return launch_inverse(plan, partial, V, twC, twR, c, s);
+}
+
+cudaError_t launch_frontend_twiddles(const SketchPlan& plan, const cms_hashes* h, char* ws, cudaStream_t s) {
+  const int n = static_cast<int>(h->n);
+  float2* twfe = reinterpret_cast<float2*>(ws + plan.off_twfe);
+  dim3 grid(static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 64)), plan.nrows, 2 * plan.d);
+  {
+    ProfScope prof_scope("k_frontend_twiddles", s);
+    k_frontend_twiddles<<<grid, 256, 0, s>>>(h->d_hs, h->d_perm, n, plan.b, plan.nrows, twfe);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_twiddle_tables(float2* twC, int C, float2* twR, int R, cudaStream_t s) {

@@ -25,9 +25,11 @@
 //    indices' partial sums are added (fixed order) and folded into
 //    Kahan-compensated accumulators in shared memory.
 #include <algorithm>
+#include <cstring>
 
 #include "cms_internal.h"
 #include "warp_fft.cuh"
+#include "sketch_generic.cuh"
 
 namespace cms {
 namespace {
@@ -66,6 +68,16 @@ struct FastArgs {
   float2* partial;
 };
 
+}  // namespace
+
+struct BatchDesc {
+  int kind;                 // 1: fast kernel task, 0: generic task
+  generic::SketchArgs g;
+  FastArgs f;
+};
+
+namespace {
+
 struct SmemLayout {
   size_t stage, rec_tw, rec_x, work, acc, tlo, thi, grp, dest, ovf, bar, total;
 };
@@ -91,8 +103,9 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   return L;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
-  extern __shared__ __align__(128) unsigned char sm[];
+// One task (t, row pair, k-range) of the fast kernel; `sm` is the block's
+// dynamic shared memory (fast_layout).
+__device__ __forceinline__ void fast_task(const FastArgs& p, const int task, unsigned char* sm) {
   const SmemLayout L = fast_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi);
   float* stage = reinterpret_cast<float*>(sm + L.stage);
   float4* rec_tw = reinterpret_cast<float4*>(sm + L.rec_tw);     // [side][e]: row 0 tw, row 1 tw
@@ -107,7 +120,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int task = blockIdx.x;
   const int kc = task % p.nkc;
   const int unit = (task / p.nkc) % p.nunits;
   const int t = task / (p.nkc * p.nunits);
@@ -218,7 +230,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   __syncthreads();
 
   // warp -> (row, side, inner index of the group); region = warp
-  const int row_w = warp >> 2;
   const int side_w = (warp >> 1) & 1;
   const int g_w = warp & 1;
   float2* region = work + warp * kRegion;
@@ -376,6 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
 
   if (timed_out) {
     if (tid == 0) atomicOr(&g_sketch_error, 1u);
+    __syncthreads();
     return;
   }
   __syncthreads();
@@ -385,8 +397,56 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
     const int r = idx / kC, f = idx % kC;
     if (r == 1 && !row1_live) continue;
     const float4 a = acc[idx];
-    float2* out = p.partial + ((static_cast<size_t>(t) * p.nrows + f1r[r]) * p.nkc + kc) * kC;
+    const uint32_t frow = r ? f1r[1] : f1r[0];
+    float2* out = p.partial + ((static_cast<size_t>(t) * p.nrows + frow) * p.nkc + kc) * kC;
     out[f] = make_float2(a.x - a.z, a.y - a.w);
+  }
+  // the shared memory (and the mbarrier in it) is reused by the next task
+  __syncthreads();
+  if (tid == 0) mbar_inval(bar);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  fast_task(p, blockIdx.x, sm);
+}
+
+// ------------------------------------------------------------- batched ----
+// One persistent launch over the tasks of many instances (sketches of
+// different (A, B) pairs, shapes and storage types).  Blocks take tasks from
+// an atomic counter in the order the host laid them out (longest first);
+// each task runs the fast or the generic body and writes only its own
+// partial row, so the result does not depend on which block ran which task.
+__global__ void __launch_bounds__(kThreads, 1)
+k_sketch_batched(const BatchDesc* __restrict__ desc, const int* __restrict__ start, int ninst,
+                 int total, int* next) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ int s_task;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_task = atomicAdd(next, 1);
+    __syncthreads();
+    const int gtask = s_task;
+    if (gtask >= total) break;
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (start[mid] <= gtask) lo = mid; else hi = mid - 1;
+    }
+    const BatchDesc& d = desc[lo];
+    const int task = gtask - start[lo];
+    if (d.kind == 1) {
+      fast_task(d.f, task, sm);
+    } else {
+      float4* sm4 = reinterpret_cast<float4*>(sm);
+      switch (d.g.dt) {
+        case CMS_F32: generic::generic_task<float>(d.g, task, sm4); break;
+        case CMS_BF16: generic::generic_task<__nv_bfloat16>(d.g, task, sm4); break;
+        default: generic::generic_task<double>(d.g, task, sm4); break;
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -401,6 +461,75 @@ uint32_t read_clear_error_sketch() {
 
 size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi) {
   return fast_layout(npad, ecap, alias, tw_shift, nhi).total;
+}
+
+size_t batch_desc_bytes() { return sizeof(BatchDesc); }
+
+size_t batch_smem_bytes(const SketchPlan& plan) { return plan.smem; }
+
+// Descriptor of one instance of a batched launch (host memory `dst`).
+void fill_batch_desc(void* dst, const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,
+                     const void* B, int64_t ldb, int64_t n1, int64_t n2, int64_t n3, int dt, char* ws) {
+  BatchDesc d{};
+  float2* partial = reinterpret_cast<float2*>(ws + plan.off_partial);
+  if (plan.fast) {
+    d.kind = 1;
+    FastArgs& a = d.f;
+    a.A = static_cast<const float*>(A); a.lda = lda;
+    a.B = static_cast<const float*>(B); a.ldb = ldb;
+    a.n1 = static_cast<int>(n1); a.n2 = static_cast<int>(n2); a.n3 = static_cast<int>(n3);
+    a.n = static_cast<int>(h->n);
+    a.npad = plan.npad;
+    a.b = plan.b;
+    a.nrows = plan.nrows;
+    a.nunits = (plan.nrows + 1) / 2;
+    a.kchunk = static_cast<int>(plan.kchunk);
+    a.nkc = plan.nkc;
+    a.alias = plan.alias ? 1 : 0;
+    a.ecap = h->fe_ecap;
+    a.tw_shift = plan.tw_shift;
+    a.nhi = plan.nhi;
+    a.rec_x = h->d_fe_x; a.rec_hs = h->d_fe_hs; a.grp = h->d_fe_grp; a.dest = h->d_fe_dest;
+    a.ovf_off = h->d_fe_ovf_off; a.ovf_x = h->d_fe_ovf_x; a.hs = h->d_hs;
+    a.partial = partial;
+  } else {
+    d.kind = 0;
+    generic::SketchArgs& a = d.g;
+    a.A = A; a.lda = lda; a.B = B; a.ldb = ldb;
+    a.n1 = static_cast<int>(n1); a.n2 = static_cast<int>(n2); a.n3 = static_cast<int>(n3);
+    a.n = static_cast<int>(h->n);
+    a.b = plan.b; a.R = static_cast<int>(plan.R); a.C = static_cast<int>(plan.C);
+    a.nrows = plan.nrows; a.d = plan.d;
+    a.nradC = plan.nradC;
+    for (int i = 0; i < 16; ++i) a.radC[i] = plan.radC[i];
+    a.G = plan.G; a.kchunk = static_cast<int>(plan.kchunk); a.nkc = plan.nkc;
+    a.perm = h->d_perm; a.off = h->d_off;
+    a.twfe = reinterpret_cast<const float2*>(ws + plan.off_twfe);
+    a.twC = reinterpret_cast<const float2*>(ws + plan.off_twC);
+    a.partial = partial;
+    a.dt = dt;
+  }
+  std::memcpy(dst, &d, sizeof(d));
+}
+
+int batch_tasks(const SketchPlan& plan) {
+  const int units = plan.fast ? plan.d * ((plan.nrows + 1) / 2) : plan.d * plan.nrows;
+  return units * plan.nkc;
+}
+
+cudaError_t launch_sketch_batched(const void* d_desc, const int* d_start, int ninst, int total,
+                                  int* d_next, size_t smem, int grid, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(d_next, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  {
+    ProfScope prof_scope("k_sketch_batched", s);
+    k_sketch_batched<<<grid, kThreads, smem, s>>>(static_cast<const BatchDesc*>(d_desc), d_start, ninst,
+                                                  total, d_next);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, const void* A,
