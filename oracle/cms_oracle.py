@@ -242,10 +242,14 @@ def sketch_bucket_values(A: np.ndarray, B: np.ndarray, tab: Tables, t: int,
         need = (z - h1) % b                      # h2(j) each i needs
         lo = np.searchsorted(h2_sorted, need, side="left")
         hi = np.searchsorted(h2_sorted, need, side="right")
-        ii = np.repeat(np.arange(n1), hi - lo)
+        counts = hi - lo
+        ii = np.repeat(np.arange(n1), counts)
         if len(ii) == 0:
             continue
-        jj = order[np.concatenate([np.arange(l, h) for l, h in zip(lo, hi) if h > l])]
+        # positions lo[i] .. hi[i]-1 of the sorted h2 table, for every i
+        starts = np.repeat(lo, counts)
+        within = np.arange(len(ii)) - np.repeat(np.cumsum(counts) - counts, counts)
+        jj = order[starts + within]
         ab = np.einsum("pk,kp->p", A[ii, :].astype(np.float64), B[:, jj].astype(np.float64))
         out[q] = np.sum(s1[ii] * s2[jj] * ab)
     return out

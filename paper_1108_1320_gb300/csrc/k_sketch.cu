@@ -34,6 +34,16 @@ using namespace generic;
 
 
 
+// w_M^m = exp(-2 pi i m / M) in FP32 for 0 <= m < M: the angle is reduced to
+// (-pi, pi] with integers first, so 2m/M has at most one rounding (none for
+// power-of-two M) before sincospif.
+__device__ __forceinline__ float2 w_pow(uint64_t m, int64_t M) {
+  const int64_t mm = 2 * static_cast<int64_t>(m) > M ? static_cast<int64_t>(m) - M : static_cast<int64_t>(m);
+  float s, c;
+  sincospif(2.0f * static_cast<float>(mm) / static_cast<float>(M), &s, &c);
+  return make_float2(c, -s);
+}
+
 // w_M^m = exp(-2 pi i m / M) for m < M, rounded from double.
 __global__ void k_twiddle_table(float2* __restrict__ tw, int M) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
@@ -58,9 +68,7 @@ __global__ void k_frontend_twiddles(const uint32_t* __restrict__ hs,
     const uint32_t w = tab[pm[e]];
     const uint64_t m = (static_cast<uint64_t>(w & kBucketMask) * static_cast<uint64_t>(f1)) %
                        static_cast<uint64_t>(b);
-    double s, c;
-    sincospi(2.0 * static_cast<double>(m) / static_cast<double>(b), &s, &c);
-    float2 v = make_float2(static_cast<float>(c), static_cast<float>(-s));
+    float2 v = w_pow(m, b);
     if (w >> 31) { v.x = -v.x; v.y = -v.y; }
     out[e] = v;
   }
@@ -108,9 +116,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(InvArgs p) {
   for (int z2 = threadIdx.x; z2 < C; z2 += blockDim.x) {
     const uint64_t m = (static_cast<uint64_t>(f1) * static_cast<uint64_t>(z2)) %
                        static_cast<uint64_t>(p.b);
-    double s, c;
-    sincospi(2.0 * static_cast<double>(m) / static_cast<double>(p.b), &s, &c);
-    const float2 w = make_float2(static_cast<float>(c), static_cast<float>(s));  // w_b^{-m}
+    const float2 w = cconj(w_pow(m, p.b));   // w_b^{-m}
     out[z2] = cmul(X[z2], w);
   }
 }
@@ -139,11 +145,12 @@ k_cols_inverse(const float2* __restrict__ V, const float2* __restrict__ twR, int
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-size_t fused_smem_bytes(int C, int G, int n) {
+size_t fused_smem_bytes(int C, int G, int n, int dt) {
   const size_t tw = static_cast<size_t>((C + 1) / 2) * 16;
   const size_t acc = static_cast<size_t>(C) * 16;
   const size_t Pb = static_cast<size_t>(2 * G) * C * 8;
-  const size_t Qb = std::max(static_cast<size_t>(2 * G) * C * 8, static_cast<size_t>(2 * G) * n * 4);
+  const size_t elem = dt == CMS_BF16 ? 2 : 4;    // staging element (BF16 stays BF16)
+  const size_t Qb = std::max(static_cast<size_t>(2 * G) * C * 8, static_cast<size_t>(2 * G) * n * elem);
   return tw + acc + Pb + Qb;
 }
 
@@ -186,6 +193,8 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
                      const void* A, int64_t lda, const void* B, int64_t ldb, bool allow_fast,
                      int nkc_override, int G_override) {
   SketchPlan p;
+  const bool bf16 = dt == CMS_BF16;
+  (void)bf16;
   p.b = h->b;
   p.d = h->d;
   if (h->C <= 0) { *why = "b is not 5-smooth (2^x 3^y 5^z): the fused FFT path needs it"; return CMS_ERR_UNSUPPORTED; }
@@ -220,21 +229,21 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   if (!p.fast) {
     int G = 0;
     for (int g = kMaxG; g >= 1; --g) {
-      if (fused_smem_bytes(static_cast<int>(p.C), g, n) <= 112 * 1024) { G = g; break; }
+      if (fused_smem_bytes(static_cast<int>(p.C), g, n, dt) <= 112 * 1024) { G = g; break; }
     }
     if (G == 0) {
       for (int g = kMaxG; g >= 1; --g)
-        if (fused_smem_bytes(static_cast<int>(p.C), g, n) <= smem_optin) { G = g; break; }
+        if (fused_smem_bytes(static_cast<int>(p.C), g, n, dt) <= smem_optin) { G = g; break; }
     }
     if (G == 0) {
       *why = "hash domain n too large for the shared-memory staging of the fused kernel";
       return CMS_ERR_UNSUPPORTED;
     }
     if (G_override > 0 && G_override <= kMaxG &&
-        fused_smem_bytes(static_cast<int>(p.C), G_override, n) <= smem_optin)
+        fused_smem_bytes(static_cast<int>(p.C), G_override, n, dt) <= smem_optin)
       G = G_override;
     p.G = G;
-    p.smem = fused_smem_bytes(static_cast<int>(p.C), G, n);
+    p.smem = fused_smem_bytes(static_cast<int>(p.C), G, n, dt);
   }
   const int G = p.G;
   const int per_sm = p.fast ? 1 : std::max<int>(1, static_cast<int>(std::min<size_t>(4, (228 * 1024) / (p.smem + 1024))));

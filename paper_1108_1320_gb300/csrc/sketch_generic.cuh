@@ -32,6 +32,13 @@ struct SketchArgs {
   int dt;            // storage type of A and B (batched launches)
 };
 
+// Staging type in shared memory: BF16 inputs stay BF16 (half the bytes, so
+// larger hash domains fit), other inputs are staged as FP32.
+template <typename T> struct Staged { using type = float; };
+template <> struct Staged<__nv_bfloat16> { using type = __nv_bfloat16; };
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 template <typename T> __device__ __forceinline__ float load_val(const T* p);
 template <> __device__ __forceinline__ float load_val<float>(const float* p) { return __ldg(p); }
 template <> __device__ __forceinline__ float load_val<double>(const double* p) {
@@ -57,7 +64,8 @@ __device__ __forceinline__ void generic_task(const SketchArgs& p, int task, floa
   float4* acc = smem4 + (C + 1) / 2;                            // C (sum re, im, comp re, im)
   float2* P = reinterpret_cast<float2*>(acc + C);               // 2 G C
   float2* Q = P + 2 * G * C;                                    // >= 2 G C, staging aliases it
-  float* val = reinterpret_cast<float*>(Q);                     // [2][G][n]
+  using S = typename Staged<T>::type;
+  S* val = reinterpret_cast<S*>(Q);                             // [2][G][n]
 
   const int kc = task % p.nkc;
   const int row = (task / p.nkc) % p.nrows;
@@ -84,14 +92,19 @@ __device__ __forceinline__ void generic_task(const SketchArgs& p, int task, floa
     __syncthreads();
     // stage a_k (column k of A) and b_k (row k of B), zero-filled to n
     for (int g = 0; g < G; ++g) {
-      float* va = val + (0 * G + g) * n;
-      float* vb = val + (1 * G + g) * n;
+      S* va = val + (0 * G + g) * n;
+      S* vb = val + (1 * G + g) * n;
       const bool live = g < gcnt;
       const T* colA = A + static_cast<size_t>(k0 + g) * p.lda;
       const T* rowB = B + static_cast<size_t>(k0 + g) * p.ldb;
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        va[i] = (live && i < p.n1) ? load_val<T>(colA + i) : 0.f;
-        vb[i] = (live && i < p.n3) ? load_val<T>(rowB + i) : 0.f;
+        if constexpr (sizeof(S) == 2) {
+          va[i] = (live && i < p.n1) ? colA[i] : __float2bfloat16(0.f);
+          vb[i] = (live && i < p.n3) ? rowB[i] : __float2bfloat16(0.f);
+        } else {
+          va[i] = (live && i < p.n1) ? load_val<T>(colA + i) : 0.f;
+          vb[i] = (live && i < p.n3) ? load_val<T>(rowB + i) : 0.f;
+        }
       }
     }
     __syncthreads();
@@ -102,7 +115,7 @@ __device__ __forceinline__ void generic_task(const SketchArgs& p, int task, floa
       const uint32_t* pm = side ? pmB : pmA;
       const uint32_t* of = side ? ofB : ofA;
       const float2* tw = side ? twB : twA;
-      const float* v = val + side * G * n;
+      const S* v = val + side * G * n;
       float2 s[kMaxG];
 #pragma unroll
       for (int g = 0; g < kMaxG; ++g) s[g] = make_float2(0.f, 0.f);
@@ -113,7 +126,7 @@ __device__ __forceinline__ void generic_task(const SketchArgs& p, int task, floa
 #pragma unroll
         for (int g = 0; g < kMaxG; ++g) {
           if (g < G) {
-            const float a = v[g * n + x];
+            const float a = to_f32(v[g * n + x]);
             s[g].x = fmaf(a, w.x, s[g].x);
             s[g].y = fmaf(a, w.y, s[g].y);
           }

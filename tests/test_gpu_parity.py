@@ -395,3 +395,25 @@ def test_reseeded_fast_path(cms):
     ref = O.sketch_definition(X.T.astype(np.float64), X.astype(np.float64), O.make_tables(99, 1024, 65536, 2))
     assert O.rel_l2(c, ref) < TOL_F32
     h.free()
+
+
+# --------------------------------------------- large hash domain (BF16) ----
+def test_large_domain_bf16_reduced_inner(cms):
+    # the large covariance shape (n = 32768 variables, b = 2^20, d = 7, BF16
+    # storage) with the inner dimension cut to 48 samples so the oracle and
+    # the test stay fast: checked on sampled buckets and the DC identity
+    m, n, b, d = 48, 32768, 1 << 20, 7
+    cov = W.covariance(m, n, 64, 0.3, seed=5, dtype=np.float32)
+    Xb, _ = W.bf16_round(cov.X)
+    X = torch.from_numpy(cov.X).to(dev(), torch.bfloat16)
+    h = cms.make_hashes(5, n, b, d)
+    c = cms.sketch_product(X.T, X, h).cpu().numpy().astype(np.float64)
+    tab = O.make_tables(5, n, b, d)
+    Xd = Xb.astype(np.float64)
+    zs = W.rng(55).choice(b, 64, replace=False)
+    for t in range(d):
+        want = O.sketch_bucket_values(Xd.T, Xd, tab, t, zs)
+        assert np.linalg.norm(c[t, zs] - want) / np.linalg.norm(want) < TOL_F32, t
+        dc = (tab.s1[t] @ Xd.T) @ (Xd @ tab.s2[t])
+        assert abs(c[t].sum() - dc) < 1e-5 * np.abs(c[t]).sum()
+    h.free()
