@@ -427,7 +427,100 @@ def context_numbers(cms, torch, X, h, c, cov, w, dev, stream):
                     "note": "torch.matmul fp32 (cuBLAS, TF32 off by default) of X^T X"}
     del Xd, wsp, c64, AB
     torch.cuda.empty_cache()
+    out["sparse_exact"] = sparse_context(cms, torch, dev)
+    out["batched"] = batched_context(cms, torch, dev)
     return out
+
+
+def sparse_context(cms, torch, dev):
+    """Exact sparse product: n = 2^20, 256 blocks (8 inner indices, 32 rows of
+    A, 32 columns of B), integer values, b = 2^20, d = 3; A CSC, B CSR."""
+    import workloads as W
+    n, b, d = 1 << 20, 1 << 20, 3
+    sb = W.sparse_blocks(n, n_blocks=256, inner=8, rows=32, cols=32, seed=3)
+    T = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)   # noqa: E731
+    args = (T(sb.a_colptr, torch.int64), T(sb.a_rowidx, torch.int32), T(sb.a_val, torch.float32),
+            T(sb.b_rowptr, torch.int64), T(sb.b_colidx, torch.int32), T(sb.b_val, torch.float32))
+    h = cms.make_hashes(3, n, b, d)
+    ws = cms.alloc_workspace(cms.sparse_workspace_size(h, n, n, n), dev)
+    c = torch.empty((d, b), dtype=torch.float32, device=dev)
+    cms.sketch_product_csr(*args, n, n, h, c=c, ws=ws)
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        cms.sketch_product_csr(*args, n, n, h, c=c, ws=ws)   # includes one host wait (nonempty-k count)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    K = 256 * 8
+    flops = d * K * (5.0 * b * math.log2(b) + 4.0 * b) + d * 2.5 * b * math.log2(b)
+    h.free()
+    return {"workload": "exact sparse n=2^20, 256 blocks x (8 inner, 32 rows, 32 cols), b=2^20, d=3",
+            "ms_per_product": ms, "products_per_s": 1e3 / ms, "nonempty_k": K,
+            "alg_tflops": flops / (ms * 1e-3) / 1e12,
+            "note": "host wall clock per call (the call waits once for the nonempty-k count)"}
+
+
+def batched_context(cms, torch, dev):
+    """64 covariance-shaped instances of uneven n (log-uniform, 5-smooth),
+    m = 2n, half FP32 / half BF16 storage, b = 16 n, d = 3: one batch through
+    a CUDA graph vs one plain FP64 launch per instance.  n is capped at 2048
+    (instead of 8192) so that the plain FP64 leg stays within seconds."""
+    import workloads as W
+    specs = W.batched_specs(64, seed=4, n_lo=512, n_hi=2048)
+    gen = torch.Generator(device=dev)
+    items, xs = [], []
+    for q, sp in enumerate(specs):
+        gen.manual_seed(sp.seed)
+        X = torch.randn((sp.m, sp.n), generator=gen, device=dev, dtype=torch.float32)
+        if sp.n_pairs:
+            perm = torch.randperm(sp.n, generator=gen, device=dev)[: 2 * sp.n_pairs].view(-1, 2)
+            z = torch.randn((sp.m, sp.n_pairs), generator=gen, device=dev)
+            X[:, perm[:, 1]] = sp.rho * X[:, perm[:, 0]] + math.sqrt(1 - sp.rho ** 2) * z
+        Xs = X.to(torch.bfloat16) if sp.dtype == "bf16" else X
+        h = cms.make_hashes(1000 + q, sp.n, 16 * sp.n, 3)
+        items.append((Xs.T, Xs, h))
+        xs.append(X)
+    batch = cms.Batch(items)
+    info = batch.info()
+    s = torch.cuda.Stream()
+    batch.run_graph(s)                 # capture + first replay
+    s.synchronize()
+    reps = 5
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        batch.run_graph(s)
+    e1.record(s)
+    s.synchronize()
+    graph_ms = e0.elapsed_time(e1) / reps
+    # plain FP64 form: one call per instance
+    plain_ms = 0.0
+    for (A, B, h), X in zip(items, xs):
+        Xd = X.double()
+        ws = cms.alloc_workspace(cms.plain_workspace_size(h, X.shape[1], X.shape[0], X.shape[1]), dev)
+        cms.sketch_product_plain_f64(Xd.T, Xd, h, ws=ws)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record()
+        cms.sketch_product_plain_f64(Xd.T, Xd, h, ws=ws)
+        z.record()
+        torch.cuda.synchronize()
+        plain_ms += a.elapsed_time(z)
+        del Xd, ws
+    flops = sum(3 * sp.m * (5.0 * 16 * sp.n * math.log2(16 * sp.n) + 4.0 * 16 * sp.n) for sp in specs)
+    batch.free()
+    for _, _, h in items:
+        h.free()
+    torch.cuda.empty_cache()
+    return {"workload": "64 covariance instances, n log-uniform [512, 2048] 5-smooth, m=2n, 32 FP32 + 32 BF16, "
+                        "b=16n, d=3", "instances": info["instances"], "tasks": info["tasks"],
+            "kernel_launches_per_run": info["launches"], "fast_kernel_instances": info["fast_instances"],
+            "graph_ms_per_batch": graph_ms, "products_per_s": 64 * 1e3 / graph_ms,
+            "alg_tflops": flops / (graph_ms * 1e-3) / 1e12,
+            "plain_f64_ms_per_batch": plain_ms, "plain_f64_products_per_s": 64 * 1e3 / plain_ms}
 
 
 def main():
