@@ -139,6 +139,22 @@ class ClockSampler:
                 "power_w_max": max((num(p[3]) or 0.0) for p in used) if used else None}
 
 
+# ------------------------------------------------------ multi-rank timing --
+def reduce_max(x: float, dist, device) -> float:
+    """Max of a per-rank time over all ranks (identity without a process group)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_rank: int, max_ms: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 # --------------------------------------------------------- CPU oracle leg --
 def oracle_sample(X: np.ndarray, w: dict, k_count: int, seed: int, rows: int = 16):
     """Time the FP64 oracle (Route F of Fig. 1 plus DECOMPRESS) on the first
@@ -264,12 +280,8 @@ def gpu_arm(args):
     cms.profile_enable(False)
     cms.check_async()
     step_ms = [a.elapsed_time(z) for a, z in zip(starts, stops)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = reduce_max(sum(step_ms), dist if world > 1 else None, dev)
+    value = job_value(world, args.steps, total_ms)
     launches = int(sum(v["launches"] for v in prof.values()))
 
     # ---- roofline of the dominant kernel (the fused sketch kernel) --------
@@ -337,12 +349,8 @@ def gpu_arm(args):
         e2e_step(1 + i)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * e2e_steps / (e2e_ms / 1e3), "unit": "products/s",
+    e2e_ms = reduce_max(e0.elapsed_time(e1), dist if world > 1 else None, dev)
+    e2e = {"value": job_value(world, e2e_steps, e2e_ms), "unit": "products/s",
            "h2d_bytes_per_step": m * n * 4,
            "d2h_bytes_per_step": d * b * 4 + len(cov.pairs) * 4,
            "steps": e2e_steps}

@@ -1,0 +1,70 @@
+"""The benchmark's multi-rank path on CPU: two gloo ranks, per-rank times
+reduced with a max, whole-job throughput from the slowest rank; the
+reference arm does no work on ranks other than 0."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    per_rank_ms = [120.0, 150.0][rank]
+    mx = bench.reduce_max(per_rank_ms, dist, torch.device("cpu"))
+    val = bench.job_value(world, 10, mx)
+    dist.barrier()
+    q.put((rank, mx, val))
+    dist.destroy_process_group()
+
+
+def test_two_rank_max_and_job_value():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, mx, val in res:
+        assert mx == 150.0                       # the slowest rank's time
+        assert abs(val - 2 * 10 / 0.150) < 1e-9  # all ranks' products over that time
+
+
+def test_single_process_reduce_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_max(3.5, None, torch.device("cpu")) == 3.5
+    assert bench.job_value(1, 200, 1000.0) == 200.0
+
+
+def test_reference_arm_idles_on_other_ranks(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+
+    class A:
+        gpus, steps, warmup = 2, 1, 3
+    bench.reference_arm(A())
+    assert capsys.readouterr().out == ""
