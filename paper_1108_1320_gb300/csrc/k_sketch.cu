@@ -219,7 +219,8 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
     p.tw_shift = sh;
     p.nhi = static_cast<int>((p.b + (static_cast<int64_t>(1) << sh) - 1) >> sh);
     const size_t sm = fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi);
-    if (sm <= smem_optin) {
+    // the front-end records hold staging indices (< 3 npad) in 16 bits
+    if (sm <= smem_optin && 3 * static_cast<int64_t>(p.npad) <= 65535) {
       p.fast = true;
       p.G = 2;
       p.threads = 256;

@@ -12,10 +12,10 @@
 //    front end has consumed the buffer, so the copy overlaps the FFTs;
 //    when A = X^T and B = X are the same bytes the rows are staged once;
 //  * the gather front end Y[f1][z2] = sum s(x) A_xk w_b^{f1 h(x)} walks
-//    per-(t, side) records (x and the two rows' twiddles) kept in shared
-//    memory for the whole task; 32 buckets of equal (capped) occupancy form
-//    a group whose lanes run in lock step, placed so that the stores to Y
-//    are free of bank conflicts;
+//    records (staging index of x and the two rows' twiddles) kept in shared
+//    memory for the whole task, laid out as one contiguous stream per warp;
+//    32 buckets of equal (capped) occupancy form a group whose lanes run in
+//    lock step, placed so that the stores to Y are free of bank conflicts;
 //  * each of the 8 warps runs one length-1024 FFT (one (row, side, k)):
 //    radix-32 in registers, twiddle, one XOR-swizzled (conflict-free)
 //    transpose through shared memory, radix-32 in registers; lane l ends
@@ -79,8 +79,11 @@ struct BatchDesc {
 namespace {
 
 struct SmemLayout {
-  size_t stage, rec_tw, rec_x, work, acc, tlo, thi, grp, dest, ovf, bar, total;
+  size_t stage, rec_tw, rec_x, work, acc, tlo, thi, wmeta, wdst, ibase, istart, slot_src, ovf, bar, total;
 };
+
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 2 * (kC / 32) / kWarps;   // (side, bucket group) items per warp: 8
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
@@ -88,34 +91,48 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   SmemLayout L{};
   size_t o = 0;
   const int nstage = alias ? 1 : 2;
-  L.stage = o;  o = al16(o + static_cast<size_t>(nstage) * kG * npad * 4);
-  L.rec_tw = o; o = al16(o + static_cast<size_t>(2) * ecap * 16);
-  L.rec_x = o;  o = al16(o + static_cast<size_t>(2) * ecap * 2);
-  L.work = o;   o = al16(o + static_cast<size_t>(kRows * 2 * kG) * kRegion * 8);
-  L.acc = o;    o = al16(o + static_cast<size_t>(kRows) * kC * 16);
-  L.tlo = o;    o = al16(o + (static_cast<size_t>(1) << tw_shift) * 8);
-  L.thi = o;    o = al16(o + static_cast<size_t>(nhi) * 8);
-  L.grp = o;    o = al16(o + static_cast<size_t>(2) * (kC / 32) * 2 * 4);
-  L.dest = o;   o = al16(o + static_cast<size_t>(2) * kC * 2);
-  L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
-  L.bar = o;    o = al16(o + 8);
+  L.stage = o;    o = al16(o + static_cast<size_t>(nstage) * kG * npad * 4);
+  L.rec_tw = o;   o = al16(o + static_cast<size_t>(2) * ecap * 16);
+  L.rec_x = o;    o = al16(o + static_cast<size_t>(2) * ecap * 2);
+  L.work = o;     o = al16(o + static_cast<size_t>(kRows * 2 * kG) * kRegion * 8);
+  L.acc = o;      o = al16(o + static_cast<size_t>(kRows) * kC * 16);
+  L.tlo = o;      o = al16(o + (static_cast<size_t>(1) << tw_shift) * 8);
+  L.thi = o;      o = al16(o + static_cast<size_t>(nhi) * 8);
+  L.wmeta = o;    o = al16(o + static_cast<size_t>(kWarps) * kItems * 4);
+  L.wdst = o;     o = al16(o + static_cast<size_t>(kWarps) * 32 * kItems * 2);
+  L.ibase = o;    o = al16(o + static_cast<size_t>(kWarps) * kItems * 4);
+  L.istart = o;   o = al16(o + static_cast<size_t>(kWarps * kItems + 1) * 4);
+  L.slot_src = o; o = al16(o + (static_cast<size_t>(2) * ecap / 32 + 1) * 4);
+  L.ovf = o;      o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
+  L.bar = o;      o = al16(o + 8);
   L.total = o;
   return L;
 }
 
 // One task (t, row pair, k-range) of the fast kernel; `sm` is the block's
 // dynamic shared memory (fast_layout).
+//
+// The gather front end is laid out per warp: warp w owns kItems (side,
+// bucket group) items, dealt in snake order so that the heavy (first)
+// groups of each side spread over all warps.  The prologue copies the
+// records of warp w's items, item after item, into one contiguous stream
+// (slot s holds 32 lanes' records), and keeps per item its padded count
+// (warp-uniform) and per lane the Y slot its bucket is stored to, so the
+// per-group loop only walks the stream.
 __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, unsigned char* sm) {
   const SmemLayout L = fast_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi);
   float* stage = reinterpret_cast<float*>(sm + L.stage);
-  float4* rec_tw = reinterpret_cast<float4*>(sm + L.rec_tw);     // [side][e]: row 0 tw, row 1 tw
-  uint16_t* rec_x = reinterpret_cast<uint16_t*>(sm + L.rec_x);
+  float4* rec_tw = reinterpret_cast<float4*>(sm + L.rec_tw);     // [slot][lane]: row 0 tw, row 1 tw
+  uint16_t* rec_x = reinterpret_cast<uint16_t*>(sm + L.rec_x);   // [slot][lane]: staging index
   float2* work = reinterpret_cast<float2*>(sm + L.work);
   float4* acc = reinterpret_cast<float4*>(sm + L.acc);
   float2* tlo = reinterpret_cast<float2*>(sm + L.tlo);
   float2* thi = reinterpret_cast<float2*>(sm + L.thi);
-  uint2* grp = reinterpret_cast<uint2*>(sm + L.grp);
-  uint16_t* dest = reinterpret_cast<uint16_t*>(sm + L.dest);
+  uint32_t* wmeta = reinterpret_cast<uint32_t*>(sm + L.wmeta);   // [warp][item]: cnt | side << 8 | ovf << 31
+  uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);     // [warp][lane][item]: Y slot (row 0, k 0)
+  uint32_t* ibase = reinterpret_cast<uint32_t*>(sm + L.ibase);   // [warp][item]: side * ecap + first record
+  uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart); // [warp][item]: first stream slot; [64]: total
+  uint32_t* slot_src = reinterpret_cast<uint32_t*>(sm + L.slot_src);
   uint16_t* ovf = reinterpret_cast<uint16_t*>(sm + L.ovf);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
 
@@ -134,7 +151,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   const int k_begin = kc * p.kchunk;
   const int k_end = min(p.n2, k_begin + p.kchunk);
 
-  // ---- prologue: tables, records, staging tails, accumulators, barrier ----
+  // ---- prologue: tables, item streams, staging tails, accumulators -------
   for (int i = tid; i < S; i += kThreads) {
     float s, c;
     sincospif(2.0f * static_cast<float>(i) / static_cast<float>(p.b), &s, &c);
@@ -146,11 +163,27 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     sincospi(a, &s, &c);
     thi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
   }
+  if (tid < kWarps * kItems) {
+    const int w = tid / kItems, j = tid % kItems;
+    const int slot = (j & 1) ? (kWarps - 1 - w) : w;
+    const int item = j * kWarps + slot;
+    const int side = item & 1, gi = item >> 1;
+    const size_t ts = static_cast<size_t>(t) * 2 + side;
+    const uint32_t gb = p.grp[(ts * (kC / 32) + gi) * 2];
+    const uint32_t gy = p.grp[(ts * (kC / 32) + gi) * 2 + 1];
+    wmeta[tid] = (gy & 0xFFu) | (static_cast<uint32_t>(side) << 8) | (gy & 0x80000000u);
+    ibase[tid] = static_cast<uint32_t>(side) * p.ecap + gb;
+  }
+  for (int i = tid; i < kWarps * 32 * kItems; i += kThreads) {
+    const int w = i / (32 * kItems), l = (i / kItems) % 32, j = i % kItems;
+    const int slot = (j & 1) ? (kWarps - 1 - w) : w;
+    const int item = j * kWarps + slot;
+    const int side = item & 1, gi = item >> 1;
+    const size_t ts = static_cast<size_t>(t) * 2 + side;
+    wdst[i] = static_cast<uint16_t>(side * kG * kRegion + p.dest[ts * kC + gi * 32 + l]);
+  }
   for (int side = 0; side < 2; ++side) {
     const size_t ts = static_cast<size_t>(t) * 2 + side;
-    for (int i = tid; i < kC / 32; i += kThreads)
-      grp[side * (kC / 32) + i] = make_uint2(p.grp[(ts * (kC / 32) + i) * 2], p.grp[(ts * (kC / 32) + i) * 2 + 1]);
-    for (int i = tid; i < kC; i += kThreads) dest[side * kC + i] = p.dest[ts * kC + i];
     for (int i = tid; i <= kC; i += kThreads)
       ovf[side * (kC + 1) + i] = static_cast<uint16_t>(p.ovf_off[ts * (kC + 1) + i]);
   }
@@ -166,14 +199,27 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     fence_proxy_async();
   }
   __syncthreads();
-  // records: x and s(x) w_b^{(h(x) f1) mod b} for both rows, padding x = n
-  for (int side = 0; side < 2; ++side) {
-    const size_t ts = static_cast<size_t>(t) * 2 + side;
-    const uint2 lastg = grp[side * (kC / 32) + kC / 32 - 1];
-    const uint32_t epad = lastg.x + 32u * (lastg.y & 0xFFFFu);
-    for (uint32_t e = tid; e < epad; e += kThreads) {
-      const uint32_t x = p.rec_x[ts * p.ecap + e];
-      const uint32_t w = p.rec_hs[ts * p.ecap + e];
+  if (tid == 0) {
+    uint32_t s = 0;
+    for (int i = 0; i < kWarps * kItems; ++i) { istart[i] = s; s += wmeta[i] & 0xFFu; }
+    istart[kWarps * kItems] = s;
+  }
+  __syncthreads();
+  if (tid < kWarps * kItems) {
+    const uint32_t c = wmeta[tid] & 0xFFu, s0 = istart[tid], b0 = ibase[tid];
+    for (uint32_t r = 0; r < c; ++r) slot_src[s0 + r] = b0 + 32u * r;
+  }
+  __syncthreads();
+  // records in stream order: staging index of x and s(x) w_b^{(h(x) f1) mod b}
+  // for both rows; padding entries (x = n) read the zeroed staging tail
+  {
+    const uint32_t nrec = istart[kWarps * kItems] * 32u;
+    const size_t tbase = static_cast<size_t>(t) * 2 * p.ecap;
+    for (uint32_t i = tid; i < nrec; i += kThreads) {
+      const uint32_t src = slot_src[i >> 5] + (i & 31u);
+      const uint32_t side = src >= p.ecap ? 1u : 0u;
+      const uint32_t x = p.rec_x[tbase + src];
+      const uint32_t w = p.rec_hs[tbase + src];
       float2 tw[kRows];
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
@@ -183,8 +229,9 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
           if (w >> 31) { tw[r].x = -tw[r].x; tw[r].y = -tw[r].y; }
         }
       }
-      rec_tw[side * p.ecap + e] = make_float4(tw[0].x, tw[0].y, tw[1].x, tw[1].y);
-      rec_x[side * p.ecap + e] = static_cast<uint16_t>(min(x, static_cast<uint32_t>(n)));
+      rec_tw[i] = make_float4(tw[0].x, tw[0].y, tw[1].x, tw[1].y);
+      const uint32_t xs = min(x, static_cast<uint32_t>(n));
+      rec_x[i] = static_cast<uint16_t>((p.alias ? 0u : side * kG * static_cast<uint32_t>(p.npad)) + xs);
     }
   }
   // lane twiddle anchors w_1024^{lane * 8 q}, q = 0..3, and the step w_1024^lane
@@ -247,54 +294,61 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     if (__syncthreads_or(!ok)) { timed_out = true; break; }
     phase ^= 1u;
     // ---- gather front end (both rows, both inner indices) ----------------
-    // items (side, bucket group) dealt to warps in snake order so that the
-    // heavy (first) groups of each side spread over all warps
-#pragma unroll 1
-    for (int j = 0; j < 2 * (kC / 32) / (kThreads / 32); ++j) {
-      const int slot = (j & 1) ? (kThreads / 32 - 1 - warp) : warp;
-      const int item = j * (kThreads / 32) + slot;
-      const int side = item & 1;
-      const int gi = item >> 1;
-      const uint2 gd = grp[side * (kC / 32) + gi];
-      const uint32_t base = gd.x;
-      const uint32_t cnt = gd.y & 0xFFFFu;
-      const int z2 = dest[side * kC + gi * 32 + lane];
-      const float* st = stage + (p.alias ? 0 : side) * kG * p.npad;
-      const float4* tw = rec_tw + side * p.ecap + base + lane;
-      const uint16_t* xs = rec_x + side * p.ecap + base + lane;
-      float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
+    {
+      const uint4 mlo = reinterpret_cast<const uint4*>(wmeta)[warp * 2];
+      const uint4 mhi = reinterpret_cast<const uint4*>(wmeta)[warp * 2 + 1];
+      const uint4 dpk = reinterpret_cast<const uint4*>(wdst)[warp * 32 + lane];
+      const uint32_t s0 = istart[warp * kItems];
+      const float4* twp = rec_tw + s0 * 32u + lane;
+      const uint16_t* xp = rec_x + s0 * 32u + lane;
+      const float* st1 = stage + p.npad;
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        const uint32_t m = j == 0 ? mlo.x : j == 1 ? mlo.y : j == 2 ? mlo.z : j == 3 ? mlo.w
+                         : j == 4 ? mhi.x : j == 5 ? mhi.y : j == 6 ? mhi.z : mhi.w;
+        const uint32_t dw = j < 2 ? dpk.x : j < 4 ? dpk.y : j < 6 ? dpk.z : dpk.w;
+        const uint32_t dst = (j & 1) ? (dw >> 16) : (dw & 0xFFFFu);
+        const uint32_t cnt = m & 0xFFu;
+        float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
 #pragma unroll 2
-      for (uint32_t e = 0; e < cnt; ++e) {
-        const int x = xs[32 * e];
-        const float4 w = tw[32 * e];
-        const float v0 = st[x];
-        const float v1 = st[p.npad + x];
-        a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
-        a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
-        a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
-        a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
-      }
-      if (gd.y >> 31) {
-        // entries past the capped count of some bucket: on-the-fly twiddles
-        const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
-        for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
-          const uint32_t x = p.ovf_x[(static_cast<size_t>(t) * 2 + side) * n + o];
-          const uint32_t wv = p.hs[(static_cast<size_t>(t) * 2 + side) * n + x];
-          float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], p.b), p.tw_shift);
-          float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], p.b), p.tw_shift);
-          if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
-          const float v0 = st[x];
-          const float v1 = st[p.npad + x];
-          a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
-          a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
-          a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
-          a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
+        for (uint32_t e = 0; e < cnt; ++e) {
+          const int x = xp[32 * e];
+          const float4 w = twp[32 * e];
+          const float v0 = stage[x];
+          const float v1 = st1[x];
+          a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
+          a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
+          a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
+          a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
         }
+        xp += 32u * cnt;
+        twp += 32u * cnt;
+        if (m >> 31) {
+          // entries past the capped count of some bucket: on-the-fly twiddles
+          const int side = static_cast<int>((m >> 8) & 1u);
+          const int z2 = static_cast<int>(dst) - side * kG * kRegion;
+          const float* st = stage + (p.alias ? 0 : side) * kG * p.npad;
+          const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
+          for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
+            const uint32_t x = p.ovf_x[(static_cast<size_t>(t) * 2 + side) * n + o];
+            const uint32_t wv = p.hs[(static_cast<size_t>(t) * 2 + side) * n + x];
+            float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], p.b), p.tw_shift);
+            float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], p.b), p.tw_shift);
+            if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
+            const float v0 = st[x];
+            const float v1 = st[p.npad + x];
+            a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
+            a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
+            a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
+            a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
+          }
+        }
+        float2* dp = work + dst;
+        dp[0] = a00;
+        dp[kRegion] = a01;
+        dp[2 * kG * kRegion] = a10;
+        dp[2 * kG * kRegion + kRegion] = a11;
       }
-      work[((0 * 2 + side) * kG + 0) * kRegion + z2] = a00;
-      work[((0 * 2 + side) * kG + 1) * kRegion + z2] = a01;
-      work[((1 * 2 + side) * kG + 0) * kRegion + z2] = a10;
-      work[((1 * 2 + side) * kG + 1) * kRegion + z2] = a11;
     }
     __syncthreads();
     // staging consumed: fetch the next group while the FFTs run
