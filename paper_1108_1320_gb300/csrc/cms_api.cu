@@ -312,6 +312,16 @@ cms_status cms_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64
                        false);
   if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
   *bytes = std::max(plan.ws_bytes, generic.ws_bytes);
+  if (n1 == n3) {
+    // A and B the same bytes (A = X^T, B = X): the fast kernel stages each
+    // row once, so its plan can differ from the two-operand one
+    const void* same = reinterpret_cast<const void*>(static_cast<uintptr_t>(256));
+    const int64_t ld = std::max<int64_t>((n1 + 3) / 4 * 4, 4);
+    SketchPlan alias;
+    r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &alias, &why, same, ld, same, ld);
+    if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+    *bytes = std::max(*bytes, alias.ws_bytes);
+  }
   return CMS_OK;
 }
 

@@ -385,7 +385,9 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
 #pragma unroll
       for (int m = 0; m < 16; ++m) region[lane + 32 * m] = x[m];
     }
-    __syncthreads();
+    // only the partner warp (same row and k slot, other side) must be done;
+    // named barrier 1 + pair index, 64 threads
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + ((warp & 1) | ((warp >> 2) << 1))) : "memory");
     // ---- spectral products: own half of the bins -------------------------
     if (g_w < gcnt) {
       if (side_w == 0) {
@@ -436,7 +438,8 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         acc[idx] = a;
       }
     }
-    __syncthreads();
+    // the next group's __syncthreads_or orders these reads of the regions
+    // before the front end overwrites them
   }
 
   if (timed_out) {

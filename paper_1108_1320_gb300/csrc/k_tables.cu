@@ -106,12 +106,27 @@ cudaError_t launch_bucket_sort(const uint32_t* hs, int d, int64_t n, int64_t C,
 namespace cms {
 namespace {
 
+// Scrambled 10-bit key of a bucket index: buckets of equal count are grouped
+// in this order, not by z2, because the x of neighbouring buckets of a linear
+// hash fall into the same shared-memory banks (x mod 32) in lock step.
+__device__ __forceinline__ uint32_t bucket_scramble(uint32_t z) {
+  z *= 0x9E3779B1u;
+  z ^= z >> 15;
+  z *= 0x85EBCA6Bu;
+  z ^= z >> 13;
+  return z >> 22;
+}
+
 // Front-end records for the C = 1024 fused kernel, one block per (t, side).
 // Buckets z2 = h mod C are ordered by capped count (<= kFeCap) descending,
-// ties by z2; consecutive runs of 32 buckets form a group whose lanes walk
-// their buckets in lock step: entry r of the bucket at group position l sits
-// at base[group] + 32 r + l (padding entries point at x = n).  Entries past
-// the kFeCap-th of a bucket go, in x order, to a per-bucket overflow list.
+// then so that each run of 32 buckets of a class holds every residue
+// z2 mod 16 twice (scrambled order within a residue).  Consecutive runs of
+// 32 buckets form a group whose lanes walk their buckets in lock step:
+// entry r of the bucket at group position l sits at base[group] + 32 r + l
+// (padding entries point at x = n).  The entries of each bucket are then
+// ordered so that, step by step, the 32 lanes' x fall into distinct banks
+// where the counts allow (greedy).  Entries past the kFeCap-th of a bucket
+// (in x order) go to a per-bucket overflow list.
 __global__ void __launch_bounds__(1024)
 k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
                   uint32_t* __restrict__ rec_x, uint32_t* __restrict__ rec_hs,
@@ -139,7 +154,22 @@ k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
   for (uint32_t x = tid; x < n; x += blockDim.x) atomicAdd(&cnt[(tab[x] & kBucketMask) % C], 1u);
   __syncthreads();
   // bitonic sort (ascending) of (kFeCap - capped count) << 16 | z2
-  key[tid] = (static_cast<uint32_t>(kFeCap - min(cnt[tid], static_cast<uint32_t>(kFeCap))) << 16) | tid;
+  {
+    // rank of this bucket among the buckets of its class (capped count) and
+    // residue z2 mod 16, in scrambled order; sorting by (class, rank / 2,
+    // residue, rank % 2) makes every run of 32 buckets of a class hold each
+    // residue twice (the Y stores of a group then need 2 wavefronts)
+    const uint32_t z = static_cast<uint32_t>(tid);
+    const uint32_t cc = min(cnt[z], static_cast<uint32_t>(kFeCap));
+    const uint32_t sk = bucket_scramble(z);
+    uint32_t rank = 0;
+    for (uint32_t o = z & 15u; o < static_cast<uint32_t>(C); o += 16u) {
+      const uint32_t so = bucket_scramble(o);
+      if (min(cnt[o], static_cast<uint32_t>(kFeCap)) == cc && (so < sk || (so == sk && o < z))) ++rank;
+    }
+    key[tid] = ((static_cast<uint32_t>(kFeCap) - cc) << 20) | ((rank >> 1) << 15) | ((z & 15u) << 11) |
+               ((rank & 1u) << 10) | z;
+  }
   __syncthreads();
   for (int size = 2; size <= C; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -163,7 +193,7 @@ k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
     uint32_t used0 = 0, used1 = 0;
     for (int i = 0; i < 32; ++i) in[i] = grpkey[i];
     for (int i = 0; i < 32; ++i) {
-      const uint32_t r = (in[i] & 0xFFFFu) & 15u;
+      const uint32_t r = (in[i] & 0x3FFu) & 15u;
       if (!(used0 >> r & 1u)) { used0 |= 1u << r; half0[n0++] = in[i]; }
       else if (!(used1 >> r & 1u)) { used1 |= 1u << r; half1[n1++] = in[i]; }
       else { pool[np++] = in[i]; }
@@ -175,7 +205,7 @@ k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
     for (int i = 0; i < 16; ++i) { grpkey[i] = half0[i]; grpkey[16 + i] = half1[i]; }
   }
   __syncthreads();
-  const uint32_t zsorted = key[tid] & 0xFFFFu;
+  const uint32_t zsorted = key[tid] & 0x3FFu;
   lanepos[zsorted] = tid;
   ds[tid] = static_cast<uint16_t>(zsorted);
   __syncthreads();
@@ -184,9 +214,9 @@ k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
     for (int g = 0; g < C / 32; ++g) {
       uint32_t m = 0;
       for (int i = 0; i < 32; ++i)
-        m = max(m, min(cnt[key[32 * g + i] & 0xFFFFu], static_cast<uint32_t>(kFeCap)));
+        m = max(m, min(cnt[key[32 * g + i] & 0x3FFu], static_cast<uint32_t>(kFeCap)));
       uint32_t any_ovf = 0;
-      for (int i = 0; i < 32; ++i) any_ovf |= cnt[key[32 * g + i] & 0xFFFFu] > static_cast<uint32_t>(kFeCap);
+      for (int i = 0; i < 32; ++i) any_ovf |= cnt[key[32 * g + i] & 0x3FFu] > static_cast<uint32_t>(kFeCap);
       gbase[g] = run;
       gp[2 * g] = run;
       gp[2 * g + 1] = m | (any_ovf << 31);   // bit 31: some bucket of the group overflows
@@ -229,6 +259,54 @@ k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
         __syncwarp();
         if (valid && lane == __ffs(grpmask) - 1) cursor[z] += __popc(grpmask);
       }
+    }
+  }
+  __syncthreads();
+  // bank-aware order of each bucket's entries: warp g owns group g, lane l
+  // the bucket at group position l.  Step r gives each lane, in order of
+  // ascending count, its remaining entry whose bank (x mod 32) is least
+  // used at this step so far; padding lanes all read x = n (one address).
+  {
+    uint32_t* used = cursor + 32 * warp;   // 32 bank counters per warp
+    const uint32_t z = key[tid] & 0x3FFu;
+    const uint32_t c = min(cnt[z], static_cast<uint32_t>(kFeCap));
+    const uint32_t gb = gbase[warp];
+    const uint32_t cm = gp[2 * warp + 1] & 0xFFFFu;
+    uint32_t xs[kFeCap], ws[kFeCap];
+    for (uint32_t r = 0; r < c; ++r) {
+      xs[r] = rx[gb + 32u * r + lane];
+      ws[r] = rh[gb + 32u * r + lane];
+    }
+    // rank of this lane by (count, lane)
+    uint32_t rank = 0;
+    for (int o = 0; o < 32; ++o) {
+      const uint32_t co = __shfl_sync(0xFFFFFFFFu, c, o);
+      rank += (co < c || (co == c && o < lane)) ? 1u : 0u;
+    }
+    for (uint32_t r = 0; r < cm; ++r) {
+      used[lane] = 0;
+      const bool pads = __any_sync(0xFFFFFFFFu, c <= r);
+      __syncwarp();
+      if (lane == 0 && pads) used[n & 31u] = 1;
+      __syncwarp();
+      for (uint32_t k = 0; k < 32; ++k) {
+        if (rank == k && r < c) {
+          uint32_t best = r, bu = 0xFFFFFFFFu;
+          for (uint32_t i = r; i < c; ++i) {
+            const uint32_t u = used[xs[i] & 31u];
+            if (u < bu) { bu = u; best = i; }
+          }
+          const uint32_t tx = xs[r], tw = ws[r];
+          xs[r] = xs[best]; ws[r] = ws[best];
+          xs[best] = tx; ws[best] = tw;
+          used[xs[r] & 31u] += 1;
+        }
+        __syncwarp();
+      }
+    }
+    for (uint32_t r = 0; r < c; ++r) {
+      rx[gb + 32u * r + lane] = xs[r];
+      rh[gb + 32u * r + lane] = ws[r];
     }
   }
 }

@@ -397,6 +397,21 @@ def test_reseeded_fast_path(cms):
     h.free()
 
 
+def test_workspace_query_covers_aliased_operands(cms):
+    # n = 2304: with A = X^T and B = X the same bytes the fast kernel stages
+    # each row once and fits in shared memory, while the two-operand form
+    # does not; a workspace of exactly cms_workspace_size() must serve both
+    m, n, b, d = 40, 2304, 32768, 2
+    X = W.gaussian(m, n, 21).astype(np.float32)
+    h = cms.make_hashes(5, n, b, d)
+    xt = torch.from_numpy(X).to(dev())
+    ws = cms.alloc_workspace(cms.workspace_size(h, n, m, n))
+    c = cms.sketch_product(xt.T, xt, h, ws=ws).cpu().numpy()
+    ref = O.sketch_definition(X.T.astype(np.float64), X.astype(np.float64), O.make_tables(5, n, b, d))
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
 # --------------------------------------------- large hash domain (BF16) ----
 def test_large_domain_bf16_reduced_inner(cms):
     # the large covariance shape (n = 32768 variables, b = 2^20, d = 7, BF16
