@@ -79,7 +79,7 @@ struct BatchDesc {
 namespace {
 
 struct SmemLayout {
-  size_t stage, rec_tw, rec_x, work, acc, tlo, thi, wmeta, wdst, ibase, istart, slot_src, ovf, bar, total;
+  size_t stage, rec_tw, rec_x, work, acc, tlo, thi, wmeta, wdst, ibase, istart, slot_src, ovf, wovf, bar, total;
 };
 
 constexpr int kWarps = kThreads / 32;
@@ -104,6 +104,7 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   L.istart = o;   o = al16(o + static_cast<size_t>(kWarps * kItems + 1) * 4);
   L.slot_src = o; o = al16(o + (static_cast<size_t>(2) * ecap / 32 + 1) * 4);
   L.ovf = o;      o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
+  L.wovf = o;     o = al16(o + static_cast<size_t>(kWarps) * 4);
   L.bar = o;      o = al16(o + 8);
   L.total = o;
   return L;
@@ -134,6 +135,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart); // [warp][item]: first stream slot; [64]: total
   uint32_t* slot_src = reinterpret_cast<uint32_t*>(sm + L.slot_src);
   uint16_t* ovf = reinterpret_cast<uint16_t*>(sm + L.ovf);
+  uint32_t* wovf = reinterpret_cast<uint32_t*>(sm + L.wovf);   // [warp]: some item overflows
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -203,6 +205,11 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     uint32_t s = 0;
     for (int i = 0; i < kWarps * kItems; ++i) { istart[i] = s; s += wmeta[i] & 0xFFu; }
     istart[kWarps * kItems] = s;
+  }
+  if (tid < kWarps) {
+    uint32_t f = 0;
+    for (int j = 0; j < kItems; ++j) f |= wmeta[tid * kItems + j] >> 31;
+    wovf[tid] = f;
   }
   __syncthreads();
   if (tid < kWarps * kItems) {
@@ -295,22 +302,19 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     phase ^= 1u;
     // ---- gather front end (both rows, both inner indices) ----------------
     {
-      const uint4 mlo = reinterpret_cast<const uint4*>(wmeta)[warp * 2];
-      const uint4 mhi = reinterpret_cast<const uint4*>(wmeta)[warp * 2 + 1];
-      const uint4 dpk = reinterpret_cast<const uint4*>(wdst)[warp * 32 + lane];
       const uint32_t s0 = istart[warp * kItems];
       const float4* twp = rec_tw + s0 * 32u + lane;
       const uint16_t* xp = rec_x + s0 * 32u + lane;
       const float* st1 = stage + p.npad;
-#pragma unroll
+      // neither loop is unrolled: the smaller loop body keeps the hot code
+      // in the instruction cache (measured faster than unrolled forms)
+#pragma unroll 1
       for (int j = 0; j < kItems; ++j) {
-        const uint32_t m = j == 0 ? mlo.x : j == 1 ? mlo.y : j == 2 ? mlo.z : j == 3 ? mlo.w
-                         : j == 4 ? mhi.x : j == 5 ? mhi.y : j == 6 ? mhi.z : mhi.w;
-        const uint32_t dw = j < 2 ? dpk.x : j < 4 ? dpk.y : j < 6 ? dpk.z : dpk.w;
-        const uint32_t dst = (j & 1) ? (dw >> 16) : (dw & 0xFFFFu);
+        const uint32_t m = wmeta[warp * kItems + j];
+        const uint32_t dst = wdst[(warp * 32 + lane) * kItems + j];
         const uint32_t cnt = m & 0xFFu;
         float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
-#pragma unroll 2
+#pragma unroll 1
         for (uint32_t e = 0; e < cnt; ++e) {
           const int x = xp[32 * e];
           const float4 w = twp[32 * e];
@@ -323,15 +327,29 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         }
         xp += 32u * cnt;
         twp += 32u * cnt;
-        if (m >> 31) {
-          // entries past the capped count of some bucket: on-the-fly twiddles
+        float2* dp = work + dst;
+        dp[0] = a00;
+        dp[kRegion] = a01;
+        dp[2 * kG * kRegion] = a10;
+        dp[2 * kG * kRegion + kRegion] = a11;
+      }
+      // entries past the capped count of some bucket (rare): the lane that
+      // stored the bucket's Y adds them, with on-the-fly twiddles
+      if (wovf[warp]) {
+#pragma unroll 1
+        for (int j = 0; j < kItems; ++j) {
+          const uint32_t m = wmeta[warp * kItems + j];
+          if (!(m >> 31)) continue;
+          const uint32_t dst = wdst[(warp * 32 + lane) * kItems + j];
           const int side = static_cast<int>((m >> 8) & 1u);
           const int z2 = static_cast<int>(dst) - side * kG * kRegion;
           const float* st = stage + (p.alias ? 0 : side) * kG * p.npad;
+          const size_t ts = static_cast<size_t>(t) * 2 + side;
+          float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
           const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
           for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
-            const uint32_t x = p.ovf_x[(static_cast<size_t>(t) * 2 + side) * n + o];
-            const uint32_t wv = p.hs[(static_cast<size_t>(t) * 2 + side) * n + x];
+            const uint32_t x = p.ovf_x[ts * n + o];
+            const uint32_t wv = p.hs[ts * n + x];
             float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], p.b), p.tw_shift);
             float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], p.b), p.tw_shift);
             if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
@@ -342,12 +360,12 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
             a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
             a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
           }
+          float2* dp = work + dst;
+          dp[0].x += a00.x; dp[0].y += a00.y;
+          dp[kRegion].x += a01.x; dp[kRegion].y += a01.y;
+          dp[2 * kG * kRegion].x += a10.x; dp[2 * kG * kRegion].y += a10.y;
+          dp[2 * kG * kRegion + kRegion].x += a11.x; dp[2 * kG * kRegion + kRegion].y += a11.y;
         }
-        float2* dp = work + dst;
-        dp[0] = a00;
-        dp[kRegion] = a01;
-        dp[2 * kG * kRegion] = a10;
-        dp[2 * kG * kRegion + kRegion] = a11;
       }
     }
     __syncthreads();
