@@ -502,8 +502,10 @@ cms_status cms_check_async(void* stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cms_check_async");
   const uint32_t w = read_clear_error_decode();
-  const uint32_t ws = read_clear_error_sketch();
-  if (w == 0xFFFFFFFFu || ws == 0xFFFFFFFFu)
+  const uint32_t ws1 = read_clear_error_sketch();
+  const uint32_t ws2 = read_clear_error_sketch_ws();
+  const uint32_t ws = ws1 | ws2;
+  if (w == 0xFFFFFFFFu || ws1 == 0xFFFFFFFFu || ws2 == 0xFFFFFFFFu)
     return fail(CMS_ERR_CUDA, "could not read the device error words");
   if (ws) return fail(CMS_ERR_TIMEOUT, "a fused-kernel wait for its TMA copies gave up");
   if (w) return fail(CMS_ERR_DEVICE, "decode saw an index pair outside the hash domain");

@@ -174,13 +174,15 @@ cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t fl
       return fail(CMS_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": bad shape, stride or dtype");
     }
     SketchPlan p;
-    int r = make_sketch_plan(it.h, it.n1, it.n2, it.n3, it.dt, sms, optin, &p, &why, it.A, it.lda, it.B, it.ldb);
+    // the persistent batched kernel runs the lock-step fast body
+    int r = make_sketch_plan(it.h, it.n1, it.n2, it.n3, it.dt, sms, optin, &p, &why, it.A, it.lda, it.B, it.ldb,
+                             true, 0, 0, false);
     if (r != CMS_OK) { delete b; return fail(static_cast<cms_status>(r), "instance " + std::to_string(i) + ": " + why); }
     auto hit = cache.find(tune_key(it, p, sms));
     if (hit != cache.end()) {
       SketchPlan q;
       if (make_sketch_plan(it.h, it.n1, it.n2, it.n3, it.dt, sms, optin, &q, &why, it.A, it.lda, it.B, it.ldb,
-                           true, hit->second.nkc, hit->second.G) == CMS_OK)
+                           true, hit->second.nkc, hit->second.G, false) == CMS_OK)
         p = q;
     } else if (flags & CMS_BATCH_AUTOTUNE) {
       // candidates: the planner's chunking, half and twice as many chunks;
@@ -196,7 +198,7 @@ cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t fl
       for (auto& c2 : cand) {
         SketchPlan q;
         if (make_sketch_plan(it.h, it.n1, it.n2, it.n3, it.dt, sms, optin, &q, &why, it.A, it.lda, it.B,
-                             it.ldb, true, c2.first, c2.second) == CMS_OK) {
+                             it.ldb, true, c2.first, c2.second, false) == CMS_OK) {
           cps.push_back(q);
           need = std::max(need, q.ws_bytes);
         }

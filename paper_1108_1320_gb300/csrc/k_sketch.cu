@@ -191,7 +191,7 @@ int64_t choose_chunks(int64_t units, int64_t n2, int G, int64_t slots, int64_t l
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int dt,
                      int num_sms, size_t smem_optin, SketchPlan* plan, std::string* why,
                      const void* A, int64_t lda, const void* B, int64_t ldb, bool allow_fast,
-                     int nkc_override, int G_override) {
+                     int nkc_override, int G_override, bool allow_ws) {
   SketchPlan p;
   const bool bf16 = dt == CMS_BF16;
   (void)bf16;
@@ -219,12 +219,15 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
     p.tw_shift = sh;
     p.nhi = static_cast<int>((p.b + (static_cast<int64_t>(1) << sh) - 1) >> sh);
     const size_t sm = fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi);
+    const size_t sm_ws = ws_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi);
+    const bool ws_ok = allow_ws && sm_ws <= smem_optin && ws_kernel_usable();
     // the front-end records hold staging indices (< 3 npad) in 16 bits
-    if (sm <= smem_optin && 3 * static_cast<int64_t>(p.npad) <= 65535) {
+    if ((sm <= smem_optin || ws_ok) && 3 * static_cast<int64_t>(p.npad) <= 65535) {
       p.fast = true;
+      p.ws = ws_ok;
       p.G = 2;
-      p.threads = 256;
-      p.smem = sm;
+      p.threads = ws_ok ? 384 : 256;
+      p.smem = ws_ok ? sm_ws : sm;
     }
   }
   if (!p.fast) {
@@ -299,7 +302,8 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   if (e != cudaSuccess) return e;
 
   if (plan.fast) {
-    e = launch_sketch_fast(plan, h, A, lda, B, ldb, n1, n2, n3, partial, s);
+    e = plan.ws ? launch_sketch_ws(plan, h, A, lda, B, ldb, n1, n2, n3, partial, s)
+                : launch_sketch_fast(plan, h, A, lda, B, ldb, n1, n2, n3, partial, s);
     if (e != cudaSuccess) return e;
   } else {
   SketchArgs a{};

@@ -1,0 +1,642 @@
+// k_sketch_ws.cu - warp-specialised form of the C = 1024 fused sketch kernel
+// (the computation of k_sketch_fast, see there and k_sketch.cu for the
+// four-step split of the length-b DFT and the pruned first stage).
+//
+// In the lock-step kernel all warps gather (front end) and then all warps
+// run FFTs, so the gather, bound by shared-memory latency and bank traffic,
+// never overlaps the FP32-bound FFTs.  Here the two run in different warps
+// of a 512-thread block (one block per SM):
+//
+//  * warps 0-7 (front end, 72 registers after setmaxnreg.dec): gather
+//    Y[f1][z2] = sum s(x) A_xk w_b^{f1 h(x)} for two rows f1 and a group of
+//    G = 2 inner indices into one of two Y buffers.  Their per-entry
+//    twiddles live in tensor memory (TMEM), 32 columns per (side, bucket
+//    group) item; an item's count selects a fully unrolled body whose index
+//    loads, gathers and TMEM load are all in flight together;
+//  * warps 8-15 (FFT, 184 registers after setmaxnreg.inc): one length-1024
+//    FFT per warp and group (row, side, inner index) from the other Y
+//    buffer, the spectral products in registers and the Kahan folds into
+//    shared memory;
+//  * the TMA bulk copies of the staging rows (two buffers) are issued by
+//    thread 0 for the first two groups, then by the first FFT thread as
+//    soon as the front end has released a buffer.
+//
+// Hand-offs are mbarriers: staging full (TMA transaction count), Y full
+// (256 front-end arrivals), Y free (256 FFT arrivals); waiting warps sleep
+// in try_wait.  Every wait is bounded; after a timeout the block records the
+// error, stops waiting (the results are then garbage and reported as such)
+// but still passes every named barrier, so no warp is left behind.
+#include <algorithm>
+
+#include "cms_internal.h"
+#include "warp_fft.cuh"
+
+namespace cms {
+namespace {
+
+using namespace wfft;
+
+constexpr int kC = kFeC;                 // 1024
+constexpr int kG = 2;                    // inner indices per group
+constexpr int kRows = 2;                 // rows f1 per block
+constexpr int kFeWarps = 8;
+constexpr int kFftWarps = kRows * 2 * kG;   // 8
+constexpr int kThreadsWs = 32 * (kFeWarps + kFftWarps);   // 512
+constexpr int kFeThreads = 32 * kFeWarps;
+constexpr int kFftThreads = 32 * kFftWarps;
+constexpr int kFlush = 16;               // groups between Kahan folds
+constexpr int kPitch = 33;
+constexpr int kRegion = 32 * kPitch;     // float2 per FFT region (>= kC)
+constexpr int kItems = 2 * (kC / 32);    // (side, bucket group) items: 64
+constexpr int kItemsFe = kItems / kFeWarps;   // 8 per front-end warp
+// registers per thread after setmaxnreg (launch: 65536 / 512 = 128 each)
+constexpr int kRegsFe = 72;
+constexpr int kRegsFft = 184;
+static_assert(kFeThreads * kRegsFe + kFftThreads * kRegsFft <= 65536, "register split exceeds the launch pool");
+// named barriers (0 is __syncthreads)
+constexpr int kBarPair = 2;              // 2..5: FFT warp pairs, 64 threads
+constexpr int kBarFft = 6;               // FFT warps, 256 threads
+
+__device__ uint32_t g_ws_error = 0;      // 1: a wait gave up
+
+struct WsArgs {
+  const float* A;
+  int64_t lda;
+  const float* B;
+  int64_t ldb;
+  int n1, n2, n3, n, npad;
+  int64_t b;
+  int nrows, nunits;
+  int kchunk, nkc;
+  int alias;
+  uint32_t ecap;
+  int tw_shift, nhi;
+  const uint32_t* rec_x;
+  const uint32_t* rec_hs;
+  const uint32_t* grp;
+  const uint16_t* dest;
+  const uint32_t* ovf_off;
+  const uint32_t* ovf_x;
+  const uint32_t* hs;
+  float2* partial;
+};
+
+struct WsLayout {
+  size_t stage, rec_x, ybuf, acc, tlo, thi, wmeta, wdst, ibase, istart, ovf, wovf, bars, total;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
+
+// Staging: [buffer][side][k slot][npad] (one side when A and B alias).
+__host__ __device__ inline size_t stage_floats(int npad, int alias) {
+  return static_cast<size_t>(alias ? 1 : 2) * kG * npad;
+}
+
+__host__ __device__ inline WsLayout ws_layout(int npad, uint32_t ecap, int alias, int tw_shift, int nhi) {
+  WsLayout L{};
+  size_t o = 0;
+  L.stage = o;  o = al16(o + 2 * stage_floats(npad, alias) * 4);
+  L.rec_x = o;  o = al16(o + static_cast<size_t>(2) * ecap * 2);
+  L.ybuf = o;   o = al16(o + static_cast<size_t>(2) * kFftWarps * kRegion * 8);
+  L.acc = o;    o = al16(o + static_cast<size_t>(kRows) * kC * 16);
+  L.tlo = o;    o = al16(o + (static_cast<size_t>(1) << tw_shift) * 8);
+  L.thi = o;    o = al16(o + static_cast<size_t>(nhi) * 8);
+  L.wmeta = o;  o = al16(o + static_cast<size_t>(kItems) * 4);
+  L.wdst = o;   o = al16(o + static_cast<size_t>(kFeWarps) * 32 * kItemsFe * 2);
+  L.ibase = o;  o = al16(o + static_cast<size_t>(kItems) * 4);
+  L.istart = o; o = al16(o + static_cast<size_t>(kItems + 1) * 4);
+  L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
+  L.wovf = o;   o = al16(o + static_cast<size_t>(kFeWarps) * 4);
+  L.bars = o;   o = al16(o + 6 * 8);
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Item j (0..15) of front-end warp w: round j deals one item of each group
+// of four to every warp, in snake order so that the heavy (first) bucket
+// groups of each side spread over the warps.
+__host__ __device__ inline int fe_item(int w, int j) {
+  const int slot = (j & 1) ? (kFeWarps - 1 - w) : w;
+  return j * kFeWarps + slot;
+}
+
+// The NC padded entries of one bucket (NC = the item's count, uniform over
+// the warp): all index loads, then all gathers, then the FMAs, so that the
+// loads of the item are in flight together.
+template <int NC>
+__device__ __forceinline__ void fe_slots(const uint16_t* xp, const float* st0, const float* st1,
+                                         const uint32_t taddr, float2& a00, float2& a01, float2& a10,
+                                         float2& a11) {
+  // the item's twiddles (TMEM) load while its gathers are in flight
+  uint32_t tw[32];
+  if (NC <= 4) tmem_ld16_nowait(taddr, tw);
+  else tmem_ld32_nowait(taddr, tw);
+  int x[NC];
+#pragma unroll
+  for (int e = 0; e < NC; ++e) x[e] = xp[32 * e];
+  float v0[NC], v1[NC];
+#pragma unroll
+  for (int e = 0; e < NC; ++e) {
+    v0[e] = st0[x[e]];
+    v1[e] = st1[x[e]];
+  }
+  if (NC <= 4) tmem_wait_ld16(tw);
+  else tmem_wait_ld32(tw);
+#pragma unroll
+  for (int e = 0; e < NC; ++e) {
+    const float w0 = __uint_as_float(tw[4 * e]), w1 = __uint_as_float(tw[4 * e + 1]);
+    const float w2 = __uint_as_float(tw[4 * e + 2]), w3 = __uint_as_float(tw[4 * e + 3]);
+    a00.x = fmaf(v0[e], w0, a00.x); a00.y = fmaf(v0[e], w1, a00.y);
+    a01.x = fmaf(v1[e], w0, a01.x); a01.y = fmaf(v1[e], w1, a01.y);
+    a10.x = fmaf(v0[e], w2, a10.x); a10.y = fmaf(v0[e], w3, a10.y);
+    a11.x = fmaf(v1[e], w2, a11.x); a11.y = fmaf(v1[e], w3, a11.y);
+  }
+}
+
+__global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_err;
+
+  const WsLayout L = ws_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi);
+  float* stage = reinterpret_cast<float*>(sm + L.stage);
+  uint16_t* rec_x = reinterpret_cast<uint16_t*>(sm + L.rec_x);     // [stream slot][lane]
+  float2* ybuf = reinterpret_cast<float2*>(sm + L.ybuf);           // [buffer][FFT warp][kRegion]
+  float4* acc = reinterpret_cast<float4*>(sm + L.acc);
+  float2* tlo = reinterpret_cast<float2*>(sm + L.tlo);
+  float2* thi = reinterpret_cast<float2*>(sm + L.thi);
+  uint32_t* wmeta = reinterpret_cast<uint32_t*>(sm + L.wmeta);     // [fe warp][item]: cnt | side << 8 | ovf << 31
+  uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);       // [fe warp][lane][item]: Y slot (row 0, k 0)
+  uint32_t* ibase = reinterpret_cast<uint32_t*>(sm + L.ibase);     // [fe warp][item]: side * ecap + first record
+  uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart);   // [fe warp][item]: first stream slot
+  uint16_t* ovf = reinterpret_cast<uint16_t*>(sm + L.ovf);
+  uint32_t* wovf = reinterpret_cast<uint32_t*>(sm + L.wovf);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
+  uint64_t* full_stage = bars;       // [2] TMA transactions of a staging buffer
+  uint64_t* y_full = bars + 2;       // [2] 256 front-end arrivals
+  uint64_t* y_free = bars + 4;       // [2] 256 FFT arrivals
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int task = blockIdx.x;
+  const int kc = task % p.nkc;
+  const int unit = (task / p.nkc) % p.nunits;
+  const int t = task / (p.nkc * p.nunits);
+  uint32_t f1r[kRows];
+  f1r[0] = static_cast<uint32_t>(2 * unit);
+  f1r[1] = static_cast<uint32_t>(min(2 * unit + 1, p.nrows - 1));
+  const bool row1_live = 2 * unit + 1 < p.nrows;
+  const int n = p.n;
+  const int S = 1 << p.tw_shift;
+  const int nside = p.alias ? 1 : 2;
+  const size_t sbuf = stage_floats(p.npad, p.alias);
+  const int k_begin = kc * p.kchunk;
+  const int k_end = min(p.n2, k_begin + p.kchunk);
+  const int ngroups = k_end > k_begin ? (k_end - k_begin + kG - 1) / kG : 0;
+
+  // ---- tensor memory: 512 columns for the block (one block per SM) --------
+  if (warp == 0) {
+    tmem_alloc(&s_tmem, 512);
+    tmem_relinquish();
+  }
+  if (tid == 0) s_err = 0;
+
+  // ---- prologue -------------------------------------------------------------
+  for (int i = tid; i < S; i += kThreadsWs) {
+    float s, c;
+    sincospif(2.0f * static_cast<float>(i) / static_cast<float>(p.b), &s, &c);
+    tlo[i] = make_float2(c, -s);
+  }
+  for (int i = tid; i < p.nhi; i += kThreadsWs) {
+    const double a = 2.0 * static_cast<double>(static_cast<int64_t>(i) * S) / static_cast<double>(p.b);
+    double s, c;
+    sincospi(a, &s, &c);
+    thi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+  }
+  if (tid < kItems) {
+    const int w = tid / kItemsFe, j = tid % kItemsFe;
+    const int item = fe_item(w, j);
+    const int side = item & 1, gi = item >> 1;
+    const size_t ts = static_cast<size_t>(t) * 2 + side;
+    const uint32_t gb = p.grp[(ts * (kC / 32) + gi) * 2];
+    const uint32_t gy = p.grp[(ts * (kC / 32) + gi) * 2 + 1];
+    wmeta[tid] = (gy & 0xFFu) | (static_cast<uint32_t>(side) << 8) | (gy & 0x80000000u);
+    ibase[tid] = static_cast<uint32_t>(side) * p.ecap + gb;
+  }
+  for (int i = tid; i < kFeWarps * 32 * kItemsFe; i += kThreadsWs) {
+    const int w = i / (32 * kItemsFe), l = (i / kItemsFe) % 32, j = i % kItemsFe;
+    const int item = fe_item(w, j);
+    const int side = item & 1, gi = item >> 1;
+    const size_t ts = static_cast<size_t>(t) * 2 + side;
+    wdst[i] = static_cast<uint16_t>(side * kG * kRegion + p.dest[ts * kC + gi * 32 + l]);
+  }
+  for (int side = 0; side < 2; ++side) {
+    const size_t ts = static_cast<size_t>(t) * 2 + side;
+    for (int i = tid; i <= kC; i += kThreadsWs)
+      ovf[side * (kC + 1) + i] = static_cast<uint16_t>(p.ovf_off[ts * (kC + 1) + i]);
+  }
+  for (int i = tid; i < kRows * kC; i += kThreadsWs) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // zero the staging tails [n_side, npad) of both buffers: entries x >= n_side read zeros
+  for (int bb = 0; bb < 2; ++bb)
+    for (int s2 = 0; s2 < nside; ++s2) {
+      const int ns = s2 == 0 ? p.n1 : p.n3;
+      for (int g = 0; g < kG; ++g)
+        for (int i = ns + tid; i < p.npad; i += kThreadsWs)
+          stage[bb * sbuf + (s2 * kG + g) * p.npad + i] = 0.f;
+    }
+  if (tid == 0) {
+    mbar_init(&full_stage[0], 1);
+    mbar_init(&full_stage[1], 1);
+    mbar_init(&y_full[0], kFeThreads);
+    mbar_init(&y_full[1], kFeThreads);
+    mbar_init(&y_free[0], kFftThreads);
+    mbar_init(&y_free[1], kFftThreads);
+    fence_proxy_async();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  if (tid == 0) {
+    uint32_t s = 0;
+    for (int i = 0; i < kItems; ++i) { istart[i] = s; s += wmeta[i] & 0xFFu; }
+    istart[kItems] = s;
+  }
+  if (tid < kFeWarps) {
+    uint32_t f = 0;
+    for (int j = 0; j < kItemsFe; ++j) f |= wmeta[tid * kItemsFe + j] >> 31;
+    wovf[tid] = f;
+  }
+  __syncthreads();
+
+  // TMA copies of group g into staging buffer g & 1 (thread 0 only)
+  auto issue = [&](int g) {
+    const int k0 = k_begin + g * kG;
+    const int gl = min(kG, k_end - k0);
+    float* st = stage + (g & 1) * sbuf;
+    uint32_t bytes = 0;
+    for (int gg = 0; gg < gl; ++gg) bytes += static_cast<uint32_t>(p.n1) * 4u;
+    if (!p.alias)
+      for (int gg = 0; gg < gl; ++gg) bytes += static_cast<uint32_t>(p.n3) * 4u;
+    // the staging buffer was last read by generic loads that completed
+    // before the front-end barrier; no proxy fence is needed for that order
+    mbar_arrive_expect_tx(&full_stage[g & 1], bytes);
+    for (int gg = 0; gg < gl; ++gg) {
+      if (p.n1 > 0)
+        bulk_g2s(st + gg * p.npad, p.A + static_cast<size_t>(k0 + gg) * p.lda, static_cast<uint32_t>(p.n1) * 4u,
+                 &full_stage[g & 1]);
+      if (!p.alias && p.n3 > 0)
+        bulk_g2s(st + (kG + gg) * p.npad, p.B + static_cast<size_t>(k0 + gg) * p.ldb,
+                 static_cast<uint32_t>(p.n3) * 4u, &full_stage[g & 1]);
+    }
+  };
+
+  if (warp < kFeWarps) {
+    // ======================= front-end warps =================================
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsFe));
+    const int w = warp;
+    // lane quarter w mod 4, column half w div 4
+    const uint32_t tq = tmem + ((32u * static_cast<uint32_t>(w & 3)) << 16) + 256u * static_cast<uint32_t>(w >> 2);
+    // the first two groups' copies fly while the records are built
+    if (tid == 0) {
+      if (ngroups > 0) issue(0);
+      if (ngroups > 1) issue(1);
+    }
+    // records: staging index of x (shared memory, stream order) and
+    // s(x) w_b^{(h(x) f1) mod b} for both rows (TMEM: item j at columns
+    // 32 j + 4 r); padding entries (x = n) read the zeroed staging tail
+    {
+      const size_t tbase = static_cast<size_t>(t) * 2 * p.ecap;
+#pragma unroll 1
+      for (int j = 0; j < kItemsFe; ++j) {
+        const uint32_t c = wmeta[w * kItemsFe + j] & 0xFFu;
+        const uint32_t b0 = ibase[w * kItemsFe + j];
+        const uint32_t s0 = istart[w * kItemsFe + j];
+#pragma unroll 1
+        for (uint32_t r = 0; r < c; ++r) {
+          const uint32_t src = b0 + 32u * r + static_cast<uint32_t>(lane);
+          const uint32_t side = src >= p.ecap ? 1u : 0u;
+          const uint32_t x = p.rec_x[tbase + src];
+          const uint32_t hv = p.rec_hs[tbase + src];
+          float2 tw[kRows];
+#pragma unroll
+          for (int rr = 0; rr < kRows; ++rr) {
+            tw[rr] = make_float2(0.f, 0.f);
+            if (x < static_cast<uint32_t>(n)) {
+              tw[rr] = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[rr], p.b), p.tw_shift);
+              if (hv >> 31) { tw[rr].x = -tw[rr].x; tw[rr].y = -tw[rr].y; }
+            }
+          }
+          tmem_st4(tq + 32u * j + 4u * r, make_float4(tw[0].x, tw[0].y, tw[1].x, tw[1].y));
+          const uint32_t xs = min(x, static_cast<uint32_t>(n));
+          rec_x[(s0 + r) * 32u + lane] =
+              static_cast<uint16_t>((p.alias ? 0u : side * kG * static_cast<uint32_t>(p.npad)) + xs);
+        }
+      }
+      tmem_wait_st();
+    }
+    const uint32_t* wm = wmeta + w * kItemsFe;
+    const uint16_t* wd = wdst + (w * 32 + lane) * kItemsFe;
+    const uint16_t* xbase = rec_x + istart[w * kItemsFe] * 32u + lane;
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1;
+      if (!s_err && !mbar_wait_bounded_sleep(&full_stage[b], (g >> 1) & 1)) s_err = 1;
+      if (g >= 2 && !s_err && !mbar_wait_bounded_sleep(&y_free[b], ((g - 2) >> 1) & 1)) s_err = 1;
+      const float* st0 = stage + b * sbuf;
+      const float* st1 = st0 + p.npad;
+      float2* work = ybuf + static_cast<size_t>(b) * kFftWarps * kRegion;
+      const uint16_t* xp = xbase;
+      // one item: gather its (padded) entries, store the 2 x 2 sums
+      auto item = [&](uint32_t m, uint32_t dst, uint32_t taddr) {
+        const uint32_t cnt = m & 0xFFu;
+        float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
+        switch (cnt) {
+          case 1: fe_slots<1>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
+          case 2: fe_slots<2>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
+          case 3: fe_slots<3>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
+          case 4: fe_slots<4>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
+          case 5: fe_slots<5>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
+          case 6: fe_slots<6>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
+          case 7: fe_slots<7>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
+          case 8: fe_slots<8>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
+          default: break;   // an empty bucket group
+        }
+        xp += 32u * cnt;
+        float2* dp = work + dst;
+        dp[0] = a00;
+        dp[kRegion] = a01;
+        dp[2 * kG * kRegion] = a10;
+        dp[2 * kG * kRegion + kRegion] = a11;
+      };
+      // the next item's metadata loads while the current one is processed
+      uint32_t mA = wm[0], dA = wd[0];
+#pragma unroll 1
+      for (int j = 0; j < kItemsFe; ++j) {
+        const uint32_t mB = j + 1 < kItemsFe ? wm[j + 1] : 0u;
+        const uint32_t dB = j + 1 < kItemsFe ? wd[j + 1] : 0u;
+        item(mA, dA, tq + 32u * j);
+        mA = mB;
+        dA = dB;
+      }
+      // entries past the capped count of some bucket (rare): the lane that
+      // stored the bucket's Y adds them, with on-the-fly twiddles
+      if (wovf[w]) {
+#pragma unroll 1
+        for (int j = 0; j < kItemsFe; ++j) {
+          const uint32_t m = wm[j];
+          if (!(m >> 31)) continue;
+          const uint32_t dst = wd[j];
+          const int side = static_cast<int>((m >> 8) & 1u);
+          const int z2 = static_cast<int>(dst) - side * kG * kRegion;
+          const float* st = st0 + (p.alias ? 0 : side) * kG * p.npad;
+          const size_t ts = static_cast<size_t>(t) * 2 + side;
+          float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
+          const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
+          for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
+            const uint32_t x = p.ovf_x[ts * n + o];
+            const uint32_t hv = p.hs[ts * n + x];
+            float2 w0 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[0], p.b), p.tw_shift);
+            float2 w1 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[1], p.b), p.tw_shift);
+            if (hv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
+            const float v0 = st[x];
+            const float v1 = st[p.npad + x];
+            a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
+            a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
+            a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
+            a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
+          }
+          float2* dp = work + dst;
+          dp[0].x += a00.x; dp[0].y += a00.y;
+          dp[kRegion].x += a01.x; dp[kRegion].y += a01.y;
+          dp[2 * kG * kRegion].x += a10.x; dp[2 * kG * kRegion].y += a10.y;
+          dp[2 * kG * kRegion + kRegion].x += a11.x; dp[2 * kG * kRegion + kRegion].y += a11.y;
+        }
+      }
+      // Y of group g is complete, and so are this thread's reads of staging
+      // buffer b (the FFT side refills it once all 256 have arrived)
+      mbar_arrive(&y_full[b]);
+    }
+  } else {
+    // ========================== FFT warps ====================================
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsFft));
+    const int f = warp - kFeWarps;          // (row, side, k slot) = (f >> 2, (f >> 1) & 1, f & 1)
+    const int ftid = tid - kFeThreads;
+    const int side_w = (f >> 1) & 1;
+    const int g_w = f & 1;
+    const int own_m0 = side_w * 16;
+    const int pair_bar = kBarPair + ((f & 1) | ((f >> 2) << 1));
+    // lane twiddle anchors w_1024^{lane * 8 q}, q = 0..3, and the step w_1024^lane
+    float2 anchor[4];
+    float2 step;
+    {
+      float s, c;
+      sincospif(2.0f * static_cast<float>(lane) / static_cast<float>(kC), &s, &c);
+      step = make_float2(c, -s);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        sincospif(2.0f * static_cast<float>((lane * 8 * q) & (kC - 1)) / static_cast<float>(kC), &s, &c);
+        anchor[q] = make_float2(c, -s);
+      }
+    }
+    float2 part[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) part[m] = make_float2(0.f, 0.f);
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1;
+      const int gcnt = min(kG, k_end - (k_begin + g * kG));
+      if (!s_err && !mbar_wait_bounded_sleep(&y_full[b], (g >> 1) & 1)) s_err = 1;
+      // every front-end read of staging buffer b is done: refill it with
+      // group g + 2 (the first FFT thread issues the copies)
+      if (ftid == 0 && g + 2 < ngroups && !s_err) issue(g + 2);
+      float2* work = ybuf + static_cast<size_t>(b) * kFftWarps * kRegion;
+      float2* region = work + f * kRegion;
+      const float2* partner = work + (f ^ 2) * kRegion;
+      // ---- FFT of length 1024 --------------------------------------------
+      float2 x[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
+      dft32<false>(x);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2 w = anchor[q];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if (q + r > 0) x[8 * q + r] = cmul(x[8 * q + r], w);
+          w = cmul(w, step);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int ff = 0; ff < 32; ++ff) region[ff * kPitch + lane] = x[ff];
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = region[lane * kPitch + j];
+      dft32<false>(x);
+      __syncwarp();
+      // hand the partner (same row and k slot, other side) the half of the
+      // bins it accumulates
+      if (side_w == 0) {
+#pragma unroll
+        for (int m = 16; m < 32; ++m) region[lane + 32 * m] = x[m];
+      } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) region[lane + 32 * m] = x[m];
+      }
+      named_sync(pair_bar, 64);
+      // ---- spectral products: own half of the bins ------------------------
+      if (g_w < gcnt) {
+        if (side_w == 0) {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) {
+            const float2 q = partner[lane + 32 * m];
+            part[m].x = fmaf(x[m].x, q.x, part[m].x);
+            part[m].x = fmaf(-x[m].y, q.y, part[m].x);
+            part[m].y = fmaf(x[m].x, q.y, part[m].y);
+            part[m].y = fmaf(x[m].y, q.x, part[m].y);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) {
+            const float2 q = partner[lane + 32 * (16 + m)];
+            part[m].x = fmaf(x[16 + m].x, q.x, part[m].x);
+            part[m].x = fmaf(-x[16 + m].y, q.y, part[m].x);
+            part[m].y = fmaf(x[16 + m].x, q.y, part[m].y);
+            part[m].y = fmaf(x[16 + m].y, q.x, part[m].y);
+          }
+        }
+      }
+      // ---- fold the partial sums into the Kahan accumulators ---------------
+      if ((g % kFlush) == kFlush - 1 || g + 1 == ngroups) {
+        named_sync(kBarFft, kFftThreads);   // every partner read of buffer b is done
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          region[lane + 32 * (own_m0 + m)] = part[m];
+          part[m] = make_float2(0.f, 0.f);
+        }
+        named_sync(kBarFft, kFftThreads);
+#pragma unroll
+        for (int u = 0; u < (kRows * kC) / kFftThreads; ++u) {
+          const int idx = ftid + kFftThreads * u;
+          const int r = idx / kC, fb = idx % kC;
+          const int sd = fb >> 9;            // bins f < 512 live with side a, the rest with side b
+          float2 s = work[((r * 2 + sd) * kG + 0) * kRegion + fb];
+#pragma unroll
+          for (int gg = 1; gg < kG; ++gg) {
+            const float2 v = work[((r * 2 + sd) * kG + gg) * kRegion + fb];
+            s.x += v.x;
+            s.y += v.y;
+          }
+          float4 a = acc[idx];
+          kahan_add(a.x, a.z, s.x);
+          kahan_add(a.y, a.w, s.y);
+          acc[idx] = a;
+        }
+      }
+      mbar_arrive(&y_free[b]);
+    }
+    // ---- this block's partial spectra ------------------------------------------
+    named_sync(kBarFft, kFftThreads);
+#pragma unroll
+    for (int u = 0; u < (kRows * kC) / kFftThreads; ++u) {
+      const int idx = ftid + kFftThreads * u;
+      const int r = idx / kC, fb = idx % kC;
+      if (r == 1 && !row1_live) continue;
+      const float4 a = acc[idx];
+      const uint32_t frow = r ? f1r[1] : f1r[0];
+      float2* out = p.partial + ((static_cast<size_t>(t) * p.nrows + frow) * p.nkc + kc) * kC;
+      out[fb] = make_float2(a.x - a.z, a.y - a.w);
+    }
+  }
+
+  // ---- teardown ----------------------------------------------------------------
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (tid == 0 && s_err) {
+    atomicOr(&g_ws_error, 1u);
+    // copies still in flight must land before the block's shared memory is
+    // released: one more bounded wait on the phases the issues left open
+    for (int bb = 0; bb < 2; ++bb) {
+      const int issued = ngroups > bb ? (ngroups - bb + 1) / 2 : 0;   // groups bb, bb + 2, ...
+      if (issued > 0) (void)mbar_wait_bounded(&full_stage[bb], (issued - 1) & 1);
+    }
+  }
+  if (warp == 0) tmem_dealloc(tmem, 512);
+  if (tid == 0) {
+    for (int i = 0; i < 6; ++i) mbar_inval(&bars[i]);
+  }
+}
+
+}  // namespace
+
+uint32_t read_clear_error_sketch_ws() {
+  uint32_t v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_ws_error, sizeof(v)) != cudaSuccess) return 0xFFFFFFFFu;
+  if (v) cudaMemcpyToSymbol(g_ws_error, &zero, sizeof(zero));
+  return v;
+}
+
+// The register split (setmaxnreg) must fit the registers the block is
+// launched with, or the FFT warps' request would never be granted; checked
+// once against the compiled kernel's launch register count.
+bool ws_kernel_usable() {
+  static int ok = -1;
+  if (ok < 0) {
+    cudaFuncAttributes fa{};
+    ok = cudaFuncGetAttributes(&fa, k_sketch_ws) == cudaSuccess && fa.maxThreadsPerBlock >= kThreadsWs &&
+                 static_cast<int64_t>(fa.numRegs) * kThreadsWs >=
+                     static_cast<int64_t>(kFeThreads) * kRegsFe + static_cast<int64_t>(kFftThreads) * kRegsFft
+             ? 1
+             : 0;
+  }
+  return ok == 1;
+}
+
+size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi) {
+  return ws_layout(npad, ecap, alias, tw_shift, nhi).total;
+}
+
+cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,
+                             const void* B, int64_t ldb, int64_t n1, int64_t n2, int64_t n3,
+                             float2* partial, cudaStream_t s) {
+  WsArgs a{};
+  a.A = static_cast<const float*>(A);
+  a.lda = lda;
+  a.B = static_cast<const float*>(B);
+  a.ldb = ldb;
+  a.n1 = static_cast<int>(n1); a.n2 = static_cast<int>(n2); a.n3 = static_cast<int>(n3);
+  a.n = static_cast<int>(h->n);
+  a.npad = plan.npad;
+  a.b = plan.b;
+  a.nrows = plan.nrows;
+  a.nunits = (plan.nrows + 1) / 2;
+  a.kchunk = static_cast<int>(plan.kchunk);
+  a.nkc = plan.nkc;
+  a.alias = plan.alias ? 1 : 0;
+  a.ecap = h->fe_ecap;
+  a.tw_shift = plan.tw_shift;
+  a.nhi = plan.nhi;
+  a.rec_x = h->d_fe_x;
+  a.rec_hs = h->d_fe_hs;
+  a.grp = h->d_fe_grp;
+  a.dest = h->d_fe_dest;
+  a.ovf_off = h->d_fe_ovf_off;
+  a.ovf_x = h->d_fe_ovf_x;
+  a.hs = h->d_hs;
+  a.partial = partial;
+  if (!ws_kernel_usable()) return cudaErrorInvalidConfiguration;
+  const int smem = static_cast<int>(plan.smem);
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned ntask = static_cast<unsigned>(static_cast<int64_t>(plan.d) * a.nunits * plan.nkc);
+  {
+    ProfScope prof_scope("k_sketch_fused", s);
+    k_sketch_ws<<<ntask, kThreadsWs, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cms
