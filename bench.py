@@ -35,7 +35,8 @@ FLUSH_BYTES = 256 << 20            # > 129 MB L2: written between timed steps
 FP32_LANES_PER_SM = 128            # Blackwell SM: 4 partitions x 32 FP32 lanes
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_sketch_fused_covariance.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1108_1320_gb300", "csrc", f)
-                  for f in ("k_sketch.cu", "k_sketch_fast.cu", "cms_common.cuh")]
+                  for f in ("k_sketch.cu", "k_sketch_fast.cu", "k_sketch_ws.cu", "warp_fft.cuh",
+                            "cms_common.cuh")]
 
 
 def workload_label(w=WORKLOAD) -> str:

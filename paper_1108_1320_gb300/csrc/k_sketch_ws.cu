@@ -21,11 +21,12 @@
 //    thread 0 for the first two groups, then by the first FFT thread as
 //    soon as the front end has released a buffer.
 //
-// Hand-offs are mbarriers: staging full (TMA transaction count), Y full
-// (256 front-end arrivals), Y free (256 FFT arrivals); waiting warps sleep
-// in try_wait.  Every wait is bounded; after a timeout the block records the
-// error, stops waiting (the results are then garbage and reported as such)
-// but still passes every named barrier, so no warp is left behind.
+// Hand-offs: staging full is an mbarrier (TMA transaction count) with a
+// bounded wait; Y full and Y free are named barriers (bar.arrive by the
+// producing warps, bar.sync by the consuming ones), on which waiting warps
+// take no issue slots.  After a timed-out copy the block records the error
+// and stops waiting for copies (the results are then garbage and reported
+// as such) but still passes every named barrier, so no warp is left behind.
 #include <algorithm>
 
 #include "cms_internal.h"
@@ -56,6 +57,8 @@ static_assert(kFeThreads * kRegsFe + kFftThreads * kRegsFft <= 65536, "register 
 // named barriers (0 is __syncthreads)
 constexpr int kBarPair = 2;              // 2..5: FFT warp pairs, 64 threads
 constexpr int kBarFft = 6;               // FFT warps, 256 threads
+constexpr int kBarYFull = 7;             // 7, 8: Y buffer b written (front end arrives, FFT syncs)
+constexpr int kBarYFree = 9;             // 9, 10: Y buffer b consumed (FFT arrives, front end syncs)
 
 __device__ uint32_t g_ws_error = 0;      // 1: a wait gave up
 
@@ -107,13 +110,19 @@ __host__ __device__ inline WsLayout ws_layout(int npad, uint32_t ecap, int alias
   L.istart = o; o = al16(o + static_cast<size_t>(kItems + 1) * 4);
   L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
   L.wovf = o;   o = al16(o + static_cast<size_t>(kFeWarps) * 4);
-  L.bars = o;   o = al16(o + 6 * 8);
+  L.bars = o;   o = al16(o + 2 * 8);
   L.total = o;
   return L;
 }
 
 __device__ __forceinline__ void named_sync(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Producer side of a named barrier: signals arrival without waiting (the
+// hardware orders this thread's prior shared-memory accesses before it).
+__device__ __forceinline__ void named_arrive(int id, int threads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
 // Item j (0..15) of front-end warp w: round j deals one item of each group
@@ -177,8 +186,6 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   uint32_t* wovf = reinterpret_cast<uint32_t*>(sm + L.wovf);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
   uint64_t* full_stage = bars;       // [2] TMA transactions of a staging buffer
-  uint64_t* y_full = bars + 2;       // [2] 256 front-end arrivals
-  uint64_t* y_free = bars + 4;       // [2] 256 FFT arrivals
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int task = blockIdx.x;
@@ -250,10 +257,6 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   if (tid == 0) {
     mbar_init(&full_stage[0], 1);
     mbar_init(&full_stage[1], 1);
-    mbar_init(&y_full[0], kFeThreads);
-    mbar_init(&y_full[1], kFeThreads);
-    mbar_init(&y_free[0], kFftThreads);
-    mbar_init(&y_free[1], kFftThreads);
     fence_proxy_async();
   }
   tmem_fence_before_sync();
@@ -344,7 +347,8 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
     for (int g = 0; g < ngroups; ++g) {
       const int b = g & 1;
       if (!s_err && !mbar_wait_bounded_sleep(&full_stage[b], (g >> 1) & 1)) s_err = 1;
-      if (g >= 2 && !s_err && !mbar_wait_bounded_sleep(&y_free[b], ((g - 2) >> 1) & 1)) s_err = 1;
+      // the FFT warps are done with Y buffer b (group g - 2)
+      if (g >= 2) named_sync(kBarYFree + b, kThreadsWs);
       const float* st0 = stage + b * sbuf;
       const float* st1 = st0 + p.npad;
       float2* work = ybuf + static_cast<size_t>(b) * kFftWarps * kRegion;
@@ -417,7 +421,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       }
       // Y of group g is complete, and so are this thread's reads of staging
       // buffer b (the FFT side refills it once all 256 have arrived)
-      mbar_arrive(&y_full[b]);
+      named_arrive(kBarYFull + b, kThreadsWs);
     }
   } else {
     // ========================== FFT warps ====================================
@@ -447,7 +451,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
     for (int g = 0; g < ngroups; ++g) {
       const int b = g & 1;
       const int gcnt = min(kG, k_end - (k_begin + g * kG));
-      if (!s_err && !mbar_wait_bounded_sleep(&y_full[b], (g >> 1) & 1)) s_err = 1;
+      named_sync(kBarYFull + b, kThreadsWs);
       // every front-end read of staging buffer b is done: refill it with
       // group g + 2 (the first FFT thread issues the copies)
       if (ftid == 0 && g + 2 < ngroups && !s_err) issue(g + 2);
@@ -535,7 +539,8 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
           acc[idx] = a;
         }
       }
-      mbar_arrive(&y_free[b]);
+      // release Y buffer b to the front end (only if it refills it)
+      if (g + 2 < ngroups) named_arrive(kBarYFree + b, kThreadsWs);
     }
     // ---- this block's partial spectra ------------------------------------------
     named_sync(kBarFft, kFftThreads);
@@ -566,7 +571,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   }
   if (warp == 0) tmem_dealloc(tmem, 512);
   if (tid == 0) {
-    for (int i = 0; i < 6; ++i) mbar_inval(&bars[i]);
+    for (int i = 0; i < 2; ++i) mbar_inval(&bars[i]);
   }
 }
 
