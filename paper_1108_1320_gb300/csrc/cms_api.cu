@@ -128,8 +128,8 @@ cms_status fill_tables(cms_hashes* h, cudaStream_t s, bool hash) {
     if (e != cudaSuccess) return cuda_fail(e, "bucket sort kernel");
   }
   if (h->fe_ecap > 0) {
-    e = launch_frontend_tables(h->d_hs, h->d, h->n, h->fe_ecap, h->d_fe_x, h->d_fe_hs, h->d_fe_grp,
-                               h->d_fe_dest, h->d_fe_ovf_off, h->d_fe_ovf_x, s);
+    e = launch_frontend_tables(h->d_hs, h->d_perm, h->d_off, h->d, h->n, h->fe_ecap, h->d_fe_x, h->d_fe_hs,
+                               h->d_fe_grp, h->d_fe_dest, h->d_fe_ovf_off, h->d_fe_ovf_x, s);
     if (e != cudaSuccess) return cuda_fail(e, "front-end table kernel");
   }
   return CMS_OK;

@@ -66,10 +66,9 @@ cudaError_t launch_bucket_sort(const uint32_t* hs, int d, int64_t n, int64_t C,
 // Front-end record tables of the C = 1024 fused kernel.
 constexpr int kFeC = 1024;        // FFT length of the specialised kernel
 constexpr int kFeCap = 8;         // bucket entries kept in the padded layout
-cudaError_t launch_frontend_tables(const uint32_t* hs, int d, int64_t n, uint32_t ecap,
-                                   uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
-                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,
-                                   cudaStream_t s);
+cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, const uint32_t* off, int d,
+                                   int64_t n, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
+                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x, cudaStream_t s);
 uint32_t read_clear_error_sketch();
 
 // Plan of the fused sketch path for one call.

@@ -126,49 +126,53 @@ __device__ __forceinline__ uint32_t bucket_scramble(uint32_t z) {
 // (padding entries point at x = n).  The entries of each bucket are then
 // ordered so that, step by step, the 32 lanes' x fall into distinct banks
 // where the counts allow (greedy).  Entries past the kFeCap-th of a bucket
-// (in x order) go to a per-bucket overflow list.
+// (in x order) go to a per-bucket overflow list.  A bucket's entries are read
+// in x order from the stable bucket sort (perm, off); the counts, group
+// bases and overflow offsets come from warp and block scans.
 __global__ void __launch_bounds__(1024)
-k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
+k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ perm,
+                  const uint32_t* __restrict__ off, uint32_t n, uint32_t ecap,
                   uint32_t* __restrict__ rec_x, uint32_t* __restrict__ rec_hs,
                   uint32_t* __restrict__ grp, uint16_t* __restrict__ dest,
                   uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x) {
   constexpr int C = kFeC;
-  __shared__ uint32_t cnt[C];
+  constexpr uint32_t kCap = static_cast<uint32_t>(kFeCap);
+  __shared__ uint32_t cnt[C];        // entries per bucket
   __shared__ uint32_t key[C];
-  __shared__ uint32_t lanepos[C];
-  __shared__ uint32_t cursor[C];
+  __shared__ uint32_t used[C];       // greedy bank counters, 32 per warp
   __shared__ uint32_t gbase[C / 32];
-  __shared__ uint32_t oof[C + 1];
+  __shared__ uint32_t gword[C / 32];  // group count | overflow flag << 31
+  __shared__ uint32_t wtot[32];
   const int ts = blockIdx.x;
   const uint32_t* tab = hs + static_cast<size_t>(ts) * n;
+  const uint32_t* pm = perm + static_cast<size_t>(ts) * n;
+  const uint32_t* of = off + static_cast<size_t>(ts) * (C + 1);
   uint32_t* rx = rec_x + static_cast<size_t>(ts) * ecap;
   uint32_t* rh = rec_hs + static_cast<size_t>(ts) * ecap;
   uint32_t* gp = grp + static_cast<size_t>(ts) * (C / 32) * 2;
   uint16_t* ds = dest + static_cast<size_t>(ts) * C;
-  uint32_t* of = ovf_off + static_cast<size_t>(ts) * (C + 1);
+  uint32_t* oo = ovf_off + static_cast<size_t>(ts) * (C + 1);
   uint32_t* ox = ovf_x + static_cast<size_t>(ts) * n;
-  const int tid = threadIdx.x;
-  cnt[tid] = 0;
-  cursor[tid] = 0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // bucket sizes from the stable bucket sort (perm lists each bucket's x in
+  // increasing order)
+  cnt[tid] = of[tid + 1] - of[tid];
+  for (uint32_t e = tid; e < ecap; e += blockDim.x) { rx[e] = n; rh[e] = 0u; }
   __syncthreads();
-  for (uint32_t x = tid; x < n; x += blockDim.x) atomicAdd(&cnt[(tab[x] & kBucketMask) % C], 1u);
-  __syncthreads();
-  // bitonic sort (ascending) of (kFeCap - capped count) << 16 | z2
   {
     // rank of this bucket among the buckets of its class (capped count) and
     // residue z2 mod 16, in scrambled order; sorting by (class, rank / 2,
     // residue, rank % 2) makes every run of 32 buckets of a class hold each
     // residue twice (the Y stores of a group then need 2 wavefronts)
     const uint32_t z = static_cast<uint32_t>(tid);
-    const uint32_t cc = min(cnt[z], static_cast<uint32_t>(kFeCap));
+    const uint32_t cc = min(cnt[z], kCap);
     const uint32_t sk = bucket_scramble(z);
     uint32_t rank = 0;
     for (uint32_t o = z & 15u; o < static_cast<uint32_t>(C); o += 16u) {
       const uint32_t so = bucket_scramble(o);
-      if (min(cnt[o], static_cast<uint32_t>(kFeCap)) == cc && (so < sk || (so == sk && o < z))) ++rank;
+      if (min(cnt[o], kCap) == cc && (so < sk || (so == sk && o < z))) ++rank;
     }
-    key[tid] = ((static_cast<uint32_t>(kFeCap) - cc) << 20) | ((rank >> 1) << 15) | ((z & 15u) << 11) |
-               ((rank & 1u) << 10) | z;
+    key[tid] = ((kCap - cc) << 20) | ((rank >> 1) << 15) | ((z & 15u) << 11) | ((rank & 1u) << 10) | z;
   }
   __syncthreads();
   for (int size = 2; size <= C; size <<= 1) {
@@ -205,124 +209,115 @@ k_frontend_tables(const uint32_t* __restrict__ hs, uint32_t n, uint32_t ecap,
     for (int i = 0; i < 16; ++i) { grpkey[i] = half0[i]; grpkey[16 + i] = half1[i]; }
   }
   __syncthreads();
-  const uint32_t zsorted = key[tid] & 0x3FFu;
-  lanepos[zsorted] = tid;
-  ds[tid] = static_cast<uint16_t>(zsorted);
+  // thread tid = group warp, lane: its bucket, the group's padded count
+  const uint32_t zs = key[tid] & 0x3FFu;
+  ds[tid] = static_cast<uint16_t>(zs);
+  const uint32_t cz = cnt[zs];
+  const uint32_t c = min(cz, kCap);
+  uint32_t cm = c;
+  for (int o = 16; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xFFFFFFFFu, cm, o));
+  const bool any_ovf = __any_sync(0xFFFFFFFFu, cz > kCap);
+  if (lane == 0) gword[warp] = cm | (any_ovf ? 0x80000000u : 0u);
+  // overflow list offsets, by bucket index: block-wide exclusive scan
+  const uint32_t ov = cnt[tid] > kCap ? cnt[tid] - kCap : 0u;
+  uint32_t incl = ov;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t2 = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += t2;
+  }
+  if (lane == 31) wtot[warp] = incl;
   __syncthreads();
-  if (tid == 0) {
-    uint32_t run = 0;
-    for (int g = 0; g < C / 32; ++g) {
-      uint32_t m = 0;
-      for (int i = 0; i < 32; ++i)
-        m = max(m, min(cnt[key[32 * g + i] & 0x3FFu], static_cast<uint32_t>(kFeCap)));
-      uint32_t any_ovf = 0;
-      for (int i = 0; i < 32; ++i) any_ovf |= cnt[key[32 * g + i] & 0x3FFu] > static_cast<uint32_t>(kFeCap);
-      gbase[g] = run;
-      gp[2 * g] = run;
-      gp[2 * g + 1] = m | (any_ovf << 31);   // bit 31: some bucket of the group overflows
-      run += 32u * m;
+  if (warp == 0) {
+    // group bases: exclusive scan of 32 x count over the 32 groups
+    const uint32_t gw = gword[lane];
+    const uint32_t v = 32u * (gw & 0xFFFFu);
+    uint32_t gi = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t2 = __shfl_up_sync(0xFFFFFFFFu, gi, o);
+      if (lane >= o) gi += t2;
     }
-    uint32_t o = 0;
-    for (int z = 0; z < C; ++z) {
-      oof[z] = o;
-      of[z] = o;
-      o += cnt[z] > static_cast<uint32_t>(kFeCap) ? cnt[z] - kFeCap : 0u;
+    gbase[lane] = gi - v;
+    gp[2 * lane] = gi - v;
+    gp[2 * lane + 1] = gw;
+    // warp offsets of the overflow scan
+    const uint32_t wv = wtot[lane];
+    uint32_t wi = wv;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t2 = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += t2;
     }
-    oof[C] = o;
-    of[C] = o;
+    wtot[lane] = wi - wv;
+    if (lane == 31) oo[C] = wi;
   }
   __syncthreads();
-  for (uint32_t e = tid; e < ecap; e += blockDim.x) { rx[e] = n; rh[e] = 0u; }
+  const uint32_t my_oof = wtot[warp] + incl - ov;   // bucket tid's first overflow slot
+  oo[tid] = my_oof;
+  cnt[tid] = my_oof;                                 // now: overflow offset by bucket
   __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31;
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  for (uint32_t base = 0; base < n; base += blockDim.x) {
-    const uint32_t x = base + tid;
-    const bool valid = x < n;
-    const uint32_t w = valid ? tab[x] : 0u;
-    const uint32_t z = valid ? (w & kBucketMask) % C : 0xFFFFFFFFu;
-    for (int wv = 0; wv < 32; ++wv) {
-      __syncthreads();
-      if (warp == wv) {
-        const uint32_t grpmask = __match_any_sync(0xFFFFFFFFu, z);
-        if (valid) {
-          const uint32_t r = cursor[z] + __popc(grpmask & lt_mask);
-          if (r < static_cast<uint32_t>(kFeCap)) {
-            const uint32_t p = lanepos[z];
-            const uint32_t pos = gbase[p >> 5] + 32u * r + (p & 31u);
-            rx[pos] = x;
-            rh[pos] = w;
-          } else {
-            ox[oof[z] + (r - kFeCap)] = x;
-          }
-        }
-        __syncwarp();
-        if (valid && lane == __ffs(grpmask) - 1) cursor[z] += __popc(grpmask);
-      }
-    }
-  }
-  __syncthreads();
-  // bank-aware order of each bucket's entries: warp g owns group g, lane l
-  // the bucket at group position l.  Step r gives each lane, in order of
-  // ascending count, its remaining entry whose bank (x mod 32) is least
-  // used at this step so far; padding lanes all read x = n (one address).
+  // this lane's entries (the first kFeCap in x order) and the overflow
+  // entries of its bucket
+  const uint32_t o0 = of[zs];
+  const uint32_t oz = cnt[zs];
+  uint32_t xs[kFeCap], wsv[kFeCap];
+#pragma unroll
+  for (uint32_t r = 0; r < kCap; ++r)
+    if (r < c) xs[r] = pm[o0 + r];
+#pragma unroll
+  for (uint32_t r = 0; r < kCap; ++r)
+    if (r < c) wsv[r] = tab[xs[r]];
+  for (uint32_t r = kCap; r < cz; ++r) ox[oz + (r - kCap)] = pm[o0 + r];
+  // bank-aware order of each bucket's entries: step r gives each lane, in
+  // order of ascending count, its remaining entry whose bank (x mod 32) is
+  // least used at this step so far; padding lanes all read x = n (one
+  // address)
   {
-    uint32_t* used = cursor + 32 * warp;   // 32 bank counters per warp
-    const uint32_t z = key[tid] & 0x3FFu;
-    const uint32_t c = min(cnt[z], static_cast<uint32_t>(kFeCap));
-    const uint32_t gb = gbase[warp];
-    const uint32_t cm = gp[2 * warp + 1] & 0xFFFFu;
-    uint32_t xs[kFeCap], ws[kFeCap];
-    for (uint32_t r = 0; r < c; ++r) {
-      xs[r] = rx[gb + 32u * r + lane];
-      ws[r] = rh[gb + 32u * r + lane];
-    }
-    // rank of this lane by (count, lane)
+    uint32_t* ub = used + 32 * warp;
     uint32_t rank = 0;
     for (int o = 0; o < 32; ++o) {
       const uint32_t co = __shfl_sync(0xFFFFFFFFu, c, o);
       rank += (co < c || (co == c && o < lane)) ? 1u : 0u;
     }
     for (uint32_t r = 0; r < cm; ++r) {
-      used[lane] = 0;
+      ub[lane] = 0;
       const bool pads = __any_sync(0xFFFFFFFFu, c <= r);
       __syncwarp();
-      if (lane == 0 && pads) used[n & 31u] = 1;
+      if (lane == 0 && pads) ub[n & 31u] = 1;
       __syncwarp();
       for (uint32_t k = 0; k < 32; ++k) {
         if (rank == k && r < c) {
           uint32_t best = r, bu = 0xFFFFFFFFu;
           for (uint32_t i = r; i < c; ++i) {
-            const uint32_t u = used[xs[i] & 31u];
+            const uint32_t u = ub[xs[i] & 31u];
             if (u < bu) { bu = u; best = i; }
           }
-          const uint32_t tx = xs[r], tw = ws[r];
-          xs[r] = xs[best]; ws[r] = ws[best];
-          xs[best] = tx; ws[best] = tw;
-          used[xs[r] & 31u] += 1;
+          const uint32_t tx = xs[r], tw = wsv[r];
+          xs[r] = xs[best]; wsv[r] = wsv[best];
+          xs[best] = tx; wsv[best] = tw;
+          ub[xs[r] & 31u] += 1;
         }
         __syncwarp();
       }
     }
-    for (uint32_t r = 0; r < c; ++r) {
-      rx[gb + 32u * r + lane] = xs[r];
-      rh[gb + 32u * r + lane] = ws[r];
-    }
+  }
+  const uint32_t gb = gbase[warp];
+  for (uint32_t r = 0; r < c; ++r) {
+    rx[gb + 32u * r + lane] = xs[r];
+    rh[gb + 32u * r + lane] = wsv[r];
   }
 }
 
 }  // namespace
 
-cudaError_t launch_frontend_tables(const uint32_t* hs, int d, int64_t n, uint32_t ecap,
-                                   uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
-                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,
-                                   cudaStream_t s) {
+cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, const uint32_t* off, int d,
+                                   int64_t n, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
+                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x, cudaStream_t s) {
   {
     ProfScope prof_scope("k_frontend_tables", s);
-    k_frontend_tables<<<2 * d, 1024, 0, s>>>(hs, static_cast<uint32_t>(n), ecap, rec_x, rec_hs,
+    k_frontend_tables<<<2 * d, 1024, 0, s>>>(hs, perm, off, static_cast<uint32_t>(n), ecap, rec_x, rec_hs,
                                              grp, dest, ovf_off, ovf_x);
   }
   return cudaGetLastError();
 }
+
 
 }  // namespace cms
