@@ -85,6 +85,7 @@ struct SketchPlan {
   size_t smem = 0;          // dynamic shared memory of the fused kernel
   bool fast = false;        // the C = 1024 register-FFT kernel applies
   bool ws = false;          // ... in its warp-specialised form (k_sketch_ws)
+  int ovcap = 0;            // overflow entries whose twiddles k_sketch_ws caches
   bool alias = false;       // A and B are the same bytes (stage once)
   int npad = 0;             // staging row length of the fast kernel (floats)
   int tw_shift = 0, nhi = 0;  // two-level w_b table: S = 2^tw_shift, nhi high entries
@@ -100,7 +101,7 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
                      const void* B = nullptr, int64_t ldb = 0, bool allow_fast = true,
                      int nkc_override = 0, int G_override = 0, bool allow_ws = true);
 size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi);
-size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi);
+size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int ovcap);
 bool ws_kernel_usable();
 cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,
                              const void* B, int64_t ldb, int64_t n1, int64_t n2, int64_t n3,

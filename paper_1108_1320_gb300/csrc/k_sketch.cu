@@ -219,12 +219,20 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
     p.tw_shift = sh;
     p.nhi = static_cast<int>((p.b + (static_cast<int64_t>(1) << sh) - 1) >> sh);
     const size_t sm = fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi);
-    const size_t sm_ws = ws_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi);
-    const bool ws_ok = allow_ws && sm_ws <= smem_optin && ws_kernel_usable();
+    // the warp-specialised kernel caches up to 1024 overflow twiddles in the
+    // shared memory left over (at least 64 entries, or it is not used)
+    const size_t ws_base = ws_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, 0);
+    // (1 KB is left for the kernel's static shared variables)
+    const int ovcap = ws_base + 64 * 18 + 1024 <= smem_optin
+                          ? static_cast<int>(std::min<size_t>(1024, (smem_optin - ws_base - 1024) / 18))
+                          : 0;
+    const size_t sm_ws = ws_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, ovcap);
+    const bool ws_ok = allow_ws && ovcap >= 64 && sm_ws <= smem_optin && ws_kernel_usable();
     // the front-end records hold staging indices (< 3 npad) in 16 bits
     if ((sm <= smem_optin || ws_ok) && 3 * static_cast<int64_t>(p.npad) <= 65535) {
       p.fast = true;
       p.ws = ws_ok;
+      p.ovcap = ws_ok ? ovcap : 0;
       p.G = 2;
       p.threads = ws_ok ? 384 : 256;
       p.smem = ws_ok ? sm_ws : sm;

@@ -149,6 +149,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   const bool row1_live = 2 * unit + 1 < p.nrows;
   const int n = p.n;
   const int S = 1 << p.tw_shift;
+  const ModB modb = make_modb(p.b);
   const int nstage = p.alias ? 1 : 2;
   const int k_begin = kc * p.kchunk;
   const int k_end = min(p.n2, k_begin + p.kchunk);
@@ -232,7 +233,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
       for (int r = 0; r < kRows; ++r) {
         tw[r] = make_float2(0.f, 0.f);
         if (x < static_cast<uint32_t>(n)) {
-          tw[r] = wb(tlo, thi, mulmod(w & kBucketMask, f1r[r], p.b), p.tw_shift);
+          tw[r] = wb(tlo, thi, mulmod(w & kBucketMask, f1r[r], modb), p.tw_shift);
           if (w >> 31) { tw[r].x = -tw[r].x; tw[r].y = -tw[r].y; }
         }
       }
@@ -350,8 +351,8 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
           for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
             const uint32_t x = p.ovf_x[ts * n + o];
             const uint32_t wv = p.hs[ts * n + x];
-            float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], p.b), p.tw_shift);
-            float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], p.b), p.tw_shift);
+            float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], modb), p.tw_shift);
+            float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], modb), p.tw_shift);
             if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
             const float v0 = st[x];
             const float v1 = st[p.npad + x];

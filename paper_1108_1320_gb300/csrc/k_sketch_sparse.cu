@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
   const int t = task / (p.nkc * p.nrows);
   const uint32_t f1 = static_cast<uint32_t>(row);
   const int S = 1 << p.tw_shift;
+  const ModB modb = make_modb(p.b);
   const int l_begin = kc * p.kchunk;
   const int l_end = min(p.K, l_begin + p.kchunk);
 
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
           if (x >= 0 && x < nside) {
             const uint32_t w = __ldg(tab + x);
             const uint32_t h = w & kBucketMask;
-            float2 tw = wb(tlo, thi, mulmod(h, f1, p.b), p.tw_shift);
+            float2 tw = wb(tlo, thi, mulmod(h, f1, modb), p.tw_shift);
             if (w >> 31) { tw.x = -tw.x; tw.y = -tw.y; }
             contrib = make_float2(v * tw.x, v * tw.y);
             z2 = h & (kC - 1);

@@ -59,6 +59,7 @@ constexpr int kBarPair = 2;              // 2..5: FFT warp pairs, 64 threads
 constexpr int kBarFft = 6;               // FFT warps, 256 threads
 constexpr int kBarYFull = 7;             // 7, 8: Y buffer b written (front end arrives, FFT syncs)
 constexpr int kBarYFree = 9;             // 9, 10: Y buffer b consumed (FFT arrives, front end syncs)
+constexpr int kBarFeOvf = 11;            // front-end warps: overflow cache written
 
 __device__ uint32_t g_ws_error = 0;      // 1: a wait gave up
 
@@ -82,10 +83,11 @@ struct WsArgs {
   const uint32_t* ovf_x;
   const uint32_t* hs;
   float2* partial;
+  int ovcap;          // overflow entries whose twiddles the prologue caches
 };
 
 struct WsLayout {
-  size_t stage, rec_x, ybuf, acc, tlo, thi, wmeta, wdst, ibase, istart, ovf, wovf, bars, total;
+  size_t stage, rec_x, ybuf, acc, tlo, thi, wmeta, wdst, ibase, istart, ovf, wovf, ovtw, ovx, bars, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
@@ -95,7 +97,8 @@ __host__ __device__ inline size_t stage_floats(int npad, int alias) {
   return static_cast<size_t>(alias ? 1 : 2) * kG * npad;
 }
 
-__host__ __device__ inline WsLayout ws_layout(int npad, uint32_t ecap, int alias, int tw_shift, int nhi) {
+__host__ __device__ inline WsLayout ws_layout(int npad, uint32_t ecap, int alias, int tw_shift, int nhi,
+                                              int ovcap) {
   WsLayout L{};
   size_t o = 0;
   L.stage = o;  o = al16(o + 2 * stage_floats(npad, alias) * 4);
@@ -110,6 +113,8 @@ __host__ __device__ inline WsLayout ws_layout(int npad, uint32_t ecap, int alias
   L.istart = o; o = al16(o + static_cast<size_t>(kItems + 1) * 4);
   L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
   L.wovf = o;   o = al16(o + static_cast<size_t>(kFeWarps) * 4);
+  L.ovtw = o;   o = al16(o + static_cast<size_t>(ovcap) * 16);
+  L.ovx = o;    o = al16(o + static_cast<size_t>(ovcap) * 2);
   L.bars = o;   o = al16(o + 2 * 8);
   L.total = o;
   return L;
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_err;
 
-  const WsLayout L = ws_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi);
+  const WsLayout L = ws_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi, p.ovcap);
   float* stage = reinterpret_cast<float*>(sm + L.stage);
   uint16_t* rec_x = reinterpret_cast<uint16_t*>(sm + L.rec_x);     // [stream slot][lane]
   float2* ybuf = reinterpret_cast<float2*>(sm + L.ybuf);           // [buffer][FFT warp][kRegion]
@@ -184,6 +189,8 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart);   // [fe warp][item]: first stream slot
   uint16_t* ovf = reinterpret_cast<uint16_t*>(sm + L.ovf);
   uint32_t* wovf = reinterpret_cast<uint32_t*>(sm + L.wovf);
+  float4* ovtw = reinterpret_cast<float4*>(sm + L.ovtw);         // cached overflow twiddles (both rows)
+  uint16_t* ovx = reinterpret_cast<uint16_t*>(sm + L.ovx);       // their staging indices
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
   uint64_t* full_stage = bars;       // [2] TMA transactions of a staging buffer
 
@@ -198,6 +205,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   const bool row1_live = 2 * unit + 1 < p.nrows;
   const int n = p.n;
   const int S = 1 << p.tw_shift;
+  const ModB modb = make_modb(p.b);
   const int nside = p.alias ? 1 : 2;
   const size_t sbuf = stage_floats(p.npad, p.alias);
   const int k_begin = kc * p.kchunk;
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
           for (int rr = 0; rr < kRows; ++rr) {
             tw[rr] = make_float2(0.f, 0.f);
             if (x < static_cast<uint32_t>(n)) {
-              tw[rr] = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[rr], p.b), p.tw_shift);
+              tw[rr] = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[rr], modb), p.tw_shift);
               if (hv >> 31) { tw[rr].x = -tw[rr].x; tw[rr].y = -tw[rr].y; }
             }
           }
@@ -341,6 +349,23 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       }
       tmem_wait_st();
     }
+    // twiddles of the entries past the capped count (overflow lists of both
+    // sides), cached for the whole task up to the shared-memory capacity
+    const uint32_t novf_a = ovf[kC];
+    const uint32_t nov = min(novf_a + static_cast<uint32_t>(ovf[(kC + 1) + kC]),
+                             static_cast<uint32_t>(p.ovcap));
+    for (uint32_t i = static_cast<uint32_t>(tid); i < nov; i += kFeThreads) {
+      const uint32_t side = i >= novf_a ? 1u : 0u;
+      const size_t ts = static_cast<size_t>(t) * 2 + side;
+      const uint32_t x = p.ovf_x[ts * n + (i - side * novf_a)];
+      const uint32_t hv = p.hs[ts * n + x];
+      float2 w0 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[0], modb), p.tw_shift);
+      float2 w1 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[1], modb), p.tw_shift);
+      if (hv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
+      ovtw[i] = make_float4(w0.x, w0.y, w1.x, w1.y);
+      ovx[i] = static_cast<uint16_t>((p.alias ? 0u : side * kG * static_cast<uint32_t>(p.npad)) + x);
+    }
+    named_sync(kBarFeOvf, kFeThreads);
     const uint32_t* wm = wmeta + w * kItemsFe;
     const uint16_t* wd = wdst + (w * 32 + lane) * kItemsFe;
     const uint16_t* xbase = rec_x + istart[w * kItemsFe] * 32u + lane;
@@ -395,22 +420,33 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
           const uint32_t dst = wd[j];
           const int side = static_cast<int>((m >> 8) & 1u);
           const int z2 = static_cast<int>(dst) - side * kG * kRegion;
-          const float* st = st0 + (p.alias ? 0 : side) * kG * p.npad;
           const size_t ts = static_cast<size_t>(t) * 2 + side;
+          const uint32_t obase = side ? novf_a : 0u;
+          const uint32_t soff = p.alias ? 0u : static_cast<uint32_t>(side * kG * p.npad);
           float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
           const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
           for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
-            const uint32_t x = p.ovf_x[ts * n + o];
-            const uint32_t hv = p.hs[ts * n + x];
-            float2 w0 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[0], p.b), p.tw_shift);
-            float2 w1 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[1], p.b), p.tw_shift);
-            if (hv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
-            const float v0 = st[x];
-            const float v1 = st[p.npad + x];
-            a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
-            a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
-            a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
-            a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
+            float4 w;
+            uint32_t xi;
+            if (obase + o < nov) {
+              w = ovtw[obase + o];
+              xi = ovx[obase + o];
+            } else {
+              // beyond the cache: twiddles on the fly
+              const uint32_t x = p.ovf_x[ts * n + o];
+              const uint32_t hv = p.hs[ts * n + x];
+              float2 w0 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[0], modb), p.tw_shift);
+              float2 w1 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[1], modb), p.tw_shift);
+              if (hv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
+              w = make_float4(w0.x, w0.y, w1.x, w1.y);
+              xi = soff + x;
+            }
+            const float v0 = st0[xi];
+            const float v1 = st1[xi];
+            a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
+            a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
+            a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
+            a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
           }
           float2* dp = work + dst;
           dp[0].x += a00.x; dp[0].y += a00.y;
@@ -600,8 +636,8 @@ bool ws_kernel_usable() {
   return ok == 1;
 }
 
-size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi) {
-  return ws_layout(npad, ecap, alias, tw_shift, nhi).total;
+size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int ovcap) {
+  return ws_layout(npad, ecap, alias, tw_shift, nhi, ovcap).total;
 }
 
 cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,
@@ -632,6 +668,7 @@ cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const 
   a.ovf_x = h->d_fe_ovf_x;
   a.hs = h->d_hs;
   a.partial = partial;
+  a.ovcap = plan.ovcap;
   if (!ws_kernel_usable()) return cudaErrorInvalidConfiguration;
   const int smem = static_cast<int>(plan.smem);
   cudaError_t e = cudaFuncSetAttribute(k_sketch_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -273,8 +273,26 @@ __device__ __forceinline__ float2 wb(const float2* tlo, const float2* thi, uint3
   return cmul(thi[m >> sh], tlo[m & ((1u << sh) - 1u)]);
 }
 
-__device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, int64_t b) {
-  return static_cast<uint32_t>((static_cast<uint64_t>(h) * f1) % static_cast<uint64_t>(b));
+// (h f1) mod b for h < b <= 2^31, f1 < 2^21 by a Barrett reduction with
+// m = floor((2^64 - 1) / b): the estimate q = mulhi(h f1, m) is floor(h f1 / b)
+// or one less (h f1 < 2^52), so one conditional subtraction is exact.
+struct ModB {
+  uint64_t b, m;
+};
+
+__device__ __forceinline__ ModB make_modb(int64_t b) {
+  ModB r;
+  r.b = static_cast<uint64_t>(b);
+  r.m = ~0ull / r.b;
+  return r;
+}
+
+__device__ __forceinline__ uint32_t mulmod(uint32_t h, uint32_t f1, const ModB& mb) {
+  const uint64_t x = static_cast<uint64_t>(h) * f1;
+  const uint64_t q = __umul64hi(x, mb.m);
+  uint64_t r = x - q * mb.b;
+  if (r >= mb.b) r -= mb.b;
+  return static_cast<uint32_t>(r);
 }
 
 

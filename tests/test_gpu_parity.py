@@ -368,6 +368,27 @@ def test_fast_kernel_overflow_buckets(cms):
     h.free()
 
 
+def test_overflow_lists_beyond_the_twiddle_cache(cms):
+    # side-a hash with 2 buckets of 1024 entries each: 2032 entries go through
+    # the overflow lists, more than the fused kernel caches per task (at most
+    # 1024), so both the cached and the on-the-fly twiddles are used; X^T X
+    # (aliased operands) as in the covariance workload
+    n, m, b = 2048, 20, 2048
+    X = W.gaussian(m, n, 31).astype(np.float32)
+    g = W.rng(6)
+    h1 = (np.arange(n) % 2 * 517)[None, :].astype(np.uint32)
+    h2 = g.integers(0, b, size=(1, n)).astype(np.uint32)
+    s1 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    s2 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    h = cms.Hashes.from_tables(h1, s1, h2, s2, b)
+    xt = torch.from_numpy(X).to(dev())
+    c = cms.sketch_product(xt.T, xt, h).cpu().numpy()
+    tab = O.Tables(h1.astype(np.int64), s1.astype(np.int64), h2.astype(np.int64), s2.astype(np.int64), b)
+    ref = O.sketch_definition(X.T.astype(np.float64), X.astype(np.float64), tab)
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
 def test_fast_and_generic_kernels_agree(cms):
     # same product through the TMA kernel (aligned rows) and the generic
     # kernel (leading dimension not a multiple of 4 floats)
