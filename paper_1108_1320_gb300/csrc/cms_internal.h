@@ -29,6 +29,7 @@ struct cms_hashes {
   uint16_t* d_fe_dest = nullptr;   // [d][2][C]
   uint32_t* d_fe_ovf_off = nullptr;  // [d][2][C+1]
   uint32_t* d_fe_ovf_x = nullptr;    // [d][2][n]
+  uint8_t* d_fe_assign = nullptr;    // [d][2][32]: bucket group of each (warp, slot), cost-balanced
 };
 
 namespace cms {
@@ -68,7 +69,8 @@ constexpr int kFeC = 1024;        // FFT length of the specialised kernel
 constexpr int kFeCap = 8;         // bucket entries kept in the padded layout
 cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, const uint32_t* off, int d,
                                    int64_t n, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
-                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x, cudaStream_t s);
+                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x, uint8_t* assign,
+                                   cudaStream_t s);
 uint32_t read_clear_error_sketch();
 
 // Plan of the fused sketch path for one call.

@@ -82,6 +82,7 @@ struct WsArgs {
   const uint32_t* ovf_off;
   const uint32_t* ovf_x;
   const uint32_t* hs;
+  const uint8_t* assign;   // [t][side][32]: bucket group of (front-end warp, slot)
   float2* partial;
   int ovcap;          // overflow entries whose twiddles the prologue caches
 };
@@ -130,12 +131,11 @@ __device__ __forceinline__ void named_arrive(int id, int threads) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// Item j (0..15) of front-end warp w: round j deals one item of each group
-// of four to every warp, in snake order so that the heavy (first) bucket
-// groups of each side spread over the warps.
-__host__ __device__ inline int fe_item(int w, int j) {
-  const int slot = (j & 1) ? (kFeWarps - 1 - w) : w;
-  return j * kFeWarps + slot;
+// Item j (0..7) of front-end warp w: side j div 4, and the bucket group that
+// the table builder dealt to slot 4 w + (j mod 4) of that side (groups
+// balanced over the warps by padded count plus longest overflow list).
+__device__ __forceinline__ int fe_group(const WsArgs& p, int t, int w, int j) {
+  return p.assign[(static_cast<size_t>(t) * 2 + (j >> 2)) * (kC / 32) + w * 4 + (j & 3)];
 }
 
 // The NC padded entries of one bucket (NC = the item's count, uniform over
@@ -233,8 +233,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   }
   if (tid < kItems) {
     const int w = tid / kItemsFe, j = tid % kItemsFe;
-    const int item = fe_item(w, j);
-    const int side = item & 1, gi = item >> 1;
+    const int side = j >> 2, gi = fe_group(p, t, w, j);
     const size_t ts = static_cast<size_t>(t) * 2 + side;
     const uint32_t gb = p.grp[(ts * (kC / 32) + gi) * 2];
     const uint32_t gy = p.grp[(ts * (kC / 32) + gi) * 2 + 1];
@@ -243,8 +242,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   }
   for (int i = tid; i < kFeWarps * 32 * kItemsFe; i += kThreadsWs) {
     const int w = i / (32 * kItemsFe), l = (i / kItemsFe) % 32, j = i % kItemsFe;
-    const int item = fe_item(w, j);
-    const int side = item & 1, gi = item >> 1;
+    const int side = j >> 2, gi = fe_group(p, t, w, j);
     const size_t ts = static_cast<size_t>(t) * 2 + side;
     wdst[i] = static_cast<uint16_t>(side * kG * kRegion + p.dest[ts * kC + gi * 32 + l]);
   }
@@ -667,6 +665,7 @@ cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const 
   a.ovf_off = h->d_fe_ovf_off;
   a.ovf_x = h->d_fe_ovf_x;
   a.hs = h->d_hs;
+  a.assign = h->d_fe_assign;
   a.partial = partial;
   a.ovcap = plan.ovcap;
   if (!ws_kernel_usable()) return cudaErrorInvalidConfiguration;

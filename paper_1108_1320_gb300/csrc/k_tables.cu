@@ -134,7 +134,8 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
                   const uint32_t* __restrict__ off, uint32_t n, uint32_t ecap,
                   uint32_t* __restrict__ rec_x, uint32_t* __restrict__ rec_hs,
                   uint32_t* __restrict__ grp, uint16_t* __restrict__ dest,
-                  uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x) {
+                  uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x,
+                  uint8_t* __restrict__ assign) {
   constexpr int C = kFeC;
   constexpr uint32_t kCap = static_cast<uint32_t>(kFeCap);
   __shared__ uint32_t cnt[C];        // entries per bucket
@@ -143,6 +144,7 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   __shared__ uint32_t gbase[C / 32];
   __shared__ uint32_t gword[C / 32];  // group count | overflow flag << 31
   __shared__ uint32_t wtot[32];
+  __shared__ uint32_t gcost[C / 32];  // slots + longest overflow list of a group
   const int ts = blockIdx.x;
   const uint32_t* tab = hs + static_cast<size_t>(ts) * n;
   const uint32_t* pm = perm + static_cast<size_t>(ts) * n;
@@ -217,7 +219,12 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   uint32_t cm = c;
   for (int o = 16; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xFFFFFFFFu, cm, o));
   const bool any_ovf = __any_sync(0xFFFFFFFFu, cz > kCap);
-  if (lane == 0) gword[warp] = cm | (any_ovf ? 0x80000000u : 0u);
+  uint32_t om = cz > kCap ? cz - kCap : 0u;
+  for (int o = 16; o > 0; o >>= 1) om = max(om, __shfl_xor_sync(0xFFFFFFFFu, om, o));
+  if (lane == 0) {
+    gword[warp] = cm | (any_ovf ? 0x80000000u : 0u);
+    gcost[warp] = cm + om;
+  }
   // overflow list offsets, by bucket index: block-wide exclusive scan
   const uint32_t ov = cnt[tid] > kCap ? cnt[tid] - kCap : 0u;
   uint32_t incl = ov;
@@ -248,6 +255,29 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
     }
     wtot[lane] = wi - wv;
     if (lane == 31) oo[C] = wi;
+  }
+  if (tid == 32) {
+    // the 32 groups dealt to 8 front-end warps x 4 slots, heaviest first to
+    // the least-loaded warp with a free slot (the warp-specialised kernel
+    // takes 4 groups of each side per warp)
+    uint8_t* as = assign + static_cast<size_t>(ts) * (C / 32);
+    int ord[C / 32];
+    for (int g = 0; g < C / 32; ++g) {
+      int q = g;
+      while (q > 0 && gcost[ord[q - 1]] < gcost[g]) { ord[q] = ord[q - 1]; --q; }
+      ord[q] = g;
+    }
+    uint32_t load[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int fill[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < C / 32; ++i) {
+      const int g = ord[i];
+      int best = -1;
+      for (int w = 0; w < 8; ++w)
+        if (fill[w] < 4 && (best < 0 || load[w] < load[best])) best = w;
+      as[best * 4 + fill[best]] = static_cast<uint8_t>(g);
+      ++fill[best];
+      load[best] += gcost[g];
+    }
   }
   __syncthreads();
   const uint32_t my_oof = wtot[warp] + incl - ov;   // bucket tid's first overflow slot
@@ -310,14 +340,16 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
 
 cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, const uint32_t* off, int d,
                                    int64_t n, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
-                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x, cudaStream_t s) {
+                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x, uint8_t* assign,
+                                   cudaStream_t s) {
   {
     ProfScope prof_scope("k_frontend_tables", s);
     k_frontend_tables<<<2 * d, 1024, 0, s>>>(hs, perm, off, static_cast<uint32_t>(n), ecap, rec_x, rec_hs,
-                                             grp, dest, ovf_off, ovf_x);
+                                             grp, dest, ovf_off, ovf_x, assign);
   }
   return cudaGetLastError();
 }
+
 
 
 }  // namespace cms
