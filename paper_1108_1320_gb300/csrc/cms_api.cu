@@ -88,14 +88,15 @@ cms_status alloc_tables(cms_hashes* h) {
     e = cudaMalloc(&h->d_off, static_cast<size_t>(h->d) * 2 * (h->C + 1) * sizeof(uint32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(bucket offsets)");
   }
-  if (h->C == kFeC && h->n <= 65535) {
+  if (h->C % 32 == 0 && fe_supported_L(h->C / 32) && h->n <= 65535) {
     h->fe_ecap = static_cast<uint32_t>(h->n + 32 * kFeCap);
     const size_t ts = static_cast<size_t>(h->d) * 2;
+    const size_t C = static_cast<size_t>(h->C);
     if ((e = cudaMalloc(&h->d_fe_x, ts * h->fe_ecap * 4)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_fe_hs, ts * h->fe_ecap * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_fe_grp, ts * (kFeC / 32) * 2 * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_fe_dest, ts * kFeC * 2)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_fe_ovf_off, ts * (kFeC + 1) * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_grp, ts * (C / 32) * 2 * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_dest, ts * C * 2)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_ovf_off, ts * (C + 1) * 4)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_fe_ovf_x, ts * h->n * 4)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_fe_assign, ts * (kFeC / 32))) != cudaSuccess)
       return cuda_fail(e, "cudaMalloc(front-end records)");
@@ -131,7 +132,7 @@ cms_status fill_tables(cms_hashes* h, cudaStream_t s, bool hash) {
     if (e != cudaSuccess) return cuda_fail(e, "bucket sort kernel");
   }
   if (h->fe_ecap > 0) {
-    e = launch_frontend_tables(h->d_hs, h->d_perm, h->d_off, h->d, h->n, h->fe_ecap, h->d_fe_x, h->d_fe_hs,
+    e = launch_frontend_tables(h->d_hs, h->d_perm, h->d_off, h->d, h->n, h->C, h->fe_ecap, h->d_fe_x, h->d_fe_hs,
                                h->d_fe_grp, h->d_fe_dest, h->d_fe_ovf_off, h->d_fe_ovf_x, h->d_fe_assign, s);
     if (e != cudaSuccess) return cuda_fail(e, "front-end table kernel");
   }

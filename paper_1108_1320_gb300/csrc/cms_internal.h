@@ -68,9 +68,13 @@ cudaError_t launch_bucket_sort(const uint32_t* hs, int d, int64_t n, int64_t C,
 constexpr int kFeC = 1024;        // FFT length of the specialised kernel
 constexpr int kFeCap = 8;         // bucket entries kept in the padded layout
 cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, const uint32_t* off, int d,
-                                   int64_t n, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
-                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x, uint8_t* assign,
-                                   cudaStream_t s);
+                                   int64_t n, int64_t C, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs,
+                                   uint32_t* grp, uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,
+                                   uint8_t* assign, cudaStream_t s);
+// The C = 32 L register-FFT kernels (front-end records exist) handle these L.
+inline bool fe_supported_L(int64_t L) {
+  return L == 16 || L == 18 || L == 20 || L == 24 || L == 25 || L == 27 || L == 30 || L == 32;
+}
 uint32_t read_clear_error_sketch();
 
 // Plan of the fused sketch path for one call.

@@ -156,12 +156,21 @@ size_t fused_smem_bytes(int C, int G, int n, int dt) {
 
 }  // namespace
 
+// b = R x C.  C = 32 L with L one of the register-FFT kernels' lengths when
+// such a factor divides b (the largest one), else the largest divisor of b
+// up to 1024 (the shared-memory kernel takes any 5-smooth C).
 bool choose_factorisation(int64_t b, int64_t* R, int64_t* C) {
   int rad[64];
   if (b < 1 || factor_radices(b, rad, 64) < 0) { *R = 0; *C = 0; return false; }
   int64_t best = 1;
   for (int64_t c = 1; c <= std::min<int64_t>(b, 1024); ++c)
     if (b % c == 0) best = c;
+  for (int64_t L = 32; L >= 16; --L) {
+    if (fe_supported_L(L) && b % (32 * L) == 0) {
+      best = 32 * L;
+      break;
+    }
+  }
   *C = best;
   *R = b / best;
   return true;
@@ -211,7 +220,7 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   const bool aligned = (A == nullptr || reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                        (B == nullptr || reinterpret_cast<uintptr_t>(B) % 16 == 0) &&
                        lda % 4 == 0 && ldb % 4 == 0 && n1 % 4 == 0 && n3 % 4 == 0;
-  if (allow_fast && dt == CMS_F32 && p.C == kFeC && h->fe_ecap > 0 && aligned) {
+  if (allow_fast && dt == CMS_F32 && p.C % 32 == 0 && fe_supported_L(p.C / 32) && h->fe_ecap > 0 && aligned) {
     p.alias = A != nullptr && A == B && lda == ldb && n1 == n3;
     p.npad = static_cast<int>(((h->n + 1) + 3) / 4 * 4);
     int sh = 0;
@@ -227,7 +236,7 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
                           ? static_cast<int>(std::min<size_t>(1024, (smem_optin - ws_base - 1024) / 18))
                           : 0;
     const size_t sm_ws = ws_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, ovcap);
-    const bool ws_ok = allow_ws && ovcap >= 64 && sm_ws <= smem_optin && ws_kernel_usable();
+    const bool ws_ok = allow_ws && p.C == kFeC && ovcap >= 64 && sm_ws <= smem_optin && ws_kernel_usable();
     // the front-end records hold staging indices (< 3 npad) in 16 bits
     if ((sm <= smem_optin || ws_ok) && 3 * static_cast<int64_t>(p.npad) <= 65535) {
       p.fast = true;

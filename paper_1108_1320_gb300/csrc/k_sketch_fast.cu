@@ -30,13 +30,14 @@
 #include "cms_internal.h"
 #include "warp_fft.cuh"
 #include "sketch_generic.cuh"
+#include "dft_codelets.cuh"
 
 namespace cms {
 namespace {
 
 using namespace wfft;
 
-constexpr int kC = kFeC;       // 1024
+constexpr int kC = kFeC;       // 1024: the largest C = 32 L
 constexpr int kG = 2;          // inner indices per group
 constexpr int kRows = 2;       // rows f1 per block
 constexpr int kThreads = 256;  // 8 warps = kRows x 2 sides x kG FFTs
@@ -66,6 +67,7 @@ struct FastArgs {
   const uint32_t* ovf_x;
   const uint32_t* hs;
   float2* partial;
+  int C, L;           // FFT length C = 32 L
 };
 
 }  // namespace
@@ -83,7 +85,8 @@ struct SmemLayout {
 };
 
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 2 * (kC / 32) / kWarps;   // (side, bucket group) items per warp: 8
+constexpr int kItems = 2 * (kC / 32) / kWarps;   // (side, bucket group) item slots per warp: 8
+constexpr uint32_t kVoidItem = 1u << 30;          // wmeta flag: slot without an item (2 L < 64)
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
@@ -166,16 +169,22 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     sincospi(a, &s, &c);
     thi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
   }
+  const int C = p.C, Lq = p.L;          // C = 32 Lq buckets per side
   if (tid < kWarps * kItems) {
     const int w = tid / kItems, j = tid % kItems;
     const int slot = (j & 1) ? (kWarps - 1 - w) : w;
     const int item = j * kWarps + slot;
     const int side = item & 1, gi = item >> 1;
-    const size_t ts = static_cast<size_t>(t) * 2 + side;
-    const uint32_t gb = p.grp[(ts * (kC / 32) + gi) * 2];
-    const uint32_t gy = p.grp[(ts * (kC / 32) + gi) * 2 + 1];
-    wmeta[tid] = (gy & 0xFFu) | (static_cast<uint32_t>(side) << 8) | (gy & 0x80000000u);
-    ibase[tid] = static_cast<uint32_t>(side) * p.ecap + gb;
+    if (item < 2 * Lq) {
+      const size_t ts = static_cast<size_t>(t) * 2 + side;
+      const uint32_t gb = p.grp[(ts * Lq + gi) * 2];
+      const uint32_t gy = p.grp[(ts * Lq + gi) * 2 + 1];
+      wmeta[tid] = (gy & 0xFFu) | (static_cast<uint32_t>(side) << 8) | (gy & 0x80000000u);
+      ibase[tid] = static_cast<uint32_t>(side) * p.ecap + gb;
+    } else {
+      wmeta[tid] = kVoidItem;
+      ibase[tid] = 0;
+    }
   }
   for (int i = tid; i < kWarps * 32 * kItems; i += kThreads) {
     const int w = i / (32 * kItems), l = (i / kItems) % 32, j = i % kItems;
@@ -183,12 +192,12 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     const int item = j * kWarps + slot;
     const int side = item & 1, gi = item >> 1;
     const size_t ts = static_cast<size_t>(t) * 2 + side;
-    wdst[i] = static_cast<uint16_t>(side * kG * kRegion + p.dest[ts * kC + gi * 32 + l]);
+    wdst[i] = item < 2 * Lq ? static_cast<uint16_t>(side * kG * kRegion + p.dest[ts * C + gi * 32 + l]) : 0;
   }
   for (int side = 0; side < 2; ++side) {
     const size_t ts = static_cast<size_t>(t) * 2 + side;
-    for (int i = tid; i <= kC; i += kThreads)
-      ovf[side * (kC + 1) + i] = static_cast<uint16_t>(p.ovf_off[ts * (kC + 1) + i]);
+    for (int i = tid; i <= C; i += kThreads)
+      ovf[side * (kC + 1) + i] = static_cast<uint16_t>(p.ovf_off[ts * (C + 1) + i]);
   }
   for (int i = tid; i < kRows * kC; i += kThreads) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   // zero the staging tails [n_side, npad): entries x >= n_side read zeros
@@ -247,11 +256,11 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   float2 step;
   {
     float s, c;
-    sincospif(2.0f * static_cast<float>(lane) / static_cast<float>(kC), &s, &c);
+    sincospif(2.0f * static_cast<float>(lane) / static_cast<float>(C), &s, &c);
     step = make_float2(c, -s);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      sincospif(2.0f * static_cast<float>((lane * 8 * q) & (kC - 1)) / static_cast<float>(kC), &s, &c);
+      sincospif(2.0f * static_cast<float>((lane * 8 * q) % C) / static_cast<float>(C), &s, &c);
       anchor[q] = make_float2(c, -s);
     }
   }
@@ -328,6 +337,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         }
         xp += 32u * cnt;
         twp += 32u * cnt;
+        if (m & kVoidItem) continue;
         float2* dp = work + dst;
         dp[0] = a00;
         dp[kRegion] = a01;
@@ -372,11 +382,20 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     __syncthreads();
     // staging consumed: fetch the next group while the FFTs run
     if (tid == 0 && k0 + kG < k_end) issue(k0 + kG);
-    // ---- FFT of length 1024, one per warp --------------------------------
+    // ---- FFT of length C = 32 L, one per warp -------------------------------
+    // lane l holds Y[l + 32 j], j < L: DFT of length L over j in registers,
+    // twiddle w_C^{l f1}, transpose, then lanes f1 < L run the DFT of length
+    // 32 over l: lane f1 ends holding bins f1 + L f2 in x[f2]
     float2 x[32];
+    if (Lq == 32) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
-    dft32<false>(x);
+      for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
+      dft32<false>(x);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = j < Lq ? region[lane + 32 * j] : make_float2(0.f, 0.f);
+      dft_reg(x, Lq);
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float2 w = anchor[q];
@@ -389,10 +408,11 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     __syncwarp();
     // transpose through the padded region: T[f][lane] at f * 33 + lane
 #pragma unroll
-    for (int f = 0; f < 32; ++f) region[f * kPitch + lane] = x[f];
+    for (int f = 0; f < 32; ++f)
+      if (f < Lq) region[f * kPitch + lane] = x[f];
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = region[lane * kPitch + j];
+    for (int j = 0; j < 32; ++j) x[j] = lane < Lq ? region[lane * kPitch + j] : make_float2(0.f, 0.f);
     dft32<false>(x);
     __syncwarp();
     // hand the partner the half of the bins it accumulates (register indices
@@ -439,22 +459,22 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         part[m] = make_float2(0.f, 0.f);
       }
       __syncthreads();
-#pragma unroll
-      for (int u = 0; u < (kRows * kC) / kThreads; ++u) {
-        const int idx = tid + kThreads * u;
-        const int r = idx / kC, f = idx % kC;
-        const int sd = f >> 9;            // bins f < 512 live with side a, the rest with side b
-        float2 s = work[((r * 2 + sd) * kG + 0) * kRegion + f];
+      for (int idx = tid; idx < kRows * C; idx += kThreads) {
+        const int r = idx / C, f = idx % C;
+        const int f2 = f / Lq;             // bin f = f1 + L f2 sits at lane f1, register f2
+        const int widx = (f - f2 * Lq) + 32 * f2;
+        const int sd = f2 >> 4;            // registers < 16 live with side a, the rest with side b
+        float2 s = work[((r * 2 + sd) * kG + 0) * kRegion + widx];
 #pragma unroll
         for (int g = 1; g < kG; ++g) {
-          const float2 v = work[((r * 2 + sd) * kG + g) * kRegion + f];
+          const float2 v = work[((r * 2 + sd) * kG + g) * kRegion + widx];
           s.x += v.x;
           s.y += v.y;
         }
-        float4 a = acc[idx];
+        float4 a = acc[r * kC + f];
         kahan_add(a.x, a.z, s.x);
         kahan_add(a.y, a.w, s.y);
-        acc[idx] = a;
+        acc[r * kC + f] = a;
       }
     }
     // the next group's __syncthreads_or orders these reads of the regions
@@ -467,14 +487,12 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     return;
   }
   __syncthreads();
-#pragma unroll
-  for (int u = 0; u < (kRows * kC) / kThreads; ++u) {
-    const int idx = tid + kThreads * u;
-    const int r = idx / kC, f = idx % kC;
+  for (int idx = tid; idx < kRows * C; idx += kThreads) {
+    const int r = idx / C, f = idx % C;
     if (r == 1 && !row1_live) continue;
-    const float4 a = acc[idx];
+    const float4 a = acc[r * kC + f];
     const uint32_t frow = r ? f1r[1] : f1r[0];
-    float2* out = p.partial + ((static_cast<size_t>(t) * p.nrows + frow) * p.nkc + kc) * kC;
+    float2* out = p.partial + ((static_cast<size_t>(t) * p.nrows + frow) * p.nkc + kc) * C;
     out[f] = make_float2(a.x - a.z, a.y - a.w);
   }
   // the shared memory (and the mbarrier in it) is reused by the next task
@@ -568,6 +586,8 @@ void fill_batch_desc(void* dst, const SketchPlan& plan, const cms_hashes* h, con
     a.rec_x = h->d_fe_x; a.rec_hs = h->d_fe_hs; a.grp = h->d_fe_grp; a.dest = h->d_fe_dest;
     a.ovf_off = h->d_fe_ovf_off; a.ovf_x = h->d_fe_ovf_x; a.hs = h->d_hs;
     a.partial = partial;
+    a.C = static_cast<int>(plan.C);
+    a.L = static_cast<int>(plan.C / 32);
   } else {
     d.kind = 0;
     generic::SketchArgs& a = d.g;
@@ -636,6 +656,8 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
   a.ovf_x = h->d_fe_ovf_x;
   a.hs = h->d_hs;
   a.partial = partial;
+  a.C = static_cast<int>(plan.C);
+  a.L = static_cast<int>(plan.C / 32);
   const int smem = static_cast<int>(plan.smem);
   cudaError_t e = cudaFuncSetAttribute(k_sketch_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

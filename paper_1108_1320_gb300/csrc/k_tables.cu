@@ -135,16 +135,19 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
                   uint32_t* __restrict__ rec_x, uint32_t* __restrict__ rec_hs,
                   uint32_t* __restrict__ grp, uint16_t* __restrict__ dest,
                   uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x,
-                  uint8_t* __restrict__ assign) {
-  constexpr int C = kFeC;
+                  uint8_t* __restrict__ assign, int C) {
+  // C = 32 L buckets (L <= 32); the block has kFeC = 1024 threads, thread z
+  // < C owning bucket z and warp g < L group g
+  constexpr int kMax = kFeC;
   constexpr uint32_t kCap = static_cast<uint32_t>(kFeCap);
-  __shared__ uint32_t cnt[C];        // entries per bucket
-  __shared__ uint32_t key[C];
-  __shared__ uint32_t used[C];       // greedy bank counters, 32 per warp
-  __shared__ uint32_t gbase[C / 32];
-  __shared__ uint32_t gword[C / 32];  // group count | overflow flag << 31
+  __shared__ uint32_t cnt[kMax];        // entries per bucket
+  __shared__ uint32_t key[kMax];
+  __shared__ uint32_t used[kMax];       // greedy bank counters, 32 per warp
+  __shared__ uint32_t gbase[kMax / 32];
+  __shared__ uint32_t gword[kMax / 32];  // group count | overflow flag << 31
   __shared__ uint32_t wtot[32];
-  __shared__ uint32_t gcost[C / 32];  // slots + longest overflow list of a group
+  __shared__ uint32_t gcost[kMax / 32];  // slots + longest overflow list of a group
+  const int L = C / 32;
   const int ts = blockIdx.x;
   const uint32_t* tab = hs + static_cast<size_t>(ts) * n;
   const uint32_t* pm = perm + static_cast<size_t>(ts) * n;
@@ -158,10 +161,10 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // bucket sizes from the stable bucket sort (perm lists each bucket's x in
   // increasing order)
-  cnt[tid] = of[tid + 1] - of[tid];
+  cnt[tid] = tid < C ? of[tid + 1] - of[tid] : 0u;
   for (uint32_t e = tid; e < ecap; e += blockDim.x) { rx[e] = n; rh[e] = 0u; }
   __syncthreads();
-  {
+  if (tid < C) {
     // rank of this bucket among the buckets of its class (capped count) and
     // residue z2 mod 16, in scrambled order; sorting by (class, rank / 2,
     // residue, rank % 2) makes every run of 32 buckets of a class hold each
@@ -175,9 +178,11 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
       if (min(cnt[o], kCap) == cc && (so < sk || (so == sk && o < z))) ++rank;
     }
     key[tid] = ((kCap - cc) << 20) | ((rank >> 1) << 15) | ((z & 15u) << 11) | ((rank & 1u) << 10) | z;
+  } else {
+    key[tid] = 0xFFFFFFFFu;   // sorts after every bucket
   }
   __syncthreads();
-  for (int size = 2; size <= C; size <<= 1) {
+  for (int size = 2; size <= kMax; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       const int partner = tid ^ stride;
       if (partner > tid) {
@@ -192,7 +197,7 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   // holds distinct z2 mod 16 where possible: the front end's 8-byte stores
   // to Y[z2] are then free of bank conflicts.  The group's bucket set (and
   // so its padded length) is unchanged.
-  if (tid < C / 32) {
+  if (tid < L) {
     uint32_t* grpkey = key + 32 * tid;
     uint32_t in[32], half0[16], half1[16], pool[32];
     int n0 = 0, n1 = 0, np = 0;
@@ -212,16 +217,17 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   }
   __syncthreads();
   // thread tid = group warp, lane: its bucket, the group's padded count
-  const uint32_t zs = key[tid] & 0x3FFu;
-  ds[tid] = static_cast<uint16_t>(zs);
-  const uint32_t cz = cnt[zs];
+  const bool live = warp < L;                         // warp-uniform
+  const uint32_t zs = live ? key[tid] & 0x3FFu : 0u;
+  if (live) ds[tid] = static_cast<uint16_t>(zs);
+  const uint32_t cz = live ? cnt[zs] : 0u;
   const uint32_t c = min(cz, kCap);
   uint32_t cm = c;
   for (int o = 16; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xFFFFFFFFu, cm, o));
   const bool any_ovf = __any_sync(0xFFFFFFFFu, cz > kCap);
   uint32_t om = cz > kCap ? cz - kCap : 0u;
   for (int o = 16; o > 0; o >>= 1) om = max(om, __shfl_xor_sync(0xFFFFFFFFu, om, o));
-  if (lane == 0) {
+  if (lane == 0 && live) {
     gword[warp] = cm | (any_ovf ? 0x80000000u : 0u);
     gcost[warp] = cm + om;
   }
@@ -235,8 +241,8 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   if (lane == 31) wtot[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    // group bases: exclusive scan of 32 x count over the 32 groups
-    const uint32_t gw = gword[lane];
+    // group bases: exclusive scan of 32 x count over the L groups
+    const uint32_t gw = lane < L ? gword[lane] : 0u;
     const uint32_t v = 32u * (gw & 0xFFFFu);
     uint32_t gi = v;
     for (int o = 1; o < 32; o <<= 1) {
@@ -244,8 +250,10 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
       if (lane >= o) gi += t2;
     }
     gbase[lane] = gi - v;
-    gp[2 * lane] = gi - v;
-    gp[2 * lane + 1] = gw;
+    if (lane < L) {
+      gp[2 * lane] = gi - v;
+      gp[2 * lane + 1] = gw;
+    }
     // warp offsets of the overflow scan
     const uint32_t wv = wtot[lane];
     uint32_t wi = wv;
@@ -256,20 +264,20 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
     wtot[lane] = wi - wv;
     if (lane == 31) oo[C] = wi;
   }
-  if (tid == 32) {
+  if (tid == 32 && C == kMax) {
     // the 32 groups dealt to 8 front-end warps x 4 slots, heaviest first to
-    // the least-loaded warp with a free slot (the warp-specialised kernel
-    // takes 4 groups of each side per warp)
-    uint8_t* as = assign + static_cast<size_t>(ts) * (C / 32);
-    int ord[C / 32];
-    for (int g = 0; g < C / 32; ++g) {
+    // the least-loaded warp with a free slot (the warp-specialised kernel,
+    // C = 1024 only, takes 4 groups of each side per warp)
+    uint8_t* as = assign + static_cast<size_t>(ts) * (kMax / 32);
+    int ord[kMax / 32];
+    for (int g = 0; g < kMax / 32; ++g) {
       int q = g;
       while (q > 0 && gcost[ord[q - 1]] < gcost[g]) { ord[q] = ord[q - 1]; --q; }
       ord[q] = g;
     }
     uint32_t load[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int fill[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < C / 32; ++i) {
+    for (int i = 0; i < kMax / 32; ++i) {
       const int g = ord[i];
       int best = -1;
       for (int w = 0; w < 8; ++w)
@@ -281,9 +289,10 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   }
   __syncthreads();
   const uint32_t my_oof = wtot[warp] + incl - ov;   // bucket tid's first overflow slot
-  oo[tid] = my_oof;
+  if (tid < C) oo[tid] = my_oof;
   cnt[tid] = my_oof;                                 // now: overflow offset by bucket
   __syncthreads();
+  if (!live) return;
   // this lane's entries (the first kFeCap in x order) and the overflow
   // entries of its bucket
   const uint32_t o0 = of[zs];
@@ -339,16 +348,17 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
 }  // namespace
 
 cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, const uint32_t* off, int d,
-                                   int64_t n, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs, uint32_t* grp,
-                                   uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x, uint8_t* assign,
-                                   cudaStream_t s) {
+                                   int64_t n, int64_t C, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs,
+                                   uint32_t* grp, uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,
+                                   uint8_t* assign, cudaStream_t s) {
   {
     ProfScope prof_scope("k_frontend_tables", s);
-    k_frontend_tables<<<2 * d, 1024, 0, s>>>(hs, perm, off, static_cast<uint32_t>(n), ecap, rec_x, rec_hs,
-                                             grp, dest, ovf_off, ovf_x, assign);
+    k_frontend_tables<<<2 * d, kFeC, 0, s>>>(hs, perm, off, static_cast<uint32_t>(n), ecap, rec_x, rec_hs,
+                                             grp, dest, ovf_off, ovf_x, assign, static_cast<int>(C));
   }
   return cudaGetLastError();
 }
+
 
 
 

@@ -128,3 +128,20 @@ def test_batch_mixes_kernel_kinds(cms):
     for c, ref in zip(batch.c, refs):
         check(c, ref)
     batch.free()
+
+
+def test_batch_c_32l_instances_run_the_fast_body(cms):
+    # b = 16 n with n even: C = 32 L (L = 30, 27, 25, 24, 32), every FP32
+    # instance on the register-FFT body, X^T X against the oracle
+    class Sp:
+        def __init__(self, n, seed):
+            self.n, self.m, self.dtype, self.seed, self.n_pairs, self.rho = n, 2 * n, "f32", seed, n // 100, 0.5
+    specs = [Sp(600, 1), Sp(648, 2), Sp(1000, 3), Sp(576, 4), Sp(1024, 5), Sp(864, 6)]
+    items, refs = make_instances(cms, specs)
+    batch = cms.Batch(items)
+    assert batch.info()["fast_instances"] == len(specs)
+    batch.run()
+    torch.cuda.synchronize()
+    for c, ref in zip(batch.c, refs):
+        check(c, ref)
+    batch.free()

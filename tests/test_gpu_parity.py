@@ -349,6 +349,28 @@ def test_fast_kernel_cases_match_oracle(cms, n1, n2, n3, b, d):
     h.free()
 
 
+# C = 32 L for the other register-FFT lengths (b chosen so that 32 L is the
+# largest supported factor): L = 30, 27, 25, 24, 20, 18, 16
+@pytest.mark.parametrize("n1,n2,n3,b,d", [
+    (300, 70, 296, 3840, 2),      # C = 960, R = 4
+    (500, 33, 500, 2592, 2),      # C = 864, R = 3
+    (256, 41, 260, 4000, 3),      # C = 800, R = 5
+    (400, 64, 400, 1536, 2),      # C = 768, R = 2
+    (200, 29, 204, 1280, 2),      # C = 640, R = 2
+    (300, 50, 300, 1152, 1),      # C = 576, R = 2
+    (100, 17, 100, 512, 2),       # C = 512, R = 1
+])
+def test_fast_kernel_c_32l_match_oracle(cms, n1, n2, n3, b, d):
+    A = W.gaussian(n1, n2, 17 + n1).astype(np.float32)
+    B = W.gaussian(n2, n3, 19 + n3).astype(np.float32)
+    n = max(n1, n3)
+    h = cms.make_hashes(41 + b, n, b, d)
+    c = cms.sketch_product(colmajor(A), rowmajor(B), h).cpu().numpy()
+    ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), O.make_tables(41 + b, n, b, d))
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
 def test_fast_kernel_overflow_buckets(cms):
     # 32 entries per occupied bucket class: half of each goes through the
     # overflow list of the gather front end
