@@ -89,7 +89,8 @@ struct SketchPlan {
   int nkc = 0;              // number of inner-index chunks
   int threads = 256;
   size_t smem = 0;          // dynamic shared memory of the fused kernel
-  bool fast = false;        // the C = 1024 register-FFT kernel applies
+  bool fast = false;        // the C = 32 L register-FFT kernel applies
+  int dt = 0;               // storage type of A and B (cms_dtype)
   bool ws = false;          // ... in its warp-specialised form (k_sketch_ws)
   int ovcap = 0;            // overflow entries whose twiddles k_sketch_ws caches
   bool alias = false;       // A and B are the same bytes (stage once)
@@ -106,7 +107,7 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
                      std::string* why, const void* A = nullptr, int64_t lda = 0,
                      const void* B = nullptr, int64_t ldb = 0, bool allow_fast = true,
                      int nkc_override = 0, int G_override = 0, bool allow_ws = true);
-size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi);
+size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int esz);
 size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int ovcap);
 bool ws_kernel_usable();
 cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,

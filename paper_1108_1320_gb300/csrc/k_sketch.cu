@@ -216,18 +216,22 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   const int n = static_cast<int>(h->n);
   const int64_t units = static_cast<int64_t>(p.d) * p.nrows;
 
-  // the C = 1024 register-FFT kernel: FP32 rows that TMA can copy
+  // the C = 32 L register-FFT kernels: FP32 or BF16 rows that TMA can copy
+  // (16-byte aligned rows and row starts)
+  p.dt = dt;
+  const int per16 = dt == CMS_BF16 ? 8 : 4;   // elements per 16 bytes
   const bool aligned = (A == nullptr || reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                        (B == nullptr || reinterpret_cast<uintptr_t>(B) % 16 == 0) &&
-                       lda % 4 == 0 && ldb % 4 == 0 && n1 % 4 == 0 && n3 % 4 == 0;
-  if (allow_fast && dt == CMS_F32 && p.C % 32 == 0 && fe_supported_L(p.C / 32) && h->fe_ecap > 0 && aligned) {
+                       lda % per16 == 0 && ldb % per16 == 0 && n1 % per16 == 0 && n3 % per16 == 0;
+  if (allow_fast && (dt == CMS_F32 || dt == CMS_BF16) && p.C % 32 == 0 && fe_supported_L(p.C / 32) &&
+      h->fe_ecap > 0 && aligned) {
     p.alias = A != nullptr && A == B && lda == ldb && n1 == n3;
-    p.npad = static_cast<int>(((h->n + 1) + 3) / 4 * 4);
+    p.npad = static_cast<int>(((h->n + 1) + per16 - 1) / per16 * per16);
     int sh = 0;
     while ((static_cast<int64_t>(1) << (2 * sh)) < p.b) ++sh;
     p.tw_shift = sh;
     p.nhi = static_cast<int>((p.b + (static_cast<int64_t>(1) << sh) - 1) >> sh);
-    const size_t sm = fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi);
+    const size_t sm = fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, dt == CMS_BF16 ? 2 : 4);
     // the warp-specialised kernel caches up to 1024 overflow twiddles in the
     // shared memory left over (at least 64 entries, or it is not used)
     const size_t ws_base = ws_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, 0);
@@ -236,14 +240,15 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
                           ? static_cast<int>(std::min<size_t>(1024, (smem_optin - ws_base - 1024) / 18))
                           : 0;
     const size_t sm_ws = ws_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, ovcap);
-    const bool ws_ok = allow_ws && p.C == kFeC && ovcap >= 64 && sm_ws <= smem_optin && ws_kernel_usable();
+    const bool ws_ok = allow_ws && dt == CMS_F32 && p.C == kFeC && ovcap >= 64 && sm_ws <= smem_optin &&
+                       ws_kernel_usable();
     // the front-end records hold staging indices (< 3 npad) in 16 bits
     if ((sm <= smem_optin || ws_ok) && 3 * static_cast<int64_t>(p.npad) <= 65535) {
       p.fast = true;
       p.ws = ws_ok;
       p.ovcap = ws_ok ? ovcap : 0;
       p.G = 2;
-      p.threads = ws_ok ? 384 : 256;
+      p.threads = ws_ok ? 512 : 256;
       p.smem = ws_ok ? sm_ws : sm;
     }
   }

@@ -48,9 +48,9 @@ constexpr int kRegion = 32 * kPitch;   // float2 per warp region (>= kC)
 __device__ uint32_t g_sketch_error = 0;   // 1: a TMA wait gave up
 
 struct FastArgs {
-  const float* A;
+  const void* A;      // FP32 or BF16 storage (the task body's template type)
   int64_t lda;
-  const float* B;
+  const void* B;
   int64_t ldb;
   int n1, n2, n3, n, npad;
   int64_t b;
@@ -68,12 +68,13 @@ struct FastArgs {
   const uint32_t* hs;
   float2* partial;
   int C, L;           // FFT length C = 32 L
+  int esz;            // bytes per stored element: 4 (FP32) or 2 (BF16)
 };
 
 }  // namespace
 
 struct BatchDesc {
-  int kind;                 // 1: fast kernel task, 0: generic task
+  int kind;                 // 1: fast task (FP32), 3: fast task (BF16), 0: generic task
   generic::SketchArgs g;
   FastArgs f;
 };
@@ -90,11 +91,12 @@ constexpr uint32_t kVoidItem = 1u << 30;          // wmeta flag: slot without an
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
-__host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int alias, int tw_shift, int nhi) {
+__host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int alias, int tw_shift, int nhi,
+                                                  int esz) {
   SmemLayout L{};
   size_t o = 0;
   const int nstage = alias ? 1 : 2;
-  L.stage = o;    o = al16(o + static_cast<size_t>(nstage) * kG * npad * 4);
+  L.stage = o;    o = al16(o + static_cast<size_t>(nstage) * kG * npad * esz);
   L.rec_tw = o;   o = al16(o + static_cast<size_t>(2) * ecap * 16);
   L.rec_x = o;    o = al16(o + static_cast<size_t>(2) * ecap * 2);
   L.work = o;     o = al16(o + static_cast<size_t>(kRows * 2 * kG) * kRegion * 8);
@@ -123,9 +125,10 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
 // (slot s holds 32 lanes' records), and keeps per item its padded count
 // (warp-uniform) and per lane the Y slot its bucket is stored to, so the
 // per-group loop only walks the stream.
+template <typename T>
 __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, unsigned char* sm) {
-  const SmemLayout L = fast_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi);
-  float* stage = reinterpret_cast<float*>(sm + L.stage);
+  const SmemLayout L = fast_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi, static_cast<int>(sizeof(T)));
+  T* stage = reinterpret_cast<T*>(sm + L.stage);      // FP32 or BF16 as stored
   float4* rec_tw = reinterpret_cast<float4*>(sm + L.rec_tw);     // [slot][lane]: row 0 tw, row 1 tw
   uint16_t* rec_x = reinterpret_cast<uint16_t*>(sm + L.rec_x);   // [slot][lane]: staging index
   float2* work = reinterpret_cast<float2*>(sm + L.work);
@@ -204,7 +207,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   for (int s2 = 0; s2 < nstage; ++s2) {
     const int nside = s2 == 0 ? p.n1 : p.n3;
     for (int g = 0; g < kG; ++g)
-      for (int i = nside + tid; i < p.npad; i += kThreads) stage[(s2 * kG + g) * p.npad + i] = 0.f;
+      for (int i = nside + tid; i < p.npad; i += kThreads) stage[(s2 * kG + g) * p.npad + i] = T(0.f);
   }
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -269,18 +272,21 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   auto issue = [&](int k0) {
     uint32_t bytes = 0;
     const int gl = min(kG, k_end - k0);
-    for (int g = 0; g < gl; ++g) bytes += static_cast<uint32_t>(p.n1) * 4u;
+    const uint32_t es = static_cast<uint32_t>(sizeof(T));
+    for (int g = 0; g < gl; ++g) bytes += static_cast<uint32_t>(p.n1) * es;
     if (!p.alias)
-      for (int g = 0; g < gl; ++g) bytes += static_cast<uint32_t>(p.n3) * 4u;
+      for (int g = 0; g < gl; ++g) bytes += static_cast<uint32_t>(p.n3) * es;
     fence_proxy_async();
     mbar_arrive_expect_tx(bar, bytes);
+    const T* A = static_cast<const T*>(p.A);
+    const T* B = static_cast<const T*>(p.B);
     for (int g = 0; g < gl; ++g) {
       if (p.n1 > 0)
-        bulk_g2s(stage + (0 * kG + g) * p.npad, p.A + static_cast<size_t>(k0 + g) * p.lda,
-                 static_cast<uint32_t>(p.n1) * 4u, bar);
+        bulk_g2s(stage + (0 * kG + g) * p.npad, A + static_cast<size_t>(k0 + g) * p.lda,
+                 static_cast<uint32_t>(p.n1) * es, bar);
       if (!p.alias && p.n3 > 0)
-        bulk_g2s(stage + (1 * kG + g) * p.npad, p.B + static_cast<size_t>(k0 + g) * p.ldb,
-                 static_cast<uint32_t>(p.n3) * 4u, bar);
+        bulk_g2s(stage + (1 * kG + g) * p.npad, B + static_cast<size_t>(k0 + g) * p.ldb,
+                 static_cast<uint32_t>(p.n3) * es, bar);
     }
   };
 
@@ -315,7 +321,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
       const uint32_t s0 = istart[warp * kItems];
       const float4* twp = rec_tw + s0 * 32u + lane;
       const uint16_t* xp = rec_x + s0 * 32u + lane;
-      const float* st1 = stage + p.npad;
+      const T* st1 = stage + p.npad;
       // neither loop is unrolled: the smaller loop body keeps the hot code
       // in the instruction cache (measured faster than unrolled forms)
 #pragma unroll 1
@@ -328,8 +334,8 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         for (uint32_t e = 0; e < cnt; ++e) {
           const int x = xp[32 * e];
           const float4 w = twp[32 * e];
-          const float v0 = stage[x];
-          const float v1 = st1[x];
+          const float v0 = generic::to_f32(stage[x]);
+          const float v1 = generic::to_f32(st1[x]);
           a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
           a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
           a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
@@ -354,7 +360,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
           const uint32_t dst = wdst[(warp * 32 + lane) * kItems + j];
           const int side = static_cast<int>((m >> 8) & 1u);
           const int z2 = static_cast<int>(dst) - side * kG * kRegion;
-          const float* st = stage + (p.alias ? 0 : side) * kG * p.npad;
+          const T* st = stage + (p.alias ? 0 : side) * kG * p.npad;
           const size_t ts = static_cast<size_t>(t) * 2 + side;
           float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
           const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
@@ -364,8 +370,8 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
             float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], modb), p.tw_shift);
             float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], modb), p.tw_shift);
             if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
-            const float v0 = st[x];
-            const float v1 = st[p.npad + x];
+            const float v0 = generic::to_f32(st[x]);
+            const float v1 = generic::to_f32(st[p.npad + x]);
             a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
             a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
             a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
@@ -501,9 +507,10 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   __syncthreads();
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   extern __shared__ __align__(128) unsigned char sm[];
-  fast_task(p, blockIdx.x, sm);
+  fast_task<T>(p, blockIdx.x, sm);
 }
 
 // ------------------------------------------------------------- batched ----
@@ -531,7 +538,9 @@ k_sketch_batched(const BatchDesc* __restrict__ desc, const int* __restrict__ sta
     const BatchDesc& d = desc[lo];
     const int task = gtask - start[lo];
     if (d.kind == 1) {
-      fast_task(d.f, task, sm);
+      fast_task<float>(d.f, task, sm);
+    } else if (d.kind == 3) {
+      fast_task<__nv_bfloat16>(d.f, task, sm);
     } else {
       float4* sm4 = reinterpret_cast<float4*>(sm);
       switch (d.g.dt) {
@@ -553,8 +562,8 @@ uint32_t read_clear_error_sketch() {
   return v;
 }
 
-size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi) {
-  return fast_layout(npad, ecap, alias, tw_shift, nhi).total;
+size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int esz) {
+  return fast_layout(npad, ecap, alias, tw_shift, nhi, esz).total;
 }
 
 size_t batch_desc_bytes() { return sizeof(BatchDesc); }
@@ -567,10 +576,11 @@ void fill_batch_desc(void* dst, const SketchPlan& plan, const cms_hashes* h, con
   BatchDesc d{};
   float2* partial = reinterpret_cast<float2*>(ws + plan.off_partial);
   if (plan.fast) {
-    d.kind = 1;
+    d.kind = dt == CMS_BF16 ? 3 : 1;
     FastArgs& a = d.f;
-    a.A = static_cast<const float*>(A); a.lda = lda;
-    a.B = static_cast<const float*>(B); a.ldb = ldb;
+    a.A = A; a.lda = lda;
+    a.B = B; a.ldb = ldb;
+    a.esz = dt == CMS_BF16 ? 2 : 4;
     a.n1 = static_cast<int>(n1); a.n2 = static_cast<int>(n2); a.n3 = static_cast<int>(n3);
     a.n = static_cast<int>(h->n);
     a.npad = plan.npad;
@@ -632,10 +642,11 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
                                int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
                                int64_t n3, float2* partial, cudaStream_t s) {
   FastArgs a{};
-  a.A = static_cast<const float*>(A);
+  a.A = A;
   a.lda = lda;
-  a.B = static_cast<const float*>(B);
+  a.B = B;
   a.ldb = ldb;
+  a.esz = plan.dt == CMS_BF16 ? 2 : 4;
   a.n1 = static_cast<int>(n1); a.n2 = static_cast<int>(n2); a.n3 = static_cast<int>(n3);
   a.n = static_cast<int>(h->n);
   a.npad = plan.npad;
@@ -659,12 +670,16 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
   a.C = static_cast<int>(plan.C);
   a.L = static_cast<int>(plan.C / 32);
   const int smem = static_cast<int>(plan.smem);
-  cudaError_t e = cudaFuncSetAttribute(k_sketch_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const bool bf = plan.dt == CMS_BF16;
+  cudaError_t e = bf ? cudaFuncSetAttribute(k_sketch_fast<__nv_bfloat16>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                     : cudaFuncSetAttribute(k_sketch_fast<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const unsigned ntask = static_cast<unsigned>(static_cast<int64_t>(plan.d) * a.nunits * plan.nkc);
   {
     ProfScope prof_scope("k_sketch_fused", s);
-    k_sketch_fast<<<ntask, kThreads, smem, s>>>(a);
+    if (bf) k_sketch_fast<__nv_bfloat16><<<ntask, kThreads, smem, s>>>(a);
+    else k_sketch_fast<float><<<ntask, kThreads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }

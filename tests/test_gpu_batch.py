@@ -114,15 +114,17 @@ def test_batch_autotune_writes_cache(cms, tmp_path):
 
 
 def test_batch_mixes_kernel_kinds(cms):
-    # n multiple of 64 -> b = 16 n is a multiple of 1024: FP32 instances use
-    # the C = 1024 kernel, BF16 / other n the generic one, in one launch
+    # even n with rows of whole 16-byte units -> the register-FFT body
+    # (FP32 or BF16 storage); odd n -> b = 16 n has no factor 32 L and rows
+    # are not 16-byte multiples -> the generic body; all in one launch
     class Sp:
         def __init__(self, n, dtype, seed):
             self.n, self.m, self.dtype, self.seed, self.n_pairs, self.rho = n, 2 * n, dtype, seed, n // 100, 0.5
-    specs = [Sp(512, "f32", 1), Sp(1000, "f32", 2), Sp(768, "bf16", 3), Sp(640, "f32", 4)]
+    specs = [Sp(512, "f32", 1), Sp(1000, "f32", 2), Sp(768, "bf16", 3), Sp(640, "f32", 4), Sp(675, "f32", 5),
+             Sp(625, "bf16", 6)]
     items, refs = make_instances(cms, specs)
     batch = cms.Batch(items)
-    assert 0 < batch.info()["fast_instances"] < len(specs)
+    assert batch.info()["fast_instances"] == 4
     batch.run()
     torch.cuda.synchronize()
     for c, ref in zip(batch.c, refs):

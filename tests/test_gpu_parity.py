@@ -139,6 +139,25 @@ def test_sketch_bf16_storage(cms):
     h.free()
 
 
+@pytest.mark.parametrize("n1,n2,n3,b,d", [
+    (304, 45, 296, 3840, 2),      # C = 960, two operands
+    (512, 33, 504, 4096, 2),      # C = 1024, two operands
+])
+def test_sketch_bf16_storage_two_operands(cms, n1, n2, n3, b, d):
+    # BF16 rows staged as BF16 by the register-FFT kernel; the sketch of the
+    # BF16 values within the FP32 tolerance
+    A = W.gaussian(n1, n2, 3 + n1).astype(np.float32)
+    B = W.gaussian(n2, n3, 5 + n3).astype(np.float32)
+    Ab, _ = W.bf16_round(A)
+    Bb, _ = W.bf16_round(B)
+    n = max(n1, n3)
+    h = cms.make_hashes(7 + b, n, b, d)
+    c = cms.sketch_product(colmajor(A, torch.bfloat16), rowmajor(B, torch.bfloat16), h).cpu().numpy()
+    ref = O.sketch_definition(Ab.astype(np.float64), Bb.astype(np.float64), O.make_tables(7 + b, n, b, d))
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
 def test_sketch_f64_storage_fused(cms):
     A = W.gaussian(128, 50, 8)
     B = W.gaussian(50, 96, 9)
