@@ -88,14 +88,15 @@ cms_status alloc_tables(cms_hashes* h) {
     e = cudaMalloc(&h->d_off, static_cast<size_t>(h->d) * 2 * (h->C + 1) * sizeof(uint32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(bucket offsets)");
   }
-  if (h->C % 32 == 0 && fe_supported_L(h->C / 32) && h->n <= 65535) {
+  if (fe_pq(h->C, nullptr, nullptr) && h->n <= 65535) {
     h->fe_ecap = static_cast<uint32_t>(h->n + 32 * kFeCap);
     const size_t ts = static_cast<size_t>(h->d) * 2;
     const size_t C = static_cast<size_t>(h->C);
+    const size_t groups = (C + 31) / 32;
     if ((e = cudaMalloc(&h->d_fe_x, ts * h->fe_ecap * 4)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_fe_hs, ts * h->fe_ecap * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_fe_grp, ts * (C / 32) * 2 * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_fe_dest, ts * C * 2)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_grp, ts * groups * 2 * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_dest, ts * groups * 32 * 2)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_fe_ovf_off, ts * (C + 1) * 4)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_fe_ovf_x, ts * h->n * 4)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_fe_assign, ts * (kFeC / 32))) != cudaSuccess)

@@ -71,9 +71,22 @@ cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, con
                                    int64_t n, int64_t C, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs,
                                    uint32_t* grp, uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,
                                    uint8_t* assign, cudaStream_t s);
-// The C = 32 L register-FFT kernels (front-end records exist) handle these L.
+// Lengths of the in-register DFT codelets (and 32, the radix-32 DFT).
 inline bool fe_supported_L(int64_t L) {
   return L == 16 || L == 18 || L == 20 || L == 24 || L == 25 || L == 27 || L == 30 || L == 32;
+}
+// The register-FFT kernels take C = P Q with P and Q codelet lengths: P
+// lanes each run a DFT of length Q, then Q lanes a DFT of length P.  P = 32
+// when possible (every lane busy in the first pass), else the largest P.
+inline bool fe_pq(int64_t C, int* P, int* Q) {
+  for (int p = 32; p >= 16; --p) {
+    if (fe_supported_L(p) && C % p == 0 && fe_supported_L(C / p)) {
+      if (P) *P = p;
+      if (Q) *Q = static_cast<int>(C / p);
+      return true;
+    }
+  }
+  return false;
 }
 uint32_t read_clear_error_sketch();
 

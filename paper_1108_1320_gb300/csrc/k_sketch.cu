@@ -156,21 +156,19 @@ size_t fused_smem_bytes(int C, int G, int n, int dt) {
 
 }  // namespace
 
-// b = R x C.  C = 32 L with L one of the register-FFT kernels' lengths when
-// such a factor divides b (the largest one), else the largest divisor of b
-// up to 1024 (the shared-memory kernel takes any 5-smooth C).
+// b = R x C.  C = P Q for the register-FFT kernels (P, Q codelet lengths)
+// when such a factor divides b (the largest one), else the largest divisor
+// of b up to 1024 (the shared-memory kernel takes any 5-smooth C).
 bool choose_factorisation(int64_t b, int64_t* R, int64_t* C) {
   int rad[64];
   if (b < 1 || factor_radices(b, rad, 64) < 0) { *R = 0; *C = 0; return false; }
-  int64_t best = 1;
-  for (int64_t c = 1; c <= std::min<int64_t>(b, 1024); ++c)
-    if (b % c == 0) best = c;
-  for (int64_t L = 32; L >= 16; --L) {
-    if (fe_supported_L(L) && b % (32 * L) == 0) {
-      best = 32 * L;
-      break;
-    }
+  int64_t best = 1, best_pq = 0;
+  for (int64_t c = 1; c <= std::min<int64_t>(b, 1024); ++c) {
+    if (b % c != 0) continue;
+    best = c;
+    if (fe_pq(c, nullptr, nullptr)) best_pq = c;
   }
+  if (best_pq > 0) best = best_pq;
   *C = best;
   *R = b / best;
   return true;
@@ -223,7 +221,7 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   const bool aligned = (A == nullptr || reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                        (B == nullptr || reinterpret_cast<uintptr_t>(B) % 16 == 0) &&
                        lda % per16 == 0 && ldb % per16 == 0 && n1 % per16 == 0 && n3 % per16 == 0;
-  if (allow_fast && (dt == CMS_F32 || dt == CMS_BF16) && p.C % 32 == 0 && fe_supported_L(p.C / 32) &&
+  if (allow_fast && (dt == CMS_F32 || dt == CMS_BF16) && fe_pq(p.C, nullptr, nullptr) &&
       h->fe_ecap > 0 && aligned) {
     p.alias = A != nullptr && A == B && lda == ldb && n1 == n3;
     p.npad = static_cast<int>(((h->n + 1) + per16 - 1) / per16 * per16);

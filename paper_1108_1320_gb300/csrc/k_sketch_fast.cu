@@ -67,7 +67,8 @@ struct FastArgs {
   const uint32_t* ovf_x;
   const uint32_t* hs;
   float2* partial;
-  int C, L;           // FFT length C = 32 L
+  int C, P, Q;        // FFT length C = P Q: P lanes x DFT-Q, then Q lanes x DFT-P
+  int G;              // bucket groups per side, ceil(C / 32)
   int esz;            // bytes per stored element: 4 (FP32) or 2 (BF16)
 };
 
@@ -172,16 +173,16 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     sincospi(a, &s, &c);
     thi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
   }
-  const int C = p.C, Lq = p.L;          // C = 32 Lq buckets per side
+  const int C = p.C, Pq = p.P, Qq = p.Q, Gq = p.G;   // C = Pq Qq buckets in Gq groups per side
   if (tid < kWarps * kItems) {
     const int w = tid / kItems, j = tid % kItems;
     const int slot = (j & 1) ? (kWarps - 1 - w) : w;
     const int item = j * kWarps + slot;
     const int side = item & 1, gi = item >> 1;
-    if (item < 2 * Lq) {
+    if (item < 2 * Gq) {
       const size_t ts = static_cast<size_t>(t) * 2 + side;
-      const uint32_t gb = p.grp[(ts * Lq + gi) * 2];
-      const uint32_t gy = p.grp[(ts * Lq + gi) * 2 + 1];
+      const uint32_t gb = p.grp[(ts * Gq + gi) * 2];
+      const uint32_t gy = p.grp[(ts * Gq + gi) * 2 + 1];
       wmeta[tid] = (gy & 0xFFu) | (static_cast<uint32_t>(side) << 8) | (gy & 0x80000000u);
       ibase[tid] = static_cast<uint32_t>(side) * p.ecap + gb;
     } else {
@@ -195,7 +196,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     const int item = j * kWarps + slot;
     const int side = item & 1, gi = item >> 1;
     const size_t ts = static_cast<size_t>(t) * 2 + side;
-    wdst[i] = item < 2 * Lq ? static_cast<uint16_t>(side * kG * kRegion + p.dest[ts * C + gi * 32 + l]) : 0;
+    wdst[i] = item < 2 * Gq ? static_cast<uint16_t>(side * kG * kRegion + p.dest[(ts * Gq + gi) * 32 + l]) : 0;
   }
   for (int side = 0; side < 2; ++side) {
     const size_t ts = static_cast<size_t>(t) * 2 + side;
@@ -388,19 +389,21 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     __syncthreads();
     // staging consumed: fetch the next group while the FFTs run
     if (tid == 0 && k0 + kG < k_end) issue(k0 + kG);
-    // ---- FFT of length C = 32 L, one per warp -------------------------------
-    // lane l holds Y[l + 32 j], j < L: DFT of length L over j in registers,
-    // twiddle w_C^{l f1}, transpose, then lanes f1 < L run the DFT of length
-    // 32 over l: lane f1 ends holding bins f1 + L f2 in x[f2]
+    // ---- FFT of length C = P Q, one per warp -------------------------------
+    // lane l < P holds Y[l + P j], j < Q: DFT of length Q over j in
+    // registers, twiddle w_C^{l f1}, transpose, then lanes f1 < Q run the DFT
+    // of length P over l: lane f1 ends holding bins f1 + Q f2 in x[f2]
     float2 x[32];
-    if (Lq == 32) {
+    if (Pq == 32 && Qq == 32) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
       dft32<false>(x);
     } else {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) x[j] = j < Lq ? region[lane + 32 * j] : make_float2(0.f, 0.f);
-      dft_reg(x, Lq);
+      for (int j = 0; j < 32; ++j)
+        x[j] = (j < Qq && lane < Pq) ? region[lane + Pq * j] : make_float2(0.f, 0.f);
+      if (Qq == 32) dft32<false>(x);
+      else dft_reg(x, Qq);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -415,11 +418,13 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     // transpose through the padded region: T[f][lane] at f * 33 + lane
 #pragma unroll
     for (int f = 0; f < 32; ++f)
-      if (f < Lq) region[f * kPitch + lane] = x[f];
+      if (f < Qq) region[f * kPitch + lane] = x[f];
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = lane < Lq ? region[lane * kPitch + j] : make_float2(0.f, 0.f);
-    dft32<false>(x);
+    for (int j = 0; j < 32; ++j)
+      x[j] = (lane < Qq && j < Pq) ? region[lane * kPitch + j] : make_float2(0.f, 0.f);
+    if (Pq == 32) dft32<false>(x);
+    else dft_reg(x, Pq);
     __syncwarp();
     // hand the partner the half of the bins it accumulates (register indices
     // must stay compile-time constants: one branch per side)
@@ -467,8 +472,8 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
       __syncthreads();
       for (int idx = tid; idx < kRows * C; idx += kThreads) {
         const int r = idx / C, f = idx % C;
-        const int f2 = f / Lq;             // bin f = f1 + L f2 sits at lane f1, register f2
-        const int widx = (f - f2 * Lq) + 32 * f2;
+        const int f2 = f / Qq;             // bin f = f1 + Q f2 sits at lane f1, register f2
+        const int widx = (f - f2 * Qq) + 32 * f2;
         const int sd = f2 >> 4;            // registers < 16 live with side a, the rest with side b
         float2 s = work[((r * 2 + sd) * kG + 0) * kRegion + widx];
 #pragma unroll
@@ -597,7 +602,8 @@ void fill_batch_desc(void* dst, const SketchPlan& plan, const cms_hashes* h, con
     a.ovf_off = h->d_fe_ovf_off; a.ovf_x = h->d_fe_ovf_x; a.hs = h->d_hs;
     a.partial = partial;
     a.C = static_cast<int>(plan.C);
-    a.L = static_cast<int>(plan.C / 32);
+    fe_pq(plan.C, &a.P, &a.Q);
+    a.G = static_cast<int>((plan.C + 31) / 32);
   } else {
     d.kind = 0;
     generic::SketchArgs& a = d.g;
@@ -668,7 +674,8 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
   a.hs = h->d_hs;
   a.partial = partial;
   a.C = static_cast<int>(plan.C);
-  a.L = static_cast<int>(plan.C / 32);
+  fe_pq(plan.C, &a.P, &a.Q);
+  a.G = static_cast<int>((plan.C + 31) / 32);
   const int smem = static_cast<int>(plan.smem);
   const bool bf = plan.dt == CMS_BF16;
   cudaError_t e = bf ? cudaFuncSetAttribute(k_sketch_fast<__nv_bfloat16>,

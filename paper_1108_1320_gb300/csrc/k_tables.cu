@@ -136,8 +136,10 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
                   uint32_t* __restrict__ grp, uint16_t* __restrict__ dest,
                   uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x,
                   uint8_t* __restrict__ assign, int C) {
-  // C = 32 L buckets (L <= 32); the block has kFeC = 1024 threads, thread z
-  // < C owning bucket z and warp g < L group g
+  // C <= 1024 buckets in L = ceil(C / 32) groups; the block has kFeC = 1024
+  // threads, thread z < C owning bucket z and warp g < L group g.  The slots
+  // of the last group without a bucket (sort key all ones) hold no entries
+  // and store their zero sums to Y[C + lane], past the buckets
   constexpr int kMax = kFeC;
   constexpr uint32_t kCap = static_cast<uint32_t>(kFeCap);
   __shared__ uint32_t cnt[kMax];        // entries per bucket
@@ -147,15 +149,15 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   __shared__ uint32_t gword[kMax / 32];  // group count | overflow flag << 31
   __shared__ uint32_t wtot[32];
   __shared__ uint32_t gcost[kMax / 32];  // slots + longest overflow list of a group
-  const int L = C / 32;
+  const int L = (C + 31) / 32;
   const int ts = blockIdx.x;
   const uint32_t* tab = hs + static_cast<size_t>(ts) * n;
   const uint32_t* pm = perm + static_cast<size_t>(ts) * n;
   const uint32_t* of = off + static_cast<size_t>(ts) * (C + 1);
   uint32_t* rx = rec_x + static_cast<size_t>(ts) * ecap;
   uint32_t* rh = rec_hs + static_cast<size_t>(ts) * ecap;
-  uint32_t* gp = grp + static_cast<size_t>(ts) * (C / 32) * 2;
-  uint16_t* ds = dest + static_cast<size_t>(ts) * C;
+  uint32_t* gp = grp + static_cast<size_t>(ts) * ((C + 31) / 32) * 2;
+  uint16_t* ds = dest + static_cast<size_t>(ts) * ((C + 31) / 32) * 32;
   uint32_t* oo = ovf_off + static_cast<size_t>(ts) * (C + 1);
   uint32_t* ox = ovf_x + static_cast<size_t>(ts) * n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -218,9 +220,10 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   __syncthreads();
   // thread tid = group warp, lane: its bucket, the group's padded count
   const bool live = warp < L;                         // warp-uniform
-  const uint32_t zs = live ? key[tid] & 0x3FFu : 0u;
-  if (live) ds[tid] = static_cast<uint16_t>(zs);
-  const uint32_t cz = live ? cnt[zs] : 0u;
+  const bool real = key[tid] != 0xFFFFFFFFu;          // the sorted slot holds a bucket
+  const uint32_t zs = real ? key[tid] & 0x3FFu : 0u;
+  if (live) ds[tid] = static_cast<uint16_t>(real ? zs : static_cast<uint32_t>(C + lane));
+  const uint32_t cz = real ? cnt[zs] : 0u;
   const uint32_t c = min(cz, kCap);
   uint32_t cm = c;
   for (int o = 16; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xFFFFFFFFu, cm, o));

@@ -368,8 +368,9 @@ def test_fast_kernel_cases_match_oracle(cms, n1, n2, n3, b, d):
     h.free()
 
 
-# C = 32 L for the other register-FFT lengths (b chosen so that 32 L is the
-# largest supported factor): L = 30, 27, 25, 24, 20, 18, 16
+# C = P Q for the other register-FFT lengths (b chosen so that P Q is the
+# largest supported factor): P = 32 with Q = 30, 27, 25, 24, 20, 18, 16, and
+# P, Q < 32
 @pytest.mark.parametrize("n1,n2,n3,b,d", [
     (300, 70, 296, 3840, 2),      # C = 960, R = 4
     (500, 33, 500, 2592, 2),      # C = 864, R = 3
@@ -378,6 +379,10 @@ def test_fast_kernel_cases_match_oracle(cms, n1, n2, n3, b, d):
     (200, 29, 204, 1280, 2),      # C = 640, R = 2
     (300, 50, 300, 1152, 1),      # C = 576, R = 2
     (100, 17, 100, 512, 2),       # C = 512, R = 1
+    (300, 40, 296, 10800, 2),     # C = 900 = 30 x 30, R = 12
+    (256, 30, 256, 10000, 2),     # C = 625 = 25 x 25, R = 16
+    (200, 25, 200, 11664, 1),     # C = 729 = 27 x 27, R = 16
+    (100, 20, 100, 2000, 2),      # C = 500 = 25 x 20, R = 4
 ])
 def test_fast_kernel_c_32l_match_oracle(cms, n1, n2, n3, b, d):
     A = W.gaussian(n1, n2, 17 + n1).astype(np.float32)
