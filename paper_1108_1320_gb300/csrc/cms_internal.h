@@ -107,7 +107,9 @@ struct SketchPlan {
   bool ws = false;          // ... in its warp-specialised form (k_sketch_ws)
   int ovcap = 0;            // overflow entries whose twiddles k_sketch_ws caches
   bool alias = false;       // A and B are the same bytes (stage once)
-  int npad = 0;             // staging row length of the fast kernel (floats)
+  int npad = 0;             // staging row length of the fast kernel (elements)
+  bool unal = false;        // rows not 16-byte aligned (the fast kernel copies aligned supersets)
+  int zpos = 0;             // (unal) staging index of the zero slot
   int tw_shift = 0, nhi = 0;  // two-level w_b table: S = 2^tw_shift, nhi high entries
   // workspace layout (byte offsets)
   size_t off_partial = 0, off_V = 0, off_twfe = 0, off_twC = 0, off_twR = 0;

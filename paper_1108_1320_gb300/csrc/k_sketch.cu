@@ -218,13 +218,22 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   // (16-byte aligned rows and row starts)
   p.dt = dt;
   const int per16 = dt == CMS_BF16 ? 8 : 4;   // elements per 16 bytes
+  // rows not in whole 16-byte units are copied as their aligned supersets
+  // (the lock-step kernel only): staged rows then start up to per16 - 1
+  // elements in, and padding reads a zero slot past every copy
   const bool aligned = (A == nullptr || reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                        (B == nullptr || reinterpret_cast<uintptr_t>(B) % 16 == 0) &&
                        lda % per16 == 0 && ldb % per16 == 0 && n1 % per16 == 0 && n3 % per16 == 0;
+  const size_t esz = dt == CMS_BF16 ? 2 : 4;
+  const bool elem_aligned = (A == nullptr || reinterpret_cast<uintptr_t>(A) % esz == 0) &&
+                            (B == nullptr || reinterpret_cast<uintptr_t>(B) % esz == 0);
   if (allow_fast && (dt == CMS_F32 || dt == CMS_BF16) && fe_pq(p.C, nullptr, nullptr) &&
-      h->fe_ecap > 0 && aligned) {
+      h->fe_ecap > 0 && elem_aligned) {
     p.alias = A != nullptr && A == B && lda == ldb && n1 == n3;
-    p.npad = static_cast<int>(((h->n + 1) + per16 - 1) / per16 * per16);
+    p.unal = !aligned;
+    p.npad = p.unal ? static_cast<int>((h->n + 3 * per16 + per16 - 1) / per16 * per16)
+                    : static_cast<int>(((h->n + 1) + per16 - 1) / per16 * per16);
+    p.zpos = p.unal ? static_cast<int>(h->n + 2 * per16) : 0;
     int sh = 0;
     while ((static_cast<int64_t>(1) << (2 * sh)) < p.b) ++sh;
     p.tw_shift = sh;
@@ -238,8 +247,8 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
                           ? static_cast<int>(std::min<size_t>(1024, (smem_optin - ws_base - 1024) / 18))
                           : 0;
     const size_t sm_ws = ws_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, ovcap);
-    const bool ws_ok = allow_ws && dt == CMS_F32 && p.C == kFeC && ovcap >= 64 && sm_ws <= smem_optin &&
-                       ws_kernel_usable();
+    const bool ws_ok = allow_ws && dt == CMS_F32 && !p.unal && p.C == kFeC && ovcap >= 64 &&
+                       sm_ws <= smem_optin && ws_kernel_usable();
     // the front-end records hold staging indices (< 3 npad) in 16 bits
     if ((sm <= smem_optin || ws_ok) && 3 * static_cast<int64_t>(p.npad) <= 65535) {
       p.fast = true;

@@ -70,6 +70,8 @@ struct FastArgs {
   int C, P, Q;        // FFT length C = P Q: P lanes x DFT-Q, then Q lanes x DFT-P
   int G;              // bucket groups per side, ceil(C / 32)
   int esz;            // bytes per stored element: 4 (FP32) or 2 (BF16)
+  int unal;           // rows not 16-byte aligned: copy the aligned superset
+  int zpos;           // (unal) staging index of the zero slot read by padding
 };
 
 }  // namespace
@@ -204,9 +206,13 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
       ovf[side * (kC + 1) + i] = static_cast<uint16_t>(p.ovf_off[ts * (C + 1) + i]);
   }
   for (int i = tid; i < kRows * kC; i += kThreads) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  // zero the staging tails [n_side, npad): entries x >= n_side read zeros
+  // zero the staging tails [n_side, npad): entries x >= n_side read zeros.
+  // Rows that are not 16-byte aligned are copied as their aligned superset
+  // (starting up to 16 bytes early, ending up to 16 bytes late), so that
+  // staged row k begins at element shift(k); such entries then read the zero
+  // slot zpos instead, past anything a copy writes
   for (int s2 = 0; s2 < nstage; ++s2) {
-    const int nside = s2 == 0 ? p.n1 : p.n3;
+    const int nside = p.unal ? p.zpos : (s2 == 0 ? p.n1 : p.n3);
     for (int g = 0; g < kG; ++g)
       for (int i = nside + tid; i < p.npad; i += kThreads) stage[(s2 * kG + g) * p.npad + i] = T(0.f);
   }
@@ -251,7 +257,8 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         }
       }
       rec_tw[i] = make_float4(tw[0].x, tw[0].y, tw[1].x, tw[1].y);
-      const uint32_t xs = min(x, static_cast<uint32_t>(n));
+      const uint32_t nsd = static_cast<uint32_t>(side ? p.n3 : p.n1);
+      const uint32_t xs = p.unal ? (x < nsd ? x : static_cast<uint32_t>(p.zpos)) : min(x, static_cast<uint32_t>(n));
       rec_x[i] = static_cast<uint16_t>((p.alias ? 0u : side * kG * static_cast<uint32_t>(p.npad)) + xs);
     }
   }
@@ -273,21 +280,30 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   auto issue = [&](int k0) {
     uint32_t bytes = 0;
     const int gl = min(kG, k_end - k0);
-    const uint32_t es = static_cast<uint32_t>(sizeof(T));
-    for (int g = 0; g < gl; ++g) bytes += static_cast<uint32_t>(p.n1) * es;
-    if (!p.alias)
-      for (int g = 0; g < gl; ++g) bytes += static_cast<uint32_t>(p.n3) * es;
-    fence_proxy_async();
-    mbar_arrive_expect_tx(bar, bytes);
     const T* A = static_cast<const T*>(p.A);
     const T* B = static_cast<const T*>(p.B);
+    // the 16-byte aligned superset of each row (the row itself when aligned)
+    auto span = [&](const T* row, int len, uintptr_t* a0) {
+      const uintptr_t a = reinterpret_cast<uintptr_t>(row);
+      *a0 = a & ~static_cast<uintptr_t>(15);
+      return static_cast<uint32_t>(((a + static_cast<uintptr_t>(len) * sizeof(T) + 15) & ~static_cast<uintptr_t>(15)) - *a0);
+    };
+    uintptr_t a0;
     for (int g = 0; g < gl; ++g) {
-      if (p.n1 > 0)
-        bulk_g2s(stage + (0 * kG + g) * p.npad, A + static_cast<size_t>(k0 + g) * p.lda,
-                 static_cast<uint32_t>(p.n1) * es, bar);
-      if (!p.alias && p.n3 > 0)
-        bulk_g2s(stage + (1 * kG + g) * p.npad, B + static_cast<size_t>(k0 + g) * p.ldb,
-                 static_cast<uint32_t>(p.n3) * es, bar);
+      if (p.n1 > 0) bytes += span(A + static_cast<size_t>(k0 + g) * p.lda, p.n1, &a0);
+      if (!p.alias && p.n3 > 0) bytes += span(B + static_cast<size_t>(k0 + g) * p.ldb, p.n3, &a0);
+    }
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, bytes);
+    for (int g = 0; g < gl; ++g) {
+      if (p.n1 > 0) {
+        const uint32_t nb = span(A + static_cast<size_t>(k0 + g) * p.lda, p.n1, &a0);
+        bulk_g2s(stage + (0 * kG + g) * p.npad, reinterpret_cast<const void*>(a0), nb, bar);
+      }
+      if (!p.alias && p.n3 > 0) {
+        const uint32_t nb = span(B + static_cast<size_t>(k0 + g) * p.ldb, p.n3, &a0);
+        bulk_g2s(stage + (1 * kG + g) * p.npad, reinterpret_cast<const void*>(a0), nb, bar);
+      }
     }
   };
 
@@ -323,6 +339,17 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
       const float4* twp = rec_tw + s0 * 32u + lane;
       const uint16_t* xp = rec_x + s0 * 32u + lane;
       const T* st1 = stage + p.npad;
+      // element offsets of the staged rows inside their aligned copies
+      int shA0 = 0, shA1 = 0, shB0 = 0, shB1 = 0;
+      if (p.unal) {
+        const T* A = static_cast<const T*>(p.A);
+        const T* B = static_cast<const T*>(p.B);
+        const int k1 = min(k0 + 1, p.n2 - 1);
+        shA0 = static_cast<int>((reinterpret_cast<uintptr_t>(A + static_cast<size_t>(k0) * p.lda) & 15) / sizeof(T));
+        shA1 = static_cast<int>((reinterpret_cast<uintptr_t>(A + static_cast<size_t>(k1) * p.lda) & 15) / sizeof(T));
+        shB0 = p.alias ? shA0 : static_cast<int>((reinterpret_cast<uintptr_t>(B + static_cast<size_t>(k0) * p.ldb) & 15) / sizeof(T));
+        shB1 = p.alias ? shA1 : static_cast<int>((reinterpret_cast<uintptr_t>(B + static_cast<size_t>(k1) * p.ldb) & 15) / sizeof(T));
+      }
       // neither loop is unrolled: the smaller loop body keeps the hot code
       // in the instruction cache (measured faster than unrolled forms)
 #pragma unroll 1
@@ -330,13 +357,16 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         const uint32_t m = wmeta[warp * kItems + j];
         const uint32_t dst = wdst[(warp * 32 + lane) * kItems + j];
         const uint32_t cnt = m & 0xFFu;
+        const bool sb = (m >> 8) & 1u;
+        const T* sg0 = stage + (sb ? shB0 : shA0);
+        const T* sg1 = st1 + (sb ? shB1 : shA1);
         float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
 #pragma unroll 1
         for (uint32_t e = 0; e < cnt; ++e) {
           const int x = xp[32 * e];
           const float4 w = twp[32 * e];
-          const float v0 = generic::to_f32(stage[x]);
-          const float v1 = generic::to_f32(st1[x]);
+          const float v0 = generic::to_f32(sg0[x]);
+          const float v1 = generic::to_f32(sg1[x]);
           a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
           a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
           a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
@@ -362,6 +392,8 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
           const int side = static_cast<int>((m >> 8) & 1u);
           const int z2 = static_cast<int>(dst) - side * kG * kRegion;
           const T* st = stage + (p.alias ? 0 : side) * kG * p.npad;
+          const int sh0 = side ? shB0 : shA0, sh1 = side ? shB1 : shA1;
+          const uint32_t nsd = static_cast<uint32_t>(side ? p.n3 : p.n1);
           const size_t ts = static_cast<size_t>(t) * 2 + side;
           float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
           const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
@@ -371,8 +403,9 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
             float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], modb), p.tw_shift);
             float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], modb), p.tw_shift);
             if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
-            const float v0 = generic::to_f32(st[x]);
-            const float v1 = generic::to_f32(st[p.npad + x]);
+            const uint32_t xr = p.unal && x >= nsd ? static_cast<uint32_t>(p.zpos) : x;
+            const float v0 = generic::to_f32(st[sh0 + xr]);
+            const float v1 = generic::to_f32(st[p.npad + sh1 + xr]);
             a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
             a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
             a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
@@ -604,6 +637,8 @@ void fill_batch_desc(void* dst, const SketchPlan& plan, const cms_hashes* h, con
     a.C = static_cast<int>(plan.C);
     fe_pq(plan.C, &a.P, &a.Q);
     a.G = static_cast<int>((plan.C + 31) / 32);
+    a.unal = plan.unal ? 1 : 0;
+    a.zpos = plan.zpos;
   } else {
     d.kind = 0;
     generic::SketchArgs& a = d.g;
@@ -676,6 +711,8 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
   a.C = static_cast<int>(plan.C);
   fe_pq(plan.C, &a.P, &a.Q);
   a.G = static_cast<int>((plan.C + 31) / 32);
+  a.unal = plan.unal ? 1 : 0;
+  a.zpos = plan.zpos;
   const int smem = static_cast<int>(plan.smem);
   const bool bf = plan.dt == CMS_BF16;
   cudaError_t e = bf ? cudaFuncSetAttribute(k_sketch_fast<__nv_bfloat16>,

@@ -33,6 +33,9 @@ def make_instances(cms, specs, d=3):
         if sp.dtype == "bf16":
             xr, _ = W.bf16_round(cov.X)
             X = torch.from_numpy(cov.X).to(dev(), torch.bfloat16)
+        elif sp.dtype == "f64":
+            xr = cov.X
+            X = torch.from_numpy(cov.X).to(dev(), torch.float64)
         else:
             xr = cov.X
             X = torch.from_numpy(cov.X).to(dev())
@@ -114,17 +117,17 @@ def test_batch_autotune_writes_cache(cms, tmp_path):
 
 
 def test_batch_mixes_kernel_kinds(cms):
-    # even n with rows of whole 16-byte units -> the register-FFT body
-    # (FP32 or BF16 storage); odd n -> b = 16 n has no factor 32 L and rows
-    # are not 16-byte multiples -> the generic body; all in one launch
+    # FP32 and BF16 storage on the register-FFT body (odd n: rows copied as
+    # their 16-byte aligned supersets, C = P Q < 32 L), FP64 storage on the
+    # generic body; all in one launch
     class Sp:
         def __init__(self, n, dtype, seed):
             self.n, self.m, self.dtype, self.seed, self.n_pairs, self.rho = n, 2 * n, dtype, seed, n // 100, 0.5
     specs = [Sp(512, "f32", 1), Sp(1000, "f32", 2), Sp(768, "bf16", 3), Sp(640, "f32", 4), Sp(675, "f32", 5),
-             Sp(625, "bf16", 6)]
+             Sp(625, "bf16", 6), Sp(600, "f64", 7)]
     items, refs = make_instances(cms, specs)
     batch = cms.Batch(items)
-    assert batch.info()["fast_instances"] == 4
+    assert batch.info()["fast_instances"] == 6
     batch.run()
     torch.cuda.synchronize()
     for c, ref in zip(batch.c, refs):

@@ -436,8 +436,10 @@ def test_overflow_lists_beyond_the_twiddle_cache(cms):
 
 
 def test_fast_and_generic_kernels_agree(cms):
-    # same product through the TMA kernel (aligned rows) and the generic
-    # kernel (leading dimension not a multiple of 4 floats)
+    # the same product through the register-FFT kernel with 16-byte aligned
+    # rows (TMA copies of the rows), with rows that are not (A's leading
+    # dimension n1 + 1: copies of the aligned supersets) and through the
+    # shared-memory kernel (FP64 storage)
     n1, n2, n3, b, d = 512, 96, 512, 16384, 3
     A = W.gaussian(n1, n2, 3).astype(np.float32)
     B = W.gaussian(n2, n3, 4).astype(np.float32)
@@ -445,10 +447,38 @@ def test_fast_and_generic_kernels_agree(cms):
     c_fast = cms.sketch_product(colmajor(A), rowmajor(B), h).cpu().numpy()
     pad_a = torch.zeros((n2, n1 + 1), device=dev())
     pad_a[:, :n1] = torch.from_numpy(A.T)
-    c_gen = cms.sketch_product(pad_a[:, :n1].T, rowmajor(B), h).cpu().numpy()
+    c_unal = cms.sketch_product(pad_a[:, :n1].T, rowmajor(B), h).cpu().numpy()
+    c_gen = cms.sketch_product(colmajor(A, torch.float64), rowmajor(B, torch.float64), h).cpu().numpy()
     ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), O.make_tables(12, 512, b, d))
     assert O.rel_l2(c_fast, ref) < TOL_F32
+    assert O.rel_l2(c_unal, ref) < TOL_F32
     assert O.rel_l2(c_gen, ref) < TOL_F32
+    h.free()
+
+
+@pytest.mark.parametrize("n1,n2,n3,b,d,dtype", [
+    (301, 37, 299, 3840, 2, torch.float32),    # odd row lengths, C = 960
+    (301, 37, 299, 3840, 2, torch.bfloat16),
+    (675, 29, 675, 10800, 2, torch.float32),   # X^T X with odd n (aliased), C = 900
+])
+def test_fast_kernel_unaligned_rows(cms, n1, n2, n3, b, d, dtype):
+    n = max(n1, n3)
+    h = cms.make_hashes(5 + b, n, b, d)
+    tab = O.make_tables(5 + b, n, b, d)
+    if n1 == n3:
+        X = W.gaussian(n2, n1, 9).astype(np.float32)
+        Xr = W.bf16_round(X)[0] if dtype == torch.bfloat16 else X
+        xt = torch.from_numpy(X).to(dev(), dtype)
+        c = cms.sketch_product(xt.T, xt, h).cpu().numpy()
+        ref = O.sketch_definition(Xr.T.astype(np.float64), Xr.astype(np.float64), tab)
+    else:
+        A = W.gaussian(n1, n2, 7).astype(np.float32)
+        B = W.gaussian(n2, n3, 8).astype(np.float32)
+        Ar = W.bf16_round(A)[0] if dtype == torch.bfloat16 else A
+        Br = W.bf16_round(B)[0] if dtype == torch.bfloat16 else B
+        c = cms.sketch_product(colmajor(A, dtype), rowmajor(B, dtype), h).cpu().numpy()
+        ref = O.sketch_definition(Ar.astype(np.float64), Br.astype(np.float64), tab)
+    assert O.rel_l2(c, ref) < TOL_F32
     h.free()
 
 
