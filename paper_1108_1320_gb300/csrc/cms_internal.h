@@ -102,7 +102,7 @@ struct SketchPlan {
   int nkc = 0;              // number of inner-index chunks
   int threads = 256;
   size_t smem = 0;          // dynamic shared memory of the fused kernel
-  bool fast = false;        // the C = 32 L register-FFT kernel applies
+  bool fast = false;        // a C = P Q register-FFT kernel applies
   int dt = 0;               // storage type of A and B (cms_dtype)
   bool ws = false;          // ... in its warp-specialised form (k_sketch_ws)
   int ovcap = 0;            // overflow entries whose twiddles k_sketch_ws caches

@@ -214,8 +214,8 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   const int n = static_cast<int>(h->n);
   const int64_t units = static_cast<int64_t>(p.d) * p.nrows;
 
-  // the C = 32 L register-FFT kernels: FP32 or BF16 rows that TMA can copy
-  // (16-byte aligned rows and row starts)
+  // the C = P Q register-FFT kernels: FP32 or BF16 rows that TMA can copy
+  // (16-byte aligned rows, or aligned supersets of unaligned ones)
   p.dt = dt;
   const int per16 = dt == CMS_BF16 ? 8 : 4;   // elements per 16 bytes
   // rows not in whole 16-byte units are copied as their aligned supersets

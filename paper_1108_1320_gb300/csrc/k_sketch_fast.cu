@@ -37,7 +37,7 @@ namespace {
 
 using namespace wfft;
 
-constexpr int kC = kFeC;       // 1024: the largest C = 32 L
+constexpr int kC = kFeC;       // 1024: the largest C = P Q
 constexpr int kG = 2;          // inner indices per group
 constexpr int kRows = 2;       // rows f1 per block
 constexpr int kThreads = 256;  // 8 warps = kRows x 2 sides x kG FFTs

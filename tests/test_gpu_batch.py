@@ -118,7 +118,7 @@ def test_batch_autotune_writes_cache(cms, tmp_path):
 
 def test_batch_mixes_kernel_kinds(cms):
     # FP32 and BF16 storage on the register-FFT body (odd n: rows copied as
-    # their 16-byte aligned supersets, C = P Q < 32 L), FP64 storage on the
+    # their 16-byte aligned supersets, C = P Q), FP64 storage on the
     # generic body; all in one launch
     class Sp:
         def __init__(self, n, dtype, seed):
