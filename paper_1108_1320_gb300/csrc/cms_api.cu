@@ -318,14 +318,18 @@ cms_status cms_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64
   if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
   *bytes = std::max(plan.ws_bytes, generic.ws_bytes);
   if (n1 == n3) {
-    // A and B the same bytes (A = X^T, B = X): the fast kernel stages each
-    // row once, so its plan can differ from the two-operand one
+    // A and B the same bytes (A = X^T, B = X): the register-FFT and cluster
+    // kernels stage each row once, so their plans can differ from the
+    // two-operand one (leading dimensions in whole 16-byte units of FP32
+    // and of BF16 cover both storage types)
     const void* same = reinterpret_cast<const void*>(static_cast<uintptr_t>(256));
-    const int64_t ld = std::max<int64_t>((n1 + 3) / 4 * 4, 4);
-    SketchPlan alias;
-    r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &alias, &why, same, ld, same, ld);
-    if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
-    *bytes = std::max(*bytes, alias.ws_bytes);
+    for (int64_t unit : {4, 8}) {
+      const int64_t ld = std::max<int64_t>((n1 + unit - 1) / unit * unit, unit);
+      SketchPlan alias;
+      r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &alias, &why, same, ld, same, ld);
+      if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+      *bytes = std::max(*bytes, alias.ws_bytes);
+    }
   }
   return CMS_OK;
 }
@@ -509,8 +513,9 @@ cms_status cms_check_async(void* stream) {
   const uint32_t w = read_clear_error_decode();
   const uint32_t ws1 = read_clear_error_sketch();
   const uint32_t ws2 = read_clear_error_sketch_ws();
-  const uint32_t ws = ws1 | ws2;
-  if (w == 0xFFFFFFFFu || ws1 == 0xFFFFFFFFu || ws2 == 0xFFFFFFFFu)
+  const uint32_t ws3 = read_clear_error_sketch_wide();
+  const uint32_t ws = ws1 | ws2 | ws3;
+  if (w == 0xFFFFFFFFu || ws1 == 0xFFFFFFFFu || ws2 == 0xFFFFFFFFu || ws3 == 0xFFFFFFFFu)
     return fail(CMS_ERR_CUDA, "could not read the device error words");
   if (ws) return fail(CMS_ERR_TIMEOUT, "a fused-kernel wait for its TMA copies gave up");
   if (w) return fail(CMS_ERR_DEVICE, "decode saw an index pair outside the hash domain");

@@ -176,13 +176,13 @@ cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t fl
     SketchPlan p;
     // the persistent batched kernel runs the lock-step fast body
     int r = make_sketch_plan(it.h, it.n1, it.n2, it.n3, it.dt, sms, optin, &p, &why, it.A, it.lda, it.B, it.ldb,
-                             true, 0, 0, false);
+                             true, 0, 0, false, false);
     if (r != CMS_OK) { delete b; return fail(static_cast<cms_status>(r), "instance " + std::to_string(i) + ": " + why); }
     auto hit = cache.find(tune_key(it, p, sms));
     if (hit != cache.end()) {
       SketchPlan q;
       if (make_sketch_plan(it.h, it.n1, it.n2, it.n3, it.dt, sms, optin, &q, &why, it.A, it.lda, it.B, it.ldb,
-                           true, hit->second.nkc, hit->second.G, false) == CMS_OK)
+                           true, hit->second.nkc, hit->second.G, false, false) == CMS_OK)
         p = q;
     } else if (flags & CMS_BATCH_AUTOTUNE) {
       // candidates: the planner's chunking, half and twice as many chunks;
@@ -198,7 +198,7 @@ cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t fl
       for (auto& c2 : cand) {
         SketchPlan q;
         if (make_sketch_plan(it.h, it.n1, it.n2, it.n3, it.dt, sms, optin, &q, &why, it.A, it.lda, it.B,
-                             it.ldb, true, c2.first, c2.second, false) == CMS_OK) {
+                             it.ldb, true, c2.first, c2.second, false, false) == CMS_OK) {
           cps.push_back(q);
           need = std::max(need, q.ws_bytes);
         }

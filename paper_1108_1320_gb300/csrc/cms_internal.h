@@ -111,17 +111,41 @@ struct SketchPlan {
   bool unal = false;        // rows not 16-byte aligned (the fast kernel copies aligned supersets)
   int zpos = 0;             // (unal) staging index of the zero slot
   int tw_shift = 0, nhi = 0;  // two-level w_b table: S = 2^tw_shift, nhi high entries
+  bool wide = false;        // the cluster kernel for C = 2^16 rows (k_sketch_wide)
   // workspace layout (byte offsets)
   size_t off_partial = 0, off_V = 0, off_twfe = 0, off_twC = 0, off_twR = 0;
+  size_t off_T = 0, off_wtab = 0;   // (wide) inverse pass buffer, bucket tables
   size_t ws_bytes = 0;
 };
+
+// Bucket tables of the cluster kernel in the workspace (byte offsets).
+struct WideTables {
+  int64_t entstride = 0, spstride = 0;
+  size_t off_ent = 0, off_rec_xv = 0, off_rec_h = 0, off_nrec = 0;
+  size_t off_sp_xv = 0, off_sp_h = 0, off_sp_bkt = 0, off_sp_cnt = 0;
+  size_t end = 0;
+};
+constexpr int64_t kWideC = 65536;   // row length of the cluster kernel
+WideTables wide_tables_layout(int d, int64_t n, size_t base);
+size_t wide_smem_bytes();
+int wide_max_clusters(int dt);
+cudaError_t launch_sketch_wide(const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,
+                               const void* B, int64_t ldb, int64_t n1, int64_t n2, int64_t n3, char* ws,
+                               float2* partial, cudaStream_t s);
+cudaError_t launch_inverse_wide(const SketchPlan& plan, const float2* partial, float2* V, float2* T,
+                                const float2* tw256, const float2* twR, float* c, cudaStream_t s);
+uint32_t read_clear_error_sketch_wide();
+// K2b alone: real inverse length-R DFT over the rows, 1/b.
+cudaError_t launch_cols_inverse(const SketchPlan& plan, const float2* V, const float2* twR, float* c,
+                                cudaStream_t s);
 
 bool choose_factorisation(int64_t b, int64_t* R, int64_t* C);
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
                      int dt, int num_sms, size_t smem_optin, SketchPlan* plan,
                      std::string* why, const void* A = nullptr, int64_t lda = 0,
                      const void* B = nullptr, int64_t ldb = 0, bool allow_fast = true,
-                     int nkc_override = 0, int G_override = 0, bool allow_ws = true);
+                     int nkc_override = 0, int G_override = 0, bool allow_ws = true,
+                     bool allow_wide = true);
 size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int esz);
 size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int ovcap);
 bool ws_kernel_usable();

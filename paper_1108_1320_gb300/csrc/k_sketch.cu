@@ -198,7 +198,7 @@ int64_t choose_chunks(int64_t units, int64_t n2, int G, int64_t slots, int64_t l
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int dt,
                      int num_sms, size_t smem_optin, SketchPlan* plan, std::string* why,
                      const void* A, int64_t lda, const void* B, int64_t ldb, bool allow_fast,
-                     int nkc_override, int G_override, bool allow_ws) {
+                     int nkc_override, int G_override, bool allow_ws, bool allow_wide) {
   SketchPlan p;
   const bool bf16 = dt == CMS_BF16;
   (void)bf16;
@@ -259,6 +259,53 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
       p.smem = ws_ok ? sm_ws : sm;
     }
   }
+  // long sketches (b a multiple of 2^16): the cluster kernel, one row of
+  // C = 2^16 bins per 8-CTA cluster, when a_k (and b_k) fit its 64 KB
+  // staging buffer as whole 16-byte units; preferred over the register-FFT
+  // kernels from R = b / 2^16 >= 4 on (few rows, each entry visited by few)
+  if (allow_wide && (dt == CMS_F32 || dt == CMS_BF16) && p.b % kWideC == 0 && aligned) {
+    const bool al = A != nullptr && A == B && lda == ldb && n1 == n3;
+    const int64_t n1s = al ? 0 : (n1 + per16 - 1) / per16 * per16;
+    const int64_t stage = al ? n1 * static_cast<int64_t>(esz) : (n1s + n3) * static_cast<int64_t>(esz);
+    const int64_t Rw = p.b / kWideC;
+    if (stage <= 65536 && h->n <= 65535 && (!p.fast || Rw >= 4) && wide_max_clusters(dt) > 0 &&
+        wide_smem_bytes() <= smem_optin) {
+      p.wide = true;
+      p.fast = false;
+      p.ws = false;
+      p.alias = al;
+      p.unal = false;
+      p.C = kWideC;
+      p.R = Rw;
+      p.nrows = static_cast<int>(Rw / 2 + 1);
+      p.nradC = 0;
+      p.G = 1;
+      p.threads = 256;
+      p.smem = wide_smem_bytes();
+    }
+  }
+  if (p.wide) {
+    const int64_t wunits = static_cast<int64_t>(p.d) * p.nrows;
+    const int64_t slots = std::max(1, wide_max_clusters(dt));
+    const int64_t lo = std::max<int64_t>(1, (slots + wunits - 1) / wunits);
+    int64_t nkc = choose_chunks(wunits, n2, 1, slots, lo, std::max<int64_t>(lo, 4 * lo));
+    if (nkc_override > 0) nkc = std::min<int64_t>(nkc_override, std::max<int64_t>(1, n2));
+    int64_t kchunk = n2 > 0 ? (n2 + nkc - 1) / nkc : 1;
+    nkc = n2 > 0 ? (n2 + kchunk - 1) / kchunk : 1;
+    p.kchunk = kchunk;
+    p.nkc = static_cast<int>(nkc);
+    size_t off = 0;
+    p.off_partial = off; off = align256(off + static_cast<size_t>(wunits) * p.nkc * kWideC * 8);
+    p.off_V = off;       off = align256(off + static_cast<size_t>(wunits) * kWideC * 8);
+    p.off_T = off;       off = align256(off + static_cast<size_t>(wunits) * kWideC * 8);
+    p.off_twfe = off;
+    p.off_twC = off;     off = align256(off + 256 * 8);
+    p.off_twR = off;     off = align256(off + static_cast<size_t>(p.R) * 8);
+    p.off_wtab = off;    off = wide_tables_layout(p.d, h->n, off).end;
+    p.ws_bytes = off;
+    *plan = p;
+    return CMS_OK;
+  }
   if (!p.fast) {
     int G = 0;
     for (int g = kMaxG; g >= 1; --g) {
@@ -312,6 +359,12 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   float2* twR = reinterpret_cast<float2*>(ws + plan.off_twR);
   const int n = static_cast<int>(h->n);
 
+  if (plan.wide) {
+    cudaError_t e = launch_twiddle_tables(twC, 256, twR, static_cast<int>(plan.R), s);
+    if (e == cudaSuccess) e = launch_sketch_wide(plan, h, A, lda, B, ldb, n1, n2, n3, ws, partial, s);
+    if (e != cudaSuccess) return e;
+    return launch_inverse_wide(plan, partial, V, reinterpret_cast<float2*>(ws + plan.off_T), twC, twR, c, s);
+  }
   {
     ProfScope prof_scope("k_twiddle_table", s);
     k_twiddle_table<<<static_cast<unsigned>((plan.C + 255) / 256), 256, 0, s>>>(twC, static_cast<int>(plan.C));
@@ -418,6 +471,13 @@ cudaError_t launch_inverse(const SketchPlan& plan, const float2* partial, float2
     ProfScope prof_scope("k_rows_inverse", s);
     k_rows_inverse<<<static_cast<unsigned>(plan.d * plan.nrows), 256, smem2, s>>>(ia);
   }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_cols_inverse(plan, V, twR, c, s);
+}
+
+cudaError_t launch_cols_inverse(const SketchPlan& plan, const float2* V, const float2* twR, float* c,
+                                cudaStream_t s) {
   dim3 g2(static_cast<unsigned>((plan.b + 255) / 256), plan.d);
   {
     ProfScope prof_scope("k_cols_inverse", s);
