@@ -41,15 +41,23 @@ using namespace wfft;
 constexpr int kCl = 8;                 // CTAs per cluster
 constexpr int kL = 8192;               // local FFT length
 constexpr int kCw = kCl * kL;          // row length C = 65536
-constexpr int kThr = 256;              // threads per CTA (8 warps)
-constexpr int kCap = 42;               // records per thread in tensor memory
-constexpr int kKeys = 2 * kL;          // (side, v) bucket keys per CTA
-constexpr int kStageBytes = 65536;     // staging row(s) of a_k, b_k
-// tensor memory: warp w reaches lanes 32 (w mod 4) .. +31 and the 256-column
-// half (w / 4); per thread: records x|v at [0, kCap), w.x at [kCap, 2 kCap),
-// w.y at [2 kCap, 3 kCap), accumulators at [128, 256) (4 bin groups x 32)
-constexpr int kAccCol = 128;
-static_assert(3 * kCap + 8 <= kAccCol + 8, "record columns overlap the accumulators beyond one load");
+#ifndef CMS_WIDE_THREADS
+#define CMS_WIDE_THREADS 256
+#endif
+constexpr int kThr = CMS_WIDE_THREADS;  // threads per CTA
+constexpr int kWarps = kThr / 32;
+constexpr int kQ = 1024 / kThr;         // bin groups q per thread (8 bins each)
+constexpr int kKeys = 2 * kL;           // (side, v) bucket keys per CTA
+constexpr int kStageBytes = 65536;      // staging row(s) of a_k, b_k
+// tensor memory: warp w reaches lanes 32 (w mod 4) .. +31 and the column
+// chunk w / 4 (kWarps / 4 chunks of kChunk columns); per thread: records
+// x|v at [0, kCap), w.x at [kCap, 2 kCap), w.y at [2 kCap, 3 kCap), the
+// accumulators of its kQ bin groups (32 columns each) at the chunk's end
+constexpr int kChunk = 512 / (kWarps / 4);
+constexpr int kAccCol = kChunk - 32 * kQ;
+constexpr int kCap = kAccCol / 3;       // records per thread
+static_assert(kThr == 256 || kThr == 512, "256 or 512 threads");
+static_assert(3 * kCap <= kAccCol, "record columns overlap the accumulators");
 
 __device__ uint32_t g_wide_error = 0;   // 1: a wait gave up
 
@@ -64,9 +72,9 @@ struct WideArgs {
   int alias;
   int esz;                 // 2 (BF16) or 4 (FP32)
   int n1s;                 // staging offset of b_k (elements) when not aliased
-  const uint32_t* rec_xv;  // [d][8][kCap][256]
-  const uint32_t* rec_h;   // [d][8][kCap][256]
-  const uint32_t* nrec;    // [d][8][256]
+  const uint32_t* rec_xv;  // [d][8][kCap][kThr]
+  const uint32_t* rec_h;   // [d][8][kCap][kThr]
+  const uint32_t* nrec;    // [d][8][kThr]
   const uint32_t* sp_xv;   // [d][8][spstride]
   const uint32_t* sp_h;
   const uint32_t* sp_bkt;  // [d][8][spstride]: bucket starts, then the end
@@ -108,6 +116,10 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 
 __device__ __forceinline__ void cluster_arrive() {
   asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void cluster_wait() {
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(kThr, 1) k_sketch_wide(WideArgs p) {
   tmem_fence_after_sync();
   const uint32_t tmem = s_tmem;
   // this thread's row of tensor memory: lane quarter (warp mod 4), column half (warp / 4)
-  const uint32_t trow = tmem + ((static_cast<uint32_t>(warp & 3) * 32u) << 16) + static_cast<uint32_t>(warp >> 2) * 256u;
+  const uint32_t trow = tmem + ((static_cast<uint32_t>(warp & 3) * 32u) << 16) + static_cast<uint32_t>(warp >> 2) * static_cast<uint32_t>(kChunk);
 
   // ---- records of this (t, u) for row f1: x|v|side|last and s(x) w_b^{f1 h(x)}
   const int nr = static_cast<int>(p.nrec[static_cast<size_t>(ts) * kThr + tid]);
@@ -236,7 +248,7 @@ __global__ void __launch_bounds__(kThr, 1) k_sketch_wide(WideArgs p) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) z[i] = 0.f;
 #pragma unroll
-    for (int g = 0; g < 4; ++g) tmem_st32(trow + kAccCol + 32 * g, z);
+    for (int g = 0; g < kQ; ++g) tmem_st32(trow + kAccCol + 32 * g, z);
   }
   tmem_wait_st();
   const int sp_nb = static_cast<int>(p.sp_cnt[static_cast<size_t>(ts) * 2]);
@@ -279,28 +291,51 @@ __global__ void __launch_bounds__(kThr, 1) k_sketch_wide(WideArgs p) {
     }
     // ---- gather front end: Y[side][v] = sum over the bucket's entries -----
     {
+      // records in batches of 8, the next batch's tensor-memory loads in
+      // flight while this one is gathered
       float2 acc = make_float2(0.f, 0.f);
+      uint32_t rx[8], rwx[8], rwy[8];
+      __syncwarp();   // warp-collective loads after the lanes' own stores
+      if (mr > 0) {
+        tmem_ld8_nowait(trow, rx);
+        tmem_ld8_nowait(trow + kCap, rwx);
+        tmem_ld8_nowait(trow + 2 * kCap, rwy);
+      }
 #pragma unroll 1
       for (int j0 = 0; j0 < mr; j0 += 8) {
-        uint32_t rx[8], rwx[8], rwy[8];
-        __syncwarp();   // warp-collective loads after the lanes' own stores
-        tmem_ld8_nowait(trow + j0, rx);
-        tmem_ld8_nowait(trow + kCap + j0, rwx);
-        tmem_ld8_nowait(trow + 2 * kCap + j0, rwy);
         tmem_wait_ld8x3(rx, rwx, rwy);
+        uint32_t cx[8];
+        float cwx[8], cwy[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          cx[i] = rx[i];
+          cwx[i] = __uint_as_float(rwx[i]);
+          cwy[i] = __uint_as_float(rwy[i]);
+        }
+        __syncwarp();
+        if (j0 + 8 < mr) {
+          tmem_ld8_nowait(trow + j0 + 8, rx);
+          tmem_ld8_nowait(trow + kCap + j0 + 8, rwx);
+          tmem_ld8_nowait(trow + 2 * kCap + j0 + 8, rwy);
+        }
+        // the batch's staged values first (independent loads in flight),
+        // then the sums; records past nr read index 0 and add nothing
+        float val[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) val[i] = stage_val<T>(stage, j0 + i < nr ? (cx[i] & 0xFFFFu) : 0u);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           if (j0 + i < nr) {
-            const uint32_t xv = rx[i];
-            const float val = stage_val<T>(stage, xv & 0xFFFFu);
-            acc.x = fmaf(val, __uint_as_float(rwx[i]), acc.x);
-            acc.y = fmaf(val, __uint_as_float(rwy[i]), acc.y);
+            const uint32_t xv = cx[i];
+            acc.x = fmaf(val[i], cwx[i], acc.x);
+            acc.y = fmaf(val[i], cwy[i], acc.y);
             if (xv >> 31) {
               Y[((xv >> 29) & 1u) * kL + ((xv >> 16) & 0x1FFFu)] = acc;
               acc = make_float2(0.f, 0.f);
             }
           }
         }
+        __syncwarp();
       }
       // buckets that did not fit the records: from global memory
       for (int sb = tid; sb < sp_nb; sb += kThr) {
@@ -323,6 +358,7 @@ __global__ void __launch_bounds__(kThr, 1) k_sketch_wide(WideArgs p) {
     // staging consumed: fetch the next inner index while the FFTs run
     if (tid == 0 && k + 1 < k_end && !timed_out) issue(k + 1);
     // ---- local FFT, radix-8 pass over r (v = m + 1024 r), both sides ------
+#pragma unroll 2
     for (int m = tid; m < 1024; m += kThr) {
       float2 w[8];
       powers7(tw8k[m], w);
@@ -344,7 +380,7 @@ __global__ void __launch_bounds__(kThr, 1) k_sketch_wide(WideArgs p) {
     // lane l holds B[l + 32 j]: DFT-32 over j, twiddle w_1024^{l q1}, transpose
     // (XOR-swizzled in place), DFT-32 over l: lane q1 ends with bins q1 + 32 q2
 #pragma unroll 1
-    for (int bi = warp; bi < 16; bi += 8) {
+    for (int bi = warp; bi < 16; bi += kWarps) {
       float2* blk = Y + bi * 1024;
       float2 x[32];
 #pragma unroll
@@ -373,38 +409,46 @@ __global__ void __launch_bounds__(kThr, 1) k_sketch_wide(WideArgs p) {
     // ---- every CTA's L_u ready: length-8 DFT over u, products, Kahan -------
     cluster_arrive();
     cluster_wait();
-#pragma unroll 1
-    for (int qi = 0; qi < 4; ++qi) {
-      const int q = tid + kThr * qi;
-      const int f2a = static_cast<int>(rank) + 8 * q;
-      float2 ga[8], gb[8];
+    {
+      // all remote loads first (16 kQ in flight per thread), then the arithmetic
+      float2 ga[kQ][8], gb[kQ][8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const uint32_t ra = map_rank(yblk + static_cast<uint32_t>(q) * 8u, static_cast<uint32_t>(u));
-        ga[u] = ld_cluster(ra);
-        gb[u] = ld_cluster(ra + static_cast<uint32_t>(kL) * 8u);
-      }
-      float2 w[8];
-      powers7(cmul(twhi[f2a >> 7], twlo[f2a & 127]), w);
+      for (int qi = 0; qi < kQ; ++qi) {
+        const uint32_t la = yblk + static_cast<uint32_t>(tid + kThr * qi) * 8u;
 #pragma unroll
-      for (int u = 1; u < 8; ++u) {
-        ga[u] = cmul(ga[u], w[u]);
-        gb[u] = cmul(gb[u], w[u]);
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t ra = map_rank(la, static_cast<uint32_t>(u));
+          ga[qi][u] = ld_cluster(ra);
+          gb[qi][u] = ld_cluster(ra + static_cast<uint32_t>(kL) * 8u);
+        }
       }
-      Dft<8, false, float2>::run(ga);
-      Dft<8, false, float2>::run(gb);
-      float a[32];
-      tmem_ld32(trow + kAccCol + 32 * qi, a);
 #pragma unroll
-      for (int f2b = 0; f2b < 8; ++f2b) {
-        const float2 pr = cmul(ga[f2b], gb[f2b]);
-        kahan_add(a[4 * f2b + 0], a[4 * f2b + 2], pr.x);
-        kahan_add(a[4 * f2b + 1], a[4 * f2b + 3], pr.y);
+      for (int qi = 0; qi < kQ; ++qi) {
+        const int f2a = static_cast<int>(rank) + 8 * (tid + kThr * qi);
+        float2 w[8];
+        powers7(cmul(twhi[f2a >> 7], twlo[f2a & 127]), w);
+#pragma unroll
+        for (int u = 1; u < 8; ++u) {
+          ga[qi][u] = cmul(ga[qi][u], w[u]);
+          gb[qi][u] = cmul(gb[qi][u], w[u]);
+        }
+        Dft<8, false, float2>::run(ga[qi]);
+        Dft<8, false, float2>::run(gb[qi]);
+        float a[32];
+        tmem_ld32(trow + kAccCol + 32 * qi, a);
+#pragma unroll
+        for (int f2b = 0; f2b < 8; ++f2b) {
+          const float2 pr = cmul(ga[qi][f2b], gb[qi][f2b]);
+          kahan_add(a[4 * f2b + 0], a[4 * f2b + 2], pr.x);
+          kahan_add(a[4 * f2b + 1], a[4 * f2b + 3], pr.y);
+        }
+        tmem_st32(trow + kAccCol + 32 * qi, a);
       }
-      tmem_st32(trow + kAccCol + 32 * qi, a);
     }
     tmem_wait_st();
-    cluster_arrive();
+    // the remote values are consumed (their loads complete): a relaxed
+    // arrival suffices to order them before the other CTAs' next front end
+    cluster_arrive_relaxed();
   }
   if (k_end > k_begin) cluster_wait();
 
@@ -412,7 +456,7 @@ __global__ void __launch_bounds__(kThr, 1) k_sketch_wide(WideArgs p) {
   {
     float2* out = p.partial + ((static_cast<size_t>(t) * p.nrows + f1) * p.nkc + kc) * kCw;
 #pragma unroll 1
-    for (int qi = 0; qi < 4; ++qi) {
+    for (int qi = 0; qi < kQ; ++qi) {
       const int q = tid + kThr * qi;
       float a[32];
       tmem_ld32(trow + kAccCol + 32 * qi, a);
@@ -457,7 +501,7 @@ struct TabArgs {
   int64_t spstride;
 };
 
-constexpr int kTabThr = 256;
+constexpr int kTabThr = kThr;   // one table column per sketch-kernel thread
 
 // exclusive scan over the block of one value per thread; returns the prefix
 // and writes the total to *total
@@ -566,8 +610,8 @@ __global__ void __launch_bounds__(kTabThr) k_wide_tables(TabArgs p) {
   }
   const uint32_t nb = pbase;   // nonempty buckets
   __syncthreads();
-  // placement: thread T takes position r * 256 + T (even rounds) or
-  // r * 256 + 255 - T (odd rounds)
+  // placement: thread T takes position r * kThr + T (even rounds) or
+  // r * kThr + kThr - 1 - T (odd rounds)
   {
     uint32_t fill = 0;
     for (uint32_t r = 0; r * kTabThr < nb; ++r) {
