@@ -438,6 +438,7 @@ def context_numbers(cms, torch, X, h, c, cov, w, dev, stream):
     torch.cuda.empty_cache()
     out["sparse_exact"] = sparse_context(cms, torch, dev)
     out["batched"] = batched_context(cms, torch, dev)
+    out["large"] = large_context(cms, torch, dev)
     return out
 
 
@@ -468,6 +469,50 @@ def sparse_context(cms, torch, dev):
             "ms_per_product": ms, "products_per_s": 1e3 / ms, "nonempty_k": K,
             "alg_tflops": flops / (ms * 1e-3) / 1e12,
             "note": "host wall clock per call (the call waits once for the nonempty-k count)"}
+
+
+def large_context(cms, torch, dev):
+    """Large covariance product at full size: X 16384 x 32768 stored as BF16
+    (N(0, 1), 4096 planted pairs of correlation 0.3), A = X^T, B = X,
+    b = 2^20, d = 7.  Runs the cluster kernel (rows of 2^16 bins)."""
+    m, n, b, d, npairs, rho = 16384, 32768, 1 << 20, 7, 4096, 0.3
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    X = torch.randn((m, n), generator=gen, device=dev, dtype=torch.float32)
+    perm = torch.randperm(n, generator=gen, device=dev)[: 2 * npairs].view(-1, 2)
+    z = torch.randn((m, npairs), generator=gen, device=dev)
+    X[:, perm[:, 1]] = rho * X[:, perm[:, 0]] + math.sqrt(1 - rho ** 2) * z
+    Xb = X.to(torch.bfloat16)
+    del X, z
+    torch.cuda.empty_cache()
+    h = cms.make_hashes(5, n, b, d)
+    ws = cms.alloc_workspace(cms.workspace_size(h, n, m, n, torch.bfloat16), dev)
+    c = torch.empty((d, b), dtype=torch.float32, device=dev)
+    cms.profile_enable(True)
+    cms.sketch_product(Xb.T, Xb, h, c=c, ws=ws)          # warm-up, and the kernel list
+    torch.cuda.synchronize()
+    kernels = cms.profile_summary()
+    cms.profile_enable(False)
+    reps = 2
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        cms.sketch_product(Xb.T, Xb, h, c=c, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    cms.check_async()
+    ms = e0.elapsed_time(e1) / reps
+    flops = total_flops(d, m, b)
+    pe = cms.decode(c, h, perm.to(torch.int64))
+    out = {"workload": "large covariance X 16384x32768 BF16, 4096 pairs rho=0.3, b=2^20, d=7",
+           "ms_per_product": ms, "products_per_s": 1e3 / ms, "alg_tflops": flops / (ms * 1e-3) / 1e12,
+           "kernels": sorted(kernels),
+           "planted_pairs": {"count": npairs, "median_estimate": float(pe.median()), "expected": rho * m}}
+    h.free()
+    del Xb, ws, c
+    torch.cuda.empty_cache()
+    return out
 
 
 def batched_context(cms, torch, dev):
