@@ -206,6 +206,29 @@ CMS_API cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t
                                           size_t ws_bytes, void* stream);
 
 /*
+ * cms_sketch_product_csr_hybrid - cms_sketch_product_csr with the sparse-k
+ * hybrid: by linearity (Sec. 2.2, eq. (1)) c is the sum of the sketches of
+ * the outer products a_k b_k; inner indices whose outer product has at
+ * most `direct_max_pairs` terms (nnz(a_k) nnz(b_k)) are sketched directly
+ * ("sketching a matrix product naively", Sec. 2.2: each term
+ * s1(i) s2(j) A_ik B_kj added to bucket (h1(i) + h2(j)) mod b, in FP64),
+ * the others through the FFT route of cms_sketch_product_csr; the two parts
+ * are added and rounded once to FP32.
+ *   direct_max_pairs : the split; < 0 selects 5 b log2(b) / 64, 0 sends
+ *                      every inner index through the FFT route.
+ *   The FP64 additions of the direct part are atomic: their order varies
+ *   between calls (results agree to FP64 rounding, exactly when the values
+ *   are integers).  Workspace: cms_sparse_workspace_size.  Other arguments,
+ *   errors and the one stream wait as cms_sketch_product_csr.
+ */
+CMS_API cms_status cms_sketch_product_csr_hybrid(const int64_t* a_colptr, const int32_t* a_rowidx,
+                                                 const void* a_val, const int64_t* b_rowptr,
+                                                 const int32_t* b_colidx, const void* b_val,
+                                                 int64_t n1, int64_t n2, int64_t n3, int32_t dt,
+                                                 const cms_hashes* h, int64_t direct_max_pairs,
+                                                 float* c, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * Batches: the paper treats one product; a batch runs COMPRESSEDPRODUCT on
  * many independent (A, B) pairs in one persistent launch.
  *

@@ -47,6 +47,8 @@ SIGNATURES = {
     "cms_sparse_workspace_size": (_I32, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
     "cms_sketch_product_csr": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _P, _P, _SZ,
                                       _P]),
+    "cms_sketch_product_csr_hybrid": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _I64, _P, _P,
+                                             _SZ, _P]),
     "cms_batch_create": (_I32, [_P, _I32, _I32, ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
     "cms_batch_run": (_I32, [_P, _P]),
     "cms_batch_run_graph": (_I32, [_P, _P]),
@@ -251,9 +253,15 @@ def sparse_workspace_size(h: Hashes, n1: int, n2: int, n3: int) -> int:
 def sketch_product_csr(a_colptr: torch.Tensor, a_rowidx: torch.Tensor, a_val: torch.Tensor,
                        b_rowptr: torch.Tensor, b_colidx: torch.Tensor, b_val: torch.Tensor,
                        n1: int, n3: int, h: Hashes, c: torch.Tensor | None = None,
-                       ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+                       ws: torch.Tensor | None = None, stream=None,
+                       direct_max_pairs: int | None = None) -> torch.Tensor:
     """COMPRESSEDPRODUCT of sparse A (CSC: colptr int64, rowidx int32) and B
-    (CSR: rowptr int64, colidx int32); returns c float32 (d, b)."""
+    (CSR: rowptr int64, colidx int32); returns c float32 (d, b).
+
+    ``direct_max_pairs`` selects the sparse-k hybrid (cms_sketch_product_csr_hybrid):
+    inner indices with at most that many outer-product terms are sketched
+    directly (-1: the library's default split); None keeps every inner index
+    on the FFT route."""
     n2 = a_colptr.numel() - 1
     if b_rowptr.numel() - 1 != n2:
         raise ValueError("A and B disagree on the inner dimension")
@@ -268,10 +276,16 @@ def sketch_product_csr(a_colptr: torch.Tensor, a_rowidx: torch.Tensor, a_val: to
         c = torch.empty((inf["d"], inf["b"]), dtype=torch.float32, device=a_colptr.device)
     if ws is None:
         ws = alloc_workspace(sparse_workspace_size(h, n1, n2, n3), a_colptr.device)
-    _check(lib().cms_sketch_product_csr(_ptr(a_colptr), _ptr(a_rowidx), _ptr(a_val), _ptr(b_rowptr),
-                                        _ptr(b_colidx), _ptr(b_val), n1, n2, n3, _DTYPES[a_val.dtype],
-                                        h.handle, _ptr(c), _ptr(ws), ws.numel() * ws.element_size(),
-                                        _stream(stream)))
+    if direct_max_pairs is None:
+        _check(lib().cms_sketch_product_csr(_ptr(a_colptr), _ptr(a_rowidx), _ptr(a_val), _ptr(b_rowptr),
+                                            _ptr(b_colidx), _ptr(b_val), n1, n2, n3, _DTYPES[a_val.dtype],
+                                            h.handle, _ptr(c), _ptr(ws), ws.numel() * ws.element_size(),
+                                            _stream(stream)))
+    else:
+        _check(lib().cms_sketch_product_csr_hybrid(_ptr(a_colptr), _ptr(a_rowidx), _ptr(a_val), _ptr(b_rowptr),
+                                                   _ptr(b_colidx), _ptr(b_val), n1, n2, n3, _DTYPES[a_val.dtype],
+                                                   h.handle, int(direct_max_pairs), _ptr(c), _ptr(ws),
+                                                   ws.numel() * ws.element_size(), _stream(stream)))
     return c
 
 

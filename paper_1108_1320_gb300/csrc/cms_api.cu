@@ -1,6 +1,7 @@
 // cms_api.cu - the C ABI declared in include/cms.h: argument checking,
 // the hash-set object, planning, and the launch sequences.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -419,6 +420,70 @@ cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t* a_rowi
   if (e == cudaSuccess) e = launch_sketch_sparse(plan, h, in, dt, klist, K, partial, s);
   if (e == cudaSuccess) e = launch_inverse(plan, partial, V, twC, twR, c, s);
   if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr");
+  return CMS_OK;
+}
+
+cms_status cms_sketch_product_csr_hybrid(const int64_t* a_colptr, const int32_t* a_rowidx, const void* a_val,
+                                         const int64_t* b_rowptr, const int32_t* b_colidx, const void* b_val,
+                                         int64_t n1, int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h,
+                                         int64_t direct_max_pairs, float* c, void* ws, size_t ws_bytes,
+                                         void* stream) {
+  cms_status st = check_shapes(h, n1, n2, n3, std::max<int64_t>(n1, 1), std::max<int64_t>(n3, 1));
+  if (st != CMS_OK) return st;
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  if (!c) return fail(CMS_ERR_INVALID_ARG, "c is NULL");
+  if (n2 > 0 && (!a_colptr || !b_rowptr)) return fail(CMS_ERR_INVALID_ARG, "pointer array is NULL");
+  if (n2 >= (1LL << 31) - 1) return fail(CMS_ERR_INVALID_ARG, "n2 too large for int32 inner indices");
+  st = check_device(h);
+  if (st != CMS_OK) return st;
+  DeviceProps dp = device_props(h->device);
+  SketchPlan worst;
+  size_t off_klist = 0;
+  std::string why;
+  int r = make_sparse_plan(h, n2, -1, dp.sms, &worst, &off_klist, &why);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  if (!ws || ws_bytes < worst.ws_bytes)
+    return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_sparse_workspace_size()");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(CMS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  // default split: direct when the outer product has at most 5 b log2(b) / 64
+  // terms (the FFT route costs about 5 b log2 b flops per inner index)
+  const int64_t limit = direct_max_pairs >= 0
+                            ? direct_max_pairs
+                            : static_cast<int64_t>(5.0 * static_cast<double>(h->b) *
+                                                   std::log2(static_cast<double>(std::max<int64_t>(h->b, 2))) / 64.0);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  int32_t* flist = reinterpret_cast<int32_t*>(w + off_klist);
+  int32_t* dlist = reinterpret_cast<int32_t*>(w + worst.off_dlist);
+  int32_t* counts = dlist + std::max<int64_t>(n2, 1);
+  double* cd = reinterpret_cast<double*>(w + worst.off_cd);
+  int32_t K[2] = {0, 0};
+  cudaError_t e = cudaSuccess;
+  if (n2 > 0) {
+    e = launch_nonempty_split(a_colptr, b_rowptr, n2, limit, flist, dlist, counts, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(K, counts, sizeof(K), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  } else {
+    e = cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t), s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr_hybrid (inner-index split)");
+  SketchPlan plan;
+  r = make_sparse_plan(h, n2, K[0], dp.sms, &plan, &off_klist, &why);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  SparseArgsHost in{a_colptr, a_rowidx, a_val, b_rowptr, b_colidx, b_val, static_cast<int>(n1),
+                    static_cast<int>(n3)};
+  if (K[0] > 0) {
+    float2* partial = reinterpret_cast<float2*>(w + plan.off_partial);
+    float2* V = reinterpret_cast<float2*>(w + plan.off_V);
+    float2* twC = reinterpret_cast<float2*>(w + plan.off_twC);
+    float2* twR = reinterpret_cast<float2*>(w + plan.off_twR);
+    e = launch_twiddle_tables(twC, static_cast<int>(plan.C), twR, static_cast<int>(plan.R), s);
+    if (e == cudaSuccess) e = launch_sketch_sparse(plan, h, in, dt, flist, K[0], partial, s);
+    if (e == cudaSuccess) e = launch_inverse(plan, partial, V, twC, twR, c, s);
+  }
+  if (e == cudaSuccess) e = launch_direct_scatter(h, in, dt, dlist, counts, K[1], cd, s);
+  if (e == cudaSuccess) e = launch_add_direct(c, cd, static_cast<int64_t>(h->d) * h->b, counts, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr_hybrid");
   return CMS_OK;
 }
 

@@ -115,6 +115,7 @@ struct SketchPlan {
   // workspace layout (byte offsets)
   size_t off_partial = 0, off_V = 0, off_twfe = 0, off_twC = 0, off_twR = 0;
   size_t off_T = 0, off_wtab = 0;   // (wide) inverse pass buffer, bucket tables
+  size_t off_dlist = 0, off_cd = 0; // (sparse) direct list + counts, FP64 direct sketch
   size_t ws_bytes = 0;
 };
 
@@ -187,6 +188,11 @@ int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, Sk
                      size_t* off_klist, std::string* why);
 cudaError_t launch_nonempty(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int32_t* klist,
                             int32_t* kcount, cudaStream_t s);
+cudaError_t launch_nonempty_split(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int64_t limit,
+                                  int32_t* flist, int32_t* dlist, int32_t* counts, cudaStream_t s);
+cudaError_t launch_direct_scatter(const cms_hashes* h, const SparseArgsHost& in, int dt, const int32_t* dlist,
+                                  const int32_t* counts, int Kd, double* cd, cudaStream_t s);
+cudaError_t launch_add_direct(float* c, const double* cd, int64_t len, const int32_t* counts, cudaStream_t s);
 cudaError_t launch_sketch_sparse(const SketchPlan& plan, const cms_hashes* h, const SparseArgsHost& in,
                                  int dt, const int32_t* klist, int K, float2* partial, cudaStream_t s);
 

@@ -295,6 +295,98 @@ k_nonempty(const int64_t* __restrict__ a_ptr, const int64_t* __restrict__ b_ptr,
   if (tid == 0) *kcount = running;
 }
 
+// Sparse-k hybrid: the nonempty inner indices split, in increasing k, into
+// those whose outer product a_k b_k has at most `limit` terms (sketched
+// directly, Sec. 2.2 "sketching a matrix product naively") and the rest
+// (the FFT route).  counts[0] = FFT list length, counts[1] = direct list.
+__global__ void __launch_bounds__(1024)
+k_nonempty_split(const int64_t* __restrict__ a_ptr, const int64_t* __restrict__ b_ptr, int64_t n2,
+                 int64_t limit, int32_t* __restrict__ flist, int32_t* __restrict__ dlist,
+                 int32_t* __restrict__ counts) {
+  __shared__ int32_t warp_tot[2][32];
+  __shared__ int32_t running[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < 2) running[tid] = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n2; base += 1024) {
+    const int64_t k = base + tid;
+    int64_t na = 0, nb = 0;
+    if (k < n2) {
+      na = a_ptr[k + 1] - a_ptr[k];
+      nb = b_ptr[k + 1] - b_ptr[k];
+    }
+    const bool live = na > 0 && nb > 0;
+    const bool direct = live && na * nb <= limit;
+    const unsigned bf = __ballot_sync(0xFFFFFFFFu, live && !direct);
+    const unsigned bd = __ballot_sync(0xFFFFFFFFu, direct);
+    const unsigned lt = (1u << lane) - 1u;
+    if (lane == 0) { warp_tot[0][warp] = __popc(bf); warp_tot[1][warp] = __popc(bd); }
+    __syncthreads();
+    int before_f = 0, before_d = 0;
+    for (int w = 0; w < warp; ++w) { before_f += warp_tot[0][w]; before_d += warp_tot[1][w]; }
+    if (live && !direct) flist[running[0] + before_f + __popc(bf & lt)] = static_cast<int32_t>(k);
+    if (direct) dlist[running[1] + before_d + __popc(bd & lt)] = static_cast<int32_t>(k);
+    __syncthreads();
+    if (tid < 2) {
+      int tot = 0;
+      for (int w = 0; w < 32; ++w) tot += warp_tot[tid][w];
+      running[tid] += tot;
+    }
+    __syncthreads();
+  }
+  if (tid < 2) counts[tid] = running[tid];
+}
+
+template <typename T> __device__ __forceinline__ double val_f64(const T* v, int64_t i);
+template <> __device__ __forceinline__ double val_f64<float>(const float* v, int64_t i) { return v[i]; }
+template <> __device__ __forceinline__ double val_f64<double>(const double* v, int64_t i) { return v[i]; }
+template <> __device__ __forceinline__ double val_f64<__nv_bfloat16>(const __nv_bfloat16* v, int64_t i) {
+  return static_cast<double>(__bfloat162float(v[i]));
+}
+
+// Direct sketch of the outer products of the listed inner indices: for every
+// nonzero pair (A_ik, B_kj) and repetition t, s1(i) s2(j) A_ik B_kj goes to
+// bucket (h1(i) + h2(j)) mod b of an FP64 accumulator (products of two FP32
+// or BF16 values are exact in FP64; the additions are atomic, so their order
+// varies, at FP64 rounding).  One block per listed k at a time.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_direct_scatter(const int64_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const T* __restrict__ a_val,
+                 const int64_t* __restrict__ b_ptr, const int32_t* __restrict__ b_idx, const T* __restrict__ b_val,
+                 int n1, int n3, int64_t n, const int32_t* __restrict__ dlist, const int32_t* __restrict__ counts,
+                 const uint32_t* __restrict__ hs, int d, int64_t b, double* __restrict__ cd) {
+  const int Kd = counts[1];
+  for (int q = blockIdx.x; q < Kd; q += gridDim.x) {
+    const int64_t k = dlist[q];
+    const int64_t a0 = a_ptr[k], na = a_ptr[k + 1] - a0;
+    const int64_t b0 = b_ptr[k], nb = b_ptr[k + 1] - b0;
+    for (int64_t pr = threadIdx.x; pr < na * nb; pr += blockDim.x) {
+      const int64_t ia = a0 + pr / nb, jb = b0 + pr % nb;
+      const int i = a_idx[ia], j = b_idx[jb];
+      if (i < 0 || i >= n1 || j < 0 || j >= n3) continue;
+      const double v = val_f64<T>(a_val, ia) * val_f64<T>(b_val, jb);
+      for (int t = 0; t < d; ++t) {
+        const uint32_t w1 = hs[(static_cast<size_t>(t) * 2 + 0) * n + i];
+        const uint32_t w2 = hs[(static_cast<size_t>(t) * 2 + 1) * n + j];
+        uint64_t z = static_cast<uint64_t>(w1 & kBucketMask) + (w2 & kBucketMask);
+        if (z >= static_cast<uint64_t>(b)) z -= static_cast<uint64_t>(b);
+        const double sv = ((w1 ^ w2) >> 31) ? -v : v;
+        atomicAdd(&cd[static_cast<size_t>(t) * b + z], sv);
+      }
+    }
+  }
+}
+
+// c = FFT-route c + direct part (rounded once to FP32), or the direct part
+// alone when no inner index took the FFT route.
+__global__ void k_add_direct(float* __restrict__ c, const double* __restrict__ cd, int64_t len,
+                             const int32_t* __restrict__ counts) {
+  const bool fft = counts[0] > 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < len;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    c[i] = static_cast<float>(fft ? static_cast<double>(c[i]) + cd[i] : cd[i]);
+}
+
 }  // namespace
 
 int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, SketchPlan* plan,
@@ -349,6 +441,9 @@ int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, Sk
   p.off_twC = off;     off = align256(off + static_cast<size_t>(p.C) * 8);
   p.off_twR = off;     off = align256(off + static_cast<size_t>(p.R) * 8);
   *off_klist = off;    off = align256(off + static_cast<size_t>(std::max<int64_t>(n2, 1) + 1) * 4);
+  // sparse-k hybrid: the direct list, the list counts, the FP64 direct sketch
+  p.off_dlist = off;   off = align256(off + static_cast<size_t>(std::max<int64_t>(n2, 1) + 2) * 4);
+  p.off_cd = off;      off = align256(off + static_cast<size_t>(p.d) * p.b * 8);
   p.ws_bytes = off;
   (void)why;
   *plan = p;
@@ -360,6 +455,49 @@ cudaError_t launch_nonempty(const int64_t* a_ptr, const int64_t* b_ptr, int64_t 
   {
     ProfScope prof_scope("k_nonempty", s);
     k_nonempty<<<1, 1024, 0, s>>>(a_ptr, b_ptr, n2, klist, kcount);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonempty_split(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int64_t limit,
+                                  int32_t* flist, int32_t* dlist, int32_t* counts, cudaStream_t s) {
+  {
+    ProfScope prof_scope("k_nonempty_split", s);
+    k_nonempty_split<<<1, 1024, 0, s>>>(a_ptr, b_ptr, n2, limit, flist, dlist, counts);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_direct_scatter(const cms_hashes* h, const SparseArgsHost& in, int dt, const int32_t* dlist,
+                                  const int32_t* counts, int Kd, double* cd, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cd, 0, static_cast<size_t>(h->d) * h->b * sizeof(double), s);
+  if (e != cudaSuccess || Kd == 0) return e;
+  const unsigned grid = static_cast<unsigned>(std::min(Kd, 65535));
+  ProfScope prof_scope("k_direct_scatter", s);
+  switch (dt) {
+    case CMS_F32:
+      k_direct_scatter<float><<<grid, 256, 0, s>>>(in.a_ptr, in.a_idx, static_cast<const float*>(in.a_val), in.b_ptr,
+                                                   in.b_idx, static_cast<const float*>(in.b_val), in.n1, in.n3, h->n,
+                                                   dlist, counts, h->d_hs, h->d, h->b, cd);
+      break;
+    case CMS_BF16:
+      k_direct_scatter<__nv_bfloat16><<<grid, 256, 0, s>>>(
+          in.a_ptr, in.a_idx, static_cast<const __nv_bfloat16*>(in.a_val), in.b_ptr, in.b_idx,
+          static_cast<const __nv_bfloat16*>(in.b_val), in.n1, in.n3, h->n, dlist, counts, h->d_hs, h->d, h->b, cd);
+      break;
+    default:
+      k_direct_scatter<double><<<grid, 256, 0, s>>>(in.a_ptr, in.a_idx, static_cast<const double*>(in.a_val), in.b_ptr,
+                                                    in.b_idx, static_cast<const double*>(in.b_val), in.n1, in.n3, h->n,
+                                                    dlist, counts, h->d_hs, h->d, h->b, cd);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_direct(float* c, const double* cd, int64_t len, const int32_t* counts, cudaStream_t s) {
+  {
+    ProfScope prof_scope("k_add_direct", s);
+    k_add_direct<<<static_cast<unsigned>(std::min<int64_t>((len + 255) / 256, 4096)), 256, 0, s>>>(c, cd, len, counts);
   }
   return cudaGetLastError();
 }

@@ -118,3 +118,87 @@ def test_exact_sparse_full_size(cms):
     exact = np.mean(np.rint(est[:AB.nnz]) == AB.data)
     assert exact > 0.8
     h.free()
+
+
+# ------------------------------------------------------ sparse-k hybrid ----
+def run_hybrid(cms, args, n1, n3, h, limit):
+    cms.profile_enable(True)
+    c = cms.sketch_product_csr(*args, n1, n3, h, direct_max_pairs=limit)
+    torch.cuda.synchronize()
+    kernels = cms.profile_summary()
+    cms.profile_enable(False)
+    cms.check_async()
+    return c.cpu().numpy(), kernels
+
+
+@pytest.mark.parametrize("limit", [-1, 0, 1024, 1 << 40])
+def test_hybrid_blocks_exact(cms, limit):
+    # integer blocks: every outer product has 32 x 32 = 1024 terms, so the
+    # default split and limit >= 1024 sketch them all directly, 0 none
+    n, b, d = 1 << 16, 1 << 16, 3
+    sb = W.sparse_blocks(n, n_blocks=64, inner=8, rows=32, cols=32, seed=n + 64)
+    A, B = sb.scipy()
+    h = cms.make_hashes(7 + b, n, b, d)
+    c, kernels = run_hybrid(cms, to_dev(sb), n, n, h, limit)
+    ref = O.sketch_definition_sparse(A, B, O.make_tables(7 + b, n, b, d))
+    np.testing.assert_array_equal(np.rint(c), ref)
+    assert O.rel_l2(c, ref) < 1e-5
+    assert ("k_sketch_sparse" in kernels) == (limit == 0)
+    assert (kernels.get("k_direct_scatter", {}).get("launches", 0) > 0) == (limit != 0)
+    h.free()
+
+
+def test_hybrid_mixed_split_real_values(cms):
+    # columns of A / rows of B with very different nonzero counts: the split
+    # sends the small outer products to the direct route, the large ones to
+    # the FFT route; their sum matches the oracle
+    n, n2, b, d = 900, 240, 8192, 3
+    g = W.rng(41)
+    dens = np.where(np.arange(n2) % 3 == 0, 0.2, 0.01)
+    A = np.where(g.random((n, n2)) < dens[None, :], g.standard_normal((n, n2)), 0.0).astype(np.float32)
+    B = np.where(g.random((n2, n)) < dens[:, None], g.standard_normal((n2, n)), 0.0).astype(np.float32)
+    import scipy.sparse as sp
+    Ac = sp.csc_matrix(A)
+    Br = sp.csr_matrix(B)
+    pairs = np.diff(Ac.indptr) * np.diff(Br.indptr)
+    limit = int(np.median(pairs[pairs > 0]))
+    assert (pairs > limit).sum() > 10 and ((pairs > 0) & (pairs <= limit)).sum() > 10
+    T = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev(), dt)   # noqa: E731
+    args = (T(Ac.indptr, torch.int64), T(Ac.indices, torch.int32), T(Ac.data, torch.float32),
+            T(Br.indptr, torch.int64), T(Br.indices, torch.int32), T(Br.data, torch.float32))
+    h = cms.make_hashes(9, n, b, d)
+    c, kernels = run_hybrid(cms, args, n, n, h, limit)
+    assert "k_sketch_sparse" in kernels and "k_direct_scatter" in kernels
+    ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), O.make_tables(9, n, b, d))
+    assert max(O.rel_l2(c[t], ref[t]) for t in range(d)) < 1e-5
+    h.free()
+
+
+def test_hybrid_without_common_inner_index_is_zero(cms):
+    n, b = 200, 2048
+    colptr = np.zeros(11, np.int64)
+    colptr[1:] = np.arange(1, 11)
+    rowptr = np.zeros(11, np.int64)
+    T = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev(), dt)   # noqa: E731
+    h = cms.make_hashes(1, n, b, 2)
+    c = torch.full((2, b), 7.0, device=dev())
+    cms.sketch_product_csr(T(colptr, torch.int64), T(np.arange(10), torch.int32),
+                           T(np.ones(10), torch.float32), T(rowptr, torch.int64),
+                           T(np.zeros(1), torch.int32), T(np.zeros(1), torch.float32), n, n, h, c=c,
+                           direct_max_pairs=-1)
+    assert torch.count_nonzero(c).item() == 0
+    h.free()
+
+
+def test_hybrid_exact_sparse_full_size(cms):
+    # the exact sparse configuration (n = b = 2^20, d = 3) through the direct
+    # route: c bit-exact after rounding, as on the FFT route
+    n, b, d = 1 << 20, 1 << 20, 3
+    sb = W.sparse_blocks(n, n_blocks=256, inner=8, rows=32, cols=32, seed=3)
+    A, B = sb.scipy()
+    h = cms.make_hashes(3, n, b, d)
+    c, kernels = run_hybrid(cms, to_dev(sb), n, n, h, -1)
+    assert "k_sketch_sparse" not in kernels
+    ref = O.sketch_definition_sparse(A, B, O.make_tables(3, n, b, d))
+    np.testing.assert_array_equal(np.rint(c), ref)
+    h.free()
