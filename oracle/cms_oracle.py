@@ -43,6 +43,11 @@ What each function follows:
   X_t = s1_t(i) s2_t(j) c_t[(h1_t(i) + h2_t(j)) mod b], median over t.  The
   median of an even number of values is the mean of the two middle ones.
 
+* ``product_diagonal`` / ``remove_diagonal`` / ``candidates`` - the
+  covariance post-steps of Sec. 3.2 and Fig. 2: the diagonal of AB, the
+  sketch of AB with its diagonal's contribution removed, and the entries
+  whose estimate exceeds a threshold.
+
 Every function here is pinned by tests under ``-m "not gpu"`` against facts
 that do not come from this module (published splitmix64 outputs, hand-worked
 hash values, the three independent sketch routes, the injective-hash and b=1
@@ -340,3 +345,59 @@ def sketch_fft_sparse(A_csc, B_csr, tab: Tables) -> np.ndarray:
             p += np.fft.fft(pa) * np.fft.fft(pb)
         c[t] = np.fft.ifft(p).real
     return c
+
+
+# --------------------------------------------------------------------------
+# Covariance post-steps (Sec. 3.2, Fig. 2).  A linear sketch of Q gives one
+# of Q~ (Q with its diagonal set to zero) by removing each diagonal entry's
+# contribution from its bucket; the decoded estimates of Q~ are then
+# thresholded into a short list of candidates for large entries.
+# --------------------------------------------------------------------------
+def product_diagonal(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """(AB)_ii = sum_k A_ik B_ki for i < min(n1, n3), in float64."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    m = min(A.shape[0], B.shape[1])
+    return np.einsum("ik,ki->i", A[:m], B[:, :m])
+
+
+def remove_diagonal(c: np.ndarray, diag: np.ndarray, tab: Tables) -> np.ndarray:
+    """Sketch of AB without its diagonal: for every i and repetition t,
+    s1_t(i) s2_t(i) diag_i leaves bucket (h1_t(i) + h2_t(i)) mod b (the
+    entry (i, i) enters the sketch there with that sign, Sec. 2.2)."""
+    out = np.array(c, dtype=np.float64, copy=True)
+    i = np.arange(len(diag))
+    for t in range(tab.d):
+        z = (tab.h1[t, i] + tab.h2[t, i]) % tab.b
+        np.subtract.at(out[t], z, tab.s1[t, i] * tab.s2[t, i] * np.asarray(diag, dtype=np.float64))
+    return out
+
+
+def candidates(c: np.ndarray, tab: Tables, n1: int, n3: int, tau: float,
+               skip_diagonal: bool = True) -> np.ndarray:
+    """Row-major (i, j) pairs whose estimate DECOMPRESS(i, j) exceeds tau in
+    absolute value (Fig. 2: thresholding the approximation), shape (q, 2).
+
+    The estimates decide set membership, so they are formed in float32, the
+    precision of the sketch c: X_t = s1 s2 c_t[...] (sign changes are exact),
+    the middle value for odd d, 0.5 (a + b) of the two middle values in
+    float32 for even d; the comparison |estimate| > tau is made in float32.
+    """
+    c32 = np.asarray(c, dtype=np.float32)
+    ii, jj = np.meshgrid(np.arange(n1), np.arange(n3), indexing="ij")
+    ii = ii.ravel()
+    jj = jj.ravel()
+    X = np.empty((tab.d, len(ii)), dtype=np.float32)
+    for t in range(tab.d):
+        z = (tab.h1[t, ii] + tab.h2[t, jj]) % tab.b
+        X[t] = c32[t][z] * (tab.s1[t, ii] * tab.s2[t, jj]).astype(np.float32)
+    X.sort(axis=0)
+    mid = tab.d // 2
+    if tab.d % 2:
+        est = X[mid]
+    else:
+        est = np.float32(0.5) * (X[mid - 1] + X[mid])
+    keep = np.abs(est) > np.float32(tau)
+    if skip_diagonal:
+        keep &= ii != jj
+    return np.stack([ii[keep], jj[keep]], axis=1).astype(np.int64)

@@ -120,3 +120,42 @@ def test_mutation_convolution_index_off_by_one(monkeypatch):
     monkeypatch.setattr(O, "sketch_convolution", bad)
     assert _fails(_run_param(pins.test_fft_route_equals_definition_and_convolution, ROUTE_CASES),
                   pins.test_fft_route_equals_convolution_at_b1024)
+
+
+def test_mutation_diagonal_removed_with_wrong_sign(monkeypatch):
+    orig = O.remove_diagonal
+
+    def bad(c, diag, tab):
+        return orig(c, -np.asarray(diag), tab)
+    monkeypatch.setattr(O, "remove_diagonal", bad)
+    assert _fails(pins.test_remove_diagonal_is_the_sketch_of_the_offdiagonal_part)
+
+
+def test_mutation_diagonal_removed_at_column_bucket(monkeypatch):
+    def bad(c, diag, tab):
+        out = np.array(c, dtype=np.float64, copy=True)
+        i = np.arange(len(diag))
+        for t in range(tab.d):
+            z = (2 * tab.h2[t, i]) % tab.b
+            np.subtract.at(out[t], z, tab.s1[t, i] * tab.s2[t, i] * diag)
+        return out
+    monkeypatch.setattr(O, "remove_diagonal", bad)
+    assert _fails(pins.test_remove_diagonal_is_the_sketch_of_the_offdiagonal_part)
+
+
+def test_mutation_diagonal_transposed_operand(monkeypatch):
+    monkeypatch.setattr(O, "product_diagonal",
+                        lambda A, B: np.einsum("ik,ik->i", np.asarray(A)[:, :1].repeat(np.asarray(A).shape[1], 1),
+                                               np.asarray(A)))
+    assert _fails(pins.test_product_diagonal_brute_force)
+
+
+def test_mutation_candidates_without_absolute_value(monkeypatch):
+    orig = O.candidates
+
+    def bad(c, tab, n1, n3, tau, skip_diagonal=True):
+        full = orig(c, tab, n1, n3, tau, skip_diagonal)
+        est = O.decompress(c, tab, full[:, 0], full[:, 1])
+        return full[est > tau]
+    monkeypatch.setattr(O, "candidates", bad)
+    assert _fails(lambda: pins.test_candidates_with_injective_hashes_are_the_large_entries(True))

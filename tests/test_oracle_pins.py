@@ -290,14 +290,54 @@ def test_fig2_planted_pair_stands_out():
     X[66] = 0.9 * X[21] + 0.1 * X[66]
     tab = O.make_tables(7, n, b, 3)
     c = O.sketch_definition(X, X.T, tab)
-    # subtract the diagonal's contribution s1(i)s2(i)(AA^T)_ii at its bucket
-    diag = (X * X).sum(axis=1)
-    for t in range(3):
-        z = (tab.h1[t, :n] + tab.h2[t, :n]) % b
-        np.subtract.at(c[t], z, tab.s1[t, :n] * tab.s2[t, :n] * diag)
+    c = O.remove_diagonal(c, O.product_diagonal(X, X.T), tab)
     est = O.decompress_dense(c, tab, n, n)
-    np.fill_diagonal(est, 0.0)
     thr = 0.5 * est[21, 66]
-    cand = set(map(tuple, np.argwhere(est > thr)))
+    cand = set(map(tuple, O.candidates(c, tab, n, n, thr)))
     assert (21, 66) in cand and (66, 21) in cand
     assert len(cand) < 0.02 * n * n
+
+
+# ----------------------------------------- covariance post-steps (Sec. 3.2) --
+def test_product_diagonal_brute_force():
+    A = W.gaussian(7, 5, 61)
+    B = W.gaussian(5, 9, 62)
+    want = [sum(A[i, k] * B[k, i] for k in range(5)) for i in range(7)]
+    np.testing.assert_allclose(O.product_diagonal(A, B), want, rtol=1e-13)
+
+
+def test_remove_diagonal_is_the_sketch_of_the_offdiagonal_part():
+    # the sketch of Q~ computed from its definition (AB with a zero
+    # diagonal, sketched as the product (AB - D) I) equals the sketch of AB
+    # with the diagonal's contributions removed
+    n1, n2, n3, b, d = 30, 11, 26, 97, 3
+    A = W.gaussian(n1, n2, 63)
+    B = W.gaussian(n2, n3, 64)
+    tab = O.make_tables(65, max(n1, n3), b, d)
+    AB = A @ B
+    off = AB.copy()
+    m = min(n1, n3)
+    off[np.arange(m), np.arange(m)] = 0.0
+    want = O.sketch_definition(off, np.eye(n3), tab)
+    got = O.remove_diagonal(O.sketch_definition(A, B, tab), O.product_diagonal(A, B), tab)
+    np.testing.assert_allclose(got, want, atol=1e-11)
+
+
+@pytest.mark.parametrize("skip", [True, False])
+def test_candidates_with_injective_hashes_are_the_large_entries(skip):
+    # with an injective splitting function every estimate is (AB)_ij itself
+    # (Sec. 2.2), so the candidates are exactly the entries above the
+    # threshold, found here by brute force
+    n1, n2, n3 = 9, 4, 8
+    A = np.round(W.gaussian(n1, n2, 66) * 4)
+    B = np.round(W.gaussian(n2, n3, 67) * 4)
+    n = max(n1, n3)
+    g = W.rng(68)
+    tab = O.Tables(np.arange(n)[None, :].repeat(3, 0), g.choice([-1, 1], size=(3, n)),
+                   (n1 * np.arange(n))[None, :].repeat(3, 0), g.choice([-1, 1], size=(3, n)), n1 * n3)
+    c = O.sketch_definition(A, B, tab)
+    AB = A @ B
+    tau = 10.5
+    want = [(i, j) for i in range(n1) for j in range(n3) if abs(AB[i, j]) > tau and (i != j or not skip)]
+    got = [tuple(p) for p in O.candidates(c, tab, n1, n3, tau, skip_diagonal=skip)]
+    assert got == want
