@@ -333,6 +333,45 @@ CMS_API cms_status cms_decode_dense(const float* c, const cms_hashes* h, int64_t
                             int64_t n3, float* out, int64_t ldo, void* stream);
 
 /*
+ * cms_sketch_remove_diagonal - covariance post-step (Sec. 3.2): a linear
+ * sketch of Q gives one of Q~, Q with its diagonal set to zero.  With c the
+ * sketch of AB (cms_sketch_product with the same operands and hashes), each
+ * entry (AB)_ii = sum_k A_ik B_ki, i < min(n1, n3), formed in FP64, is
+ * subtracted with sign s1_t(i) s2_t(i) from bucket (h1_t(i) + h2_t(i)) mod b
+ * of every repetition t, in place.  For A = X^T, B = X this removes the
+ * variances sum_k X_ki^2 (Fig. 2: "subtracting the contribution of diagonal
+ * elements").
+ *   A, lda, B, ldb, n1, n2, n3, dt : as cms_sketch_product.
+ *   c : device float [d][b], updated in place (FP32 atomic subtractions:
+ *       when several i share a bucket their order is unspecified).
+ * Errors: CMS_ERR_INVALID_ARG for bad shapes, dtype or NULL pointers.
+ */
+CMS_API cms_status cms_sketch_remove_diagonal(const void* A, int64_t lda, const void* B, int64_t ldb,
+                                              int64_t n1, int64_t n2, int64_t n3, int32_t dt,
+                                              const cms_hashes* h, float* c, void* stream);
+
+/*
+ * cms_decode_threshold - the thresholding of Fig. 2: every (i, j), i < n1,
+ * j < n3, whose estimate DECOMPRESS(i, j) (as cms_decode_dense) has
+ * |estimate| > tau, skipping i = j when skip_diagonal is nonzero, without
+ * forming the dense n1 x n3 matrix.
+ *   ij_out    : device int64 [capacity][2], the hits in row-major order
+ *               (i ascending, then j ascending), the first `capacity` of them.
+ *   val_out   : device float [capacity], their estimates.
+ *   count_out : device int64, the number of hits (may exceed capacity: call
+ *               again with a larger buffer).
+ *   ws        : device scratch of at least 8 (n1 + 1) bytes, 8-byte aligned.
+ * The estimates are formed in FP32 (the even-d median is 0.5 (a + b) in
+ * FP32), as is the comparison with tau.  Asynchronous on `stream`.
+ * Errors: CMS_ERR_INVALID_ARG (bad sizes, tau < 0 or NaN, NULL pointers),
+ * CMS_ERR_WORKSPACE (ws too small or misaligned).
+ */
+CMS_API cms_status cms_decode_threshold(const float* c, const cms_hashes* h, int64_t n1, int64_t n3,
+                                        float tau, int32_t skip_diagonal, int64_t* ij_out,
+                                        float* val_out, int64_t capacity, int64_t* count_out,
+                                        void* ws, size_t ws_bytes, void* stream);
+
+/*
  * cms_merge - c_out[t][z] = sum over the `count` partial sketches (device
  * float [d][b] each, pointers in a host array) in index order.  The sketch
  * is linear in the outer products of eq. (1) (Sec. 2.2), so sketches of

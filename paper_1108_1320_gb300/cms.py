@@ -47,6 +47,8 @@ SIGNATURES = {
     "cms_sparse_workspace_size": (_I32, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
     "cms_sketch_product_csr": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _P, _P, _SZ,
                                       _P]),
+    "cms_sketch_remove_diagonal": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P]),
+    "cms_decode_threshold": (_I32, [_P, _P, _I64, _I64, ctypes.c_float, _I32, _P, _P, _I64, _P, _P, _SZ, _P]),
     "cms_sketch_product_csr_hybrid": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _I64, _P, _P,
                                              _SZ, _P]),
     "cms_batch_create": (_I32, [_P, _I32, _I32, ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
@@ -401,6 +403,33 @@ def decode_dense(c: torch.Tensor, h: Hashes, n1: int, n3: int, out: torch.Tensor
     _check(lib().cms_decode_dense(_ptr(c), h.handle, n1, n3, _ptr(out), out.stride(0) if n1 else n3,
                                   _stream(stream)))
     return out
+
+
+def remove_diagonal(A: torch.Tensor, B: torch.Tensor, h: Hashes, c: torch.Tensor, stream=None) -> torch.Tensor:
+    """Sec. 3.2: turn the sketch c of AB (in place) into the sketch of AB with
+    its diagonal set to zero; A, B as for sketch_product."""
+    n1, n2, n3, lda, ldb = _ab_args(A, B)
+    _check(lib().cms_sketch_remove_diagonal(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype], h.handle,
+                                            _ptr(c), _stream(stream)))
+    return c
+
+
+def decode_threshold(c: torch.Tensor, h: Hashes, n1: int, n3: int, tau: float, skip_diagonal: bool = True,
+                     capacity: int = 1 << 16, stream=None):
+    """Fig. 2's thresholding: (ij int64 (q, 2), estimates float32 (q,), count)
+    for every (i, j) with |estimate| > tau in row-major order; when count
+    exceeds capacity only the first capacity hits are returned."""
+    dev = c.device
+    ij = torch.empty((max(capacity, 1), 2), dtype=torch.int64, device=dev)
+    val = torch.empty(max(capacity, 1), dtype=torch.float32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = torch.empty(n1 + 1, dtype=torch.int64, device=dev)
+    _check(lib().cms_decode_threshold(_ptr(c.contiguous()), h.handle, n1, n3, float(tau), 1 if skip_diagonal else 0,
+                                      _ptr(ij), _ptr(val), capacity, _ptr(cnt), _ptr(ws), ws.numel() * 8,
+                                      _stream(stream)))
+    q = int(cnt.item())
+    k = min(q, capacity)
+    return ij[:k], val[:k], q
 
 
 def merge(parts: list[torch.Tensor], out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

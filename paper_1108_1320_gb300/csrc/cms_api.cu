@@ -560,6 +560,41 @@ cms_status cms_decode_dense(const float* c, const cms_hashes* h, int64_t n1, int
   return CMS_OK;
 }
 
+cms_status cms_sketch_remove_diagonal(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
+                                      int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h, float* c,
+                                      void* stream) {
+  cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
+  if (st != CMS_OK) return st;
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  if (!c) return fail(CMS_ERR_INVALID_ARG, "c is NULL");
+  if (n2 > 0 && std::min(n1, n3) > 0 && (!A || !B)) return fail(CMS_ERR_INVALID_ARG, "A or B is NULL");
+  st = check_device(h);
+  if (st != CMS_OK) return st;
+  cudaError_t e = launch_remove_diagonal(A, lda, B, ldb, n1, n2, n3, dt, h, c, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_remove_diagonal");
+  return CMS_OK;
+}
+
+cms_status cms_decode_threshold(const float* c, const cms_hashes* h, int64_t n1, int64_t n3, float tau,
+                                int32_t skip_diagonal, int64_t* ij_out, float* val_out, int64_t capacity,
+                                int64_t* count_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  if (n1 < 0 || n3 < 0 || n1 > h->n || n3 > h->n) return fail(CMS_ERR_INVALID_ARG, "bad n1 or n3");
+  if (capacity < 0) return fail(CMS_ERR_INVALID_ARG, "capacity < 0");
+  if (!count_out || (n1 > 0 && n3 > 0 && !c) || (capacity > 0 && (!ij_out || !val_out)))
+    return fail(CMS_ERR_INVALID_ARG, "NULL pointer");
+  if (!(tau >= 0.f)) return fail(CMS_ERR_INVALID_ARG, "tau must be a number >= 0");
+  if (!ws || ws_bytes < static_cast<size_t>(n1 + 1) * sizeof(int64_t))
+    return fail(CMS_ERR_WORKSPACE, "workspace must hold 8 (n1 + 1) bytes");
+  if (reinterpret_cast<uintptr_t>(ws) % 8 != 0) return fail(CMS_ERR_WORKSPACE, "workspace must be 8-byte aligned");
+  cms_status st = check_device(h);
+  if (st != CMS_OK) return st;
+  cudaError_t e = launch_decode_threshold(c, h, n1, n3, tau, skip_diagonal ? 1 : 0, ij_out, val_out, capacity,
+                                          count_out, static_cast<int64_t*>(ws), static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_decode_threshold");
+  return CMS_OK;
+}
+
 cms_status cms_merge(const float* const* parts, int32_t count, int32_t d, int64_t b, float* c_out,
                      void* stream) {
   if (count < 0 || d < 1 || b < 1) return fail(CMS_ERR_INVALID_ARG, "bad count, d or b");

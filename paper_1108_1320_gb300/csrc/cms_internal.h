@@ -205,6 +205,11 @@ cudaError_t launch_decode_pairs_f64(const double* c, const cms_hashes* h,
 cudaError_t launch_decode_dense_f32(const float* c, const cms_hashes* h,
                                     int64_t n1, int64_t n3, float* out,
                                     int64_t ldo, cudaStream_t s);
+cudaError_t launch_decode_threshold(const float* c, const cms_hashes* h, int64_t n1, int64_t n3, float tau,
+                                    int skip_diagonal, int64_t* ij, float* val, int64_t capacity,
+                                    int64_t* count, int64_t* rowcnt, cudaStream_t s);
+cudaError_t launch_remove_diagonal(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
+                                   int64_t n3, int dt, const cms_hashes* h, float* c, cudaStream_t s);
 cudaError_t launch_merge(const float* const* parts, int count, int64_t len,
                          float* out, cudaStream_t s);
 

@@ -66,6 +66,110 @@ __global__ void k_decode_dense(const T* __restrict__ c, const uint32_t* __restri
   }
 }
 
+// Thresholded decode (Fig. 2: the approximation is thresholded into a short
+// list of candidates): pass 1 counts, per row i, the j with
+// |estimate(i, j)| > tau (i != j when skip_diagonal); pass 2 turns the
+// counts into row offsets; pass 3 recomputes the estimates and writes the
+// hits of row i in increasing j from its offset (row-major order overall,
+// independent of scheduling).
+__device__ __forceinline__ bool thresh_hit(float v, float tau, int skip, int64_t i, int64_t j) {
+  return fabsf(v) > tau && !(skip && i == j);
+}
+
+__global__ void __launch_bounds__(256)
+k_thresh_count(const float* __restrict__ c, const uint32_t* __restrict__ hs, int64_t n, uint32_t b, int d,
+               int64_t n1, int64_t n3, float tau, int skip, int64_t* __restrict__ rowcnt) {
+  __shared__ int64_t part[8];
+  for (int64_t i = blockIdx.x; i < n1; i += gridDim.x) {
+    int64_t cnt = 0;
+    for (int64_t j = threadIdx.x; j < n3; j += blockDim.x)
+      cnt += thresh_hit(estimate(c, hs, n, b, d, i, j), tau, skip, i, j) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t s = 0;
+      for (int w = 0; w < 8; ++w) s += part[w];
+      rowcnt[i] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// exclusive scan of rowcnt[0..n1) in place; rowcnt[n1] and *total get the sum
+__global__ void __launch_bounds__(1024) k_thresh_scan(int64_t* __restrict__ rowcnt, int64_t n1,
+                                                      int64_t* __restrict__ total) {
+  __shared__ int64_t wsum[32];
+  __shared__ int64_t running;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) running = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n1; base += 1024) {
+    const int64_t i = base + tid;
+    const int64_t v = i < n1 ? rowcnt[i] : 0;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int64_t before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    if (i < n1) rowcnt[i] = running + before + x - v;
+    __syncthreads();
+    if (tid == 0) {
+      int64_t s = 0;
+      for (int w = 0; w < 32; ++w) s += wsum[w];
+      running += s;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    rowcnt[n1] = running;
+    *total = running;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_thresh_write(const float* __restrict__ c, const uint32_t* __restrict__ hs, int64_t n, uint32_t b, int d,
+               int64_t n1, int64_t n3, float tau, int skip, const int64_t* __restrict__ rowoff,
+               int64_t capacity, int64_t* __restrict__ ij, float* __restrict__ val) {
+  __shared__ int wcnt[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t i = blockIdx.x; i < n1; i += gridDim.x) {
+    if (rowoff[i] == rowoff[i + 1]) continue;   // uniform over the block
+    int64_t pos = rowoff[i];
+    for (int64_t j0 = 0; j0 < n3; j0 += blockDim.x) {
+      const int64_t j = j0 + threadIdx.x;
+      float v = 0.f;
+      bool hit = false;
+      if (j < n3) {
+        v = estimate(c, hs, n, b, d, i, j);
+        hit = thresh_hit(v, tau, skip, i, j);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) wcnt[warp] = __popc(bal);
+      __syncthreads();
+      int64_t before = 0, tot = 0;
+      for (int w = 0; w < 8; ++w) {
+        if (w < warp) before += wcnt[w];
+        tot += wcnt[w];
+      }
+      if (hit) {
+        const int64_t q = pos + before + __popc(bal & ((1u << lane) - 1u));
+        if (q < capacity) {
+          ij[2 * q] = i;
+          ij[2 * q + 1] = j;
+          val[q] = v;
+        }
+      }
+      pos += tot;
+      __syncthreads();
+    }
+  }
+}
+
 struct PartPtrs {
   const float* p[32];
 };
@@ -120,6 +224,28 @@ cudaError_t launch_decode_dense_f32(const float* c, const cms_hashes* h, int64_t
     ProfScope prof_scope("k_decode_dense", s);
     k_decode_dense<float><<<grid, 256, 0, s>>>(c, h->d_hs, h->n, static_cast<uint32_t>(h->b), h->d,
                                                n1, n3, out, ldo);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_threshold(const float* c, const cms_hashes* h, int64_t n1, int64_t n3, float tau,
+                                    int skip_diagonal, int64_t* ij, float* val, int64_t capacity,
+                                    int64_t* count, int64_t* rowcnt, cudaStream_t s) {
+  if (n1 == 0 || n3 == 0) return cudaMemsetAsync(count, 0, sizeof(int64_t), s);
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>(n1, 65535));
+  const uint32_t b = static_cast<uint32_t>(h->b);
+  {
+    ProfScope prof_scope("k_thresh_count", s);
+    k_thresh_count<<<grid, 256, 0, s>>>(c, h->d_hs, h->n, b, h->d, n1, n3, tau, skip_diagonal, rowcnt);
+  }
+  {
+    ProfScope prof_scope("k_thresh_scan", s);
+    k_thresh_scan<<<1, 1024, 0, s>>>(rowcnt, n1, count);
+  }
+  {
+    ProfScope prof_scope("k_thresh_write", s);
+    k_thresh_write<<<grid, 256, 0, s>>>(c, h->d_hs, h->n, b, h->d, n1, n3, tau, skip_diagonal, rowcnt,
+                                        capacity, ij, val);
   }
   return cudaGetLastError();
 }
