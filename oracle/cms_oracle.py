@@ -48,6 +48,10 @@ What each function follows:
   sketch of AB with its diagonal's contribution removed, and the entries
   whose estimate exceeds a threshold.
 
+* ``draw_sign4_coefficients`` / ``sign4`` / ``ams_frobenius`` /
+  ``frobenius_bound`` - Sec. 5.2: AMS sketches X = (s1^T A)(B s2) of AB
+  with 4-wise independent signs and the bound 32 median X^2 on ||AB||_F^2.
+
 Every function here is pinned by tests under ``-m "not gpu"`` against facts
 that do not come from this module (published splitmix64 outputs, hand-worked
 hash values, the three independent sketch routes, the injective-hash and b=1
@@ -401,3 +405,56 @@ def candidates(c: np.ndarray, tab: Tables, n1: int, n3: int, tau: float,
     if skip_diagonal:
         keep &= ii != jj
     return np.stack([ii[keep], jj[keep]], axis=1).astype(np.int64)
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.2: an upper bound on ||AB||_F / sqrt(b) from AMS sketches of AB.
+# X = sum_ij s1(i) s2(j) (AB)_ij = (s1^T A)(B s2) (Sec. 2.1: the AMS sketch
+# of AB is the sum of those of its outer products); with 4-wise independent
+# s1, s2, X^2 is an unbiased estimate of ||AB||_F^2 with variance at most
+# 8 E[X^2]^2, so 32 times the median of d values of X^2 bounds ||AB||_F^2
+# from above with high probability.  The 4-wise independent signs are
+# degree-3 polynomials over Z_p, p = 2^31 - 1, reduced mod 2 (the same
+# mapping to {+1, -1} as the 2-wise signs; the paper names no family).
+# --------------------------------------------------------------------------
+def draw_sign4_coefficients(seed: int, d: int) -> np.ndarray:
+    """Coefficients (a0, a1, a2, a3) of s1 and s2 for each repetition t, drawn
+    with splitmix64 in the order t, function (s1, s2), a0..a3, each r mod p.
+    Shape (d, 2, 4), int64."""
+    out = np.zeros((d, 2, 4), dtype=np.int64)
+    state = seed & _MASK64
+    for t in range(d):
+        for f in range(2):
+            for q in range(4):
+                state, r = splitmix64(state)
+                out[t, f, q] = r % P31
+    return out
+
+
+def sign4(coef: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """1 - 2 (((a3 x^3 + a2 x^2 + a1 x + a0) mod p) mod 2) for 0-based x,
+    with Python integers (exact)."""
+    a0, a1, a2, a3 = (int(v) for v in coef)
+    out = np.empty(len(x), dtype=np.int64)
+    for q, xv in enumerate(np.asarray(x, dtype=np.int64).tolist()):
+        v = (((a3 * xv + a2) * xv + a1) * xv + a0) % P31
+        out[q] = 1 - 2 * (v % 2)
+    return out
+
+
+def ams_frobenius(A: np.ndarray, B: np.ndarray, seed: int, d: int) -> np.ndarray:
+    """X_t = (s1_t^T A)(B s2_t) for t = 0..d-1, float64."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    coef = draw_sign4_coefficients(seed, d)
+    X = np.empty(d, dtype=np.float64)
+    for t in range(d):
+        s1 = sign4(coef[t, 0], np.arange(A.shape[0]))
+        s2 = sign4(coef[t, 1], np.arange(B.shape[1]))
+        X[t] = (s1 @ A) @ (B @ s2)
+    return X
+
+
+def frobenius_bound(X: np.ndarray) -> float:
+    """32 times the median of the X_t^2: a bound on ||AB||_F^2 (Sec. 5.2)."""
+    return 32.0 * float(median(np.asarray(X, dtype=np.float64) ** 2))

@@ -159,3 +159,27 @@ def test_mutation_candidates_without_absolute_value(monkeypatch):
         return full[est > tau]
     monkeypatch.setattr(O, "candidates", bad)
     assert _fails(lambda: pins.test_candidates_with_injective_hashes_are_the_large_entries(True))
+
+
+def test_mutation_sign4_without_cubic_term(monkeypatch):
+    def bad(coef, x):
+        a0, a1, a2, _ = (int(v) for v in coef)
+        return np.array([1 - 2 * (((a2 * xv + a1) * xv + a0) % ((1 << 31) - 1) % 2)
+                         for xv in np.asarray(x).tolist()], dtype=np.int64)
+    monkeypatch.setattr(O, "sign4", bad)
+    assert _fails(pins.test_sign4_hand_worked_values)
+
+
+def test_mutation_ams_with_one_sign_vector_for_both_sides(monkeypatch):
+    def bad(A, B, seed, d):
+        A = np.asarray(A, dtype=np.float64)
+        B = np.asarray(B, dtype=np.float64)
+        coef = O.draw_sign4_coefficients(seed, d)
+        X = np.empty(d)
+        for t in range(d):
+            s1 = O.sign4(coef[t, 0], np.arange(A.shape[0]))
+            s2 = O.sign4(coef[t, 0], np.arange(B.shape[1]))
+            X[t] = (s1 @ A) @ (B @ s2)
+        return X
+    monkeypatch.setattr(O, "ams_frobenius", bad)
+    assert _fails(pins.test_ams_estimate_is_the_signed_sum_of_ab)

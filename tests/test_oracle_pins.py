@@ -341,3 +341,69 @@ def test_candidates_with_injective_hashes_are_the_large_entries(skip):
     want = [(i, j) for i in range(n1) for j in range(n3) if abs(AB[i, j]) > tau and (i != j or not skip)]
     got = [tuple(p) for p in O.candidates(c, tab, n1, n3, tau, skip_diagonal=skip)]
     assert got == want
+
+
+# ------------------------------------------------ Sec. 5.2 (AMS, 4-wise) ----
+def test_sign4_hand_worked_values():
+    # a0..a3 = 5, 3, 2, 7: x = 0 -> 5 (odd, -1); x = 1 -> 17 (odd, -1);
+    # x = 2 -> 5 + 6 + 8 + 56 = 75 (odd, -1); x = 3 -> 5 + 9 + 18 + 189 = 221 (odd);
+    # x = 4 -> 5 + 12 + 32 + 448 = 497 (odd); x = 5 -> 5 + 15 + 50 + 875 = 945 (odd)
+    coef = np.array([5, 3, 2, 7])
+    assert O.sign4(coef, np.arange(6)).tolist() == [-1] * 6
+    # a3 x^3 wraps the modulus: x = 2^11, a3 = 1: 2^33 mod (2^31 - 1) = 4 (even, +1)
+    assert O.sign4(np.array([0, 0, 0, 1]), np.array([1 << 11])).tolist() == [1]
+    # x = 2^11 with a1 = 1 only: 2048 (even, +1); a0 = p - 1 (even): +1; a0 = p - 2: -1
+    assert O.sign4(np.array([0, 1, 0, 0]), np.array([1 << 11])).tolist() == [1]
+    assert O.sign4(np.array([(1 << 31) - 2, 0, 0, 0]), np.array([9])).tolist() == [1]
+    assert O.sign4(np.array([(1 << 31) - 3, 0, 0, 0]), np.array([9])).tolist() == [-1]
+
+
+def test_sign4_coefficients_in_range_and_ordered():
+    coef = O.draw_sign4_coefficients(123, 3)
+    assert coef.shape == (3, 2, 4)
+    assert coef.min() >= 0 and coef.max() < (1 << 31) - 1
+    state = 123
+    flat = []
+    for _ in range(24):
+        state, r = O.splitmix64(state)
+        flat.append(r % ((1 << 31) - 1))
+    assert coef.reshape(-1).tolist() == flat
+
+
+def test_ams_estimate_is_the_signed_sum_of_ab():
+    A = W.gaussian(9, 4, 71)
+    B = W.gaussian(4, 7, 72)
+    X = O.ams_frobenius(A, B, 73, 3)
+    coef = O.draw_sign4_coefficients(73, 3)
+    AB = A @ B
+    for t in range(3):
+        s1 = O.sign4(coef[t, 0], np.arange(9))
+        s2 = O.sign4(coef[t, 1], np.arange(7))
+        want = sum(s1[i] * s2[j] * AB[i, j] for i in range(9) for j in range(7))
+        assert abs(X[t] - want) < 1e-10
+
+
+def test_ams_square_unbiased_and_variance_bound():
+    # Sec. 5.2: E[X^2] = ||AB||_F^2, Var[X^2] <= 8 E[X^2]^2 (4-wise signs)
+    A = W.gaussian(12, 5, 74)
+    B = W.gaussian(5, 10, 75)
+    fro2 = float(np.sum((A @ B) ** 2))
+    X = O.ams_frobenius(A, B, 76, 4000)
+    sq = X ** 2
+    se = np.sqrt(8.0) * fro2 / np.sqrt(len(sq))      # the standard error the bound allows
+    assert abs(sq.mean() - fro2) < 4 * se
+    assert sq.var() <= 8 * fro2 ** 2 * 1.3
+    # and the bound of 32 medians is above ||AB||_F^2 for most seeds
+    ok = sum(O.frobenius_bound(O.ams_frobenius(A, B, 1000 + q, 9)) >= fro2 for q in range(60))
+    assert ok >= 57
+
+
+def test_sign4_four_wise_products_vanish_on_average():
+    # for 4 distinct points the product of the signs has mean 0 over draws
+    xs = np.array([0, 1, 2, 3])
+    prods = []
+    for q in range(3000):
+        c = O.draw_sign4_coefficients(5000 + q, 1)[0, 0]
+        s = O.sign4(c, xs)
+        prods.append(int(np.prod(s)))
+    assert abs(np.mean(prods)) < 4 / np.sqrt(3000)
