@@ -372,6 +372,33 @@ CMS_API cms_status cms_decode_threshold(const float* c, const cms_hashes* h, int
                                         void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * cms_frobenius_workspace_size / cms_frobenius_estimate - Sec. 5.2: an upper
+ * bound on ||AB||_F^2 (hence on the sketch's error scale ||AB||_F / sqrt(b))
+ * from d AMS sketches of AB,
+ *   X_t = sum_ij s1_t(i) s2_t(j) (AB)_ij = sum_k (s1_t . a_k)(b_k . s2_t),
+ * with 4-wise independent signs s(x) = 1 - 2 (((a3 x^3 + a2 x^2 + a1 x + a0)
+ * mod p) mod 2), p = 2^31 - 1, whose coefficients are drawn by splitmix64
+ * from `seed` (order: t, then s1 and s2, then a0..a3; each r mod p).  X_t^2
+ * estimates ||AB||_F^2 without bias; the bound is 32 times the median of the
+ * X_t^2 (even d: mean of the two middle ones).  One pass over A and B;
+ * sums in FP64.
+ *   A, lda, B, ldb, n1, n2, n3, dt : as cms_sketch_product.
+ *   est_out   : device double [d], the X_t.
+ *   bound_out : device double [1], 32 median X_t^2.
+ *   ws        : device scratch of cms_frobenius_workspace_size bytes,
+ *               256-byte aligned.
+ * Errors: CMS_ERR_INVALID_ARG (sizes, d outside [1, 64], NULL pointers),
+ * CMS_ERR_WORKSPACE.
+ */
+CMS_API cms_status cms_frobenius_workspace_size(int64_t n1, int64_t n2, int64_t n3, int32_t d,
+                                                size_t* bytes);
+CMS_API cms_status cms_frobenius_estimate(const void* A, int64_t lda, const void* B, int64_t ldb,
+                                          int64_t n1, int64_t n2, int64_t n3, int32_t dt,
+                                          uint64_t seed, int32_t d, double* est_out,
+                                          double* bound_out, void* ws, size_t ws_bytes,
+                                          void* stream);
+
+/*
  * cms_merge - c_out[t][z] = sum over the `count` partial sketches (device
  * float [d][b] each, pointers in a host array) in index order.  The sketch
  * is linear in the outer products of eq. (1) (Sec. 2.2), so sketches of

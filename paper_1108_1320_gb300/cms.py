@@ -47,6 +47,9 @@ SIGNATURES = {
     "cms_sparse_workspace_size": (_I32, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
     "cms_sketch_product_csr": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _P, _P, _SZ,
                                       _P]),
+    "cms_frobenius_workspace_size": (_I32, [_I64, _I64, _I64, _I32, ctypes.POINTER(_SZ)]),
+    "cms_frobenius_estimate": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, ctypes.c_uint64, _I32, _P, _P,
+                                      _P, _SZ, _P]),
     "cms_sketch_remove_diagonal": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P]),
     "cms_decode_threshold": (_I32, [_P, _P, _I64, _I64, ctypes.c_float, _I32, _P, _P, _I64, _P, _P, _SZ, _P]),
     "cms_sketch_product_csr_hybrid": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _I64, _P, _P,
@@ -430,6 +433,21 @@ def decode_threshold(c: torch.Tensor, h: Hashes, n1: int, n3: int, tau: float, s
     q = int(cnt.item())
     k = min(q, capacity)
     return ij[:k], val[:k], q
+
+
+def frobenius_estimate(A: torch.Tensor, B: torch.Tensor, seed: int, d: int, stream=None):
+    """Sec. 5.2: (X float64 (d,), bound) with X_t the AMS sketches of AB under
+    4-wise independent signs and bound = 32 median X_t^2 >= ||AB||_F^2 (whp)."""
+    n1, n2, n3, lda, ldb = _ab_args(A, B)
+    need = _SZ()
+    _check(lib().cms_frobenius_workspace_size(n1, n2, n3, d, ctypes.byref(need)))
+    ws = alloc_workspace(need.value, A.device)
+    est = torch.empty(d, dtype=torch.float64, device=A.device)
+    bound = torch.empty(1, dtype=torch.float64, device=A.device)
+    _check(lib().cms_frobenius_estimate(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype],
+                                        seed & ((1 << 64) - 1), d, _ptr(est), _ptr(bound), _ptr(ws),
+                                        ws.numel() * ws.element_size(), _stream(stream)))
+    return est, float(bound.item())
 
 
 def merge(parts: list[torch.Tensor], out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -595,6 +595,32 @@ cms_status cms_decode_threshold(const float* c, const cms_hashes* h, int64_t n1,
   return CMS_OK;
 }
 
+cms_status cms_frobenius_workspace_size(int64_t n1, int64_t n2, int64_t n3, int32_t d, size_t* bytes) {
+  if (!bytes) return fail(CMS_ERR_INVALID_ARG, "bytes is NULL");
+  if (n1 < 0 || n2 < 0 || n3 < 0 || d < 1 || d > kMaxD) return fail(CMS_ERR_INVALID_ARG, "bad sizes or d");
+  *bytes = frobenius_ws_bytes(n1, n2, n3, d);
+  return CMS_OK;
+}
+
+cms_status cms_frobenius_estimate(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
+                                  int64_t n3, int32_t dt, uint64_t seed, int32_t d, double* est_out,
+                                  double* bound_out, void* ws, size_t ws_bytes, void* stream) {
+  if (n1 < 0 || n2 < 0 || n3 < 0 || n1 >= (1LL << 31) || n3 >= (1LL << 31))
+    return fail(CMS_ERR_INVALID_ARG, "bad n1, n2 or n3");
+  if (d < 1 || d > kMaxD) return fail(CMS_ERR_INVALID_ARG, "d must be in [1, 64]");
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  if (n2 > 1 && (lda < n1 || ldb < n3)) return fail(CMS_ERR_INVALID_ARG, "lda < n1 or ldb < n3");
+  if (!est_out || !bound_out) return fail(CMS_ERR_INVALID_ARG, "est_out or bound_out is NULL");
+  if (n2 > 0 && ((n1 > 0 && !A) || (n3 > 0 && !B))) return fail(CMS_ERR_INVALID_ARG, "A or B is NULL");
+  if (!ws || ws_bytes < frobenius_ws_bytes(n1, n2, n3, d))
+    return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_frobenius_workspace_size()");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(CMS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaError_t e = launch_frobenius(A, lda, B, ldb, n1, n2, n3, dt, seed, d, est_out, bound_out,
+                                   static_cast<char*>(ws), static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_frobenius_estimate");
+  return CMS_OK;
+}
+
 cms_status cms_merge(const float* const* parts, int32_t count, int32_t d, int64_t b, float* c_out,
                      void* stream) {
   if (count < 0 || d < 1 || b < 1) return fail(CMS_ERR_INVALID_ARG, "bad count, d or b");

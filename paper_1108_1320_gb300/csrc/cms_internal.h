@@ -210,6 +210,10 @@ cudaError_t launch_decode_threshold(const float* c, const cms_hashes* h, int64_t
                                     int64_t* count, int64_t* rowcnt, cudaStream_t s);
 cudaError_t launch_remove_diagonal(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
                                    int64_t n3, int dt, const cms_hashes* h, float* c, cudaStream_t s);
+size_t frobenius_ws_bytes(int64_t n1, int64_t n2, int64_t n3, int d);
+cudaError_t launch_frobenius(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
+                             int64_t n3, int dt, uint64_t seed, int d, double* est, double* bound, char* ws,
+                             cudaStream_t s);
 cudaError_t launch_merge(const float* const* parts, int count, int64_t len,
                          float* out, cudaStream_t s);
 
