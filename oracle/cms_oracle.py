@@ -52,6 +52,9 @@ What each function follows:
   ``frobenius_bound`` - Sec. 5.2: AMS sketches X = (s1^T A)(B s2) of AB
   with 4-wise independent signs and the bound 32 median X^2 on ||AB||_F^2.
 
+* ``nnz_doubling`` - Sec. 5.1: the doubling search over b that stops when
+  at most b/5 buckets are nonzero for every repetition.
+
 Every function here is pinned by tests under ``-m "not gpu"`` against facts
 that do not come from this module (published splitmix64 outputs, hand-worked
 hash values, the three independent sketch routes, the injective-hash and b=1
@@ -458,3 +461,33 @@ def ams_frobenius(A: np.ndarray, B: np.ndarray, seed: int, d: int) -> np.ndarray
 def frobenius_bound(X: np.ndarray) -> float:
     """32 times the median of the X_t^2: a bound on ||AB||_F^2 (Sec. 5.2)."""
     return 32.0 * float(median(np.asarray(X, dtype=np.float64) ** 2))
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.1: the doubling search for the number of nonzero entries of AB.
+# Sketches of AB are taken with b = 2, 4, 8, ... until at most b/5 buckets
+# are nonzero for every one of the d splitting functions; random diagonal
+# scalings of A and B (Schwartz-Zippel) make a bucket zero only when every
+# entry of AB hashed to it is zero, so the test is on the bucket pattern of
+# the nonzero entries of AB.  The splitting functions of size b are those of
+# Fig. 1 drawn from `seed` (the same (a, c) for every b).
+# --------------------------------------------------------------------------
+def nnz_doubling(rows: np.ndarray, cols: np.ndarray, seed: int, d: int, b_max: int) -> tuple[int, int]:
+    """(b, distinct) for the nonzero entries (rows[q], cols[q]) of AB: the
+    first b = 2^r <= b_max at which every repetition has at most b/5 distinct
+    buckets (h1(i) + h2(j)) mod b, and the largest of those counts; (-1, 0)
+    when b_max is reached first."""
+    coef = draw_coefficients(seed, d)
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    b = 2
+    while b <= b_max:
+        worst = 0
+        for t in range(d):
+            z = (hash_bucket(coef[t, 0, 0], coef[t, 0, 1], rows, b) +
+                 hash_bucket(coef[t, 2, 0], coef[t, 2, 1], cols, b)) % b
+            worst = max(worst, len(np.unique(z)))
+        if 5 * worst <= b:
+            return b, worst
+        b *= 2
+    return -1, 0

@@ -183,3 +183,18 @@ def test_mutation_ams_with_one_sign_vector_for_both_sides(monkeypatch):
         return X
     monkeypatch.setattr(O, "ams_frobenius", bad)
     assert _fails(pins.test_ams_estimate_is_the_signed_sum_of_ab)
+
+
+def test_mutation_doubling_with_row_hash_only(monkeypatch):
+    def bad(rows, cols, seed, d, b_max):
+        coef = O.draw_coefficients(seed, d)
+        rows = np.asarray(rows, dtype=np.int64)
+        b = 2
+        while b <= b_max:
+            worst = max(len(np.unique(O.hash_bucket(coef[t, 0, 0], coef[t, 0, 1], rows, b))) for t in range(d))
+            if 5 * worst <= b:
+                return b, worst
+            b *= 2
+        return -1, 0
+    monkeypatch.setattr(O, "nnz_doubling", bad)
+    assert _fails(pins.test_nnz_doubling_stops_at_the_first_b_with_a_fifth_occupied)

@@ -407,3 +407,43 @@ def test_sign4_four_wise_products_vanish_on_average():
         s = O.sign4(c, xs)
         prods.append(int(np.prod(s)))
     assert abs(np.mean(prods)) < 4 / np.sqrt(3000)
+
+
+# ------------------------------------------- Sec. 5.1 (doubling search) ----
+def _distinct_buckets(rows, cols, seed, d, b):
+    coef = O.draw_coefficients(seed, d)
+    out = []
+    for t in range(d):
+        h1 = [((int(coef[t, 0, 0]) * int(i) + int(coef[t, 0, 1])) % ((1 << 31) - 1)) % b for i in rows]
+        h2 = [((int(coef[t, 2, 0]) * int(j) + int(coef[t, 2, 1])) % ((1 << 31) - 1)) % b for j in cols]
+        out.append(len({(x + y) % b for x, y in zip(h1, h2)}))
+    return out
+
+
+def test_nnz_doubling_stops_at_the_first_b_with_a_fifth_occupied():
+    # brute force with Python integers: the returned b is the first power of
+    # two whose every repetition occupies at most b/5 buckets
+    g = W.rng(101)
+    rows = g.integers(0, 500, 60)
+    cols = g.integers(0, 500, 60)
+    b, worst = O.nnz_doubling(rows, cols, 102, 4, 1 << 16)
+    assert b > 0
+    assert max(_distinct_buckets(rows, cols, 102, 4, b)) == worst and 5 * worst <= b
+    bb = 2
+    while bb < b:
+        assert 5 * max(_distinct_buckets(rows, cols, 102, 4, bb)) > bb
+        bb *= 2
+
+
+def test_nnz_doubling_is_a_five_approximation():
+    # the search ends by the time b/5 reaches the number of nonzeros, so
+    # b <= 10 nnz; and (whp, Sec. 5.1) b is at least the number of nonzeros
+    g = W.rng(103)
+    ok = 0
+    for q in range(40):
+        nnz = int(g.integers(20, 400))
+        flat = g.choice(1000 * 1000, nnz, replace=False)
+        b, worst = O.nnz_doubling(flat // 1000, flat % 1000, 200 + q, 5, 1 << 20)
+        assert 0 < b <= 10 * nnz and worst <= nnz
+        ok += b >= nnz
+    assert ok >= 36
