@@ -399,6 +399,32 @@ CMS_API cms_status cms_frobenius_estimate(const void* A, int64_t lda, const void
                                           void* stream);
 
 /*
+ * cms_nnz_workspace_size / cms_nnz_estimate - Sec. 5.1: the doubling search
+ * for the number of nonzero entries of AB (sparse A by columns, B by rows,
+ * as cms_sketch_product_csr).  For b = 2, 4, 8, ... up to b_max it sketches
+ * (D1 A)(B D2), D1 and D2 random diagonal scalings in [1, 2) (so that, by
+ * the Schwartz-Zippel lemma, a bucket sums to zero only when every entry of
+ * AB hashed to it is zero), with the d splitting and sign functions of
+ * Fig. 1 drawn from `seed` (as cms_make_hashes; range b), every term added
+ * in FP64; a bucket counts as zero when |sum| <= 1e-9 (sum of |terms|).  It
+ * stops at the first b where every repetition has at most b/5 nonzero
+ * buckets: then b bounds the number of nonzeros from above with
+ * probability 1 - (3/4)^d, and b <= 10 nnz(AB).
+ *   b_out       : host int64, that b, or -1 when b_max was passed first.
+ *   buckets_out : host int64, the largest count of nonzero buckets at b.
+ *   ws          : device scratch of cms_nnz_workspace_size(d, b_max) bytes.
+ * The call waits for the stream once per doubling step.
+ * Errors: CMS_ERR_INVALID_ARG (sizes, d outside [1, 64], b_max outside
+ * [2, 2^30], NULL pointers), CMS_ERR_WORKSPACE.
+ */
+CMS_API cms_status cms_nnz_workspace_size(int32_t d, int64_t b_max, size_t* bytes);
+CMS_API cms_status cms_nnz_estimate(const int64_t* a_colptr, const int32_t* a_rowidx, const void* a_val,
+                                    const int64_t* b_rowptr, const int32_t* b_colidx, const void* b_val,
+                                    int64_t n1, int64_t n2, int64_t n3, int32_t dt, uint64_t seed,
+                                    int32_t d, int64_t b_max, int64_t* b_out, int64_t* buckets_out,
+                                    void* ws, size_t ws_bytes, void* stream);
+
+/*
  * cms_merge - c_out[t][z] = sum over the `count` partial sketches (device
  * float [d][b] each, pointers in a host array) in index order.  The sketch
  * is linear in the outer products of eq. (1) (Sec. 2.2), so sketches of

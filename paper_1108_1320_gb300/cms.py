@@ -50,6 +50,9 @@ SIGNATURES = {
     "cms_frobenius_workspace_size": (_I32, [_I64, _I64, _I64, _I32, ctypes.POINTER(_SZ)]),
     "cms_frobenius_estimate": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, ctypes.c_uint64, _I32, _P, _P,
                                       _P, _SZ, _P]),
+    "cms_nnz_workspace_size": (_I32, [_I32, _I64, ctypes.POINTER(_SZ)]),
+    "cms_nnz_estimate": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, ctypes.c_uint64, _I32, _I64,
+                                ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P, _SZ, _P]),
     "cms_sketch_remove_diagonal": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P]),
     "cms_decode_threshold": (_I32, [_P, _P, _I64, _I64, ctypes.c_float, _I32, _P, _P, _I64, _P, _P, _SZ, _P]),
     "cms_sketch_product_csr_hybrid": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _I64, _P, _P,
@@ -433,6 +436,25 @@ def decode_threshold(c: torch.Tensor, h: Hashes, n1: int, n3: int, tau: float, s
     q = int(cnt.item())
     k = min(q, capacity)
     return ij[:k], val[:k], q
+
+
+def nnz_estimate(a_colptr: torch.Tensor, a_rowidx: torch.Tensor, a_val: torch.Tensor,
+                 b_rowptr: torch.Tensor, b_colidx: torch.Tensor, b_val: torch.Tensor, n1: int, n3: int,
+                 seed: int, d: int, b_max: int = 1 << 24, stream=None):
+    """Sec. 5.1 doubling search: (b, buckets) with b the first power of two at
+    which every repetition has at most b/5 nonzero buckets (-1 if b_max was
+    passed), buckets the largest such count."""
+    n2 = a_colptr.numel() - 1
+    need = _SZ()
+    _check(lib().cms_nnz_workspace_size(d, b_max, ctypes.byref(need)))
+    ws = alloc_workspace(need.value, a_colptr.device)
+    b_out = _I64()
+    k_out = _I64()
+    _check(lib().cms_nnz_estimate(_ptr(a_colptr), _ptr(a_rowidx), _ptr(a_val), _ptr(b_rowptr), _ptr(b_colidx),
+                                  _ptr(b_val), n1, n2, n3, _DTYPES[a_val.dtype], seed & ((1 << 64) - 1), d, b_max,
+                                  ctypes.byref(b_out), ctypes.byref(k_out), _ptr(ws), ws.numel() * ws.element_size(),
+                                  _stream(stream)))
+    return b_out.value, k_out.value
 
 
 def frobenius_estimate(A: torch.Tensor, B: torch.Tensor, seed: int, d: int, stream=None):

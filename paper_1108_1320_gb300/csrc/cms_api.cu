@@ -621,6 +621,35 @@ cms_status cms_frobenius_estimate(const void* A, int64_t lda, const void* B, int
   return CMS_OK;
 }
 
+cms_status cms_nnz_workspace_size(int32_t d, int64_t b_max, size_t* bytes) {
+  if (!bytes) return fail(CMS_ERR_INVALID_ARG, "bytes is NULL");
+  if (d < 1 || d > kMaxD || b_max < 2 || b_max > (1LL << 30)) return fail(CMS_ERR_INVALID_ARG, "bad d or b_max");
+  *bytes = nnz_ws_bytes(d, b_max);
+  return CMS_OK;
+}
+
+cms_status cms_nnz_estimate(const int64_t* a_colptr, const int32_t* a_rowidx, const void* a_val,
+                            const int64_t* b_rowptr, const int32_t* b_colidx, const void* b_val, int64_t n1,
+                            int64_t n2, int64_t n3, int32_t dt, uint64_t seed, int32_t d, int64_t b_max,
+                            int64_t* b_out, int64_t* buckets_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!b_out || !buckets_out) return fail(CMS_ERR_INVALID_ARG, "b_out or buckets_out is NULL");
+  if (n1 < 0 || n2 < 0 || n3 < 0 || n1 >= (1LL << 31) || n3 >= (1LL << 31) || n2 >= (1LL << 31) - 1)
+    return fail(CMS_ERR_INVALID_ARG, "bad n1, n2 or n3");
+  if (d < 1 || d > kMaxD || b_max < 2 || b_max > (1LL << 30)) return fail(CMS_ERR_INVALID_ARG, "bad d or b_max");
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  if (n2 > 0 && (!a_colptr || !b_rowptr)) return fail(CMS_ERR_INVALID_ARG, "pointer array is NULL");
+  if (!ws || ws_bytes < nnz_ws_bytes(d, b_max))
+    return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_nnz_workspace_size()");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(CMS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  Coeffs co;
+  draw_coeffs(seed, d, &co);
+  SparseArgsHost in{a_colptr, a_rowidx, a_val, b_rowptr, b_colidx, b_val, static_cast<int>(n1), static_cast<int>(n3)};
+  cudaError_t e = run_nnz_doubling(in, dt, n2, co, seed, d, b_max, static_cast<char*>(ws), b_out, buckets_out,
+                                   static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_nnz_estimate");
+  return CMS_OK;
+}
+
 cms_status cms_merge(const float* const* parts, int32_t count, int32_t d, int64_t b, float* c_out,
                      void* stream) {
   if (count < 0 || d < 1 || b < 1) return fail(CMS_ERR_INVALID_ARG, "bad count, d or b");

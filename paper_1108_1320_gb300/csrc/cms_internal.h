@@ -211,6 +211,9 @@ cudaError_t launch_decode_threshold(const float* c, const cms_hashes* h, int64_t
 cudaError_t launch_remove_diagonal(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
                                    int64_t n3, int dt, const cms_hashes* h, float* c, cudaStream_t s);
 size_t frobenius_ws_bytes(int64_t n1, int64_t n2, int64_t n3, int d);
+size_t nnz_ws_bytes(int d, int64_t b_max);
+cudaError_t run_nnz_doubling(const SparseArgsHost& in, int dt, int64_t n2, const Coeffs& co, uint64_t seed,
+                             int d, int64_t b_max, char* ws, int64_t* b_out, int64_t* worst_out, cudaStream_t s);
 cudaError_t launch_frobenius(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
                              int64_t n3, int dt, uint64_t seed, int d, double* est, double* bound, char* ws,
                              cudaStream_t s);

@@ -115,6 +115,77 @@ __global__ void k_ams_bound(const double* __restrict__ est, int d, double* __res
 
 size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+// ---------------------------------------------------------------------------
+// Sec. 5.1: one step of the doubling search for the number of nonzeros of AB.
+// The sketch of (D1 A)(B D2) with random diagonal scalings D1, D2 (values in
+// [1, 2) from two splitmix64 streams indexed by i and j), so that a bucket
+// sum vanishes (whp, Schwartz-Zippel) only when every entry of AB hashed to
+// it is zero.  Every term s1(i) s2(j) D1_i D2_j A_ik B_kj of every nonempty
+// inner index is added to its bucket in FP64, its magnitude to a second
+// accumulator; a bucket counts as zero when |sum| <= 1e-9 (sum of |terms|)
+// (exact cancellation inside an entry of AB leaves only FP64 rounding).
+// Splitting and sign functions: those of Fig. 1 drawn from the seed, with
+// range b.
+__device__ __forceinline__ double unit_scale(uint64_t stream, uint64_t idx) {
+  uint64_t z = stream + (idx + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return 1.0 + static_cast<double>(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_nnz_scatter(const int64_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const T* __restrict__ a_val,
+              const int64_t* __restrict__ b_ptr, const int32_t* __restrict__ b_idx, const T* __restrict__ b_val,
+              int n1, int n3, int64_t n2, Coeffs co, int d, uint32_t b, uint64_t seed, double* __restrict__ cd,
+              double* __restrict__ ca) {
+  for (int64_t k = blockIdx.x; k < n2; k += gridDim.x) {
+    const int64_t a0 = a_ptr[k], na = a_ptr[k + 1] - a0;
+    const int64_t b0 = b_ptr[k], nb = b_ptr[k + 1] - b0;
+    if (na <= 0 || nb <= 0) continue;
+    for (int64_t pr = threadIdx.x; pr < na * nb; pr += blockDim.x) {
+      const int64_t ia = a0 + pr / nb, jb = b0 + pr % nb;
+      const int i = a_idx[ia], j = b_idx[jb];
+      if (i < 0 || i >= n1 || j < 0 || j >= n3) continue;
+      const double v = unit_scale(seed ^ 0xA5A5A5A5A5A5A5A5ULL, static_cast<uint64_t>(i)) *
+                       unit_scale(seed ^ 0x5A5A5A5A5A5A5A5AULL, static_cast<uint64_t>(j)) *
+                       to_f64e(a_val[ia]) * to_f64e(b_val[jb]);
+      for (int t = 0; t < d; ++t) {
+        const uint32_t* c = co.v[t];
+        const uint32_t h1 = poly_p31(c[0], c[1], static_cast<uint32_t>(i)) % b;
+        const uint32_t g1 = poly_p31(c[2], c[3], static_cast<uint32_t>(i)) & 1u;
+        const uint32_t h2 = poly_p31(c[4], c[5], static_cast<uint32_t>(j)) % b;
+        const uint32_t g2 = poly_p31(c[6], c[7], static_cast<uint32_t>(j)) & 1u;
+        uint32_t z = h1 + h2;
+        if (z >= b) z -= b;
+        atomicAdd(&cd[static_cast<size_t>(t) * b + z], (g1 ^ g2) ? -v : v);
+        atomicAdd(&ca[static_cast<size_t>(t) * b + z], fabs(v));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_nnz_count(const double* __restrict__ cd, const double* __restrict__ ca, uint32_t b,
+            unsigned long long* __restrict__ cnt) {
+  __shared__ unsigned int part[8];
+  const int t = blockIdx.y;
+  unsigned int c = 0;
+  for (uint32_t z = blockIdx.x * blockDim.x + threadIdx.x; z < b; z += gridDim.x * blockDim.x) {
+    const double s = cd[static_cast<size_t>(t) * b + z], m = ca[static_cast<size_t>(t) * b + z];
+    c += (m > 0.0 && fabs(s) > 1e-9 * m) ? 1u : 0u;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long sum = 0;
+    for (int w = 0; w < 8; ++w) sum += part[w];
+    atomicAdd(&cnt[t], sum);
+  }
+}
+
 }  // namespace
 
 size_t frobenius_ws_bytes(int64_t n1, int64_t n2, int64_t n3, int d) {
@@ -166,6 +237,66 @@ cudaError_t launch_frobenius(const void* A, int64_t lda, const void* B, int64_t 
     k_ams_bound<<<1, 1, 0, s>>>(est, d, bound);
   }
   return cudaGetLastError();
+}
+
+size_t nnz_ws_bytes(int d, int64_t b_max) {
+  return 2 * al256(static_cast<size_t>(d) * b_max * 8) + 256;
+}
+
+cudaError_t run_nnz_doubling(const SparseArgsHost& in, int dt, int64_t n2, const Coeffs& co, uint64_t seed, int d,
+                             int64_t b_max, char* ws, int64_t* b_out, int64_t* worst_out, cudaStream_t s) {
+  double* cd = reinterpret_cast<double*>(ws);
+  double* ca = reinterpret_cast<double*>(ws + al256(static_cast<size_t>(d) * b_max * 8));
+  unsigned long long* cnt =
+      reinterpret_cast<unsigned long long*>(ws + 2 * al256(static_cast<size_t>(d) * b_max * 8));
+  *b_out = -1;
+  *worst_out = 0;
+  unsigned long long host[kMaxD];
+  const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(n2, 65535)));
+  for (int64_t b = 2; b <= b_max; b *= 2) {
+    const size_t bytes = static_cast<size_t>(d) * b * 8;
+    cudaError_t e = cudaMemsetAsync(cd, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ca, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, static_cast<size_t>(d) * 8, s);
+    if (e != cudaSuccess) return e;
+    if (n2 > 0) {
+      ProfScope prof_scope("k_nnz_scatter", s);
+      const uint32_t bb = static_cast<uint32_t>(b);
+      switch (dt) {
+        case CMS_F32:
+          k_nnz_scatter<float><<<grid, 256, 0, s>>>(in.a_ptr, in.a_idx, static_cast<const float*>(in.a_val), in.b_ptr,
+                                                    in.b_idx, static_cast<const float*>(in.b_val), in.n1, in.n3, n2,
+                                                    co, d, bb, seed, cd, ca);
+          break;
+        case CMS_BF16:
+          k_nnz_scatter<__nv_bfloat16><<<grid, 256, 0, s>>>(
+              in.a_ptr, in.a_idx, static_cast<const __nv_bfloat16*>(in.a_val), in.b_ptr, in.b_idx,
+              static_cast<const __nv_bfloat16*>(in.b_val), in.n1, in.n3, n2, co, d, bb, seed, cd, ca);
+          break;
+        default:
+          k_nnz_scatter<double><<<grid, 256, 0, s>>>(in.a_ptr, in.a_idx, static_cast<const double*>(in.a_val),
+                                                     in.b_ptr, in.b_idx, static_cast<const double*>(in.b_val), in.n1,
+                                                     in.n3, n2, co, d, bb, seed, cd, ca);
+          break;
+      }
+    }
+    {
+      ProfScope prof_scope("k_nnz_count", s);
+      dim3 g(static_cast<unsigned>(std::min<int64_t>((b + 255) / 256, 1024)), d);
+      k_nnz_count<<<g, 256, 0, s>>>(cd, ca, static_cast<uint32_t>(b), cnt);
+    }
+    e = cudaMemcpyAsync(host, cnt, static_cast<size_t>(d) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    int64_t worst = 0;
+    for (int t = 0; t < d; ++t) worst = std::max<int64_t>(worst, static_cast<int64_t>(host[t]));
+    if (5 * worst <= b) {
+      *b_out = b;
+      *worst_out = worst;
+      return cudaSuccess;
+    }
+  }
+  return cudaSuccess;
 }
 
 }  // namespace cms
