@@ -55,6 +55,11 @@ What each function follows:
 * ``nnz_doubling`` - Sec. 5.1: the doubling search over b that stops when
   at most b/5 buckets are nonzero for every repetition.
 
+* ``code_bits`` / ``decode_code`` / ``masked_sketches`` /
+  ``significant_from_sketches`` / ``find_significant`` - Sec. 4, Fig. 3
+  (FINDSIGNIFICANTENTRIES) with a balanced repetition code in place of the
+  expander code the paper leaves undefined.
+
 Every function here is pinned by tests under ``-m "not gpu"`` against facts
 that do not come from this module (published splitmix64 outputs, hand-worked
 hash values, the three independent sketch routes, the injective-hash and b=1
@@ -491,3 +496,91 @@ def nnz_doubling(rows: np.ndarray, cols: np.ndarray, seed: int, d: int, b_max: i
             return b, worst
         b *= 2
     return -1, 0
+
+
+# --------------------------------------------------------------------------
+# Sec. 4, Fig. 3: FINDSIGNIFICANTENTRIES.  2 l sketches with the same hash
+# functions of the masked products (I_{E_r} A) B (r < l) and A (B I_{E_r})
+# (r >= l), where E : [n] -> {0, 1}^l is an error-correcting code; for every
+# repetition t and bucket k the bits X_r > Delta/2 of X_r = |p^(t,r)[k]| are
+# decoded into a position (i, j); positions inserted for at least d/2 of
+# the (t, k) are returned.  The paper asks for an expander code and defines
+# none; here E is a balanced repetition code: for each of the L bits of x
+# (L = ceil(log2 max(n1, n3)), least significant first) rho copies of the
+# bit and rho copies of its complement, l = 2 rho L.  DECODE takes a
+# majority vote per bit (ties rejected) and rejects a string farther than
+# l/4 from the decoded codeword (so the all-zero string of an empty bucket
+# decodes to nothing).
+# --------------------------------------------------------------------------
+def code_length(n1: int, n3: int, rho: int) -> tuple[int, int]:
+    """(L, l): bits per index and code length."""
+    L = max(1, int(np.ceil(np.log2(max(n1, n3, 2)))))
+    return L, 2 * rho * L
+
+
+def code_bits(x: int, L: int, rho: int) -> np.ndarray:
+    """E(x) as a 0/1 array of length 2 rho L."""
+    out = np.zeros(2 * rho * L, dtype=np.int64)
+    for q in range(L):
+        bit = (int(x) >> q) & 1
+        out[q * 2 * rho: q * 2 * rho + rho] = bit
+        out[q * 2 * rho + rho: (q + 1) * 2 * rho] = 1 - bit
+    return out
+
+
+def decode_code(s: np.ndarray, L: int, rho: int) -> int:
+    """x with E(x) closest to s by per-bit majority, or -1 (a tie, or the
+    string farther than l/4 from E(x))."""
+    s = np.asarray(s, dtype=np.int64)
+    x = 0
+    dist = 0
+    for q in range(L):
+        seg = s[q * 2 * rho: (q + 1) * 2 * rho]
+        votes = int(seg[:rho].sum() + (rho - seg[rho:].sum()))
+        if 2 * votes == 2 * rho:
+            return -1
+        bit = 1 if votes > rho else 0
+        x |= bit << q
+        dist += (2 * rho - votes) if bit else votes
+    return x if 4 * dist <= 2 * rho * L else -1
+
+
+def masked_sketches(A: np.ndarray, B: np.ndarray, tab: Tables, rho: int) -> np.ndarray:
+    """The 2 l sketches of (3), shape (2 l, d, b), by the definition route."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    n1, n3 = A.shape[0], B.shape[1]
+    L, ell = code_length(n1, n3, rho)
+    Ei = np.stack([code_bits(i, L, rho) for i in range(n1)])      # (n1, l)
+    Ej = np.stack([code_bits(j, L, rho) for j in range(n3)])      # (n3, l)
+    out = np.empty((2 * ell, tab.d, tab.b))
+    for r in range(ell):
+        out[r] = sketch_definition(A * Ei[:, r:r + 1], B, tab)
+        out[ell + r] = sketch_definition(A, B * Ej[:, r][None, :], tab)
+    return out
+
+
+def significant_from_sketches(P: np.ndarray, n1: int, n3: int, delta: float, rho: int) -> np.ndarray:
+    """Fig. 3 on given sketches P (2 l, d, b): the positions inserted for at
+    least d/2 of the (t, k), sorted, shape (q, 2).  The bits X_r > Delta/2
+    are decided in float32 (the precision of the sketches)."""
+    L, ell = code_length(n1, n3, rho)
+    P32 = np.abs(np.asarray(P, dtype=np.float32))
+    _, d, b = P32.shape
+    counts: dict = {}
+    for t in range(d):
+        bits = (P32[:, t, :] > np.float32(delta) / np.float32(2)).astype(np.int64)   # (2 l, b)
+        for k in np.nonzero(bits.any(axis=0))[0]:
+            i = decode_code(bits[:ell, k], L, rho)
+            j = decode_code(bits[ell:, k], L, rho)
+            if 0 <= i < n1 and 0 <= j < n3:
+                counts[(i, j)] = counts.get((i, j), 0) + 1
+    keep = sorted(p for p, c in counts.items() if 2 * c >= d)
+    return np.array(keep, dtype=np.int64).reshape(-1, 2)
+
+
+def find_significant(A: np.ndarray, B: np.ndarray, tab: Tables, delta: float, rho: int) -> np.ndarray:
+    """FINDSIGNIFICANTENTRIES(Delta) of Fig. 3 from the masked sketches."""
+    A = np.asarray(A)
+    B = np.asarray(B)
+    return significant_from_sketches(masked_sketches(A, B, tab, rho), A.shape[0], B.shape[1], delta, rho)

@@ -198,3 +198,26 @@ def test_mutation_doubling_with_row_hash_only(monkeypatch):
         return -1, 0
     monkeypatch.setattr(O, "nnz_doubling", bad)
     assert _fails(pins.test_nnz_doubling_stops_at_the_first_b_with_a_fifth_occupied)
+
+
+def test_mutation_decode_without_distance_check(monkeypatch):
+    def bad(s, L, rho):
+        s = np.asarray(s, dtype=np.int64)
+        x = 0
+        for q in range(L):
+            seg = s[q * 2 * rho: (q + 1) * 2 * rho]
+            x |= (1 if seg[:rho].sum() >= (seg[rho:] == 0).sum() and seg[:rho].sum() > 0 else 0) << q
+        return x
+    monkeypatch.setattr(O, "decode_code", bad)
+    assert _fails(pins.test_code_round_trip_and_error_correction)
+
+
+def test_mutation_masks_swapped_between_sides(monkeypatch):
+    orig = O.masked_sketches
+
+    def bad(A, B, tab, rho):
+        P = orig(A, B, tab, rho)
+        ell = P.shape[0] // 2
+        return np.concatenate([P[ell:], P[:ell]])
+    monkeypatch.setattr(O, "masked_sketches", bad)
+    assert _fails(pins.test_find_significant_returns_the_planted_entries)

@@ -447,3 +447,47 @@ def test_nnz_doubling_is_a_five_approximation():
         assert 0 < b <= 10 * nnz and worst <= nnz
         ok += b >= nnz
     assert ok >= 36
+
+
+# ------------------------------------- Sec. 4 (FINDSIGNIFICANTENTRIES) -----
+def test_code_round_trip_and_error_correction():
+    L, rho = 7, 3
+    g = W.rng(130)
+    for x in [0, 1, 77, 127] + g.integers(0, 128, 20).tolist():
+        e = O.code_bits(x, L, rho)
+        assert len(e) == 2 * rho * L and e.sum() == rho * L
+        assert O.decode_code(e, L, rho) == x
+        # one flip in every bit's group of 2 rho is corrected (votes stay a majority)
+        f = e.copy()
+        for q in range(L):
+            f[q * 2 * rho + g.integers(0, 2 * rho)] ^= 1
+        assert O.decode_code(f, L, rho) == x
+    # an empty bucket (all bits 0) and an all-ones string decode to nothing
+    assert O.decode_code(np.zeros(2 * rho * L, dtype=np.int64), L, rho) == -1
+    assert O.decode_code(np.ones(2 * rho * L, dtype=np.int64), L, rho) == -1
+    # rho = 1: a flip makes a tie, which is rejected
+    e = O.code_bits(5, 3, 1)
+    e[0] ^= 1
+    assert O.decode_code(e, 3, 1) == -1
+
+
+def test_find_significant_returns_the_planted_entries():
+    # AB with a few large entries over small noise, b large enough that the
+    # large entries rarely share a bucket: the result is the set of entries
+    # above Delta, found by brute force
+    n1, n2, n3, b, d = 40, 6, 36, 8192, 5
+    g = W.rng(131)
+    A = 0.01 * g.standard_normal((n1, n2))
+    B = 0.01 * g.standard_normal((n2, n3))
+    big = [(3, 5), (17, 30), (39, 0), (21, 21)]
+    for q, (i, j) in enumerate(big):
+        A[i, q] += 10.0
+        B[q, j] += 10.0 + q
+    AB = A @ B
+    delta = 50.0
+    want = sorted((int(i), int(j)) for i, j in zip(*np.nonzero(np.abs(AB) > delta)))
+    assert len(want) >= len(big)
+    tab = O.make_tables(132, max(n1, n3), b, d)
+    for rho in (1, 2):
+        got = [tuple(p) for p in O.find_significant(A, B, tab, delta, rho)]
+        assert got == want
