@@ -425,6 +425,47 @@ CMS_API cms_status cms_nnz_estimate(const int64_t* a_colptr, const int32_t* a_ro
                                     void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * FINDSIGNIFICANTENTRIES (Sec. 4, Fig. 3).
+ *
+ * cms_find_significant - 2 l sketches of AB with the hashes h: for r < l of
+ * (I_{E_r} A) B (rows i of A kept when bit r of E(i) is 1), for r >= l of
+ * A (B I_{E_{r-l}}); for every repetition t and bucket k the bits
+ * |p^(t,r)[k]| > delta/2 are decoded into a position (i, j); positions
+ * decoded for at least d/2 of the (t, k) are returned.  E is a balanced
+ * repetition code (the paper's expander code is not defined there): for
+ * each of the L = ceil(log2 max(n1, n3)) bits of x, least significant
+ * first, rho copies of the bit then rho copies of its complement,
+ * l = 2 rho L; decoding is a majority vote per bit, a tie or a string
+ * farther than l/4 from the decoded codeword decodes to nothing.  Cost:
+ * 2 l sketch products.
+ *   A, lda, B, ldb, n1, n2, n3, dt : as cms_sketch_product (n1, n3 >= 1).
+ *   delta     : the magnitude threshold Delta (>= 0).
+ *   rho       : copies per bit, 1..8.
+ *   ij_out    : device int64 [capacity][2], the positions (in the order of
+ *               the device's atomic appends; sort for a canonical order).
+ *   count_out : device int64, the number of positions (may exceed capacity).
+ *   ws        : device scratch of cms_significant_workspace_size bytes,
+ *               256-byte aligned.
+ * cms_decode_significant - the decode and vote alone, on 2 l given
+ * sketches (device float [2 l][d][b], as above), with a scratch of
+ * cms_significant_decode_workspace_size bytes.
+ * Errors: CMS_ERR_INVALID_ARG, CMS_ERR_WORKSPACE, and those of
+ * cms_sketch_product.
+ */
+CMS_API cms_status cms_significant_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
+                                                  int32_t dt, int32_t rho, size_t* bytes);
+CMS_API cms_status cms_find_significant(const void* A, int64_t lda, const void* B, int64_t ldb,
+                                        int64_t n1, int64_t n2, int64_t n3, int32_t dt,
+                                        const cms_hashes* h, float delta, int32_t rho, int64_t* ij_out,
+                                        int64_t capacity, int64_t* count_out, void* ws, size_t ws_bytes,
+                                        void* stream);
+CMS_API cms_status cms_significant_decode_workspace_size(const cms_hashes* h, size_t* bytes);
+CMS_API cms_status cms_decode_significant(const float* sketches, const cms_hashes* h, int64_t n1,
+                                          int64_t n3, float delta, int32_t rho, int64_t* ij_out,
+                                          int64_t capacity, int64_t* count_out, void* ws,
+                                          size_t ws_bytes, void* stream);
+
+/*
  * cms_merge - c_out[t][z] = sum over the `count` partial sketches (device
  * float [d][b] each, pointers in a host array) in index order.  The sketch
  * is linear in the outer products of eq. (1) (Sec. 2.2), so sketches of

@@ -53,6 +53,11 @@ SIGNATURES = {
     "cms_nnz_workspace_size": (_I32, [_I32, _I64, ctypes.POINTER(_SZ)]),
     "cms_nnz_estimate": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, ctypes.c_uint64, _I32, _I64,
                                 ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P, _SZ, _P]),
+    "cms_significant_workspace_size": (_I32, [_P, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(_SZ)]),
+    "cms_find_significant": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, ctypes.c_float, _I32, _P, _I64,
+                                    _P, _P, _SZ, _P]),
+    "cms_significant_decode_workspace_size": (_I32, [_P, ctypes.POINTER(_SZ)]),
+    "cms_decode_significant": (_I32, [_P, _P, _I64, _I64, ctypes.c_float, _I32, _P, _I64, _P, _P, _SZ, _P]),
     "cms_sketch_remove_diagonal": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P]),
     "cms_decode_threshold": (_I32, [_P, _P, _I64, _I64, ctypes.c_float, _I32, _P, _P, _I64, _P, _P, _SZ, _P]),
     "cms_sketch_product_csr_hybrid": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _I64, _P, _P,
@@ -436,6 +441,45 @@ def decode_threshold(c: torch.Tensor, h: Hashes, n1: int, n3: int, tau: float, s
     q = int(cnt.item())
     k = min(q, capacity)
     return ij[:k], val[:k], q
+
+
+def _sorted_positions(ij: torch.Tensor, count: torch.Tensor, capacity: int):
+    q = int(count.item())
+    out = ij[:min(q, capacity)]
+    if out.shape[0] > 1:
+        order = torch.argsort(out[:, 0] * (int(out[:, 1].max()) + 1) + out[:, 1])
+        out = out[order]
+    return out, q
+
+
+def find_significant(A: torch.Tensor, B: torch.Tensor, h: Hashes, delta: float, rho: int = 1,
+                     capacity: int = 1 << 16, stream=None):
+    """FINDSIGNIFICANTENTRIES (Sec. 4, Fig. 3): positions (q, 2) int64, sorted
+    row-major, and their count (which may exceed capacity)."""
+    n1, n2, n3, lda, ldb = _ab_args(A, B)
+    need = _SZ()
+    _check(lib().cms_significant_workspace_size(h.handle, n1, n2, n3, _DTYPES[A.dtype], rho, ctypes.byref(need)))
+    ws = alloc_workspace(need.value, A.device)
+    ij = torch.empty((max(capacity, 1), 2), dtype=torch.int64, device=A.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=A.device)
+    _check(lib().cms_find_significant(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype], h.handle,
+                                      float(delta), rho, _ptr(ij), capacity, _ptr(cnt), _ptr(ws),
+                                      ws.numel() * ws.element_size(), _stream(stream)))
+    return _sorted_positions(ij, cnt, capacity)
+
+
+def decode_significant(sketches: torch.Tensor, h: Hashes, n1: int, n3: int, delta: float, rho: int = 1,
+                       capacity: int = 1 << 16, stream=None):
+    """Fig. 3's decode and vote on given sketches (float32 (2 l, d, b))."""
+    need = _SZ()
+    _check(lib().cms_significant_decode_workspace_size(h.handle, ctypes.byref(need)))
+    ws = alloc_workspace(need.value, sketches.device)
+    ij = torch.empty((max(capacity, 1), 2), dtype=torch.int64, device=sketches.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=sketches.device)
+    _check(lib().cms_decode_significant(_ptr(sketches.contiguous()), h.handle, n1, n3, float(delta), rho, _ptr(ij),
+                                        capacity, _ptr(cnt), _ptr(ws), ws.numel() * ws.element_size(),
+                                        _stream(stream)))
+    return _sorted_positions(ij, cnt, capacity)
 
 
 def nnz_estimate(a_colptr: torch.Tensor, a_rowidx: torch.Tensor, a_val: torch.Tensor,

@@ -650,6 +650,121 @@ cms_status cms_nnz_estimate(const int64_t* a_colptr, const int32_t* a_rowidx, co
   return CMS_OK;
 }
 
+namespace {
+// Workspace of cms_find_significant: the sketch path's scratch, one masked
+// operand, the 2 l sketches and the decode scratch.
+struct SigLayout {
+  size_t sk = 0, mask = 0, P = 0, dec = 0, total = 0;
+  int ell = 0;
+  int64_t ld0 = 0, ld1 = 0;
+};
+
+cms_status sig_layout(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int32_t dt, int32_t rho,
+                      SigLayout* L) {
+  auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+  size_t sk = 0;
+  cms_status st = cms_workspace_size(h, n1, n2, n3, dt, &sk);
+  if (st != CMS_OK) return st;
+  const size_t esz = dt == CMS_BF16 ? 2 : (dt == CMS_F64 ? 8 : 4);
+  L->ell = significant_code_length(n1, n3, rho, nullptr);
+  L->ld0 = std::max<int64_t>((n1 + 7) / 8 * 8, 8);
+  L->ld1 = std::max<int64_t>((n3 + 7) / 8 * 8, 8);
+  size_t o = 0;
+  L->sk = o;   o += al(sk);
+  L->mask = o; o += al(static_cast<size_t>(std::max(L->ld0, L->ld1)) * std::max<int64_t>(n2, 1) * esz);
+  L->P = o;    o += al(static_cast<size_t>(2 * L->ell) * h->d * h->b * sizeof(float));
+  L->dec = o;  o += al(significant_decode_ws_bytes(h->d, h->b));
+  L->total = o;
+  return CMS_OK;
+}
+}  // namespace
+
+cms_status cms_significant_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int32_t dt,
+                                          int32_t rho, size_t* bytes) {
+  if (!bytes) return fail(CMS_ERR_INVALID_ARG, "bytes is NULL");
+  if (rho < 1 || rho > 8) return fail(CMS_ERR_INVALID_ARG, "rho must be in [1, 8]");
+  SigLayout L;
+  cms_status st = sig_layout(h, n1, n2, n3, dt, rho, &L);
+  if (st != CMS_OK) return st;
+  *bytes = L.total;
+  return CMS_OK;
+}
+
+cms_status cms_decode_significant(const float* sketches, const cms_hashes* h, int64_t n1, int64_t n3, float delta,
+                                  int32_t rho, int64_t* ij_out, int64_t capacity, int64_t* count_out, void* ws,
+                                  size_t ws_bytes, void* stream) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  if (n1 < 1 || n3 < 1 || n1 > h->n || n3 > h->n) return fail(CMS_ERR_INVALID_ARG, "bad n1 or n3");
+  if (rho < 1 || rho > 8) return fail(CMS_ERR_INVALID_ARG, "rho must be in [1, 8]");
+  if (!(delta >= 0.f)) return fail(CMS_ERR_INVALID_ARG, "delta must be a number >= 0");
+  if (capacity < 0 || !sketches || !count_out || (capacity > 0 && !ij_out))
+    return fail(CMS_ERR_INVALID_ARG, "NULL pointer or capacity < 0");
+  if (!ws || ws_bytes < significant_decode_ws_bytes(h->d, h->b))
+    return fail(CMS_ERR_WORKSPACE, "workspace smaller than cms_significant_decode_workspace_size()");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(CMS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cms_status st = check_device(h);
+  if (st != CMS_OK) return st;
+  cudaError_t e = launch_decode_significant(sketches, h, n1, n3, delta, rho, ij_out, capacity, count_out,
+                                            static_cast<char*>(ws), static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cms_decode_significant");
+  return CMS_OK;
+}
+
+cms_status cms_significant_decode_workspace_size(const cms_hashes* h, size_t* bytes) {
+  if (!h || !bytes) return fail(CMS_ERR_INVALID_ARG, "NULL argument");
+  *bytes = significant_decode_ws_bytes(h->d, h->b);
+  return CMS_OK;
+}
+
+cms_status cms_find_significant(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
+                                int64_t n3, int32_t dt, const cms_hashes* h, float delta, int32_t rho,
+                                int64_t* ij_out, int64_t capacity, int64_t* count_out, void* ws, size_t ws_bytes,
+                                void* stream) {
+  cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
+  if (st != CMS_OK) return st;
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  if (n1 < 1 || n3 < 1) return fail(CMS_ERR_INVALID_ARG, "n1 and n3 must be >= 1");
+  if (rho < 1 || rho > 8) return fail(CMS_ERR_INVALID_ARG, "rho must be in [1, 8]");
+  if (!(delta >= 0.f)) return fail(CMS_ERR_INVALID_ARG, "delta must be a number >= 0");
+  if (capacity < 0 || !count_out || (capacity > 0 && !ij_out)) return fail(CMS_ERR_INVALID_ARG, "NULL pointer");
+  if (n2 > 0 && (!A || !B)) return fail(CMS_ERR_INVALID_ARG, "A or B is NULL");
+  st = check_device(h);
+  if (st != CMS_OK) return st;
+  SigLayout L;
+  st = sig_layout(h, n1, n2, n3, dt, rho, &L);
+  if (st != CMS_OK) return st;
+  if (!ws || ws_bytes < L.total)
+    return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_significant_workspace_size()");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(CMS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  DeviceProps dp = device_props(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  void* M = w + L.mask;
+  float* P = reinterpret_cast<float*>(w + L.P);
+  const size_t per = static_cast<size_t>(h->d) * h->b;
+  for (int r = 0; r < 2 * L.ell; ++r) {
+    const bool side1 = r >= L.ell;
+    const int rr = side1 ? r - L.ell : r;
+    const void* Ao = side1 ? A : M;
+    const void* Bo = side1 ? M : B;
+    const int64_t la = side1 ? lda : L.ld0;
+    const int64_t lb = side1 ? L.ld1 : ldb;
+    cudaError_t e = side1 ? launch_mask_copy(B, ldb, M, L.ld1, n3, n2, rr, rho, dt, s)
+                          : launch_mask_copy(A, lda, M, L.ld0, n1, n2, rr, rho, dt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cms_find_significant (mask)");
+    SketchPlan plan;
+    std::string why;
+    int rc = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &plan, &why, Ao, la, Bo, lb);
+    if (rc != CMS_OK) return fail(static_cast<cms_status>(rc), why);
+    if (plan.ws_bytes > L.mask - L.sk) return fail(CMS_ERR_WORKSPACE, "internal: sketch scratch too small");
+    e = launch_sketch(plan, h, Ao, la, Bo, lb, n1, n2, n3, dt, P + r * per, w + L.sk, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cms_find_significant (sketch)");
+  }
+  cudaError_t e = launch_decode_significant(P, h, n1, n3, delta, rho, ij_out, capacity, count_out, w + L.dec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cms_find_significant (decode)");
+  return CMS_OK;
+}
+
 cms_status cms_merge(const float* const* parts, int32_t count, int32_t d, int64_t b, float* c_out,
                      void* stream) {
   if (count < 0 || d < 1 || b < 1) return fail(CMS_ERR_INVALID_ARG, "bad count, d or b");

@@ -211,6 +211,13 @@ cudaError_t launch_decode_threshold(const float* c, const cms_hashes* h, int64_t
 cudaError_t launch_remove_diagonal(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
                                    int64_t n3, int dt, const cms_hashes* h, float* c, cudaStream_t s);
 size_t frobenius_ws_bytes(int64_t n1, int64_t n2, int64_t n3, int d);
+int significant_code_length(int64_t n1, int64_t n3, int rho, int* L);
+size_t significant_decode_ws_bytes(int d, int64_t b);
+cudaError_t launch_decode_significant(const float* P, const cms_hashes* h, int64_t n1, int64_t n3, float delta,
+                                      int rho, int64_t* ij, int64_t capacity, int64_t* count, char* ws,
+                                      cudaStream_t s);
+cudaError_t launch_mask_copy(const void* src, int64_t lds, void* dst, int64_t ldd, int64_t nx, int64_t n2, int r,
+                             int rho, int dt, cudaStream_t s);
 size_t nnz_ws_bytes(int d, int64_t b_max);
 cudaError_t run_nnz_doubling(const SparseArgsHost& in, int dt, int64_t n2, const Coeffs& co, uint64_t seed,
                              int d, int64_t b_max, char* ws, int64_t* b_out, int64_t* worst_out, cudaStream_t s);
