@@ -556,13 +556,12 @@ def large_context(cms, torch, dev):
     return out
 
 
-def batched_context(cms, torch, dev):
-    """64 covariance-shaped instances of uneven n (log-uniform, 5-smooth),
-    m = 2n, half FP32 / half BF16 storage, b = 16 n, d = 3: one batch through
-    a CUDA graph vs one plain FP64 launch per instance.  n is capped at 2048
-    (instead of 8192) so that the plain FP64 leg stays within seconds."""
+def batched_context(cms, torch, dev, n_hi: int = 8192):
+    """64 covariance-shaped instances of uneven n (log-uniform in [512, n_hi],
+    5-smooth), m = 2n, half FP32 / half BF16 storage, b = 16 n, d = 3: one
+    batch through a CUDA graph vs one plain FP64 launch per instance."""
     import workloads as W
-    specs = W.batched_specs(64, seed=4, n_lo=512, n_hi=2048)
+    specs = W.batched_specs(64, seed=4, n_lo=512, n_hi=n_hi)
     gen = torch.Generator(device=dev)
     items, xs = [], []
     for q, sp in enumerate(specs):
@@ -610,7 +609,7 @@ def batched_context(cms, torch, dev):
     for _, _, h in items:
         h.free()
     torch.cuda.empty_cache()
-    return {"workload": "64 covariance instances, n log-uniform [512, 2048] 5-smooth, m=2n, 32 FP32 + 32 BF16, "
+    return {"workload": f"64 covariance instances, n log-uniform [512, {n_hi}] 5-smooth, m=2n, 32 FP32 + 32 BF16, "
                         "b=16n, d=3", "instances": info["instances"], "tasks": info["tasks"],
             "kernel_launches_per_run": info["launches"], "fast_kernel_instances": info["fast_instances"],
             "graph_ms_per_batch": graph_ms, "products_per_s": 64 * 1e3 / graph_ms,
