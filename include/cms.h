@@ -130,6 +130,29 @@ CMS_API cms_status cms_workspace_size(const cms_hashes* h, int64_t n1, int64_t n
                               int64_t n3, int32_t dt, size_t* bytes);
 
 /*
+ * cms_plan_kernel - which fused kernel cms_sketch_product would run for
+ * these arguments (the choice depends on b, n, the storage type, the
+ * alignment of A and B and whether they alias), without running it:
+ *   CMS_KERNEL_SHARED_MEMORY      shared-memory Stockham FFTs (any 5-smooth b)
+ *   CMS_KERNEL_LOCKSTEP           register FFTs, C = P Q, records in shared memory
+ *   CMS_KERNEL_LOCKSTEP_TMEM      the same with the records in tensor memory
+ *   CMS_KERNEL_WARP_SPECIALISED   register FFTs, C = 1024, FP32, front-end
+ *                                 and FFT warps apart
+ *   CMS_KERNEL_CLUSTER            rows of 2^16 bins over 8-CTA clusters
+ * Errors: those of cms_sketch_product's argument checks.
+ */
+enum {
+  CMS_KERNEL_SHARED_MEMORY = 0,
+  CMS_KERNEL_LOCKSTEP = 1,
+  CMS_KERNEL_LOCKSTEP_TMEM = 2,
+  CMS_KERNEL_WARP_SPECIALISED = 3,
+  CMS_KERNEL_CLUSTER = 4
+};
+CMS_API cms_status cms_plan_kernel(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
+                                   int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h,
+                                   int32_t* kernel_out);
+
+/*
  * cms_sketch_product - COMPRESSEDPRODUCT(A, B, b, d) of Fig. 1 (Lemma 1):
  *   c[t][z] = sum over (i,j) with (h1_t(i)+h2_t(j)) mod b = z of
  *             s1_t(i) s2_t(j) (AB)_ij,

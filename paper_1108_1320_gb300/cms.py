@@ -58,6 +58,7 @@ SIGNATURES = {
                                     _P, _P, _SZ, _P]),
     "cms_significant_decode_workspace_size": (_I32, [_P, ctypes.POINTER(_SZ)]),
     "cms_decode_significant": (_I32, [_P, _P, _I64, _I64, ctypes.c_float, _I32, _P, _I64, _P, _P, _SZ, _P]),
+    "cms_plan_kernel": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, ctypes.POINTER(_I32)]),
     "cms_sketch_remove_diagonal": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P]),
     "cms_decode_threshold": (_I32, [_P, _P, _I64, _I64, ctypes.c_float, _I32, _P, _P, _I64, _P, _P, _SZ, _P]),
     "cms_sketch_product_csr_hybrid": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _P, _I64, _P, _P,
@@ -240,6 +241,18 @@ def sketch_product(A: torch.Tensor, B: torch.Tensor, h: Hashes, c: torch.Tensor 
     _check(lib().cms_sketch_product(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype], h.handle,
                                     _ptr(c), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
     return c
+
+
+KERNEL_NAMES = {0: "shared_memory", 1: "lockstep", 2: "lockstep_tmem", 3: "warp_specialised", 4: "cluster"}
+
+
+def plan_kernel(A: torch.Tensor, B: torch.Tensor, h: Hashes) -> str:
+    """The fused kernel sketch_product(A, B, h) would run (see KERNEL_NAMES)."""
+    n1, n2, n3, lda, ldb = _ab_args(A, B)
+    out = _I32()
+    _check(lib().cms_plan_kernel(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype], h.handle,
+                                 ctypes.byref(out)))
+    return KERNEL_NAMES[out.value]
 
 
 def sketch_product_noalloc(A: torch.Tensor, B: torch.Tensor, h: Hashes,

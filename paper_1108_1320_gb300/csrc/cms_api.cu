@@ -335,6 +335,24 @@ cms_status cms_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64
   return CMS_OK;
 }
 
+cms_status cms_plan_kernel(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
+                           int64_t n3, int32_t dt, const cms_hashes* h, int32_t* kernel_out) {
+  if (!kernel_out) return fail(CMS_ERR_INVALID_ARG, "kernel_out is NULL");
+  cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
+  if (st != CMS_OK) return st;
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  DeviceProps dp = device_props(h->device);
+  SketchPlan plan;
+  std::string why;
+  int r = make_sketch_plan(h, n1, n2, n3, dt, dp.sms, dp.smem_optin, &plan, &why, A, lda, B, ldb);
+  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  *kernel_out = plan.wide ? CMS_KERNEL_CLUSTER
+                          : plan.ws ? CMS_KERNEL_WARP_SPECIALISED
+                                    : plan.fast ? (plan.tmem_rec ? CMS_KERNEL_LOCKSTEP_TMEM : CMS_KERNEL_LOCKSTEP)
+                                                : CMS_KERNEL_SHARED_MEMORY;
+  return CMS_OK;
+}
+
 cms_status cms_sketch_product(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
                               int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h, float* c,
                               void* ws, size_t ws_bytes, void* stream) {

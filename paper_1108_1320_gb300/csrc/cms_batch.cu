@@ -38,6 +38,7 @@ struct cms_batch {
   size_t smem = 0;
   int grid = 0;
   int launches = 0;
+  int use_tmem = 0;   // some instance keeps its twiddle records in tensor memory
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -254,6 +255,9 @@ cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t fl
     smem = std::max(smem, p.smem);
   }
   b->total_tasks = total;
+  b->use_tmem = 0;
+  for (const auto& p : b->plans) b->use_tmem |= (p.fast && p.tmem_rec) ? 1 : 0;
+  if (b->use_tmem) smem = std::max(smem, kSmemOneBlockPerSm);
   b->smem = smem;
   b->grid = std::max(1, std::min(total, sms));
   if ((e = cudaMalloc(&b->d_desc, desc.size())) != cudaSuccess ||
@@ -289,7 +293,7 @@ cms_status cms_batch_run(cms_batch* b, void* stream) {
     if (!b->plans[i].fast) e = launch_frontend_twiddles(b->plans[i], b->items[i].h, b->ws + b->ws_off[i], s);
   if (e == cudaSuccess)
     e = launch_sketch_batched(b->d_desc, b->d_start, static_cast<int>(b->items.size()), b->total_tasks,
-                              b->d_next, b->smem, b->grid, s);
+                              b->d_next, b->smem, b->grid, b->use_tmem, s);
   for (size_t i = 0; i < b->items.size() && e == cudaSuccess; ++i) {
     const SketchPlan& p = b->plans[i];
     char* w = b->ws + b->ws_off[i];

@@ -112,6 +112,7 @@ struct SketchPlan {
   int zpos = 0;             // (unal) staging index of the zero slot
   int tw_shift = 0, nhi = 0;  // two-level w_b table: S = 2^tw_shift, nhi high entries
   bool wide = false;        // the cluster kernel for C = 2^16 rows (k_sketch_wide)
+  bool tmem_rec = false;    // the lock-step kernel keeps its twiddle records in tensor memory
   // workspace layout (byte offsets)
   size_t off_partial = 0, off_V = 0, off_twfe = 0, off_twC = 0, off_twR = 0;
   size_t off_T = 0, off_wtab = 0;   // (wide) inverse pass buffer, bucket tables
@@ -147,7 +148,10 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
                      const void* B = nullptr, int64_t ldb = 0, bool allow_fast = true,
                      int nkc_override = 0, int G_override = 0, bool allow_ws = true,
                      bool allow_wide = true);
-size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int esz);
+size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int esz, int tmem_rec);
+// Shared memory that keeps a block alone on its SM (a tensor-memory
+// allocation of 512 columns then never waits on another block).
+constexpr size_t kSmemOneBlockPerSm = 116 * 1024;
 size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int ovcap);
 bool ws_kernel_usable();
 cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,
@@ -176,7 +180,7 @@ void fill_batch_desc(void* dst, const SketchPlan& plan, const cms_hashes* h, con
                      const void* B, int64_t ldb, int64_t n1, int64_t n2, int64_t n3, int dt, char* ws);
 int batch_tasks(const SketchPlan& plan);
 cudaError_t launch_sketch_batched(const void* d_desc, const int* d_start, int ninst, int total,
-                                  int* d_next, size_t smem, int grid, cudaStream_t s);
+                                  int* d_next, size_t smem, int grid, int use_tmem, cudaStream_t s);
 
 // Sparse inputs (A by columns, B by rows).
 struct SparseArgsHost {

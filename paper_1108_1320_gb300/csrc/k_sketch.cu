@@ -238,7 +238,13 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
     while ((static_cast<int64_t>(1) << (2 * sh)) < p.b) ++sh;
     p.tw_shift = sh;
     p.nhi = static_cast<int>((p.b + (static_cast<int64_t>(1) << sh) - 1) >> sh);
-    const size_t sm = fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, dt == CMS_BF16 ? 2 : 4);
+    const size_t sm = fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, dt == CMS_BF16 ? 2 : 4, 0);
+    // large hash domains: the records of two rows (16 bytes per entry) may
+    // not fit beside the staging rows; the lock-step kernel then keeps them
+    // in tensor memory (and asks for a whole SM)
+    const size_t sm_tm = std::max(kSmemOneBlockPerSm,
+                                  fast_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi,
+                                                  dt == CMS_BF16 ? 2 : 4, 1));
     // the warp-specialised kernel caches up to 1024 overflow twiddles in the
     // shared memory left over (at least 64 entries, or it is not used)
     const size_t ws_base = ws_smem_bytes(p.npad, h->fe_ecap, p.alias ? 1 : 0, p.tw_shift, p.nhi, 0);
@@ -250,13 +256,14 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
     const bool ws_ok = allow_ws && dt == CMS_F32 && !p.unal && p.C == kFeC && ovcap >= 64 &&
                        sm_ws <= smem_optin && ws_kernel_usable();
     // the front-end records hold staging indices (< 3 npad) in 16 bits
-    if ((sm <= smem_optin || ws_ok) && 3 * static_cast<int64_t>(p.npad) <= 65535) {
+    if ((sm <= smem_optin || ws_ok || sm_tm <= smem_optin) && 3 * static_cast<int64_t>(p.npad) <= 65535) {
       p.fast = true;
       p.ws = ws_ok;
+      p.tmem_rec = !ws_ok && sm > smem_optin;
       p.ovcap = ws_ok ? ovcap : 0;
       p.G = 2;
       p.threads = ws_ok ? 512 : 256;
-      p.smem = ws_ok ? sm_ws : sm;
+      p.smem = ws_ok ? sm_ws : (p.tmem_rec ? sm_tm : sm);
     }
   }
   // long sketches (b a multiple of 2^16): the cluster kernel, one row of

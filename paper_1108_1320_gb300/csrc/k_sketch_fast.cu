@@ -72,6 +72,7 @@ struct FastArgs {
   int esz;            // bytes per stored element: 4 (FP32) or 2 (BF16)
   int unal;           // rows not 16-byte aligned: copy the aligned superset
   int zpos;           // (unal) staging index of the zero slot read by padding
+  int tmem_rec;       // twiddle records in tensor memory (large n) instead of shared memory
 };
 
 }  // namespace
@@ -95,12 +96,12 @@ constexpr uint32_t kVoidItem = 1u << 30;          // wmeta flag: slot without an
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
 __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int alias, int tw_shift, int nhi,
-                                                  int esz) {
+                                                  int esz, int tmem_rec) {
   SmemLayout L{};
   size_t o = 0;
   const int nstage = alias ? 1 : 2;
   L.stage = o;    o = al16(o + static_cast<size_t>(nstage) * kG * npad * esz);
-  L.rec_tw = o;   o = al16(o + static_cast<size_t>(2) * ecap * 16);
+  L.rec_tw = o;   o = al16(o + (tmem_rec ? 0 : static_cast<size_t>(2) * ecap * 16));
   L.rec_x = o;    o = al16(o + static_cast<size_t>(2) * ecap * 2);
   L.work = o;     o = al16(o + static_cast<size_t>(kRows * 2 * kG) * kRegion * 8);
   L.acc = o;      o = al16(o + static_cast<size_t>(kRows) * kC * 16);
@@ -128,9 +129,17 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
 // (slot s holds 32 lanes' records), and keeps per item its padded count
 // (warp-uniform) and per lane the Y slot its bucket is stored to, so the
 // per-group loop only walks the stream.
+//
+// With tmem_rec the twiddle records live in tensor memory instead (for
+// hash domains whose records do not fit in shared memory): warp w's item j
+// owns the 32 columns 32 j .. 32 j + 31 of its lane quarter (w mod 4) and
+// column half (w / 4), entry e at columns 32 j + 4 e .. + 3 (an item holds
+// at most 8 entries per lane: the capped bucket count); `trow` is the
+// warp's tensor-memory row address.
 template <typename T>
-__device__ __forceinline__ void fast_task(const FastArgs& p, const int task, unsigned char* sm) {
-  const SmemLayout L = fast_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi, static_cast<int>(sizeof(T)));
+__device__ __forceinline__ void fast_task(const FastArgs& p, const int task, unsigned char* sm, uint32_t trow) {
+  const SmemLayout L = fast_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi, static_cast<int>(sizeof(T)),
+                                   p.tmem_rec);
   T* stage = reinterpret_cast<T*>(sm + L.stage);      // FP32 or BF16 as stored
   float4* rec_tw = reinterpret_cast<float4*>(sm + L.rec_tw);     // [slot][lane]: row 0 tw, row 1 tw
   uint16_t* rec_x = reinterpret_cast<uint16_t*>(sm + L.rec_x);   // [slot][lane]: staging index
@@ -239,28 +248,51 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   __syncthreads();
   // records in stream order: staging index of x and s(x) w_b^{(h(x) f1) mod b}
   // for both rows; padding entries (x = n) read the zeroed staging tail
+  const size_t tbase = static_cast<size_t>(t) * 2 * p.ecap;
+  auto rec_twiddles = [&](uint32_t i) {
+    const uint32_t src = slot_src[i >> 5] + (i & 31u);
+    const uint32_t x = p.rec_x[tbase + src];
+    const uint32_t w = p.rec_hs[tbase + src];
+    float2 tw[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      tw[r] = make_float2(0.f, 0.f);
+      if (x < static_cast<uint32_t>(n)) {
+        tw[r] = wb(tlo, thi, mulmod(w & kBucketMask, f1r[r], modb), p.tw_shift);
+        if (w >> 31) { tw[r].x = -tw[r].x; tw[r].y = -tw[r].y; }
+      }
+    }
+    return make_float4(tw[0].x, tw[0].y, tw[1].x, tw[1].y);
+  };
   {
     const uint32_t nrec = istart[kWarps * kItems] * 32u;
-    const size_t tbase = static_cast<size_t>(t) * 2 * p.ecap;
     for (uint32_t i = tid; i < nrec; i += kThreads) {
       const uint32_t src = slot_src[i >> 5] + (i & 31u);
       const uint32_t side = src >= p.ecap ? 1u : 0u;
       const uint32_t x = p.rec_x[tbase + src];
-      const uint32_t w = p.rec_hs[tbase + src];
-      float2 tw[kRows];
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        tw[r] = make_float2(0.f, 0.f);
-        if (x < static_cast<uint32_t>(n)) {
-          tw[r] = wb(tlo, thi, mulmod(w & kBucketMask, f1r[r], modb), p.tw_shift);
-          if (w >> 31) { tw[r].x = -tw[r].x; tw[r].y = -tw[r].y; }
-        }
-      }
-      rec_tw[i] = make_float4(tw[0].x, tw[0].y, tw[1].x, tw[1].y);
+      if (!p.tmem_rec) rec_tw[i] = rec_twiddles(i);
       const uint32_t nsd = static_cast<uint32_t>(side ? p.n3 : p.n1);
       const uint32_t xs = p.unal ? (x < nsd ? x : static_cast<uint32_t>(p.zpos)) : min(x, static_cast<uint32_t>(n));
       rec_x[i] = static_cast<uint16_t>((p.alias ? 0u : side * kG * static_cast<uint32_t>(p.npad)) + xs);
     }
+  }
+  if (p.tmem_rec) {
+    // each warp writes its own items' twiddles to its tensor-memory row
+#pragma unroll 1
+    for (int j = 0; j < kItems; ++j) {
+      const uint32_t cnt = wmeta[warp * kItems + j] & 0xFFu;
+      const uint32_t s0 = istart[warp * kItems + j];
+      float v[32];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (static_cast<uint32_t>(e) < cnt) w4 = rec_twiddles((s0 + e) * 32u + lane);
+        v[4 * e + 0] = w4.x; v[4 * e + 1] = w4.y; v[4 * e + 2] = w4.z; v[4 * e + 3] = w4.w;
+      }
+      __syncwarp();   // the tensor-memory store is warp-collective
+      tmem_st32(trow + 32u * static_cast<uint32_t>(j), v);
+    }
+    tmem_wait_st();
   }
   // lane twiddle anchors w_1024^{lane * 8 q}, q = 0..3, and the step w_1024^lane
   float2 anchor[4];
@@ -361,16 +393,36 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         const T* sg0 = stage + (sb ? shB0 : shA0);
         const T* sg1 = st1 + (sb ? shB1 : shA1);
         float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
+        if (p.tmem_rec) {
+          // the item's (at most 8) entries' twiddles in one tensor-memory load
+          float wr[32];
+          __syncwarp();
+          tmem_ld32(trow + 32u * static_cast<uint32_t>(j), wr);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            if (static_cast<uint32_t>(e) < cnt) {
+              const int x = xp[32 * e];
+              const float v0 = generic::to_f32(sg0[x]);
+              const float v1 = generic::to_f32(sg1[x]);
+              const float4 w = make_float4(wr[4 * e], wr[4 * e + 1], wr[4 * e + 2], wr[4 * e + 3]);
+              a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
+              a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
+              a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
+              a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
+            }
+          }
+        } else {
 #pragma unroll 1
-        for (uint32_t e = 0; e < cnt; ++e) {
-          const int x = xp[32 * e];
-          const float4 w = twp[32 * e];
-          const float v0 = generic::to_f32(sg0[x]);
-          const float v1 = generic::to_f32(sg1[x]);
-          a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
-          a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
-          a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
-          a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
+          for (uint32_t e = 0; e < cnt; ++e) {
+            const int x = xp[32 * e];
+            const float4 w = twp[32 * e];
+            const float v0 = generic::to_f32(sg0[x]);
+            const float v1 = generic::to_f32(sg1[x]);
+            a00.x = fmaf(v0, w.x, a00.x); a00.y = fmaf(v0, w.y, a00.y);
+            a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
+            a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
+            a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
+          }
         }
         xp += 32u * cnt;
         twp += 32u * cnt;
@@ -545,10 +597,35 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   __syncthreads();
 }
 
+// Tensor memory for the records of tmem_rec tasks: 512 columns per block
+// (the launch asks for enough shared memory that one block fits per SM, so
+// the allocation never waits on another block); returns this warp's row.
+__device__ __forceinline__ uint32_t tmem_take(uint32_t* slot) {
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    tmem_alloc(slot, 512);
+    tmem_relinquish();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  return *slot + ((static_cast<uint32_t>(warp & 3) * 32u) << 16) + static_cast<uint32_t>(warp >> 2) * 256u;
+}
+
+__device__ __forceinline__ void tmem_give(uint32_t* slot) {
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(*slot, 512);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
   extern __shared__ __align__(128) unsigned char sm[];
-  fast_task<T>(p, blockIdx.x, sm);
+  __shared__ uint32_t s_tmem;
+  const uint32_t trow = p.tmem_rec ? tmem_take(&s_tmem) : 0u;
+  fast_task<T>(p, blockIdx.x, sm, trow);
+  if (p.tmem_rec) tmem_give(&s_tmem);
 }
 
 // ------------------------------------------------------------- batched ----
@@ -559,9 +636,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_fast(FastArgs p) {
 // partial row, so the result does not depend on which block ran which task.
 __global__ void __launch_bounds__(kThreads, 1)
 k_sketch_batched(const BatchDesc* __restrict__ desc, const int* __restrict__ start, int ninst,
-                 int total, int* next) {
+                 int total, int* next, int use_tmem) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ int s_task;
+  __shared__ uint32_t s_tmem;
+  const uint32_t trow = use_tmem ? tmem_take(&s_tmem) : 0u;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_task = atomicAdd(next, 1);
@@ -576,9 +655,9 @@ k_sketch_batched(const BatchDesc* __restrict__ desc, const int* __restrict__ sta
     const BatchDesc& d = desc[lo];
     const int task = gtask - start[lo];
     if (d.kind == 1) {
-      fast_task<float>(d.f, task, sm);
+      fast_task<float>(d.f, task, sm, trow);
     } else if (d.kind == 3) {
-      fast_task<__nv_bfloat16>(d.f, task, sm);
+      fast_task<__nv_bfloat16>(d.f, task, sm, trow);
     } else {
       float4* sm4 = reinterpret_cast<float4*>(sm);
       switch (d.g.dt) {
@@ -589,6 +668,7 @@ k_sketch_batched(const BatchDesc* __restrict__ desc, const int* __restrict__ sta
       __syncthreads();
     }
   }
+  if (use_tmem) tmem_give(&s_tmem);
 }
 
 }  // namespace
@@ -600,8 +680,8 @@ uint32_t read_clear_error_sketch() {
   return v;
 }
 
-size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int esz) {
-  return fast_layout(npad, ecap, alias, tw_shift, nhi, esz).total;
+size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int esz, int tmem_rec) {
+  return fast_layout(npad, ecap, alias, tw_shift, nhi, esz, tmem_rec).total;
 }
 
 size_t batch_desc_bytes() { return sizeof(BatchDesc); }
@@ -639,6 +719,7 @@ void fill_batch_desc(void* dst, const SketchPlan& plan, const cms_hashes* h, con
     a.G = static_cast<int>((plan.C + 31) / 32);
     a.unal = plan.unal ? 1 : 0;
     a.zpos = plan.zpos;
+    a.tmem_rec = plan.tmem_rec ? 1 : 0;
   } else {
     d.kind = 0;
     generic::SketchArgs& a = d.g;
@@ -665,7 +746,7 @@ int batch_tasks(const SketchPlan& plan) {
 }
 
 cudaError_t launch_sketch_batched(const void* d_desc, const int* d_start, int ninst, int total,
-                                  int* d_next, size_t smem, int grid, cudaStream_t s) {
+                                  int* d_next, size_t smem, int grid, int use_tmem, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_sketch_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -674,7 +755,7 @@ cudaError_t launch_sketch_batched(const void* d_desc, const int* d_start, int ni
   {
     ProfScope prof_scope("k_sketch_batched", s);
     k_sketch_batched<<<grid, kThreads, smem, s>>>(static_cast<const BatchDesc*>(d_desc), d_start, ninst,
-                                                  total, d_next);
+                                                  total, d_next, use_tmem);
   }
   return cudaGetLastError();
 }
@@ -713,6 +794,7 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
   a.G = static_cast<int>((plan.C + 31) / 32);
   a.unal = plan.unal ? 1 : 0;
   a.zpos = plan.zpos;
+  a.tmem_rec = plan.tmem_rec ? 1 : 0;
   const int smem = static_cast<int>(plan.smem);
   const bool bf = plan.dt == CMS_BF16;
   cudaError_t e = bf ? cudaFuncSetAttribute(k_sketch_fast<__nv_bfloat16>,

@@ -150,3 +150,28 @@ def test_batch_c_32l_instances_run_the_fast_body(cms):
     for c, ref in zip(batch.c, refs):
         check(c, ref)
     batch.free()
+
+
+def test_batch_large_instances_keep_records_in_tensor_memory(cms):
+    # n up to 7776 (the configuration's upper range): the two-row twiddle
+    # records no longer fit in shared memory and go to tensor memory; every
+    # instance still runs the register-FFT body; checked on sampled buckets
+    class Sp:
+        def __init__(self, n, dtype, seed):
+            self.n, self.m, self.dtype, self.seed, self.n_pairs, self.rho = n, 48, dtype, seed, n // 100, 0.5
+    specs = [Sp(7776, "f32", 1), Sp(6912, "bf16", 2), Sp(1000, "f32", 3), Sp(5760, "f32", 4)]
+    items, refs = make_instances(cms, specs)
+    batch = cms.Batch(items)
+    assert batch.info()["fast_instances"] == len(specs)
+    batch.run()
+    torch.cuda.synchronize()
+    cms.check_async()
+    for q, (Xd, tab) in enumerate(refs):
+        c = batch.c[q].cpu().numpy().astype(np.float64)
+        zs = W.rng(70 + q).choice(tab.b, 32, replace=False)
+        for t in range(tab.d):
+            want = O.sketch_bucket_values(Xd.T, Xd, tab, t, zs)
+            assert np.linalg.norm(c[t, zs] - want) / np.linalg.norm(want) < 1e-5, (q, t)
+    batch.free()
+    for _, _, h in items:
+        h.free()

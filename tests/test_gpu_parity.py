@@ -529,3 +529,36 @@ def test_large_domain_bf16_reduced_inner(cms):
         dc = (tab.s1[t] @ Xd.T) @ (Xd @ tab.s2[t])
         assert abs(c[t].sum() - dc) < 1e-5 * np.abs(c[t]).sum()
     h.free()
+
+
+# ------------------------------------- records in tensor memory (large n) ----
+@pytest.mark.parametrize("n1,n2,n3,b,d,dtype,alias", [
+    (6000, 24, 6000, 96000, 2, torch.float32, True),     # C = 960
+    (4096, 20, 4096, 65536, 3, torch.bfloat16, True),    # C = 1024, BF16 (not the FP32-only warp-specialised kernel)
+    (5000, 17, 4400, 80000, 2, torch.float32, False),    # C = 800, two operands
+])
+def test_lockstep_kernel_with_tensor_memory_records(cms, n1, n2, n3, b, d, dtype, alias):
+    n = max(n1, n3)
+    h = cms.make_hashes(60 + d, n, b, d)
+    tab = O.make_tables(60 + d, n, b, d)
+    if alias:
+        X = W.gaussian(n2, n1, 61).astype(np.float32)
+        Xr = W.bf16_round(X)[0] if dtype == torch.bfloat16 else X
+        xt = torch.from_numpy(X).to(dev(), dtype)
+        A, B = xt.T, xt
+        Ad, Bd = Xr.T.astype(np.float64), Xr.astype(np.float64)
+    else:
+        Ah = W.gaussian(n1, n2, 62).astype(np.float32)
+        Bh = W.gaussian(n2, n3, 63).astype(np.float32)
+        A, B = colmajor(Ah, dtype), rowmajor(Bh, dtype)
+        Ad, Bd = Ah.astype(np.float64), Bh.astype(np.float64)
+    assert cms.plan_kernel(A, B, h) == "lockstep_tmem"
+    c = cms.sketch_product(A, B, h).cpu().numpy().astype(np.float64)
+    cms.check_async()
+    zs = W.rng(64).choice(b, 64, replace=False)
+    for t in range(d):
+        want = O.sketch_bucket_values(Ad, Bd, tab, t, zs)
+        assert np.linalg.norm(c[t, zs] - want) / np.linalg.norm(want) < TOL_F32, t
+        dc = (tab.s1[t][:n1] @ Ad) @ (Bd @ tab.s2[t][:n3])
+        assert abs(c[t].sum() - dc) < 1e-5 * np.abs(c[t]).sum()
+    h.free()
