@@ -13,6 +13,7 @@
 // cms_batch_run_graph captures that sequence once in a CUDA graph and
 // replays it.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -147,6 +148,26 @@ using namespace cms;
 
 extern "C" {
 
+constexpr int kBatchWaves = 12;
+
+// Work of an instance in conventional flops: d n2 5 b log2 b.
+double instance_work(const cms_instance& it) {
+  const double b = static_cast<double>(it.h->b);
+  return static_cast<double>(it.h->d) * static_cast<double>(std::max<int64_t>(it.n2, 1)) * 5.0 * b *
+         std::log2(std::max(b, 2.0));
+}
+
+// Chunks of instance `it` (planned as p) under the batch budget: tasks in
+// proportion to its share of the batch's work, at least one per unit.
+int batch_chunks(const cms_instance& it, const SketchPlan& p, const cms_instance* items, int count, int sms) {
+  double total = 0.0;
+  for (int i = 0; i < count; ++i) total += instance_work(items[i]);
+  if (!(total > 0.0)) return 0;
+  const double units = static_cast<double>(p.d) * (p.fast ? (p.nrows + 1) / 2 : p.nrows);
+  const double tasks = static_cast<double>(kBatchWaves) * sms * instance_work(it) / total;
+  return std::max(1, static_cast<int>(std::lround(tasks / std::max(units, 1.0))));
+}
+
 cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t flags,
                             const char* tune_cache, void* stream, cms_batch** out) {
   if (!out) return fail(CMS_ERR_INVALID_ARG, "out is NULL");
@@ -179,6 +200,18 @@ cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t fl
     int r = make_sketch_plan(it.h, it.n1, it.n2, it.n3, it.dt, sms, optin, &p, &why, it.A, it.lda, it.B, it.ldb,
                              true, 0, 0, false, false);
     if (r != CMS_OK) { delete b; return fail(static_cast<cms_status>(r), "instance " + std::to_string(i) + ": " + why); }
+    // k-chunking for the batch as a whole: each instance gets tasks in
+    // proportion to its work out of a budget of kBatchWaves waves over the
+    // SMs (the planner alone would split every instance to fill the GPU by
+    // itself: many short tasks, each repeating its prologue and writing a
+    // partial row)
+    {
+      const int nkc = batch_chunks(it, p, items, count, sms);
+      SketchPlan q;
+      if (nkc > 0 && make_sketch_plan(it.h, it.n1, it.n2, it.n3, it.dt, sms, optin, &q, &why, it.A, it.lda, it.B,
+                                      it.ldb, true, nkc, 0, false, false) == CMS_OK)
+        p = q;
+    }
     auto hit = cache.find(tune_key(it, p, sms));
     if (hit != cache.end()) {
       SketchPlan q;
