@@ -417,11 +417,13 @@ cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t* a_rowi
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
   int32_t* klist = reinterpret_cast<int32_t*>(w + off_klist);
+  int32_t* dlist = reinterpret_cast<int32_t*>(w + worst.off_dlist);
+  int32_t* counts = dlist + std::max<int64_t>(n2, 1);
   int32_t K = 0;
   cudaError_t e = cudaSuccess;
   if (n2 > 0) {
-    e = launch_nonempty(a_colptr, b_rowptr, n2, klist, klist + n2, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&K, klist + n2, sizeof(K), cudaMemcpyDeviceToHost, s);
+    e = launch_nonempty_split(a_colptr, b_rowptr, n2, -1, klist, dlist, counts, counts + 2, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&K, counts, sizeof(K), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr (nonempty inner indices)");
   }
@@ -478,7 +480,7 @@ cms_status cms_sketch_product_csr_hybrid(const int64_t* a_colptr, const int32_t*
   int32_t K[2] = {0, 0};
   cudaError_t e = cudaSuccess;
   if (n2 > 0) {
-    e = launch_nonempty_split(a_colptr, b_rowptr, n2, limit, flist, dlist, counts, s);
+    e = launch_nonempty_split(a_colptr, b_rowptr, n2, limit, flist, dlist, counts, counts + 2, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(K, counts, sizeof(K), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   } else {

@@ -190,10 +190,11 @@ struct SparseArgsHost {
 };
 int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, SketchPlan* plan,
                      size_t* off_klist, std::string* why);
-cudaError_t launch_nonempty(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int32_t* klist,
-                            int32_t* kcount, cudaStream_t s);
+// Ordered split of the nonempty inner indices into the FFT list (flist)
+// and the direct list (dlist; limit < 0: none); counts[0..1] their lengths;
+// scratch holds 2 x 1024 ints.
 cudaError_t launch_nonempty_split(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int64_t limit,
-                                  int32_t* flist, int32_t* dlist, int32_t* counts, cudaStream_t s);
+                                  int32_t* flist, int32_t* dlist, int32_t* counts, int32_t* scratch, cudaStream_t s);
 cudaError_t launch_direct_scatter(const cms_hashes* h, const SparseArgsHost& in, int dt, const int32_t* dlist,
                                   const int32_t* counts, int Kd, double* cd, cudaStream_t s);
 cudaError_t launch_add_direct(float* c, const double* cd, int64_t len, const int32_t* counts, cudaStream_t s);

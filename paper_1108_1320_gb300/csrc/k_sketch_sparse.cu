@@ -29,6 +29,7 @@ constexpr int kThreads = 256;  // 8 warps = 2 sides x kG
 constexpr int kFlush = 8;      // groups between Kahan folds
 constexpr int kPitch = 33;
 constexpr int kRegion = 32 * kPitch;
+constexpr int kSplitBlocks = 1024;   // chunks of the inner-index split
 
 struct SparseArgs {
   const int64_t* ptr0;         // colptr of A (side 0)
@@ -264,68 +265,102 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
   }
 }
 
-// Compaction of the inner indices with a nonzero column of A and row of B,
-// in increasing k (one block; exclusive scan per chunk of 1024).
-__global__ void __launch_bounds__(1024)
-k_nonempty(const int64_t* __restrict__ a_ptr, const int64_t* __restrict__ b_ptr, int64_t n2,
-           int32_t* __restrict__ klist, int32_t* __restrict__ kcount) {
-  __shared__ int32_t warp_tot[32];
-  __shared__ int32_t running;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) running = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < n2; base += 1024) {
-    const int64_t k = base + tid;
-    const int flag = (k < n2 && a_ptr[k + 1] > a_ptr[k] && b_ptr[k + 1] > b_ptr[k]) ? 1 : 0;
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, flag);
-    const int in_warp = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) warp_tot[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0;
-    for (int w = 0; w < warp; ++w) before += warp_tot[w];
-    if (flag) klist[running + before + in_warp] = static_cast<int32_t>(k);
-    __syncthreads();
-    if (tid == 0) {
-      int tot = 0;
-      for (int w = 0; w < 32; ++w) tot += warp_tot[w];
-      running += tot;
-    }
-    __syncthreads();
-  }
-  if (tid == 0) *kcount = running;
-}
-
 // Sparse-k hybrid: the nonempty inner indices split, in increasing k, into
 // those whose outer product a_k b_k has at most `limit` terms (sketched
 // directly, Sec. 2.2 "sketching a matrix product naively") and the rest
-// (the FFT route).  counts[0] = FFT list length, counts[1] = direct list.
+// (the FFT route); limit < 0 sends every nonempty index to the FFT route.
+// Three passes over contiguous chunks of k (one block each): counts per
+// chunk, an exclusive scan of the chunk counts, and an ordered write of
+// every chunk from its offsets.  counts[0] = FFT list length, counts[1] =
+// direct list length.
+__device__ __forceinline__ void classify_k(const int64_t* __restrict__ a_ptr, const int64_t* __restrict__ b_ptr,
+                                           int64_t n2, int64_t limit, int64_t k, bool* fft, bool* direct) {
+  int64_t na = 0, nb = 0;
+  if (k < n2) {
+    na = a_ptr[k + 1] - a_ptr[k];
+    nb = b_ptr[k + 1] - b_ptr[k];
+  }
+  const bool live = na > 0 && nb > 0;
+  *direct = live && limit >= 0 && na * nb <= limit;
+  *fft = live && !*direct;
+}
+
 __global__ void __launch_bounds__(1024)
-k_nonempty_split(const int64_t* __restrict__ a_ptr, const int64_t* __restrict__ b_ptr, int64_t n2,
-                 int64_t limit, int32_t* __restrict__ flist, int32_t* __restrict__ dlist,
-                 int32_t* __restrict__ counts) {
+k_split_count(const int64_t* __restrict__ a_ptr, const int64_t* __restrict__ b_ptr, int64_t n2, int64_t limit,
+              int64_t chunk, int32_t* __restrict__ part) {
+  __shared__ int32_t tot[2];
+  if (threadIdx.x < 2) tot[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t k0 = static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t k1 = min(n2, k0 + chunk);
+  int cf = 0, cd = 0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    bool f, dr;
+    classify_k(a_ptr, b_ptr, n2, limit, k, &f, &dr);
+    cf += f;
+    cd += dr;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cf += __shfl_down_sync(0xFFFFFFFFu, cf, o);
+    cd += __shfl_down_sync(0xFFFFFFFFu, cd, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&tot[0], cf);
+    atomicAdd(&tot[1], cd);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) part[2 * blockIdx.x + threadIdx.x] = tot[threadIdx.x];
+}
+
+// exclusive scan of the nblk chunk counts (nblk <= 1024) in place
+__global__ void __launch_bounds__(1024) k_split_scan(int32_t* __restrict__ part, int nblk,
+                                                     int32_t* __restrict__ counts) {
+  __shared__ int32_t wsum[2][32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int side = 0; side < 2; ++side) {
+    const int32_t v = tid < nblk ? part[2 * tid + side] : 0;
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[side][warp] = x;
+    __syncthreads();
+    int32_t before = 0, total = 0;
+    for (int w = 0; w < 32; ++w) {
+      if (w < warp) before += wsum[side][w];
+      total += wsum[side][w];
+    }
+    if (tid < nblk) part[2 * tid + side] = before + x - v;
+    if (tid == 0) counts[side] = total;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+k_split_write(const int64_t* __restrict__ a_ptr, const int64_t* __restrict__ b_ptr, int64_t n2, int64_t limit,
+              int64_t chunk, const int32_t* __restrict__ part, int32_t* __restrict__ flist,
+              int32_t* __restrict__ dlist) {
   __shared__ int32_t warp_tot[2][32];
   __shared__ int32_t running[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid < 2) running[tid] = 0;
+  if (tid < 2) running[tid] = part[2 * blockIdx.x + tid];
   __syncthreads();
-  for (int64_t base = 0; base < n2; base += 1024) {
+  const int64_t k0 = static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t k1 = min(n2, k0 + chunk);
+  for (int64_t base = k0; base < k1; base += 1024) {
     const int64_t k = base + tid;
-    int64_t na = 0, nb = 0;
-    if (k < n2) {
-      na = a_ptr[k + 1] - a_ptr[k];
-      nb = b_ptr[k + 1] - b_ptr[k];
-    }
-    const bool live = na > 0 && nb > 0;
-    const bool direct = live && na * nb <= limit;
-    const unsigned bf = __ballot_sync(0xFFFFFFFFu, live && !direct);
-    const unsigned bd = __ballot_sync(0xFFFFFFFFu, direct);
+    bool f = false, dr = false;
+    if (k < k1) classify_k(a_ptr, b_ptr, n2, limit, k, &f, &dr);
+    const unsigned bf = __ballot_sync(0xFFFFFFFFu, f);
+    const unsigned bd = __ballot_sync(0xFFFFFFFFu, dr);
     const unsigned lt = (1u << lane) - 1u;
     if (lane == 0) { warp_tot[0][warp] = __popc(bf); warp_tot[1][warp] = __popc(bd); }
     __syncthreads();
     int before_f = 0, before_d = 0;
     for (int w = 0; w < warp; ++w) { before_f += warp_tot[0][w]; before_d += warp_tot[1][w]; }
-    if (live && !direct) flist[running[0] + before_f + __popc(bf & lt)] = static_cast<int32_t>(k);
-    if (direct) dlist[running[1] + before_d + __popc(bd & lt)] = static_cast<int32_t>(k);
+    if (f) flist[running[0] + before_f + __popc(bf & lt)] = static_cast<int32_t>(k);
+    if (dr) dlist[running[1] + before_d + __popc(bd & lt)] = static_cast<int32_t>(k);
     __syncthreads();
     if (tid < 2) {
       int tot = 0;
@@ -334,7 +369,6 @@ k_nonempty_split(const int64_t* __restrict__ a_ptr, const int64_t* __restrict__ 
     }
     __syncthreads();
   }
-  if (tid < 2) counts[tid] = running[tid];
 }
 
 template <typename T> __device__ __forceinline__ double val_f64(const T* v, int64_t i);
@@ -442,7 +476,7 @@ int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, Sk
   p.off_twR = off;     off = align256(off + static_cast<size_t>(p.R) * 8);
   *off_klist = off;    off = align256(off + static_cast<size_t>(std::max<int64_t>(n2, 1) + 1) * 4);
   // sparse-k hybrid: the direct list, the list counts, the FP64 direct sketch
-  p.off_dlist = off;   off = align256(off + static_cast<size_t>(std::max<int64_t>(n2, 1) + 2) * 4);
+  p.off_dlist = off;   off = align256(off + (static_cast<size_t>(std::max<int64_t>(n2, 1)) + 2 + 2 * kSplitBlocks) * 4);
   p.off_cd = off;      off = align256(off + static_cast<size_t>(p.d) * p.b * 8);
   p.ws_bytes = off;
   (void)why;
@@ -450,21 +484,16 @@ int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, Sk
   return CMS_OK;
 }
 
-cudaError_t launch_nonempty(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int32_t* klist,
-                            int32_t* kcount, cudaStream_t s) {
-  {
-    ProfScope prof_scope("k_nonempty", s);
-    k_nonempty<<<1, 1024, 0, s>>>(a_ptr, b_ptr, n2, klist, kcount);
-  }
-  return cudaGetLastError();
-}
-
 cudaError_t launch_nonempty_split(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int64_t limit,
-                                  int32_t* flist, int32_t* dlist, int32_t* counts, cudaStream_t s) {
-  {
-    ProfScope prof_scope("k_nonempty_split", s);
-    k_nonempty_split<<<1, 1024, 0, s>>>(a_ptr, b_ptr, n2, limit, flist, dlist, counts);
-  }
+                                  int32_t* flist, int32_t* dlist, int32_t* counts, int32_t* scratch, cudaStream_t s) {
+  if (n2 <= 0) return cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t), s);
+  const int64_t nblk = std::min<int64_t>(kSplitBlocks, (n2 + 1023) / 1024);
+  const int64_t chunk = ((n2 + nblk - 1) / nblk + 1023) / 1024 * 1024;
+  const unsigned g = static_cast<unsigned>((n2 + chunk - 1) / chunk);
+  ProfScope prof_scope("k_nonempty_split", s);
+  k_split_count<<<g, 1024, 0, s>>>(a_ptr, b_ptr, n2, limit, chunk, scratch);
+  k_split_scan<<<1, 1024, 0, s>>>(scratch, static_cast<int>(g), counts);
+  k_split_write<<<g, 1024, 0, s>>>(a_ptr, b_ptr, n2, limit, chunk, scratch, flist, dlist);
   return cudaGetLastError();
 }
 
