@@ -129,7 +129,7 @@ __device__ __forceinline__ uint32_t bucket_scramble(uint32_t z) {
 // (in x order) go to a per-bucket overflow list.  A bucket's entries are read
 // in x order from the stable bucket sort (perm, off); the counts, group
 // bases and overflow offsets come from warp and block scans.
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, 1)
 k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ perm,
                   const uint32_t* __restrict__ off, uint32_t n, uint32_t ecap,
                   uint32_t* __restrict__ rec_x, uint32_t* __restrict__ rec_hs,
@@ -164,6 +164,7 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   // bucket sizes from the stable bucket sort (perm lists each bucket's x in
   // increasing order)
   cnt[tid] = tid < C ? of[tid + 1] - of[tid] : 0u;
+  used[tid] = bucket_scramble(static_cast<uint32_t>(tid));   // scrambled bucket order, read by the rank loop
   for (uint32_t e = tid; e < ecap; e += blockDim.x) { rx[e] = n; rh[e] = 0u; }
   __syncthreads();
   if (tid < C) {
@@ -173,10 +174,10 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
     // residue twice (the Y stores of a group then need 2 wavefronts)
     const uint32_t z = static_cast<uint32_t>(tid);
     const uint32_t cc = min(cnt[z], kCap);
-    const uint32_t sk = bucket_scramble(z);
+    const uint32_t sk = used[z];
     uint32_t rank = 0;
     for (uint32_t o = z & 15u; o < static_cast<uint32_t>(C); o += 16u) {
-      const uint32_t so = bucket_scramble(o);
+      const uint32_t so = used[o];
       if (min(cnt[o], kCap) == cc && (so < sk || (so == sk && o < z))) ++rank;
     }
     key[tid] = ((kCap - cc) << 20) | ((rank >> 1) << 15) | ((z & 15u) << 11) | ((rank & 1u) << 10) | z;
@@ -328,6 +329,7 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
       for (uint32_t k = 0; k < 32; ++k) {
         if (rank == k && r < c) {
           uint32_t best = r, bu = 0xFFFFFFFFu;
+#pragma unroll 4
           for (uint32_t i = r; i < c; ++i) {
             const uint32_t u = ub[xs[i] & 31u];
             if (u < bu) { bu = u; best = i; }
