@@ -145,21 +145,17 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   __shared__ uint32_t cnt[kMax];        // entries per bucket
   __shared__ uint32_t key[kMax];
   __shared__ uint32_t used[kMax];       // greedy bank counters, 32 per warp
-  __shared__ uint32_t gbase[kMax / 32];
   __shared__ uint32_t gword[kMax / 32];  // group count | overflow flag << 31
   __shared__ uint32_t wtot[32];
   __shared__ uint32_t gcost[kMax / 32];  // slots + longest overflow list of a group
   const int L = (C + 31) / 32;
   const int ts = blockIdx.x;
-  const uint32_t* tab = hs + static_cast<size_t>(ts) * n;
-  const uint32_t* pm = perm + static_cast<size_t>(ts) * n;
   const uint32_t* of = off + static_cast<size_t>(ts) * (C + 1);
   uint32_t* rx = rec_x + static_cast<size_t>(ts) * ecap;
   uint32_t* rh = rec_hs + static_cast<size_t>(ts) * ecap;
   uint32_t* gp = grp + static_cast<size_t>(ts) * ((C + 31) / 32) * 2;
   uint16_t* ds = dest + static_cast<size_t>(ts) * ((C + 31) / 32) * 32;
   uint32_t* oo = ovf_off + static_cast<size_t>(ts) * (C + 1);
-  uint32_t* ox = ovf_x + static_cast<size_t>(ts) * n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // bucket sizes from the stable bucket sort (perm lists each bucket's x in
   // increasing order)
@@ -253,7 +249,6 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
       const uint32_t t2 = __shfl_up_sync(0xFFFFFFFFu, gi, o);
       if (lane >= o) gi += t2;
     }
-    gbase[lane] = gi - v;
     if (lane < L) {
       gp[2 * lane] = gi - v;
       gp[2 * lane + 1] = gw;
@@ -294,13 +289,41 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   __syncthreads();
   const uint32_t my_oof = wtot[warp] + incl - ov;   // bucket tid's first overflow slot
   if (tid < C) oo[tid] = my_oof;
-  cnt[tid] = my_oof;                                 // now: overflow offset by bucket
-  __syncthreads();
-  if (!live) return;
-  // this lane's entries (the first kFeCap in x order) and the overflow
-  // entries of its bucket
+  // the records themselves are placed by k_frontend_records
+}
+
+// Records of one bucket group (one warp per (t, side, group)): each lane's
+// entries (the first kFeCap of its bucket in x order) and the overflow
+// entries of its bucket.  The entries are ordered bank-aware: step r gives
+// each lane, in order of ascending count, its remaining entry whose bank
+// (x mod 32) is least used at this step so far; padding lanes all read
+// x = n (one address).  The order is sequential over the lanes, so the
+// groups run as separate warps spread over the SMs.
+__global__ void __launch_bounds__(32)
+k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ perm,
+                   const uint32_t* __restrict__ off, uint32_t n, uint32_t ecap, uint32_t* __restrict__ rec_x,
+                   uint32_t* __restrict__ rec_hs, const uint32_t* __restrict__ grp, const uint16_t* __restrict__ dest,
+                   const uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x, int C) {
+  constexpr uint32_t kCap = static_cast<uint32_t>(kFeCap);
+  __shared__ uint32_t ub[32];
+  const int L = (C + 31) / 32;
+  const int ts = blockIdx.x / L, g = blockIdx.x % L;
+  const int lane = threadIdx.x;
+  const uint32_t* tab = hs + static_cast<size_t>(ts) * n;
+  const uint32_t* pm = perm + static_cast<size_t>(ts) * n;
+  const uint32_t* of = off + static_cast<size_t>(ts) * (C + 1);
+  uint32_t* rx = rec_x + static_cast<size_t>(ts) * ecap;
+  uint32_t* rh = rec_hs + static_cast<size_t>(ts) * ecap;
+  const uint32_t gb = grp[(static_cast<size_t>(ts) * L + g) * 2];
+  const uint32_t cm = grp[(static_cast<size_t>(ts) * L + g) * 2 + 1] & 0xFFFFu;
+  const uint32_t zd = dest[static_cast<size_t>(ts) * L * 32 + 32 * g + lane];
+  const bool real = zd < static_cast<uint32_t>(C);
+  const uint32_t zs = real ? zd : 0u;
+  const uint32_t cz = real ? of[zs + 1] - of[zs] : 0u;
+  const uint32_t c = min(cz, kCap);
   const uint32_t o0 = of[zs];
-  const uint32_t oz = cnt[zs];
+  const uint32_t oz = ovf_off[static_cast<size_t>(ts) * (C + 1) + zs];
+  uint32_t* ox = ovf_x + static_cast<size_t>(ts) * n;
   uint32_t xs[kFeCap], wsv[kFeCap];
 #pragma unroll
   for (uint32_t r = 0; r < kCap; ++r)
@@ -309,41 +332,33 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   for (uint32_t r = 0; r < kCap; ++r)
     if (r < c) wsv[r] = tab[xs[r]];
   for (uint32_t r = kCap; r < cz; ++r) ox[oz + (r - kCap)] = pm[o0 + r];
-  // bank-aware order of each bucket's entries: step r gives each lane, in
-  // order of ascending count, its remaining entry whose bank (x mod 32) is
-  // least used at this step so far; padding lanes all read x = n (one
-  // address)
-  {
-    uint32_t* ub = used + 32 * warp;
-    uint32_t rank = 0;
-    for (int o = 0; o < 32; ++o) {
-      const uint32_t co = __shfl_sync(0xFFFFFFFFu, c, o);
-      rank += (co < c || (co == c && o < lane)) ? 1u : 0u;
-    }
-    for (uint32_t r = 0; r < cm; ++r) {
-      ub[lane] = 0;
-      const bool pads = __any_sync(0xFFFFFFFFu, c <= r);
-      __syncwarp();
-      if (lane == 0 && pads) ub[n & 31u] = 1;
-      __syncwarp();
-      for (uint32_t k = 0; k < 32; ++k) {
-        if (rank == k && r < c) {
-          uint32_t best = r, bu = 0xFFFFFFFFu;
+  uint32_t rank = 0;
+  for (int o = 0; o < 32; ++o) {
+    const uint32_t co = __shfl_sync(0xFFFFFFFFu, c, o);
+    rank += (co < c || (co == c && o < lane)) ? 1u : 0u;
+  }
+  for (uint32_t r = 0; r < cm; ++r) {
+    ub[lane] = 0;
+    const bool pads = __any_sync(0xFFFFFFFFu, c <= r);
+    __syncwarp();
+    if (lane == 0 && pads) ub[n & 31u] = 1;
+    __syncwarp();
+    for (uint32_t k = 0; k < 32; ++k) {
+      if (rank == k && r < c) {
+        uint32_t best = r, bu = 0xFFFFFFFFu;
 #pragma unroll 4
-          for (uint32_t i = r; i < c; ++i) {
-            const uint32_t u = ub[xs[i] & 31u];
-            if (u < bu) { bu = u; best = i; }
-          }
-          const uint32_t tx = xs[r], tw = wsv[r];
-          xs[r] = xs[best]; wsv[r] = wsv[best];
-          xs[best] = tx; wsv[best] = tw;
-          ub[xs[r] & 31u] += 1;
+        for (uint32_t i = r; i < c; ++i) {
+          const uint32_t u = ub[xs[i] & 31u];
+          if (u < bu) { bu = u; best = i; }
         }
-        __syncwarp();
+        const uint32_t tx = xs[r], tw = wsv[r];
+        xs[r] = xs[best]; wsv[r] = wsv[best];
+        xs[best] = tx; wsv[best] = tw;
+        ub[xs[r] & 31u] += 1;
       }
+      __syncwarp();
     }
   }
-  const uint32_t gb = gbase[warp];
   for (uint32_t r = 0; r < c; ++r) {
     rx[gb + 32u * r + lane] = xs[r];
     rh[gb + 32u * r + lane] = wsv[r];
@@ -361,10 +376,13 @@ cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, con
     k_frontend_tables<<<2 * d, kFeC, 0, s>>>(hs, perm, off, static_cast<uint32_t>(n), ecap, rec_x, rec_hs,
                                              grp, dest, ovf_off, ovf_x, assign, static_cast<int>(C));
   }
+  {
+    ProfScope prof_scope("k_frontend_records", s);
+    const unsigned groups = static_cast<unsigned>(2 * d * ((C + 31) / 32));
+    k_frontend_records<<<groups, 32, 0, s>>>(hs, perm, off, static_cast<uint32_t>(n), ecap, rec_x, rec_hs, grp,
+                                              dest, ovf_off, ovf_x, static_cast<int>(C));
+  }
   return cudaGetLastError();
 }
-
-
-
 
 }  // namespace cms
