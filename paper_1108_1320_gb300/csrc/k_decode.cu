@@ -25,9 +25,51 @@ __device__ __forceinline__ T median_of(T* x, int d) {
   return (d & 1) ? x[mid] : static_cast<T>(0.5) * (x[mid - 1] + x[mid]);
 }
 
+// The same estimate for a compile-time d: the d values stay in registers
+// and are sorted by odd-even transposition (d rounds of compare-exchange,
+// the order an insertion sort gives for the same values).
+template <typename T, int D>
+__device__ __forceinline__ T estimate_fixed(const T* __restrict__ c, const uint32_t* __restrict__ hs,
+                                            int64_t n, uint32_t b, int64_t i, int64_t j) {
+  T x[D];
+#pragma unroll
+  for (int t = 0; t < D; ++t) {
+    const uint32_t wa = __ldg(hs + (static_cast<size_t>(2 * t) * n + i));
+    const uint32_t wb = __ldg(hs + (static_cast<size_t>(2 * t + 1) * n + j));
+    uint32_t z = (wa & kBucketMask) + (wb & kBucketMask);
+    if (z >= b) z -= b;
+    T v = __ldg(c + static_cast<size_t>(t) * b + z);
+    if ((wa ^ wb) >> 31) v = -v;
+    x[t] = v;
+  }
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+#pragma unroll
+    for (int a = r & 1; a + 1 < D; a += 2) {
+      const T lo = x[a], hi = x[a + 1];
+      const bool sw = lo > hi;
+      x[a] = sw ? hi : lo;
+      x[a + 1] = sw ? lo : hi;
+    }
+  }
+  constexpr int mid = D >> 1;
+  return (D & 1) ? x[mid] : static_cast<T>(0.5) * (x[mid - 1] + x[mid]);
+}
+
 template <typename T>
 __device__ __forceinline__ T estimate(const T* __restrict__ c, const uint32_t* __restrict__ hs,
                                       int64_t n, uint32_t b, int d, int64_t i, int64_t j) {
+  switch (d) {
+    case 1: return estimate_fixed<T, 1>(c, hs, n, b, i, j);
+    case 2: return estimate_fixed<T, 2>(c, hs, n, b, i, j);
+    case 3: return estimate_fixed<T, 3>(c, hs, n, b, i, j);
+    case 4: return estimate_fixed<T, 4>(c, hs, n, b, i, j);
+    case 5: return estimate_fixed<T, 5>(c, hs, n, b, i, j);
+    case 6: return estimate_fixed<T, 6>(c, hs, n, b, i, j);
+    case 7: return estimate_fixed<T, 7>(c, hs, n, b, i, j);
+    case 8: return estimate_fixed<T, 8>(c, hs, n, b, i, j);
+    default: break;
+  }
   T x[kMaxD];
   for (int t = 0; t < d; ++t) {
     const uint32_t wa = __ldg(hs + (static_cast<size_t>(2 * t) * n + i));
