@@ -337,31 +337,46 @@ k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__
     const uint32_t co = __shfl_sync(0xFFFFFFFFu, c, o);
     rank += (co < c || (co == c && o < lane)) ? 1u : 0u;
   }
-  for (uint32_t r = 0; r < cm; ++r) {
+  // steps r unrolled so that every index into xs / wsv is a constant (the
+  // arrays stay in registers); the lanes with no entry left at step r have
+  // the lowest ranks and take no turn
+#pragma unroll
+  for (uint32_t r = 0; r < kCap; ++r) {
+    if (r >= cm) break;
     ub[lane] = 0;
-    const bool pads = __any_sync(0xFFFFFFFFu, c <= r);
+    const uint32_t done = __ballot_sync(0xFFFFFFFFu, c <= r);
     __syncwarp();
-    if (lane == 0 && pads) ub[n & 31u] = 1;
+    if (lane == 0 && done) ub[n & 31u] = 1;
     __syncwarp();
-    for (uint32_t k = 0; k < 32; ++k) {
-      if (rank == k && r < c) {
-        uint32_t best = r, bu = 0xFFFFFFFFu;
-#pragma unroll 4
-        for (uint32_t i = r; i < c; ++i) {
-          const uint32_t u = ub[xs[i] & 31u];
-          if (u < bu) { bu = u; best = i; }
+    for (uint32_t k = __popc(done); k < 32; ++k) {
+      if (rank == k) {
+        uint32_t best = r, bu = ub[xs[r] & 31u];
+#pragma unroll
+        for (uint32_t i = r + 1; i < kCap; ++i) {
+          if (i < c) {
+            const uint32_t u = ub[xs[i] & 31u];
+            if (u < bu) { bu = u; best = i; }
+          }
         }
-        const uint32_t tx = xs[r], tw = wsv[r];
-        xs[r] = xs[best]; wsv[r] = wsv[best];
-        xs[best] = tx; wsv[best] = tw;
+#pragma unroll
+        for (uint32_t i = r + 1; i < kCap; ++i) {
+          if (best == i) {
+            const uint32_t tx = xs[r], tw = wsv[r];
+            xs[r] = xs[i]; wsv[r] = wsv[i];
+            xs[i] = tx; wsv[i] = tw;
+          }
+        }
         ub[xs[r] & 31u] += 1;
       }
       __syncwarp();
     }
   }
-  for (uint32_t r = 0; r < c; ++r) {
-    rx[gb + 32u * r + lane] = xs[r];
-    rh[gb + 32u * r + lane] = wsv[r];
+#pragma unroll
+  for (uint32_t r = 0; r < kCap; ++r) {
+    if (r < c) {
+      rx[gb + 32u * r + lane] = xs[r];
+      rh[gb + 32u * r + lane] = wsv[r];
+    }
   }
 }
 
