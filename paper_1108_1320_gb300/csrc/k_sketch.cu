@@ -90,6 +90,15 @@ struct InvArgs {
   float2* V;
 };
 
+// s + e += x with the rounding error of each add carried in e (Neumaier's
+// variant of Kahan summation: the larger magnitude decides which error term
+// is exact).
+__device__ __forceinline__ void neumaier_add(float& s, float& e, float x) {
+  const float t = s + x;
+  e += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+
 // K2a: one block per (t, f1).
 __global__ void __launch_bounds__(256) k_rows_inverse(InvArgs p) {
   extern __shared__ float2 sm2[];
@@ -102,20 +111,23 @@ __global__ void __launch_bounds__(256) k_rows_inverse(InvArgs p) {
   for (int i = threadIdx.x; i < C; i += blockDim.x) twC[i] = p.twC[i];
   const float2* part = p.partial + static_cast<size_t>(tr) * p.nkc * C;
   for (int f2 = threadIdx.x; f2 < C; f2 += blockDim.x) {
-    double sx = 0.0, sy = 0.0;
+    // the k-chunk partials in chunk order, compensated (Neumaier) in FP32:
+    // the error of the plain FP64 sum without its FP64 adds
+    float sx = 0.f, ex = 0.f, sy = 0.f, ey = 0.f;
+#pragma unroll 4
     for (int kc = 0; kc < p.nkc; ++kc) {
-      const float2 v = part[static_cast<size_t>(kc) * C + f2];
-      sx += v.x;
-      sy += v.y;
+      const float2 v = __ldg(part + static_cast<size_t>(kc) * C + f2);
+      neumaier_add(sx, ex, v.x);
+      neumaier_add(sy, ey, v.y);
     }
-    P[f2] = make_float2(static_cast<float>(sx), static_cast<float>(sy));
+    P[f2] = make_float2(sx + ex, sy + ey);
   }
   __syncthreads();
   float2* X = fft_block<true>(P, Q, C, 1, p.radC, p.nradC, twC);
   float2* out = p.V + static_cast<size_t>(tr) * C;
   for (int z2 = threadIdx.x; z2 < C; z2 += blockDim.x) {
-    const uint64_t m = (static_cast<uint64_t>(f1) * static_cast<uint64_t>(z2)) %
-                       static_cast<uint64_t>(p.b);
+    // f1 <= R / 2 and z2 < C, so f1 z2 < b / 2 needs no reduction mod b
+    const uint64_t m = static_cast<uint64_t>(f1) * static_cast<uint64_t>(z2);
     const float2 w = cconj(w_pow(m, p.b));   // w_b^{-m}
     out[z2] = cmul(X[z2], w);
   }
@@ -134,9 +146,12 @@ k_cols_inverse(const float2* __restrict__ V, const float2* __restrict__ twR, int
   const float2* Vt = V + static_cast<size_t>(t) * nrows * C + z2;
   float sum = Vt[0].x;
   const bool even = (R % 2) == 0;
+  int e = 0;   // f1 z1 mod R, stepped (z1 < R)
   for (int f1 = 1; f1 < nrows; ++f1) {
+    e += z1;
+    if (e >= R) e -= R;
     const float2 v = Vt[static_cast<size_t>(f1) * C];
-    const float2 w = twR[(static_cast<int64_t>(f1) * z1) % R];   // w_R^{f1 z1}
+    const float2 w = __ldg(twR + e);                             // w_R^{f1 z1}
     const float term = v.x * w.x + v.y * w.y;                    // Re(v conj(w))
     sum += (even && 2 * f1 == R) ? term : 2.f * term;
   }
