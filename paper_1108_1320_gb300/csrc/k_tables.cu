@@ -40,18 +40,40 @@ k_bucket_sort(const uint32_t* __restrict__ hs, uint32_t n, uint32_t C,
   for (uint32_t x = threadIdx.x; x < n; x += blockDim.x)
     atomicAdd(&cnt[(tab[x] & kBucketMask) % C], 1u);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (uint32_t z = 0; z < C; ++z) {
-      const uint32_t v = cnt[z];
-      of[z] = run;
-      cnt[z] = run;            // becomes the placement cursor
-      run += v;
-    }
-    of[C] = run;
-  }
-  __syncthreads();
+  // exclusive scan of the counts, 1024 buckets per round (warp shuffles,
+  // then the 32 warp totals); cnt becomes the placement cursor
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ uint32_t wsum[kSortThreads / 32];
+  __shared__ uint32_t rtot;
+  uint32_t run = 0;
+  for (uint32_t z0 = 0; z0 < C; z0 += kSortThreads) {
+    const uint32_t z = z0 + threadIdx.x;
+    const uint32_t v = z < C ? cnt[z] : 0u;
+    uint32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t wv = wsum[lane];
+      uint32_t wi = wv;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+        if (lane >= o) wi += u;
+      }
+      wsum[lane] = wi - wv;
+      if (lane == 31) rtot = wi;
+    }
+    __syncthreads();
+    const uint32_t ex = run + wsum[warp] + incl - v;
+    if (z < C) { of[z] = ex; cnt[z] = ex; }
+    run += rtot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) of[C] = run;
+  __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (uint32_t base = 0; base < n; base += blockDim.x) {
     const uint32_t x = base + threadIdx.x;
