@@ -218,23 +218,31 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   // holds distinct z2 mod 16 where possible: the front end's 8-byte stores
   // to Y[z2] are then free of bank conflicts.  The group's bucket set (and
   // so its padded length) is unchanged.
-  if (tid < L) {
-    uint32_t* grpkey = key + 32 * tid;
-    uint32_t in[32], half0[16], half1[16], pool[32];
-    int n0 = 0, n1 = 0, np = 0;
-    uint32_t used0 = 0, used1 = 0;
-    for (int i = 0; i < 32; ++i) in[i] = grpkey[i];
-    for (int i = 0; i < 32; ++i) {
-      const uint32_t r = (in[i] & 0x3FFu) & 15u;
-      if (!(used0 >> r & 1u)) { used0 |= 1u << r; half0[n0++] = in[i]; }
-      else if (!(used1 >> r & 1u)) { used1 |= 1u << r; half1[n1++] = in[i]; }
-      else { pool[np++] = in[i]; }
+  // One warp per group, lane i holding the group's i-th key: the first
+  // bucket of each residue (in group order) goes to the first half, the
+  // second to the second half, the rest fill the first half up to 16 and
+  // then the second, all in group order.
+  if (warp < L) {
+    uint32_t* grpkey = key + 32 * warp;
+    const uint32_t kv = grpkey[lane];
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t same = __match_any_sync(0xFFFFFFFFu, (kv & 0x3FFu) & 15u);
+    const uint32_t occ = __popc(same & lt);          // earlier keys of this residue
+    const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, occ == 0);
+    const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, occ == 1);
+    const uint32_t bp = __ballot_sync(0xFFFFFFFFu, occ >= 2);
+    const uint32_t n0 = __popc(b0), n1 = __popc(b1);
+    uint32_t slot;
+    if (occ == 0) {
+      slot = __popc(b0 & lt);
+    } else if (occ == 1) {
+      slot = 16u + __popc(b1 & lt);
+    } else {
+      const uint32_t pp = __popc(bp & lt);
+      slot = n0 + pp < 16u ? n0 + pp : 16u + n1 + (pp - (16u - n0));
     }
-    for (int i = 0; i < np; ++i) {
-      if (n0 < 16) half0[n0++] = pool[i];
-      else half1[n1++] = pool[i];
-    }
-    for (int i = 0; i < 16; ++i) { grpkey[i] = half0[i]; grpkey[16 + i] = half1[i]; }
+    __syncwarp();
+    grpkey[slot] = kv;
   }
   __syncthreads();
   // thread tid = group warp, lane: its bucket, the group's padded count
@@ -285,27 +293,31 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
     wtot[lane] = wi - wv;
     if (lane == 31) oo[C] = wi;
   }
-  if (tid == 32 && C == kMax) {
-    // the 32 groups dealt to 8 front-end warps x 4 slots, heaviest first to
-    // the least-loaded warp with a free slot (the warp-specialised kernel,
-    // C = 1024 only, takes 4 groups of each side per warp)
+  if (warp == 1 && C == kMax) {
+    // the 32 groups dealt to 8 front-end warps x 4 slots, heaviest first
+    // (equal costs: lower group first) to the least-loaded warp with a free
+    // slot (equal loads: lower warp); the warp-specialised kernel, C = 1024
+    // only, takes 4 groups of each side per warp.  Lane g holds group g's
+    // cost and its rank in that order; lanes 0..7 hold the warps' loads.
     uint8_t* as = assign + static_cast<size_t>(ts) * (kMax / 32);
-    int ord[kMax / 32];
-    for (int g = 0; g < kMax / 32; ++g) {
-      int q = g;
-      while (q > 0 && gcost[ord[q - 1]] < gcost[g]) { ord[q] = ord[q - 1]; --q; }
-      ord[q] = g;
+    const uint32_t myc = gcost[lane];
+    uint32_t rk = 0;
+    for (int o = 0; o < 32; ++o) {
+      const uint32_t co = __shfl_sync(0xFFFFFFFFu, myc, o);
+      rk += (co > myc || (co == myc && o < lane)) ? 1u : 0u;
     }
-    uint32_t load[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int fill[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < kMax / 32; ++i) {
-      const int g = ord[i];
-      int best = -1;
-      for (int w = 0; w < 8; ++w)
-        if (fill[w] < 4 && (best < 0 || load[w] < load[best])) best = w;
-      as[best * 4 + fill[best]] = static_cast<uint8_t>(g);
-      ++fill[best];
-      load[best] += gcost[g];
+    uint32_t load = 0, fill = 0;
+    for (uint32_t i = 0; i < 32; ++i) {
+      const int g = __ffs(__ballot_sync(0xFFFFFFFFu, rk == i)) - 1;
+      const uint32_t cg = __shfl_sync(0xFFFFFFFFu, myc, g);
+      uint64_t key = (lane < 8 && fill < 4) ? ((static_cast<uint64_t>(load) << 8) | static_cast<uint64_t>(lane))
+                                            : ~0ull;
+      for (int o = 4; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(0xFFFFFFFFu, key, o));
+      if (lane < 8 && static_cast<uint64_t>(lane) == (key & 0xFFu)) {
+        as[lane * 4 + fill] = static_cast<uint8_t>(g);
+        ++fill;
+        load += cg;
+      }
     }
   }
   __syncthreads();
