@@ -139,18 +139,19 @@ __device__ __forceinline__ uint32_t bucket_scramble(uint32_t z) {
   return z >> 22;
 }
 
-// Front-end records for the C = 1024 fused kernel, one block per (t, side).
+// Front-end tables for the C = 1024 fused kernel, one block per (t, side).
 // Buckets z2 = h mod C are ordered by capped count (<= kFeCap) descending,
 // then so that each run of 32 buckets of a class holds every residue
 // z2 mod 16 twice (scrambled order within a residue).  Consecutive runs of
 // 32 buckets form a group whose lanes walk their buckets in lock step:
 // entry r of the bucket at group position l sits at base[group] + 32 r + l
-// (padding entries point at x = n).  The entries of each bucket are then
-// ordered so that, step by step, the 32 lanes' x fall into distinct banks
-// where the counts allow (greedy).  Entries past the kFeCap-th of a bucket
-// (in x order) go to a per-bucket overflow list.  A bucket's entries are read
-// in x order from the stable bucket sort (perm, off); the counts, group
-// bases and overflow offsets come from warp and block scans.
+// (padding entries point at x = n, the fill this kernel writes).  Entries
+// past the kFeCap-th of a bucket (in x order) go to a per-bucket overflow
+// list.  This kernel writes each group's base and count, each group
+// position's bucket, the overflow offsets (warp and block scans over the
+// bucket counts of the stable bucket sort (perm, off)) and the dealing of
+// the groups to the front-end warps; k_frontend_records then places the
+// entries of each group.
 __global__ void __launch_bounds__(1024, 1)
 k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ perm,
                   const uint32_t* __restrict__ off, uint32_t n, uint32_t ecap,
