@@ -117,8 +117,8 @@ def test_fft_route_equals_definition_and_convolution(n1, n2, n3, b, d):
 
 
 def test_fft_route_equals_convolution_at_b1024():
-    # the survey's config-1 shape scaled down in n: direct O(b^2) convolution
-    # vs the FFT route at b = 1024
+    # the plain-method shape (b = 1024, d = 1) scaled down in n: direct
+    # O(b^2) convolution vs the FFT route at b = 1024
     A, B, tab = _random_problem(64, 32, 64, 1024, 1, 7)
     cf = O.sketch_fft(A, B, tab)
     cc = O.sketch_convolution(A, B, tab)
