@@ -21,9 +21,9 @@ __global__ void k_hash_tables(Coeffs co, int d, uint32_t n, uint32_t b,
 }
 
 // Stable counting sort of x in {0..n-1} by key (bucket mod C), one block per
-// (t, side).  Counts use integer shared atomics (exact); placement walks the
-// indices in order, warp by warp, so equal keys keep increasing x: the
-// result does not depend on scheduling.
+// (t, side), C <= 1024.  Counts use integer shared atomics (exact); the
+// placement orders equal keys by warp, then by lane, i.e. by increasing x:
+// the result does not depend on scheduling.
 constexpr int kSortThreads = 1024;
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -74,23 +74,38 @@ k_bucket_sort(const uint32_t* __restrict__ hs, uint32_t n, uint32_t C,
   }
   if (threadIdx.x == 0) of[C] = run;
   __syncthreads();
+  // placement, 1024 indices per round: per warp, the count of each key
+  // among its 32 indices (match_any); per key, the offsets of the warps'
+  // runs in warp order; each index then lands at cursor + warp offset +
+  // its rank among the equal keys of its warp (x order within a key)
+  uint32_t* tot = cnt + C;                                        // C
+  uint16_t* wc = reinterpret_cast<uint16_t*>(tot + C);            // [warp][C]
   const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint32_t nwc = (kSortThreads / 32) * C;
   for (uint32_t base = 0; base < n; base += blockDim.x) {
     const uint32_t x = base + threadIdx.x;
     const bool valid = x < n;
     const uint32_t key = valid ? (tab[x] & kBucketMask) % C : 0xFFFFFFFFu;
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-      __syncthreads();
-      if (warp == w) {
-        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key);
-        if (valid) {
-          const uint32_t rank = __popc(grp & lt_mask);
-          pm[cnt[key] + rank] = x;
-        }
-        __syncwarp();
-        if (valid && lane == __ffs(grp) - 1) cnt[key] += __popc(grp);
+    for (uint32_t i = threadIdx.x; i < nwc; i += blockDim.x) wc[i] = 0;
+    __syncthreads();
+    const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key);
+    const uint32_t rank = __popc(grp & lt_mask);
+    if (valid && lane == __ffs(grp) - 1) wc[warp * C + key] = static_cast<uint16_t>(__popc(grp));
+    __syncthreads();
+    for (uint32_t z = threadIdx.x; z < C; z += blockDim.x) {
+      uint32_t acc = 0;
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        const uint32_t v = wc[w * C + z];
+        wc[w * C + z] = static_cast<uint16_t>(acc);
+        acc += v;
       }
+      tot[z] = acc;
     }
+    __syncthreads();
+    if (valid) pm[cnt[key] + wc[warp * C + key] + rank] = x;
+    __syncthreads();
+    for (uint32_t z = threadIdx.x; z < C; z += blockDim.x) cnt[z] += tot[z];
+    __syncthreads();
   }
 }
 
@@ -109,7 +124,9 @@ cudaError_t launch_hash_tables(const Coeffs& co, int d, int64_t n, int64_t b,
 
 cudaError_t launch_bucket_sort(const uint32_t* hs, int d, int64_t n, int64_t C,
                                uint32_t* perm, uint32_t* off, cudaStream_t s) {
-  const size_t smem = static_cast<size_t>(C) * sizeof(uint32_t);
+  if (C < 1 || C > kSortThreads) return cudaErrorInvalidValue;
+  // cursors and round totals (u32) and per-warp key counts (u16)
+  const size_t smem = static_cast<size_t>(C) * (2 * sizeof(uint32_t) + (kSortThreads / 32) * sizeof(uint16_t));
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
