@@ -115,6 +115,7 @@ struct SketchPlan {
   bool tmem_rec = false;    // the lock-step kernel keeps its twiddle records in tensor memory
   // workspace layout (byte offsets)
   size_t off_partial = 0, off_V = 0, off_twfe = 0, off_twC = 0, off_twR = 0;
+  size_t off_thi = 0;   // warp-specialised kernel: w_b^{i 2^tw_shift}, i < nhi
   size_t off_T = 0, off_wtab = 0;   // (wide) inverse pass buffer, bucket tables
   size_t off_dlist = 0, off_cd = 0; // (sparse) direct list + counts, FP64 direct sketch
   size_t ws_bytes = 0;
@@ -154,9 +155,11 @@ size_t fast_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi
 constexpr size_t kSmemOneBlockPerSm = 116 * 1024;
 size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int ovcap);
 bool ws_kernel_usable();
+// thi: the kernel's high twiddle table w_b^{i 2^tw_shift}, i < nhi, already
+// filled (k_twiddle_table with a high table; SketchPlan::off_thi)
 cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,
                              const void* B, int64_t ldb, int64_t n1, int64_t n2, int64_t n3,
-                             float2* partial, cudaStream_t s);
+                             float2* partial, float2* thi, cudaStream_t s);
 uint32_t read_clear_error_sketch_ws();
 cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, const void* A,
                                int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,

@@ -44,12 +44,27 @@ __device__ __forceinline__ float2 w_pow(uint64_t m, int64_t M) {
   return make_float2(c, -s);
 }
 
-// w_M^m = exp(-2 pi i m / M) for m < M, rounded from double.
-__global__ void k_twiddle_table(float2* __restrict__ tw, int M) {
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
-    double s, c;
-    sincospi(2.0 * static_cast<double>(m) / static_cast<double>(M), &s, &c);
-    tw[m] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+// w_M^m = exp(-2 pi i m / M) for m < M, rounded from double, by the first
+// ceil(M / 256) blocks; with hi != nullptr the blocks after them write
+// hi[i] = w_b^{i S} for i < nhi (the high half of the warp-specialised
+// kernel's split twiddle w_b^m = w_b^{m mod S} w_b^{(m div S) S}).
+__global__ void k_twiddle_table(float2* __restrict__ tw, int M, float2* __restrict__ hi, int S, int nhi,
+                                int64_t b) {
+  const int nbt = (M + 255) / 256;
+  if (static_cast<int>(blockIdx.x) < nbt) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += nbt * blockDim.x) {
+      double s, c;
+      sincospi(2.0 * static_cast<double>(m) / static_cast<double>(M), &s, &c);
+      tw[m] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+    }
+  } else if (hi != nullptr) {
+    const int i = (static_cast<int>(blockIdx.x) - nbt) * blockDim.x + threadIdx.x;
+    if (i < nhi) {
+      const double a = 2.0 * static_cast<double>(static_cast<int64_t>(i) * S) / static_cast<double>(b);
+      double s, c;
+      sincospi(a, &s, &c);
+      hi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+    }
   }
 }
 
@@ -366,6 +381,7 @@ int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, in
   p.off_twfe = off;    off = align256(off + static_cast<size_t>(units) * 2 * h->n * 8);  // both kernels: same size
   p.off_twC = off;     off = align256(off + static_cast<size_t>(p.C) * 8);
   p.off_twR = off;     off = align256(off + static_cast<size_t>(p.R) * 8);
+  p.off_thi = off;     off = align256(off + (p.ws ? static_cast<size_t>(p.nhi) * 8 : 0));
   p.ws_bytes = off;
   *plan = p;
   return CMS_OK;
@@ -389,11 +405,16 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   }
   {
     ProfScope prof_scope("k_twiddle_table", s);
-    k_twiddle_table<<<static_cast<unsigned>((plan.C + 255) / 256), 256, 0, s>>>(twC, static_cast<int>(plan.C));
+    // with the warp-specialised kernel's high twiddles in extra blocks
+    const int nhb = plan.ws ? (plan.nhi + 255) / 256 : 0;
+    k_twiddle_table<<<static_cast<unsigned>((plan.C + 255) / 256 + nhb), 256, 0, s>>>(
+        twC, static_cast<int>(plan.C), plan.ws ? reinterpret_cast<float2*>(ws + plan.off_thi) : nullptr,
+        1 << plan.tw_shift, plan.nhi, plan.b);
   }
   {
     ProfScope prof_scope("k_twiddle_table", s);
-    k_twiddle_table<<<static_cast<unsigned>((plan.R + 255) / 256), 256, 0, s>>>(twR, static_cast<int>(plan.R));
+    k_twiddle_table<<<static_cast<unsigned>((plan.R + 255) / 256), 256, 0, s>>>(twR, static_cast<int>(plan.R),
+                                                                                nullptr, 1, 0, plan.b);
   }
   if (!plan.fast) {
     dim3 grid(static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 64)), plan.nrows, 2 * plan.d);
@@ -406,7 +427,8 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   if (e != cudaSuccess) return e;
 
   if (plan.fast) {
-    e = plan.ws ? launch_sketch_ws(plan, h, A, lda, B, ldb, n1, n2, n3, partial, s)
+    e = plan.ws ? launch_sketch_ws(plan, h, A, lda, B, ldb, n1, n2, n3, partial,
+                                   reinterpret_cast<float2*>(ws + plan.off_thi), s)
                 : launch_sketch_fast(plan, h, A, lda, B, ldb, n1, n2, n3, partial, s);
     if (e != cudaSuccess) return e;
   } else {
@@ -466,11 +488,11 @@ cudaError_t launch_frontend_twiddles(const SketchPlan& plan, const cms_hashes* h
 cudaError_t launch_twiddle_tables(float2* twC, int C, float2* twR, int R, cudaStream_t s) {
   {
     ProfScope prof_scope("k_twiddle_table", s);
-    k_twiddle_table<<<static_cast<unsigned>((C + 255) / 256), 256, 0, s>>>(twC, C);
+    k_twiddle_table<<<static_cast<unsigned>((C + 255) / 256), 256, 0, s>>>(twC, C, nullptr, 1, 0, 1);
   }
   {
     ProfScope prof_scope("k_twiddle_table", s);
-    k_twiddle_table<<<static_cast<unsigned>((R + 255) / 256), 256, 0, s>>>(twR, R);
+    k_twiddle_table<<<static_cast<unsigned>((R + 255) / 256), 256, 0, s>>>(twR, R, nullptr, 1, 0, 1);
   }
   return cudaGetLastError();
 }

@@ -87,6 +87,7 @@ struct WsArgs {
   const uint32_t* hs;
   const uint8_t* assign;   // [t][side][32]: bucket group of (front-end warp, slot)
   float2* partial;
+  const float2* thi_g;  // w_b^{i 2^tw_shift}, i < nhi (k_twiddle_table, FP64)
   int ovcap;          // overflow entries whose twiddles the prologue caches
 };
 
@@ -228,12 +229,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
     sincospif(2.0f * static_cast<float>(i) / static_cast<float>(p.b), &s, &c);
     tlo[i] = make_float2(c, -s);
   }
-  for (int i = tid; i < p.nhi; i += kThreadsWs) {
-    const double a = 2.0 * static_cast<double>(static_cast<int64_t>(i) * S) / static_cast<double>(p.b);
-    double s, c;
-    sincospi(a, &s, &c);
-    thi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
-  }
+  for (int i = tid; i < p.nhi; i += kThreadsWs) thi[i] = p.thi_g[i];
   if (tid < kItems) {
     const int w = tid / kItemsFe, j = tid % kItemsFe;
     const int side = j >> 2, gi = fe_group(p, t, w, j);
@@ -644,7 +640,7 @@ size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, 
 
 cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const void* A, int64_t lda,
                              const void* B, int64_t ldb, int64_t n1, int64_t n2, int64_t n3,
-                             float2* partial, cudaStream_t s) {
+                             float2* partial, float2* thi, cudaStream_t s) {
   WsArgs a{};
   a.A = static_cast<const float*>(A);
   a.lda = lda;
@@ -671,6 +667,7 @@ cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const 
   a.hs = h->d_hs;
   a.assign = h->d_fe_assign;
   a.partial = partial;
+  a.thi_g = thi;
   a.ovcap = plan.ovcap;
   if (!ws_kernel_usable()) return cudaErrorInvalidConfiguration;
   const int smem = static_cast<int>(plan.smem);
