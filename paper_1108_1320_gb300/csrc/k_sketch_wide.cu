@@ -28,6 +28,7 @@
 // kCap entries per thread; buckets that do not fit go to a spill list that
 // every inner index walks from global memory (twiddles computed on the fly).
 #include <algorithm>
+#include <atomic>
 
 #include "cms_internal.h"
 #include "sketch_generic.cuh"
@@ -772,9 +773,10 @@ WideTables wide_tables_layout(int d, int64_t n, size_t base) {
 
 // Active clusters of the kernel's launch shape (0: it cannot run here).
 int wide_max_clusters(int dt) {
-  static int cached[2] = {-1, -1};
+  static std::atomic<int> cached[2] = {{-1}, {-1}};   // concurrent first calls store the same value
   const int i = dt == CMS_BF16 ? 1 : 0;
-  if (cached[i] >= 0) return cached[i];
+  const int c = cached[i].load(std::memory_order_relaxed);
+  if (c >= 0) return c;
   const void* fn = i ? reinterpret_cast<const void*>(k_sketch_wide<__nv_bfloat16>)
                      : reinterpret_cast<const void*>(k_sketch_wide<float>);
   const int smem = static_cast<int>(wide_smem_bytes());
@@ -794,7 +796,7 @@ int wide_max_clusters(int dt) {
     if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) nc = 0;
   }
   (void)cudaGetLastError();
-  cached[i] = nc;
+  cached[i].store(nc, std::memory_order_relaxed);
   return nc;
 }
 
