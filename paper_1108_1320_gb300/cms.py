@@ -197,6 +197,29 @@ def make_hashes(seed: int, n: int, b: int, d: int) -> Hashes:
     return Hashes.make(seed, n, b, d)
 
 
+def _check_buf(t, name: str, device, dtype=None, numel: int = 0) -> None:
+    """A caller-supplied device buffer: the library only sees its pointer, so
+    its device, dtype, layout and size are checked here."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda or t.device != torch.device(device):
+        raise ValueError(f"{name} must be a CUDA tensor on {device}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, {numel} are needed")
+
+
+def _sketch_out(c, h: "Hashes", device, dtype=torch.float32):
+    inf = h.info()
+    if c is None:
+        return torch.empty((inf["d"], inf["b"]), dtype=dtype, device=device)
+    _check_buf(c, "c", device, dtype, inf["d"] * inf["b"])
+    return c
+
+
 def _ab_args(A: torch.Tensor, B: torch.Tensor):
     if A.dim() != 2 or B.dim() != 2:
         raise ValueError("A and B must be 2-D")
@@ -206,8 +229,8 @@ def _ab_args(A: torch.Tensor, B: torch.Tensor):
         raise ValueError(f"inner dimensions differ: {n2} vs {n2b}")
     if A.dtype != B.dtype or A.dtype not in _DTYPES:
         raise ValueError("A and B must share a dtype in {float32, bfloat16, float64}")
-    if not (A.is_cuda and B.is_cuda):
-        raise ValueError("A and B must be CUDA tensors")
+    if not (A.is_cuda and B.is_cuda) or A.device != B.device:
+        raise ValueError("A and B must be CUDA tensors on one device")
     if n1 > 1 and A.stride(0) != 1:
         raise ValueError("A must be column-major (A.stride(0) == 1), e.g. X.T")
     if n3 > 1 and B.stride(1) != 1:
@@ -232,12 +255,11 @@ def sketch_product(A: torch.Tensor, B: torch.Tensor, h: Hashes, c: torch.Tensor 
                    ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """COMPRESSEDPRODUCT (Fig. 1): returns c, float32 of shape (d, b)."""
     n1, n2, n3, lda, ldb = _ab_args(A, B)
-    inf = h.info()
-    if c is None:
-        c = torch.empty((inf["d"], inf["b"]), dtype=torch.float32, device=A.device)
+    c = _sketch_out(c, h, A.device)
     need = workspace_size(h, n1, n2, n3, A.dtype)
     if ws is None:
         ws = alloc_workspace(need, A.device)
+    _check_buf(ws, "ws", A.device)
     _check(lib().cms_sketch_product(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype], h.handle,
                                     _ptr(c), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
     return c
@@ -262,9 +284,7 @@ def sketch_product_noalloc(A: torch.Tensor, B: torch.Tensor, h: Hashes,
     (shared by all calls on the device; calls overlapping on the GPU race).
     Returns c, float32 (d, b)."""
     n1, n2, n3, lda, ldb = _ab_args(A, B)
-    inf = h.info()
-    if c is None:
-        c = torch.empty((inf["d"], inf["b"]), dtype=torch.float32, device=A.device)
+    c = _sketch_out(c, h, A.device)
     _check(lib().cms_sketch_product_noalloc(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype],
                                             h.handle, _ptr(c), _stream(stream)))
     return c
@@ -297,11 +317,14 @@ def sketch_product_csr(a_colptr: torch.Tensor, a_rowidx: torch.Tensor, a_val: to
             raise ValueError("pointer arrays must be contiguous CUDA int64, index arrays int32")
     if a_val.dtype != b_val.dtype or a_val.dtype not in _DTYPES:
         raise ValueError("values must share a dtype in {float32, bfloat16, float64}")
-    inf = h.info()
-    if c is None:
-        c = torch.empty((inf["d"], inf["b"]), dtype=torch.float32, device=a_colptr.device)
+    dev = a_colptr.device
+    for t_, nm in ((a_rowidx, "a_rowidx"), (b_rowptr, "b_rowptr"), (b_colidx, "b_colidx"), (a_val, "a_val"),
+                   (b_val, "b_val")):
+        _check_buf(t_, nm, dev)
+    c = _sketch_out(c, h, dev)
     if ws is None:
-        ws = alloc_workspace(sparse_workspace_size(h, n1, n2, n3), a_colptr.device)
+        ws = alloc_workspace(sparse_workspace_size(h, n1, n2, n3), dev)
+    _check_buf(ws, "ws", dev)
     if direct_max_pairs is None:
         _check(lib().cms_sketch_product_csr(_ptr(a_colptr), _ptr(a_rowidx), _ptr(a_val), _ptr(b_rowptr),
                                             _ptr(b_colidx), _ptr(b_val), n1, n2, n3, _DTYPES[a_val.dtype],
@@ -386,11 +409,10 @@ def sketch_product_plain_f64(A: torch.Tensor, B: torch.Tensor, h: Hashes,
     n1, n2, n3, lda, ldb = _ab_args(A, B)
     if A.dtype != torch.float64:
         raise ValueError("the plain path takes float64 A and B")
-    inf = h.info()
-    if c is None:
-        c = torch.empty((inf["d"], inf["b"]), dtype=torch.float64, device=A.device)
+    c = _sketch_out(c, h, A.device, torch.float64)
     if ws is None:
         ws = alloc_workspace(plain_workspace_size(h, n1, n2, n3), A.device)
+    _check_buf(ws, "ws", A.device)
     _check(lib().cms_sketch_product_plain_f64(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, h.handle,
                                               _ptr(c), _ptr(ws), ws.numel() * ws.element_size(),
                                               _stream(stream)))
@@ -405,8 +427,14 @@ def decode(c: torch.Tensor, h: Hashes, ij: torch.Tensor, out: torch.Tensor | Non
         raise ValueError("ij must be int64 of shape (q, 2)")
     q = ij.shape[0]
     c = c.contiguous()
+    if c.dtype not in (torch.float32, torch.float64):
+        raise ValueError("c must be float32 or float64")
+    inf = h.info()
+    _check_buf(c, "c", c.device, c.dtype, inf["d"] * inf["b"])
+    _check_buf(ij, "ij", c.device)
     if out is None:
         out = torch.empty(q, dtype=c.dtype, device=c.device)
+    _check_buf(out, "out", c.device, c.dtype, q)
     if c.dtype == torch.float64:
         _check(lib().cms_decode_f64(_ptr(c), h.handle, _ptr(ij), q, _ptr(out), _stream(stream)))
     elif c.dtype == torch.float32:
@@ -420,10 +448,14 @@ def decode_dense(c: torch.Tensor, h: Hashes, n1: int, n3: int, out: torch.Tensor
                  stream=None) -> torch.Tensor:
     """All n1 x n3 estimates, row-major float32."""
     c = c.contiguous()
-    if c.dtype != torch.float32:
-        raise ValueError("c must be float32")
+    inf = h.info()
+    _check_buf(c, "c", c.device, torch.float32, inf["d"] * inf["b"])
     if out is None:
         out = torch.empty((n1, n3), dtype=torch.float32, device=c.device)
+    if (not isinstance(out, torch.Tensor) or not out.is_cuda or out.device != c.device
+            or out.dtype != torch.float32 or out.dim() != 2 or tuple(out.shape) != (n1, n3)
+            or (n3 > 1 and out.stride(1) != 1)):
+        raise ValueError("out must be a float32 CUDA tensor of shape (n1, n3) with unit column stride, on c's device")
     _check(lib().cms_decode_dense(_ptr(c), h.handle, n1, n3, _ptr(out), out.stride(0) if n1 else n3,
                                   _stream(stream)))
     return out
@@ -433,6 +465,8 @@ def remove_diagonal(A: torch.Tensor, B: torch.Tensor, h: Hashes, c: torch.Tensor
     """Sec. 3.2: turn the sketch c of AB (in place) into the sketch of AB with
     its diagonal set to zero; A, B as for sketch_product."""
     n1, n2, n3, lda, ldb = _ab_args(A, B)
+    inf = h.info()
+    _check_buf(c, "c", A.device, torch.float32, inf["d"] * inf["b"])
     _check(lib().cms_sketch_remove_diagonal(_ptr(A), lda, _ptr(B), ldb, n1, n2, n3, _DTYPES[A.dtype], h.handle,
                                             _ptr(c), _stream(stream)))
     return c
@@ -444,11 +478,14 @@ def decode_threshold(c: torch.Tensor, h: Hashes, n1: int, n3: int, tau: float, s
     for every (i, j) with |estimate| > tau in row-major order; when count
     exceeds capacity only the first capacity hits are returned."""
     dev = c.device
+    c = c.contiguous()
+    inf = h.info()
+    _check_buf(c, "c", dev, torch.float32, inf["d"] * inf["b"])
     ij = torch.empty((max(capacity, 1), 2), dtype=torch.int64, device=dev)
     val = torch.empty(max(capacity, 1), dtype=torch.float32, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     ws = torch.empty(n1 + 1, dtype=torch.int64, device=dev)
-    _check(lib().cms_decode_threshold(_ptr(c.contiguous()), h.handle, n1, n3, float(tau), 1 if skip_diagonal else 0,
+    _check(lib().cms_decode_threshold(_ptr(c), h.handle, n1, n3, float(tau), 1 if skip_diagonal else 0,
                                       _ptr(ij), _ptr(val), capacity, _ptr(cnt), _ptr(ws), ws.numel() * 8,
                                       _stream(stream)))
     q = int(cnt.item())
@@ -484,12 +521,17 @@ def find_significant(A: torch.Tensor, B: torch.Tensor, h: Hashes, delta: float, 
 def decode_significant(sketches: torch.Tensor, h: Hashes, n1: int, n3: int, delta: float, rho: int = 1,
                        capacity: int = 1 << 16, stream=None):
     """Fig. 3's decode and vote on given sketches (float32 (2 l, d, b))."""
+    sketches = sketches.contiguous()
+    inf = h.info()
+    if sketches.dim() != 3 or tuple(sketches.shape[1:]) != (inf["d"], inf["b"]) or sketches.shape[0] % 2:
+        raise ValueError("sketches must have shape (2 l, d, b)")
+    _check_buf(sketches, "sketches", sketches.device, torch.float32)
     need = _SZ()
     _check(lib().cms_significant_decode_workspace_size(h.handle, ctypes.byref(need)))
     ws = alloc_workspace(need.value, sketches.device)
     ij = torch.empty((max(capacity, 1), 2), dtype=torch.int64, device=sketches.device)
     cnt = torch.zeros(1, dtype=torch.int64, device=sketches.device)
-    _check(lib().cms_decode_significant(_ptr(sketches.contiguous()), h.handle, n1, n3, float(delta), rho, _ptr(ij),
+    _check(lib().cms_decode_significant(_ptr(sketches), h.handle, n1, n3, float(delta), rho, _ptr(ij),
                                         capacity, _ptr(cnt), _ptr(ws), ws.numel() * ws.element_size(),
                                         _stream(stream)))
     return _sorted_positions(ij, cnt, capacity)
@@ -531,9 +573,17 @@ def frobenius_estimate(A: torch.Tensor, B: torch.Tensor, seed: int, d: int, stre
 
 def merge(parts: list[torch.Tensor], out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Sum of partial sketches over disjoint inner-index ranges (linearity, eq. (1))."""
+    if not parts:
+        raise ValueError("parts is empty")
     d, b = parts[0].shape
+    dev = parts[0].device
+    for i, p_ in enumerate(parts):
+        if p_.dim() != 2 or tuple(p_.shape) != (d, b):
+            raise ValueError("parts must share one (d, b) shape")
+        _check_buf(p_, f"parts[{i}]", dev, torch.float32, d * b)
     if out is None:
-        out = torch.empty((d, b), dtype=torch.float32, device=parts[0].device)
+        out = torch.empty((d, b), dtype=torch.float32, device=dev)
+    _check_buf(out, "out", dev, torch.float32, d * b)
     arr = (ctypes.c_void_p * len(parts))(*[p.data_ptr() for p in parts])
     _check(lib().cms_merge(arr, len(parts), d, b, _ptr(out), _stream(stream)))
     return out

@@ -31,6 +31,7 @@
 // and stops waiting for copies (the results are then garbage and reported
 // as such) but still passes every named barrier, so no warp is left behind.
 #include <algorithm>
+#include <atomic>
 
 #include "cms_internal.h"
 #include "warp_fft.cuh"
@@ -622,16 +623,18 @@ uint32_t read_clear_error_sketch_ws() {
 // launched with, or the FFT warps' request would never be granted; checked
 // once against the compiled kernel's launch register count.
 bool ws_kernel_usable() {
-  static int ok = -1;
-  if (ok < 0) {
+  static std::atomic<int> ok{-1};   // concurrent first calls store the same value
+  int v = ok.load(std::memory_order_relaxed);
+  if (v < 0) {
     cudaFuncAttributes fa{};
-    ok = cudaFuncGetAttributes(&fa, k_sketch_ws) == cudaSuccess && fa.maxThreadsPerBlock >= kThreadsWs &&
-                 static_cast<int64_t>(fa.numRegs) * kThreadsWs >=
-                     static_cast<int64_t>(kFeThreads) * kRegsFe + static_cast<int64_t>(kFftThreads) * kRegsFft
-             ? 1
-             : 0;
+    v = cudaFuncGetAttributes(&fa, k_sketch_ws) == cudaSuccess && fa.maxThreadsPerBlock >= kThreadsWs &&
+                static_cast<int64_t>(fa.numRegs) * kThreadsWs >=
+                    static_cast<int64_t>(kFeThreads) * kRegsFe + static_cast<int64_t>(kFftThreads) * kRegsFft
+            ? 1
+            : 0;
+    ok.store(v, std::memory_order_relaxed);
   }
-  return ok == 1;
+  return v == 1;
 }
 
 size_t ws_smem_bytes(int npad, uint32_t ecap, int alias, int tw_shift, int nhi, int ovcap) {

@@ -310,6 +310,45 @@ def test_invalid_arguments(cms):
     h7.free()
 
 
+def test_binding_rejects_bad_buffers(cms):
+    # the library sees only pointers: the binding checks every caller buffer
+    # (device, dtype, layout, size) before a call can reach a kernel
+    n, b, d = 64, 1024, 3
+    h = cms.make_hashes(2, n, b, d)
+    A = torch.zeros((n, 8), device=dev()).T.contiguous().T
+    B = torch.zeros((8, n), device=dev())
+    c = cms.sketch_product(A, B, h)
+    bad_c = [torch.zeros((d, b - 1), device=dev()),                  # too small
+             torch.zeros((d, b), device=dev(), dtype=torch.float64),  # wrong dtype
+             torch.zeros((d, b)),                                     # host memory
+             torch.zeros((b, d), device=dev()).T]                     # not contiguous
+    for cc in bad_c:
+        with pytest.raises(ValueError):
+            cms.sketch_product(A, B, h, c=cc)
+        with pytest.raises(ValueError):
+            cms.remove_diagonal(A, B, h, cc)
+    with pytest.raises(ValueError):
+        cms.sketch_product(A, B, h, ws=torch.empty(1 << 20, dtype=torch.uint8))   # host workspace
+    with pytest.raises(ValueError):
+        cms.sketch_product(A, B.cpu(), h)                                         # B on the host
+    ij = torch.zeros((10, 2), dtype=torch.int64, device=dev())
+    with pytest.raises(ValueError):
+        cms.decode(c[:, : b // 2], h, ij)                                         # c shorter than d b
+    with pytest.raises(ValueError):
+        cms.decode(c, h, ij, out=torch.empty(9, device=dev()))                    # out too small
+    with pytest.raises(ValueError):
+        cms.decode(c, h, ij.cpu())                                                # pairs on the host
+    with pytest.raises(ValueError):
+        cms.decode_dense(c, h, n, n, out=torch.empty((n, n - 1), device=dev()))  # wrong out shape
+    with pytest.raises(ValueError):
+        cms.decode_threshold(c[:1], h, n, n, 1.0)                                 # one repetition only
+    with pytest.raises(ValueError):
+        cms.merge([c, torch.zeros((d, b - 1), device=dev())])                     # parts disagree
+    with pytest.raises(ValueError):
+        cms.merge([c], out=torch.zeros((d, b), device=dev(), dtype=torch.float64))
+    h.free()
+
+
 # ------------------------------------------------- Theorem 5, on the GPU ---
 def test_theorem5_exact_sparse_on_gpu(cms):
     n, b = 64, 1024
