@@ -49,7 +49,7 @@ constexpr int kFftWarps = kRows * 2 * kG;   // 8
 constexpr int kThreadsWs = 32 * (kFeWarps + kFftWarps);   // 512
 constexpr int kFeThreads = 32 * kFeWarps;
 constexpr int kFftThreads = 32 * kFftWarps;
-constexpr int kFlush = 16;               // groups between Kahan folds
+constexpr int kFlush = 32;               // groups between Kahan folds
 constexpr int kPitch = 33;
 constexpr int kRegion = 32 * kPitch;     // float2 per FFT region (>= kC)
 constexpr int kItems = 2 * (kC / 32);    // (side, bucket group) items: 64
