@@ -68,3 +68,34 @@ def test_reference_arm_idles_on_other_ranks(monkeypatch, capsys):
         gpus, steps, warmup = 2, 1, 3
     bench.reference_arm(A())
     assert capsys.readouterr().out == ""
+
+
+def test_roofline_bookkeeping():
+    # the algorithmic flop count of the fused step, Sec. 2.2: per repetition
+    # and inner index one packed complex length-b FFT (5 b log2 b) and the
+    # spectral multiply-accumulate (8 flops x b/2 bins), plus one inverse
+    # (2.5 b log2 b) per repetition; covariance shape: 1.127e11 per launch
+    sys.path.insert(0, ROOT)
+    import bench
+    d, K, b = 5, 4096, 65536
+    assert bench.sketch_flops(d, K, b) == d * K * (5 * b * 16 + 4 * b)
+    assert abs(bench.sketch_flops(d, K, b) - 1.1274e11) / 1.1274e11 < 1e-3
+    assert bench.total_flops(d, K, b) == bench.sketch_flops(d, K, b) + d * 2.5 * b * 16
+    assert bench.sketch_flops(3, 1, 1) == 3 * 4          # log2 1 = 0: the MAC term alone
+
+
+def test_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    # the DRAM traffic figure is reported only for the kernel source it was
+    # captured on: any change to a kernel file makes it null
+    sys.path.insert(0, ROOT)
+    import json
+    import bench
+    rec = {"source_sha": bench.kernel_source_hash(), "dram_bytes_per_launch_full": 123}
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.load_traffic() == 123
+    f.write_text(json.dumps(dict(rec, source_sha="0" * 16)))
+    assert bench.load_traffic() is None
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "absent.json"))
+    assert bench.load_traffic() is None
