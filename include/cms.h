@@ -122,6 +122,20 @@ CMS_API cms_status cms_hashes_tables(const cms_hashes* h, uint32_t* h1, int8_t* 
                              uint32_t* h2, int8_t* s2);
 
 /*
+ * cms_hashes_buckets - copy the bucket lists of repetition t and side
+ * (0: h1 over rows of A, 1: h2 over columns of B) to host buffers
+ * (synchronous; test and inspection use).  With C from cms_hashes_info:
+ *   perm uint32 [n]: 0..n-1 stably sorted by h(x) mod C (equal keys keep
+ *                    increasing x), the order the fused kernels' gather
+ *                    front ends read a bucket class in (Sec. 2.2 scatter);
+ *   off  uint32 [C + 1]: start of class z in perm; off[C] = n.
+ * Either pointer may be NULL.  Errors: CMS_ERR_INVALID_ARG (t or side out
+ * of range), CMS_ERR_UNSUPPORTED (C = 0: b is not 5-smooth, no lists).
+ */
+CMS_API cms_status cms_hashes_buckets(const cms_hashes* h, int32_t t, int32_t side, uint32_t* perm,
+                              uint32_t* off);
+
+/*
  * cms_workspace_size - bytes of device workspace cms_sketch_product needs
  * for these shapes (A n1 x n2, B n2 x n3, storage dtype dt).  Host output.
  * Errors: CMS_ERR_INVALID_ARG, CMS_ERR_UNSUPPORTED.

@@ -41,6 +41,7 @@ SIGNATURES = {
                                ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "cms_hashes_coeffs": (_I32, [_P, _I32, _P]),
     "cms_hashes_tables": (_I32, [_P, _P, _P, _P, _P]),
+    "cms_hashes_buckets": (_I32, [_P, _I32, _I32, _P, _P]),
     "cms_workspace_size": (_I32, [_P, _I64, _I64, _I64, _I32, ctypes.POINTER(_SZ)]),
     "cms_sketch_product": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P, _SZ, _P]),
     "cms_sketch_product_noalloc": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _I64, _I32, _P, _P, _P]),
@@ -180,6 +181,15 @@ class Hashes:
         _check(lib().cms_hashes_tables(self.handle, h1.ctypes.data, s1.ctypes.data, h2.ctypes.data,
                                        s2.ctypes.data))
         return h1, s1, h2, s2
+
+    def buckets(self, t: int, side: int):
+        """(perm uint32 [n], off uint32 [C + 1]): the indices of repetition t,
+        side 0 (rows of A) or 1 (columns of B), stably sorted by bucket mod C."""
+        inf = self.info()
+        perm = np.zeros(inf["n"], np.uint32)
+        off = np.zeros(max(inf["C"], 0) + 1, np.uint32)
+        _check(lib().cms_hashes_buckets(self.handle, t, side, perm.ctypes.data, off.ctypes.data))
+        return perm, off
 
     def free(self):
         if self._h:

@@ -301,6 +301,24 @@ static cms_status check_shapes(const cms_hashes* h, int64_t n1, int64_t n2, int6
   return CMS_OK;
 }
 
+cms_status cms_hashes_buckets(const cms_hashes* h, int32_t t, int32_t side, uint32_t* perm, uint32_t* off) {
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
+  if (t < 0 || t >= h->d || side < 0 || side > 1) return fail(CMS_ERR_INVALID_ARG, "t or side out of range");
+  if (h->C <= 0 || !h->d_perm || !h->d_off) return fail(CMS_ERR_UNSUPPORTED, "no bucket lists (b is not 5-smooth)");
+  cms_status st = check_device(h);
+  if (st != CMS_OK) return st;
+  const size_t ts = static_cast<size_t>(t) * 2 + static_cast<size_t>(side);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && perm)
+    e = cudaMemcpy(perm, h->d_perm + ts * h->n, static_cast<size_t>(h->n) * sizeof(uint32_t),
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && off)
+    e = cudaMemcpy(off, h->d_off + ts * (h->C + 1), static_cast<size_t>(h->C + 1) * sizeof(uint32_t),
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cms_hashes_buckets");
+  return CMS_OK;
+}
+
 cms_status cms_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3, int32_t dt,
                               size_t* bytes) {
   if (!bytes) return fail(CMS_ERR_INVALID_ARG, "bytes is NULL");

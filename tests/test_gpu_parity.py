@@ -63,6 +63,32 @@ def test_hash_tables_bit_exact(cms, seed, n, b, d):
     h.free()
 
 
+@pytest.mark.parametrize("seed,n,b,d", [(2, 2048, 65536, 5), (3, 1000, 2000, 3), (6, 70000, 1 << 20, 2),
+                                        (7, 5000, 1, 1), (8, 333, 3 * 1024, 2)])
+def test_bucket_lists_are_the_stable_sort(cms, seed, n, b, d):
+    # the gather front ends read each bucket class z = h(x) mod C in the order
+    # of a stable sort of x by z: perm and off must equal numpy's stable
+    # argsort and class counts of the oracle's tables, bit for bit
+    h = cms.make_hashes(seed, n, b, d)
+    C = h.info()["C"]
+    tab = O.make_tables(seed, n, b, d)
+    for t in range(d):
+        for side, hh in ((0, tab.h1), (1, tab.h2)):
+            perm, off = h.buckets(t, side)
+            key = np.asarray(hh[t], dtype=np.int64) % C
+            np.testing.assert_array_equal(perm, np.argsort(key, kind="stable"))
+            np.testing.assert_array_equal(off, np.concatenate([[0], np.cumsum(np.bincount(key, minlength=C))]))
+    h.free()
+
+
+def test_bucket_lists_need_a_factorisation(cms):
+    h = cms.make_hashes(1, 64, 7, 1)            # prime b: no FFT split, no lists
+    with pytest.raises(cms.CmsError) as e:
+        h.buckets(0, 0)
+    assert e.value.status == 2
+    h.free()
+
+
 def test_reseed_matches_fresh_tables(cms):
     h = cms.make_hashes(10, 3000, 4096, 3)
     h.reseed(11)
