@@ -7,13 +7,13 @@
 // never overlaps the FP32-bound FFTs.  Here the two run in different warps
 // of a 512-thread block (one block per SM):
 //
-//  * warps 8-15 (front end, 72 registers after setmaxnreg.dec): gather
+//  * warps 8-15 (front end, 64 registers after setmaxnreg.dec): gather
 //    Y[f1][z2] = sum s(x) A_xk w_b^{f1 h(x)} for two rows f1 and a group of
 //    G = 2 inner indices into one of two Y buffers.  Their per-entry
 //    twiddles live in tensor memory (TMEM), 32 columns per (side, bucket
 //    group) item; an item's count selects a fully unrolled body whose index
 //    loads, gathers and TMEM load are all in flight together;
-//  * warps 0-7 (FFT, 184 registers after setmaxnreg.inc): one length-1024
+//  * warps 0-7 (FFT, 192 registers after setmaxnreg.inc): one length-1024
 //    FFT per warp and group (row, side, inner index) from the other Y
 //    buffer, the spectral products in registers and the Kahan folds into
 //    shared memory;
@@ -55,8 +55,8 @@ constexpr int kRegion = 32 * kPitch;     // float2 per FFT region (>= kC)
 constexpr int kItems = 2 * (kC / 32);    // (side, bucket group) items: 64
 constexpr int kItemsFe = kItems / kFeWarps;   // 8 per front-end warp
 // registers per thread after setmaxnreg (launch: 65536 / 512 = 128 each)
-constexpr int kRegsFe = 72;
-constexpr int kRegsFft = 184;
+constexpr int kRegsFe = 64;
+constexpr int kRegsFft = 192;
 static_assert(kFeThreads * kRegsFe + kFftThreads * kRegsFft <= 65536, "register split exceeds the launch pool");
 // named barriers (0 is __syncthreads)
 constexpr int kBarPair = 2;              // 2..5: FFT warp pairs, 64 threads
