@@ -63,3 +63,18 @@ def test_null_arguments_are_rejected_without_cuda(lib):
 def test_build_flags_target_sm103a():
     from paper_1108_1320_gb300 import build as b
     assert "arch=compute_103a,code=sm_103a" in b.ARCH
+
+
+def test_binding_buffer_checks_without_cuda():
+    # the binding's check of caller buffers is plain Python: host tensors,
+    # wrong dtypes, non-contiguous views and short buffers are refused
+    # before any library call
+    import torch
+    from paper_1108_1320_gb300 import cms
+    with pytest.raises(TypeError):
+        cms._check_buf([1.0], "c", "cuda:0")
+    with pytest.raises(ValueError, match="CUDA"):
+        cms._check_buf(torch.zeros(8), "c", "cuda:0", torch.float32, 8)
+    meta = torch.empty((4, 8), device="meta")
+    with pytest.raises(ValueError, match="CUDA"):
+        cms._check_buf(meta, "c", "cuda:0")
