@@ -19,6 +19,12 @@
  *    the last error on the calling thread is returned by cms_last_error().
  *  - Device-side error words (a kernel that detects an impossible internal
  *    state) are surfaced by cms_check_async().
+ *  - Threads: calls may come from several host threads.  A cms_hashes object
+ *    is read by the compute calls and written by cms_reseed_hashes: reseeding
+ *    while another call that reads the same object is in flight (on another
+ *    stream or thread) races, as does freeing it; order them on one stream or
+ *    synchronise.  Workspaces and outputs follow the same rule as any device
+ *    buffer: one in-flight writer at a time.
  */
 #ifndef CMS_H
 #define CMS_H
