@@ -22,6 +22,8 @@
 #include <string>
 #include <vector>
 
+#include <unistd.h>
+
 #include "cms_internal.h"
 
 struct cms_batch {
@@ -78,10 +80,24 @@ std::map<std::string, Tuned> load_cache(const char* path) {
   return m;
 }
 
+// Written to a temporary file beside it and renamed over it, so that a
+// reader (or another process) never sees a partly written cache; the cache
+// only saves tuning time, so a failed write is dropped.
 void save_cache(const char* path, const std::map<std::string, Tuned>& m) {
   if (!path) return;
-  std::ofstream f(path, std::ios::trunc);
-  for (const auto& kv : m) f << kv.first << " " << kv.second.nkc << " " << kv.second.G << " " << kv.second.ms << "\n";
+  const std::string tmp = std::string(path) + ".tmp." + std::to_string(static_cast<long long>(getpid()));
+  {
+    std::ofstream f(tmp, std::ios::trunc);
+    if (!f) return;
+    for (const auto& kv : m)
+      f << kv.first << " " << kv.second.nkc << " " << kv.second.G << " " << kv.second.ms << "\n";
+    f.flush();
+    if (!f) {
+      std::remove(tmp.c_str());
+      return;
+    }
+  }
+  if (std::rename(tmp.c_str(), path) != 0) std::remove(tmp.c_str());
 }
 
 int num_sms(int dev) {
