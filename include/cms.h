@@ -517,6 +517,19 @@ CMS_API cms_status cms_decode_significant(const float* sketches, const cms_hashe
 CMS_API cms_status cms_merge(const float* const* parts, int32_t count, int32_t d,
                      int64_t b, float* c_out, void* stream);
 
+/*
+ * cms_selftest_wait - self-test of the failure detection.  Every wait a
+ * kernel of this library makes on another agent (a TMA copy completing an
+ * mbarrier phase) gives up after a fixed limit (2 s of %globaltimer), records
+ * that in a device word and lets the kernel finish, so that the host gets
+ * CMS_ERR_TIMEOUT instead of a hung device.  This call runs that bounded wait
+ * on a phase nothing completes (one thread, one block) on the given stream and
+ * synchronises it: it returns CMS_ERR_TIMEOUT when the wait gave up (the
+ * designed outcome, after about 2 s), CMS_ERR_DEVICE if the wait completed,
+ * CMS_ERR_CUDA if a CUDA call failed.  The device stays usable afterwards.
+ */
+CMS_API cms_status cms_selftest_wait(void* stream);
+
 /* Surface asynchronous device errors for work queued on `stream`:
  * synchronises the stream, then reads and clears the device error word. */
 CMS_API cms_status cms_check_async(void* stream);

@@ -78,6 +78,7 @@ SIGNATURES = {
     "cms_decode_dense": (_I32, [_P, _P, _I64, _I64, _P, _I64, _P]),
     "cms_merge": (_I32, [_P, _I32, _I32, _I64, _P, _P]),
     "cms_check_async": (_I32, [_P]),
+    "cms_selftest_wait": (_I32, [_P]),
     "cms_profile_enable": (_I32, [_I32]),
     "cms_profile_summary": (_I32, [_P, _SZ, ctypes.POINTER(_SZ)]),
     "cms_status_string": (ctypes.c_char_p, [_I32]),
@@ -601,6 +602,13 @@ def merge(parts: list[torch.Tensor], out: torch.Tensor | None = None, stream=Non
 
 def check_async(stream=None):
     _check(lib().cms_check_async(_stream(stream)))
+
+
+def selftest_wait(stream=None):
+    """Failure-detection self-test: the library's bounded wait on a phase that
+    nothing completes.  Raises CmsError with status CMS_ERR_TIMEOUT (5) when
+    the wait gave up, the designed outcome (about 2 s)."""
+    _check(lib().cms_selftest_wait(_stream(stream)))
 
 
 def profile_enable(on: bool = True):

@@ -815,6 +815,14 @@ cms_status cms_merge(const float* const* parts, int32_t count, int32_t d, int64_
   return CMS_OK;
 }
 
+cms_status cms_selftest_wait(void* stream) {
+  uint32_t outcome = 0;
+  const cudaError_t e = run_selftest_wait(static_cast<cudaStream_t>(stream), &outcome);
+  if (e != cudaSuccess) return cuda_fail(e, "cms_selftest_wait");
+  if (outcome == 1) return fail(CMS_ERR_TIMEOUT, "the bounded wait gave up, as designed");
+  return fail(CMS_ERR_DEVICE, "the self-test wait did not give up");
+}
+
 cms_status cms_check_async(void* stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cms_check_async");

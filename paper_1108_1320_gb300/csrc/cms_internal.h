@@ -161,6 +161,10 @@ cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const 
                              const void* B, int64_t ldb, int64_t n1, int64_t n2, int64_t n3,
                              float2* partial, float2* thi, cudaStream_t s);
 uint32_t read_clear_error_sketch_ws();
+// Failure-detection self-test: one bounded wait on an mbarrier phase that
+// nothing completes; *outcome = 1 when it gave up (designed), 2 when it
+// completed.  Synchronous on s.
+cudaError_t run_selftest_wait(cudaStream_t s, uint32_t* outcome);
 cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, const void* A,
                                int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
                                int64_t n3, float2* partial, cudaStream_t s);
