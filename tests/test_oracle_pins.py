@@ -491,3 +491,43 @@ def test_find_significant_returns_the_planted_entries():
     for rho in (1, 2):
         got = [tuple(p) for p in O.find_significant(A, B, tab, delta, rho)]
         assert got == want
+
+
+# ------------------------------------ single row and column; Parseval (FFT) --
+def test_single_row_and_column_is_one_bucket():
+    # n1 = n3 = 1: AB is the number sum_k A_0k B_k0, and every route of the
+    # sketch puts s1(0) s2(0) AB into bucket (h1(0) + h2(0)) mod b alone
+    b, d = 40, 3
+    A = W.gaussian(1, 13, 61)
+    B = W.gaussian(13, 1, 62)
+    tab = O.make_tables(63, 1, b, d)
+    ab = float(sum(A[0, k] * B[k, 0] for k in range(13)))
+    for route in (O.sketch_fft, O.sketch_definition, O.sketch_convolution):
+        c = route(A, B, tab)
+        for t in range(d):
+            z = (int(tab.h1[t][0]) + int(tab.h2[t][0])) % b
+            want = np.zeros(b)
+            want[z] = int(tab.s1[t][0]) * int(tab.s2[t][0]) * ab
+            np.testing.assert_allclose(c[t], want, rtol=1e-12, atol=1e-12)
+
+
+def test_parseval_holds_for_the_fft_route():
+    # energy of c = (1/b) x energy of the product spectrum sum_k PA_k PB_k,
+    # with the count sketches built here by loops and their spectra taken with
+    # an explicit DFT matrix (no FFT routine): pins the FFT route's inverse
+    # scaling and its real output
+    n1, n2, n3, b, d = 12, 7, 9, 24, 2
+    A, B, tab = _random_problem(n1, n2, n3, b, d, 71)
+    c = O.sketch_fft(A, B, tab)
+    F = np.exp(-2j * np.pi * np.outer(np.arange(b), np.arange(b)) / b)
+    for t in range(d):
+        spec = np.zeros(b, dtype=np.complex128)
+        for k in range(n2):
+            pa = np.zeros(b)
+            pb = np.zeros(b)
+            for i in range(n1):
+                pa[tab.h1[t][i]] += tab.s1[t][i] * A[i, k]
+            for j in range(n3):
+                pb[tab.h2[t][j]] += tab.s2[t][j] * B[k, j]
+            spec += (F @ pa) * (F @ pb)
+        assert abs(np.sum(c[t] ** 2) - np.sum(np.abs(spec) ** 2) / b) <= 1e-9 * np.sum(np.abs(spec) ** 2) / b
