@@ -210,7 +210,9 @@ CMS_API cms_status cms_sketch_product(const void* A, int64_t lda, const void* B,
  *   (the covariance shape n = 2048, b = 65536, d = 5 needs about 18 MiB).
  *   The call allocates nothing.  Its first call on a device looks up the
  *   array's device address (cudaGetSymbolAddress) with that device current;
- *   make that first call before any stream capture.
+ *   make that first call before any stream capture.  The address is cached
+ *   per device for the life of the process; it does not survive a
+ *   cudaDeviceReset (after one, reload the library before calling again).
  *   All calls on a device share the array, which keeps the previous call's
  *   contents (no part of it needs to start at zero): calls that overlap on
  *   the GPU (other streams or host threads) race and must be serialised by

@@ -292,14 +292,30 @@ cms_status cms_hashes_tables(const cms_hashes* h, uint32_t* h1, int8_t* s1, uint
 
 static cms_status check_shapes(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
                                int64_t lda, int64_t ldb) {
-  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
   if (n1 < 0 || n2 < 0 || n3 < 0) return fail(CMS_ERR_INVALID_ARG, "negative dimension");
+  if (n2 > (1LL << 31) - 1) return fail(CMS_ERR_INVALID_ARG, "n2 too large (inner indices are 32-bit)");
+  if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
   if (n1 > h->n || n3 > h->n) return fail(CMS_ERR_INVALID_ARG, "n1 and n3 must be <= the hash domain n");
-  if (n2 > (1LL << 31) - 1) return fail(CMS_ERR_INVALID_ARG, "n2 too large");
   if (lda < std::max<int64_t>(n1, 1)) return fail(CMS_ERR_INVALID_ARG, "lda < n1");
   if (ldb < std::max<int64_t>(n3, 1)) return fail(CMS_ERR_INVALID_ARG, "ldb < n3");
   return CMS_OK;
 }
+
+}  // extern "C"
+
+namespace cms {
+int check_dense_call(const cms_hashes* h, const void* A, int64_t lda, const void* B, int64_t ldb,
+                     int64_t n1, int64_t n2, int64_t n3, int32_t dt, const float* c) {
+  cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
+  if (st != CMS_OK) return st;
+  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
+  if (!c) return fail(CMS_ERR_INVALID_ARG, "c is NULL");
+  if (n2 > 0 && ((n1 > 0 && !A) || (n3 > 0 && !B))) return fail(CMS_ERR_INVALID_ARG, "A or B is NULL");
+  return check_device(h);
+}
+}  // namespace cms
+
+extern "C" {
 
 cms_status cms_hashes_buckets(const cms_hashes* h, int32_t t, int32_t side, uint32_t* perm, uint32_t* off) {
   if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
@@ -374,12 +390,7 @@ cms_status cms_plan_kernel(const void* A, int64_t lda, const void* B, int64_t ld
 cms_status cms_sketch_product(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
                               int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h, float* c,
                               void* ws, size_t ws_bytes, void* stream) {
-  cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
-  if (st != CMS_OK) return st;
-  if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
-  if (!c) return fail(CMS_ERR_INVALID_ARG, "c is NULL");
-  if (n2 > 0 && ((n1 > 0 && !A) || (n3 > 0 && !B))) return fail(CMS_ERR_INVALID_ARG, "A or B is NULL");
-  st = check_device(h);
+  cms_status st = static_cast<cms_status>(cms::check_dense_call(h, A, lda, B, ldb, n1, n2, n3, dt, c));
   if (st != CMS_OK) return st;
   DeviceProps dp = device_props(h->device);
   SketchPlan plan;

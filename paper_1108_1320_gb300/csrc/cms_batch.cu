@@ -12,6 +12,7 @@
 //   * per instance, the fixed-order reduction and inverse FFT.
 // cms_batch_run_graph captures that sequence once in a CUDA graph and
 // replays it.
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -85,7 +86,11 @@ std::map<std::string, Tuned> load_cache(const char* path) {
 // only saves tuning time, so a failed write is dropped.
 void save_cache(const char* path, const std::map<std::string, Tuned>& m) {
   if (!path) return;
-  const std::string tmp = std::string(path) + ".tmp." + std::to_string(static_cast<long long>(getpid()));
+  // process id and a process-wide counter: two batches tuning on different
+  // host threads of one process never write the same temporary file
+  static std::atomic<unsigned long long> serial{0};
+  const std::string tmp = std::string(path) + ".tmp." + std::to_string(static_cast<long long>(getpid())) + "." +
+                          std::to_string(serial.fetch_add(1));
   {
     std::ofstream f(tmp, std::ios::trunc);
     if (!f) return;

@@ -37,6 +37,16 @@ namespace cms {
 // Thread-local error text (set by the C entry points).
 void set_error(const std::string& msg);
 
+// Argument checks of the dense sketch entry points (cms_sketch_product and
+// cms_sketch_product_noalloc share them, so both refuse the same inputs with
+// the same text): hashes present, 0 <= n1, n3 <= hash domain n,
+// 0 <= n2 < 2^31 (inner indices are 32-bit in the kernels), lda >= n1,
+// ldb >= n3, a known dtype, c non-NULL, A and B non-NULL when they have
+// entries, and the current device the one the hashes live on.  Sets the
+// error text and returns its status, or CMS_OK.
+int check_dense_call(const cms_hashes* h, const void* A, int64_t lda, const void* B, int64_t ldb,
+                     int64_t n1, int64_t n2, int64_t n3, int32_t dt, const float* c);
+
 // Brackets the launches in its scope with CUDA events on stream s while
 // profiling is enabled (cms_profile_enable); a no-op otherwise.
 class ProfScope {

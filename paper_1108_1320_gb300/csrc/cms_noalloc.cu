@@ -64,25 +64,11 @@ extern "C" {
 cms_status cms_sketch_product_noalloc(const void* A, int64_t lda, const void* B, int64_t ldb,
                                       int64_t n1, int64_t n2, int64_t n3, int32_t dt,
                                       const cms_hashes* h, float* c, void* stream) {
-  if (!h) { set_error("hashes is NULL"); return CMS_ERR_INVALID_ARG; }
-  if (n1 < 0 || n2 < 0 || n3 < 0 || n1 > h->n || n3 > h->n) {
-    set_error("bad shape: need 0 <= n1, n3 <= hash domain n and n2 >= 0");
-    return CMS_ERR_INVALID_ARG;
-  }
-  if (lda < (n1 > 1 ? n1 : 1) || ldb < (n3 > 1 ? n3 : 1)) {
-    set_error("lda < n1 or ldb < n3");
-    return CMS_ERR_INVALID_ARG;
-  }
-  if (dt != CMS_F32 && dt != CMS_BF16 && dt != CMS_F64) { set_error("unknown dtype"); return CMS_ERR_INVALID_ARG; }
-  if (!c) { set_error("c is NULL"); return CMS_ERR_INVALID_ARG; }
-  if (n2 > 0 && ((n1 > 0 && !A) || (n3 > 0 && !B))) { set_error("A or B is NULL"); return CMS_ERR_INVALID_ARG; }
+  const int chk = check_dense_call(h, A, lda, B, ldb, n1, n2, n3, dt, c);
+  if (chk != CMS_OK) return static_cast<cms_status>(chk);
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) { set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e)); return CMS_ERR_CUDA; }
-  if (dev != h->device) {
-    set_error("current device differs from the device the hashes were made on");
-    return CMS_ERR_INVALID_ARG;
-  }
   int sms = 0, optin = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

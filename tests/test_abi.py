@@ -78,3 +78,50 @@ def test_binding_buffer_checks_without_cuda():
     meta = torch.empty((4, 8), device="meta")
     with pytest.raises(ValueError, match="CUDA"):
         cms._check_buf(meta, "c", "cuda:0")
+
+
+def test_package_exports_every_public_binding_function():
+    # every public function and class of the binding is reachable from the
+    # package itself (tests and users call paper_1108_1320_gb300.<name>)
+    import inspect
+
+    import paper_1108_1320_gb300 as pkg
+    from paper_1108_1320_gb300 import cms
+    public = [n for n, v in vars(cms).items()
+              if not n.startswith("_") and (inspect.isfunction(v) or inspect.isclass(v))
+              and getattr(v, "__module__", "") == cms.__name__]
+    assert public
+    missing = [n for n in public if not hasattr(pkg, n)]
+    assert not missing, f"not exported from the package: {missing}"
+    assert set(public) <= set(pkg.__all__)
+
+
+def test_every_package_attribute_the_tests_call_exists():
+    # scan the GPU test files for cms.<name> calls made on the package
+    # fixture and check each name resolves on the package
+    import glob
+
+    import paper_1108_1320_gb300 as pkg
+    names = set()
+    for path in glob.glob(os.path.join(ROOT, "tests", "test_*.py")):
+        src = open(path).read()
+        if path.endswith("test_abi.py") or "import paper_1108_1320_gb300 as m\n" not in src:
+            continue
+        names |= set(re.findall(r"\bcms\.([A-Za-z]\w+)\b", src))
+    from paper_1108_1320_gb300 import cms as binding
+    missing = [n for n in sorted(names) if not hasattr(pkg, n) and not hasattr(binding, n)]
+    assert not missing, missing
+    missing_pkg = [n for n in sorted(names) if not hasattr(pkg, n) and not n.startswith("_")]
+    assert not missing_pkg, f"tests call these on the package, which lacks them: {missing_pkg}"
+
+
+def test_noalloc_rejects_n2_beyond_32_bits_without_cuda(lib):
+    # the allocation-free entry point refuses the same shapes as the
+    # workspace one, with the same text, before any CUDA call: n2 >= 2^31
+    # (inner indices are 32-bit in the kernels) is checked before the hashes
+    for fn, extra in ((lib.cms_sketch_product_noalloc, (None,)),
+                      (lib.cms_sketch_product, (None, 0, None))):
+        assert fn(None, 1, None, 1, 1, 1 << 31, 1, 0, None, None, *extra) == 1
+        assert b"n2 too large" in lib.cms_last_error()
+        assert fn(None, 1, None, 1, 1, -1, 1, 0, None, None, *extra) == 1
+        assert b"negative dimension" in lib.cms_last_error()
