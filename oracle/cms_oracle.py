@@ -39,6 +39,9 @@ What each function follows:
   anti-diagonals.
 * ``sketch_bucket_values`` - c_t[z] for a few buckets z straight from the
   definition, one bucket at a time (for full-size spot checks).
+* ``sketch_bucket_values_rows`` - the same values for many buckets at once,
+  from A's rows and B's columns given as contiguous row arrays (the rows of
+  X^T for the covariance use), each (AB)_ij a float64 dot product.
 * ``decompress`` / ``decompress_dense`` - DECOMPRESS of Fig. 1:
   X_t = s1_t(i) s2_t(j) c_t[(h1_t(i) + h2_t(j)) mod b], median over t.  The
   median of an even number of values is the mean of the two middle ones.
@@ -269,6 +272,53 @@ def sketch_bucket_values(A: np.ndarray, B: np.ndarray, tab: Tables, t: int,
         jj = order[starts + within]
         ab = np.einsum("pk,kp->p", A[ii, :].astype(np.float64), B[:, jj].astype(np.float64))
         out[q] = np.sum(s1[ii] * s2[jj] * ab)
+    return out
+
+
+def sketch_bucket_values_rows(A_rows: np.ndarray, B_cols: np.ndarray, tab: Tables, t: int,
+                              zs: np.ndarray, chunk: int = 1024) -> np.ndarray:
+    """c_t[z] for the listed buckets z straight from the definition (Sec. 2.2).
+
+    ``A_rows[i]`` is row i of A (n1 x n2) and ``B_cols[j]`` is column j of B
+    (n2 x n3), both as C-contiguous row arrays of any float dtype.  Every pair
+    (i, j) with (h1(i) + h2(j)) mod b = z contributes s1(i) s2(j) (AB)_ij,
+    where (AB)_ij = sum_k A_ik B_kj is accumulated in float64.  The pairs of
+    all listed buckets are collected first and their dot products formed in
+    chunks, so that thousands of buckets of a large product cost one pass over
+    the needed rows.
+    """
+    n1 = A_rows.shape[0]
+    n3 = B_cols.shape[0]
+    b = tab.b
+    zs = np.asarray(zs, dtype=np.int64)
+    h1, s1 = tab.h1[t, :n1].astype(np.int64), tab.s1[t, :n1].astype(np.float64)
+    h2, s2 = tab.h2[t, :n3].astype(np.int64), tab.s2[t, :n3].astype(np.float64)
+    order = np.argsort(h2, kind="stable")
+    h2_sorted = h2[order]
+    ii_all, jj_all, qq_all = [], [], []
+    for q, z in enumerate(zs):
+        need = (z - h1) % b                      # the h2(j) that row i needs
+        lo = np.searchsorted(h2_sorted, need, side="left")
+        hi = np.searchsorted(h2_sorted, need, side="right")
+        counts = hi - lo
+        ii = np.repeat(np.arange(n1), counts)
+        if len(ii) == 0:
+            continue
+        starts = np.repeat(lo, counts)
+        within = np.arange(len(ii)) - np.repeat(np.cumsum(counts) - counts, counts)
+        ii_all.append(ii)
+        jj_all.append(order[starts + within])
+        qq_all.append(np.full(len(ii), q, dtype=np.int64))
+    out = np.zeros(len(zs), dtype=np.float64)
+    if not ii_all:
+        return out
+    ii = np.concatenate(ii_all)
+    jj = np.concatenate(jj_all)
+    qq = np.concatenate(qq_all)
+    for p0 in range(0, len(ii), chunk):
+        i_c, j_c = ii[p0:p0 + chunk], jj[p0:p0 + chunk]
+        ab = np.einsum("pk,pk->p", A_rows[i_c], B_cols[j_c], dtype=np.float64, casting="safe")
+        np.add.at(out, qq[p0:p0 + chunk], s1[i_c] * s2[j_c] * ab)
     return out
 
 

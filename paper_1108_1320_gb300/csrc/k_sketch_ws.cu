@@ -93,7 +93,7 @@ struct WsArgs {
 };
 
 struct WsLayout {
-  size_t stage, rec_x, ybuf, acc, tlo, thi, wmeta, wdst, ibase, istart, ovf, wovf, ovtw, ovx, bars, total;
+  size_t stage, rec_x, ybuf, acc, tlo, thi, wmeta, wdst, ibase, istart, wcls, wcol, ovf, wovf, ovtw, ovx, bars, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
@@ -117,6 +117,8 @@ __host__ __device__ inline WsLayout ws_layout(int npad, uint32_t ecap, int alias
   L.wdst = o;   o = al16(o + static_cast<size_t>(kFeWarps) * 32 * kItemsFe * 2);
   L.ibase = o;  o = al16(o + static_cast<size_t>(kItems) * 4);
   L.istart = o; o = al16(o + static_cast<size_t>(kItems + 1) * 4);
+  L.wcls = o;   o = al16(o + static_cast<size_t>(kFeWarps) * 16);
+  L.wcol = o;   o = al16(o + static_cast<size_t>(kItems) * 2);
   L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
   L.wovf = o;   o = al16(o + static_cast<size_t>(kFeWarps) * 4);
   L.ovtw = o;   o = al16(o + static_cast<size_t>(ovcap) * 16);
@@ -143,37 +145,123 @@ __device__ __forceinline__ int fe_group(const WsArgs& p, int t, int w, int j) {
   return p.assign[(static_cast<size_t>(t) * 2 + (j >> 2)) * (kC / 32) + w * 4 + (j & 3)];
 }
 
-// The NC padded entries of one bucket (NC = the item's count, uniform over
-// the warp): all index loads, then all gathers, then the FMAs, so that the
-// loads of the item are in flight together.
-template <int NC>
-__device__ __forceinline__ void fe_slots(const uint16_t* xp, const float* st0, const float* st1,
-                                         const uint32_t taddr, float2& a00, float2& a01, float2& a10,
-                                         float2& a11) {
-  // the item's twiddles (TMEM) load while its gathers are in flight
+// Tensor-memory loads of N consecutive columns of this thread's row into
+// r[0..N-1], without waiting (N = 4, 8, 16; the column is a multiple of N).
+template <int N>
+__device__ __forceinline__ void tmem_ld_part(uint32_t taddr, uint32_t* r) {
+  if constexpr (N == 4) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+  } else if constexpr (N == 8) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+  } else {
+    static_assert(N == 16, "4, 8 or 16 columns");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+  }
+}
+
+// The records of a chunk: NCOL = 4, 8, 12 or 16 columns from a column that
+// is a multiple of 16 (or of NCOL below 16), 20, 24, 28 or 32 columns from a
+// multiple of 32; each load starts on a multiple of its own size.
+template <int NCOL>
+__device__ __forceinline__ void tmem_ld_chunk(uint32_t taddr, uint32_t (&r)[32]) {
+  if constexpr (NCOL == 32) {
+    tmem_ld32_nowait(taddr, r);
+  } else {
+    constexpr int A16 = NCOL & 16, A8 = NCOL & 8, A4 = NCOL & 4;
+    if constexpr (A16 != 0) tmem_ld_part<16>(taddr, r);
+    if constexpr (A8 != 0) tmem_ld_part<8>(taddr + A16, r + A16);
+    if constexpr (A4 != 0) tmem_ld_part<4>(taddr + A16 + A8, r + A16 + A8);
+  }
+}
+
+// Tensor-memory footprint of a chunk of K items of count C: 32 columns for
+// C >= 5, 16 columns otherwise (C = 1 chunks hold 4 items, C = 2 chunks 2);
+// a lone item of count 1 takes 4 columns of its block.
+template <int C, int K>
+__device__ __forceinline__ constexpr int fe_chunk_cols() {
+  return C >= 5 ? 32 : (C == 1 && K == 1 ? 4 : 16);
+}
+
+// K consecutive items of count C (C padded entries per lane each): every
+// index load, gather and the tensor-memory load of the chunk are in flight
+// together, then each item's 2 x 2 sums (rows x inner indices) go to its Y
+// slot.  The first entry of a sum is a product, the rest are FMAs.
+template <int C, int K>
+__device__ __forceinline__ void fe_chunk(const uint16_t*& xp, uint32_t& tc, int& pos, const uint16_t* wd,
+                                         float2* work, const float* st0, const float* st1) {
+  constexpr int S = C * K;
   uint32_t tw[32];
-  if (NC <= 4) tmem_ld16_nowait(taddr, tw);
-  else tmem_ld32_nowait(taddr, tw);
-  int x[NC];
+  tmem_ld_chunk<4 * S>(tc, tw);
+  int x[S];
 #pragma unroll
-  for (int e = 0; e < NC; ++e) x[e] = xp[32 * e];
-  float v0[NC], v1[NC];
+  for (int e = 0; e < S; ++e) x[e] = xp[32 * e];
+  float v0[S], v1[S];
 #pragma unroll
-  for (int e = 0; e < NC; ++e) {
+  for (int e = 0; e < S; ++e) {
     v0[e] = st0[x[e]];
     v1[e] = st1[x[e]];
   }
-  if (NC <= 4) tmem_wait_ld16(tw);
+  if constexpr (4 * S <= 16) tmem_wait_ld16(tw);
   else tmem_wait_ld32(tw);
 #pragma unroll
-  for (int e = 0; e < NC; ++e) {
-    const float w0 = __uint_as_float(tw[4 * e]), w1 = __uint_as_float(tw[4 * e + 1]);
-    const float w2 = __uint_as_float(tw[4 * e + 2]), w3 = __uint_as_float(tw[4 * e + 3]);
-    a00.x = fmaf(v0[e], w0, a00.x); a00.y = fmaf(v0[e], w1, a00.y);
-    a01.x = fmaf(v1[e], w0, a01.x); a01.y = fmaf(v1[e], w1, a01.y);
-    a10.x = fmaf(v0[e], w2, a10.x); a10.y = fmaf(v0[e], w3, a10.y);
-    a11.x = fmaf(v1[e], w2, a11.x); a11.y = fmaf(v1[e], w3, a11.y);
+  for (int it = 0; it < K; ++it) {
+    float2 a00, a01, a10, a11;   // [row][k]
+#pragma unroll
+    for (int e = 0; e < C; ++e) {
+      const int q = it * C + e;
+      const float w0 = __uint_as_float(tw[4 * q]), w1 = __uint_as_float(tw[4 * q + 1]);
+      const float w2 = __uint_as_float(tw[4 * q + 2]), w3 = __uint_as_float(tw[4 * q + 3]);
+      if (e == 0) {
+        a00 = make_float2(v0[q] * w0, v0[q] * w1);
+        a01 = make_float2(v1[q] * w0, v1[q] * w1);
+        a10 = make_float2(v0[q] * w2, v0[q] * w3);
+        a11 = make_float2(v1[q] * w2, v1[q] * w3);
+      } else {
+        a00.x = fmaf(v0[q], w0, a00.x); a00.y = fmaf(v0[q], w1, a00.y);
+        a01.x = fmaf(v1[q], w0, a01.x); a01.y = fmaf(v1[q], w1, a01.y);
+        a10.x = fmaf(v0[q], w2, a10.x); a10.y = fmaf(v0[q], w3, a10.y);
+        a11.x = fmaf(v1[q], w2, a11.x); a11.y = fmaf(v1[q], w3, a11.y);
+      }
+    }
+    float2* dp = work + wd[pos + it];
+    dp[0] = a00;
+    dp[kRegion] = a01;
+    dp[2 * kG * kRegion] = a10;
+    dp[2 * kG * kRegion + kRegion] = a11;
   }
+  pos += K;
+  xp += 32 * S;
+  tc += fe_chunk_cols<C, K>();
+}
+
+// The n items of count C of a front-end warp, in chunks of 4 (C = 1) or 2
+// (C = 2) items where whole chunks remain, then one item at a time (a lone
+// item of count 2 keeps a 16-column block to itself, one of count 1 takes 4
+// columns of the last block).
+template <int C>
+__device__ __forceinline__ void fe_class(int n, const uint16_t*& xp, uint32_t& tc, int& pos, const uint16_t* wd,
+                                         float2* work, const float* st0, const float* st1) {
+  constexpr int K = C == 1 ? 4 : (C == 2 ? 2 : 1);
+  int i = 0;
+  if constexpr (K > 1) {
+#pragma unroll 1
+    for (; i + K <= n; i += K) fe_chunk<C, K>(xp, tc, pos, wd, work, st0, st1);
+  }
+#pragma unroll 1
+  for (; i < n; ++i) fe_chunk<C, 1>(xp, tc, pos, wd, work, st0, st1);
 }
 
 __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
@@ -192,6 +280,8 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);       // [fe warp][lane][item]: Y slot (row 0, k 0)
   uint32_t* ibase = reinterpret_cast<uint32_t*>(sm + L.ibase);     // [fe warp][item]: side * ecap + first record
   uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart);   // [fe warp][item]: first stream slot
+  uint8_t* wcls = reinterpret_cast<uint8_t*>(sm + L.wcls);         // [fe warp][count]: items of that count
+  uint16_t* wcol = reinterpret_cast<uint16_t*>(sm + L.wcol);       // [fe warp][item]: first TMEM column
   uint16_t* ovf = reinterpret_cast<uint16_t*>(sm + L.ovf);
   uint32_t* wovf = reinterpret_cast<uint32_t*>(sm + L.wovf);
   float4* ovtw = reinterpret_cast<float4*>(sm + L.ovtw);         // cached overflow twiddles (both rows)
@@ -269,15 +359,79 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tmem = s_tmem;
+  // each front-end warp's items in order of decreasing count (stable), so
+  // that its group loop runs one unrolled body per count class
+  {
+    int rank = 0;
+    uint32_t pm_meta = 0, pm_base = 0;
+    uint16_t pm_dst[32];
+    if (tid < kItems) {
+      const int w = tid / kItemsFe, j = tid % kItemsFe;
+      const uint32_t cj = wmeta[tid] & 0xFFu;
+#pragma unroll
+      for (int i = 0; i < kItemsFe; ++i) {
+        const uint32_t ci = wmeta[w * kItemsFe + i] & 0xFFu;
+        rank += (ci > cj || (ci == cj && i < j)) ? 1 : 0;
+      }
+      pm_meta = wmeta[tid];
+      pm_base = ibase[tid];
+#pragma unroll
+      for (int l = 0; l < 32; ++l) pm_dst[l] = wdst[(w * 32 + l) * kItemsFe + j];
+    }
+    __syncthreads();
+    if (tid < kItems) {
+      const int w = tid / kItemsFe;
+      wmeta[w * kItemsFe + rank] = pm_meta;
+      ibase[w * kItemsFe + rank] = pm_base;
+#pragma unroll
+      for (int l = 0; l < 32; ++l) wdst[(w * 32 + l) * kItemsFe + rank] = pm_dst[l];
+    }
+    __syncthreads();
+  }
   if (tid == 0) {
     uint32_t s = 0;
     for (int i = 0; i < kItems; ++i) { istart[i] = s; s += wmeta[i] & 0xFFu; }
     istart[kItems] = s;
   }
   if (tid < kFeWarps) {
-    uint32_t f = 0;
-    for (int j = 0; j < kItemsFe; ++j) f |= wmeta[tid * kItemsFe + j] >> 31;
+    uint32_t f = 0, cnt[kItemsFe];
+#pragma unroll
+    for (int j = 0; j < kItemsFe; ++j) {
+      const uint32_t m = wmeta[tid * kItemsFe + j];
+      f |= m >> 31;
+      cnt[j] = m & 0xFFu;
+    }
     wovf[tid] = f;
+    int ncls[9];
+#pragma unroll
+    for (int c = 0; c <= 8; ++c) {
+      int k = 0;
+#pragma unroll
+      for (int j = 0; j < kItemsFe; ++j) k += cnt[j] == static_cast<uint32_t>(c) ? 1 : 0;
+      ncls[c] = k;
+      wcls[tid * 16 + c] = static_cast<uint8_t>(k);
+    }
+    // tensor-memory columns of the items (decreasing count): 32 per item of
+    // count >= 5, 16 per item of count 3 or 4, 16 per pair of count 2 and
+    // per quad of count 1 (a lone pair or quad member at the start of its
+    // block), so every chunk load starts on a multiple of its size; at most
+    // 8 x 32 = 256 columns per warp
+    uint32_t col = 0;
+    int q = 0;
+#pragma unroll
+    for (int c = 8; c >= 1; --c)
+      for (int i = 0; i < ncls[c]; ++i, ++q) {
+        if (c >= 5) { wcol[tid * kItemsFe + q] = static_cast<uint16_t>(col); col += 32; }
+        else if (c >= 3) { wcol[tid * kItemsFe + q] = static_cast<uint16_t>(col); col += 16; }
+        else if (c == 2) {
+          wcol[tid * kItemsFe + q] = static_cast<uint16_t>(col + 8 * (i & 1));
+          if ((i & 1) || i + 1 == ncls[c]) col += 16;
+        } else {
+          wcol[tid * kItemsFe + q] = static_cast<uint16_t>(col + 4 * (i & 3));
+          if ((i & 3) == 3 || i + 1 == ncls[c]) col += 16;
+        }
+      }
+    for (; q < kItemsFe; ++q) wcol[tid * kItemsFe + q] = 0;
   }
   __syncthreads();
 
@@ -316,8 +470,9 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       if (ngroups > 1) issue(1);
     }
     // records: staging index of x (shared memory, stream order) and
-    // s(x) w_b^{(h(x) f1) mod b} for both rows (TMEM: item j at columns
-    // 32 j + 4 r); padding entries (x = n) read the zeroed staging tail
+    // s(x) w_b^{(h(x) f1) mod b} for both rows (TMEM: entry r of item j at
+    // column wcol[j] + 4 r); padding entries (x = n) read the zeroed staging
+    // tail
     {
       const size_t tbase = static_cast<size_t>(t) * 2 * p.ecap;
 #pragma unroll 1
@@ -340,7 +495,8 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
               if (hv >> 31) { tw[rr].x = -tw[rr].x; tw[rr].y = -tw[rr].y; }
             }
           }
-          tmem_st4(tq + 32u * j + 4u * r, make_float4(tw[0].x, tw[0].y, tw[1].x, tw[1].y));
+          tmem_st4(tq + static_cast<uint32_t>(wcol[w * kItemsFe + j]) + 4u * r,
+                   make_float4(tw[0].x, tw[0].y, tw[1].x, tw[1].y));
           const uint32_t xs = min(x, static_cast<uint32_t>(n));
           rec_x[(s0 + r) * 32u + lane] =
               static_cast<uint16_t>((p.alias ? 0u : side * kG * static_cast<uint32_t>(p.npad)) + xs);
@@ -376,38 +532,28 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       const float* st0 = stage + b * sbuf;
       const float* st1 = st0 + p.npad;
       float2* work = ybuf + static_cast<size_t>(b) * kFftWarps * kRegion;
+      // the items by count class, largest first (the order of the records)
       const uint16_t* xp = xbase;
-      // one item: gather its (padded) entries, store the 2 x 2 sums
-      auto item = [&](uint32_t m, uint32_t dst, uint32_t taddr) {
-        const uint32_t cnt = m & 0xFFu;
-        float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;   // [row][k]
-        switch (cnt) {
-          case 1: fe_slots<1>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
-          case 2: fe_slots<2>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
-          case 3: fe_slots<3>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
-          case 4: fe_slots<4>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
-          case 5: fe_slots<5>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
-          case 6: fe_slots<6>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
-          case 7: fe_slots<7>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
-          case 8: fe_slots<8>(xp, st0, st1, taddr, a00, a01, a10, a11); break;
-          default: break;   // an empty bucket group
-        }
-        xp += 32u * cnt;
-        float2* dp = work + dst;
-        dp[0] = a00;
-        dp[kRegion] = a01;
-        dp[2 * kG * kRegion] = a10;
-        dp[2 * kG * kRegion + kRegion] = a11;
-      };
-      // the next item's metadata loads while the current one is processed
-      uint32_t mA = wm[0], dA = wd[0];
+      uint32_t tc = tq;
+      int pos = 0;
+      const uint8_t* ncl = wcls + w * 16;
+      fe_class<8>(ncl[8], xp, tc, pos, wd, work, st0, st1);
+      fe_class<7>(ncl[7], xp, tc, pos, wd, work, st0, st1);
+      fe_class<6>(ncl[6], xp, tc, pos, wd, work, st0, st1);
+      fe_class<5>(ncl[5], xp, tc, pos, wd, work, st0, st1);
+      fe_class<4>(ncl[4], xp, tc, pos, wd, work, st0, st1);
+      fe_class<3>(ncl[3], xp, tc, pos, wd, work, st0, st1);
+      fe_class<2>(ncl[2], xp, tc, pos, wd, work, st0, st1);
+      fe_class<1>(ncl[1], xp, tc, pos, wd, work, st0, st1);
+      // empty bucket groups: zeros
 #pragma unroll 1
-      for (int j = 0; j < kItemsFe; ++j) {
-        const uint32_t mB = j + 1 < kItemsFe ? wm[j + 1] : 0u;
-        const uint32_t dB = j + 1 < kItemsFe ? wd[j + 1] : 0u;
-        item(mA, dA, tq + 32u * j);
-        mA = mB;
-        dA = dB;
+      for (; pos < kItemsFe; ++pos) {
+        float2* dp = work + wd[pos];
+        const float2 z = make_float2(0.f, 0.f);
+        dp[0] = z;
+        dp[kRegion] = z;
+        dp[2 * kG * kRegion] = z;
+        dp[2 * kG * kRegion + kRegion] = z;
       }
       // entries past the capped count of some bucket (rare): the lane that
       // stored the bucket's Y adds them, with on-the-fly twiddles

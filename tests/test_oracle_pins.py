@@ -134,6 +134,24 @@ def test_bucket_values_match_full_definition():
                                    rtol=1e-12, atol=1e-12)
 
 
+def test_batched_bucket_values_match_full_definition():
+    # the many-bucket form (rows of A and columns of B, chunked dot products)
+    # gives every bucket of the definition, with chunks that split buckets,
+    # float32 rows widened exactly, and a bucket list with repeats
+    A, B, tab = _random_problem(61, 23, 47, 96, 3, 5)
+    cd = O.sketch_definition(A, B, tab)
+    zs = np.array(list(range(96)) + [7, 7])
+    for t in range(3):
+        got = O.sketch_bucket_values_rows(np.ascontiguousarray(A), np.ascontiguousarray(B.T), tab, t, zs,
+                                          chunk=17)
+        np.testing.assert_allclose(got, cd[t, zs], rtol=1e-12, atol=1e-12 * np.abs(cd).max())
+    A32, B32 = A.astype(np.float32), B.astype(np.float32)
+    cd32 = O.sketch_definition(A32.astype(np.float64), B32.astype(np.float64), tab)
+    got = O.sketch_bucket_values_rows(np.ascontiguousarray(A32), np.ascontiguousarray(B32.T), tab, 1,
+                                      np.arange(96))
+    np.testing.assert_allclose(got, cd32[1], rtol=1e-12, atol=1e-12 * np.abs(cd32).max())
+
+
 # ------------------------------------------- special cases -> brute force ---
 def test_injective_hash_gives_exact_product():
     # h1(i) = i, h2(j) = n1 j, b = n1 n3: every (i, j) has its own bucket
