@@ -448,17 +448,12 @@ cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t* a_rowi
   int32_t* klist = reinterpret_cast<int32_t*>(w + off_klist);
   int32_t* dlist = reinterpret_cast<int32_t*>(w + worst.off_dlist);
   int32_t* counts = dlist + std::max<int64_t>(n2, 1);
-  int32_t K = 0;
-  cudaError_t e = cudaSuccess;
-  if (n2 > 0) {
-    e = launch_nonempty_split(a_colptr, b_rowptr, n2, -1, klist, dlist, counts, counts + 2, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&K, counts, sizeof(K), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr (nonempty inner indices)");
-  }
-  SketchPlan plan;
-  r = make_sparse_plan(h, n2, K, dp.sms, &plan, &off_klist, &why);
-  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  // the list of nonempty inner indices and its length stay on the device:
+  // the FFT route runs the plan's worst-case chunking and reads the length
+  // there, so the call returns without waiting for the GPU
+  cudaError_t e = launch_nonempty_split(a_colptr, b_rowptr, n2, -1, klist, dlist, counts, counts + 2, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr (nonempty inner indices)");
+  const SketchPlan& plan = worst;
   float2* partial = reinterpret_cast<float2*>(w + plan.off_partial);
   float2* V = reinterpret_cast<float2*>(w + plan.off_V);
   float2* twC = reinterpret_cast<float2*>(w + plan.off_twC);
@@ -466,7 +461,7 @@ cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t* a_rowi
   SparseArgsHost in{a_colptr, a_rowidx, a_val, b_rowptr, b_colidx, b_val, static_cast<int>(n1),
                     static_cast<int>(n3)};
   e = launch_twiddle_tables(twC, static_cast<int>(plan.C), twR, static_cast<int>(plan.R), s);
-  if (e == cudaSuccess) e = launch_sketch_sparse(plan, h, in, dt, klist, K, partial, s);
+  if (e == cudaSuccess) e = launch_sketch_sparse(plan, h, in, dt, klist, counts, 0, partial, s);
   if (e == cudaSuccess) e = launch_inverse(plan, partial, V, twC, twR, c, s);
   if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr");
   return CMS_OK;
@@ -506,31 +501,24 @@ cms_status cms_sketch_product_csr_hybrid(const int64_t* a_colptr, const int32_t*
   int32_t* dlist = reinterpret_cast<int32_t*>(w + worst.off_dlist);
   int32_t* counts = dlist + std::max<int64_t>(n2, 1);
   double* cd = reinterpret_cast<double*>(w + worst.off_cd);
-  int32_t K[2] = {0, 0};
-  cudaError_t e = cudaSuccess;
-  if (n2 > 0) {
-    e = launch_nonempty_split(a_colptr, b_rowptr, n2, limit, flist, dlist, counts, counts + 2, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(K, counts, sizeof(K), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  } else {
-    e = cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t), s);
-  }
+  // both lists and their lengths stay on the device (no host wait): the FFT
+  // route and the inverse return at once when its list is empty, and the
+  // direct scatter strides over the direct list's length
+  cudaError_t e = launch_nonempty_split(a_colptr, b_rowptr, n2, limit, flist, dlist, counts, counts + 2, s);
   if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr_hybrid (inner-index split)");
-  SketchPlan plan;
-  r = make_sparse_plan(h, n2, K[0], dp.sms, &plan, &off_klist, &why);
-  if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
+  const SketchPlan& plan = worst;
   SparseArgsHost in{a_colptr, a_rowidx, a_val, b_rowptr, b_colidx, b_val, static_cast<int>(n1),
                     static_cast<int>(n3)};
-  if (K[0] > 0) {
+  {
     float2* partial = reinterpret_cast<float2*>(w + plan.off_partial);
     float2* V = reinterpret_cast<float2*>(w + plan.off_V);
     float2* twC = reinterpret_cast<float2*>(w + plan.off_twC);
     float2* twR = reinterpret_cast<float2*>(w + plan.off_twR);
     e = launch_twiddle_tables(twC, static_cast<int>(plan.C), twR, static_cast<int>(plan.R), s);
-    if (e == cudaSuccess) e = launch_sketch_sparse(plan, h, in, dt, flist, K[0], partial, s);
-    if (e == cudaSuccess) e = launch_inverse(plan, partial, V, twC, twR, c, s);
+    if (e == cudaSuccess) e = launch_sketch_sparse(plan, h, in, dt, flist, counts, 1, partial, s);
+    if (e == cudaSuccess) e = launch_inverse(plan, partial, V, twC, twR, c, s, counts);
   }
-  if (e == cudaSuccess) e = launch_direct_scatter(h, in, dt, dlist, counts, K[1], cd, s);
+  if (e == cudaSuccess) e = launch_direct_scatter(h, in, dt, dlist, counts, n2, cd, s);
   if (e == cudaSuccess) e = launch_add_direct(c, cd, static_cast<int64_t>(h->d) * h->b, counts, s);
   if (e != cudaSuccess) return cuda_fail(e, "cms_sketch_product_csr_hybrid");
   return CMS_OK;

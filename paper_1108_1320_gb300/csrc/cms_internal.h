@@ -150,7 +150,8 @@ cudaError_t launch_inverse_wide(const SketchPlan& plan, const float2* partial, f
 uint32_t read_clear_error_sketch_wide();
 // K2b alone: real inverse length-R DFT over the rows, 1/b.
 cudaError_t launch_cols_inverse(const SketchPlan& plan, const float2* V, const float2* twR, float* c,
-                                cudaStream_t s);
+                                cudaStream_t s,
+                                const int32_t* skip_if_zero = nullptr);
 
 bool choose_factorisation(int64_t b, int64_t* R, int64_t* C);
 int make_sketch_plan(const cms_hashes* h, int64_t n1, int64_t n2, int64_t n3,
@@ -186,8 +187,11 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h,
 
 // Fixed-order reduction of the k-range partials, inverse FFT, 1/b (K2a, K2b);
 // twC / twR must hold w_C^m and w_R^m (launch_twiddle_tables).
+// skip_if_zero (device, optional): when it holds 0 every block returns and c
+// is left as it is.
 cudaError_t launch_inverse(const SketchPlan& plan, const float2* partial, float2* V, const float2* twC,
-                           const float2* twR, float* c, cudaStream_t s);
+                           const float2* twR, float* c, cudaStream_t s,
+                           const int32_t* skip_if_zero = nullptr);
 cudaError_t launch_twiddle_tables(float2* twC, int C, float2* twR, int R, cudaStream_t s);
 cudaError_t launch_frontend_twiddles(const SketchPlan& plan, const cms_hashes* h, char* ws, cudaStream_t s);
 
@@ -212,11 +216,17 @@ int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, Sk
 // scratch holds 2 x 1024 ints.
 cudaError_t launch_nonempty_split(const int64_t* a_ptr, const int64_t* b_ptr, int64_t n2, int64_t limit,
                                   int32_t* flist, int32_t* dlist, int32_t* counts, int32_t* scratch, cudaStream_t s);
+// The direct list's length is read on the device (counts[1]); n2 bounds it.
 cudaError_t launch_direct_scatter(const cms_hashes* h, const SparseArgsHost& in, int dt, const int32_t* dlist,
-                                  const int32_t* counts, int Kd, double* cd, cudaStream_t s);
+                                  const int32_t* counts, int64_t n2, double* cd, cudaStream_t s);
 cudaError_t launch_add_direct(float* c, const double* cd, int64_t len, const int32_t* counts, cudaStream_t s);
+// FFT route over the nonempty inner indices klist[0..*kcount) (the length is
+// read on the device, so the call needs no host wait); plan.nkc chunks per
+// (repetition, row), trailing ones empty.  skip_empty: blocks return at once
+// when the list is empty (the caller's inverse then skips too).
 cudaError_t launch_sketch_sparse(const SketchPlan& plan, const cms_hashes* h, const SparseArgsHost& in,
-                                 int dt, const int32_t* klist, int K, float2* partial, cudaStream_t s);
+                                 int dt, const int32_t* klist, const int32_t* kcount, int skip_empty,
+                                 float2* partial, cudaStream_t s);
 
 cudaError_t launch_decode_pairs_f32(const float* c, const cms_hashes* h,
                                     const int64_t* ij, int64_t q, float* out,

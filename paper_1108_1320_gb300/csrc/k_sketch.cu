@@ -103,6 +103,7 @@ struct InvArgs {
   const float2* partial;
   const float2* twC;
   float2* V;
+  const int32_t* skip_if_zero;   // optional: return at once when it holds 0
 };
 
 // s + e += x with the rounding error of each add carried in e (Neumaier's
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(InvArgs p) {
   float2* twC = sm2;
   float2* P = twC + C;
   float2* Q = P + C;
+  if (p.skip_if_zero && *p.skip_if_zero == 0) return;
   const int tr = blockIdx.x;   // t * nrows + f1
   const int f1 = tr % p.nrows;
   for (int i = threadIdx.x; i < C; i += blockDim.x) twC[i] = p.twC[i];
@@ -152,7 +154,8 @@ __global__ void __launch_bounds__(256) k_rows_inverse(InvArgs p) {
 // above R/2 taken as conjugates of rows below it.
 __global__ void __launch_bounds__(256)
 k_cols_inverse(const float2* __restrict__ V, const float2* __restrict__ twR, int64_t b,
-               int R, int C, int nrows, float* __restrict__ c) {
+               int R, int C, int nrows, float* __restrict__ c, const int32_t* __restrict__ skip_if_zero) {
+  if (skip_if_zero && *skip_if_zero == 0) return;
   const int t = blockIdx.y;
   const int64_t z = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (z >= b) return;
@@ -498,14 +501,14 @@ cudaError_t launch_twiddle_tables(float2* twC, int C, float2* twR, int R, cudaSt
 }
 
 cudaError_t launch_inverse(const SketchPlan& plan, const float2* partial, float2* V, const float2* twC,
-                           const float2* twR, float* c, cudaStream_t s) {
+                           const float2* twR, float* c, cudaStream_t s, const int32_t* skip_if_zero) {
   cudaError_t e = cudaSuccess;
   InvArgs ia{};
   ia.b = plan.b; ia.R = static_cast<int>(plan.R); ia.C = static_cast<int>(plan.C);
   ia.nrows = plan.nrows; ia.d = plan.d; ia.nkc = plan.nkc;
   ia.nradC = plan.nradC;
   for (int i = 0; i < 16; ++i) ia.radC[i] = plan.radC[i];
-  ia.partial = partial; ia.twC = twC; ia.V = V;
+  ia.partial = partial; ia.twC = twC; ia.V = V; ia.skip_if_zero = skip_if_zero;
   const int smem2 = static_cast<int>(3 * plan.C * 8);
   if (smem2 > 48 * 1024) {
     e = cudaFuncSetAttribute(k_rows_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
@@ -517,16 +520,16 @@ cudaError_t launch_inverse(const SketchPlan& plan, const float2* partial, float2
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_cols_inverse(plan, V, twR, c, s);
+  return launch_cols_inverse(plan, V, twR, c, s, skip_if_zero);
 }
 
 cudaError_t launch_cols_inverse(const SketchPlan& plan, const float2* V, const float2* twR, float* c,
-                                cudaStream_t s) {
+                                cudaStream_t s, const int32_t* skip_if_zero) {
   dim3 g2(static_cast<unsigned>((plan.b + 255) / 256), plan.d);
   {
     ProfScope prof_scope("k_cols_inverse", s);
     k_cols_inverse<<<g2, 256, 0, s>>>(V, twR, plan.b, static_cast<int>(plan.R), static_cast<int>(plan.C),
-                                      plan.nrows, c);
+                                      plan.nrows, c, skip_if_zero);
   }
   return cudaGetLastError();
 }

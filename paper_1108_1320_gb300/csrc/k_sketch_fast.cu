@@ -803,7 +803,7 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
   if (e != cudaSuccess) return e;
   const unsigned ntask = static_cast<unsigned>(static_cast<int64_t>(plan.d) * a.nunits * plan.nkc);
   {
-    ProfScope prof_scope("k_sketch_fused", s);
+    ProfScope prof_scope("k_sketch_fast", s);
     if (bf) k_sketch_fast<__nv_bfloat16><<<ntask, kThreads, smem, s>>>(a);
     else k_sketch_fast<float><<<ntask, kThreads, smem, s>>>(a);
   }

@@ -42,9 +42,10 @@ struct SparseArgs {
   int n;
   int64_t b;
   int nrows;
-  int kchunk, nkc;
+  int nkc;                     // k-chunks per (repetition, row): fixed by the launch
   const int32_t* klist;
-  int K;
+  const int32_t* kcount;       // device: length of klist (written by the split kernels)
+  int skip_empty;              // 1: a block returns at once when the list is empty
   const uint32_t* hs;
   int tw_shift, nhi;
   float2* partial;
@@ -82,8 +83,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
   const uint32_t f1 = static_cast<uint32_t>(row);
   const int S = 1 << p.tw_shift;
   const ModB modb = make_modb(p.b);
-  const int l_begin = kc * p.kchunk;
-  const int l_end = min(p.K, l_begin + p.kchunk);
+  // the chunking follows the list length found on the device: nkc chunks of
+  // a whole number of groups; trailing chunks may be empty (zero partials)
+  const int K = *p.kcount;
+  if (p.skip_empty && K == 0) return;
+  const int kchunk = max(kG, ((K + p.nkc - 1) / p.nkc + kG - 1) / kG * kG);
+  const int l_begin = min(K, kc * kchunk);
+  const int l_end = min(K, l_begin + kchunk);
 
   for (int i = tid; i < S; i += kThreads) {
     float s, c;
@@ -498,10 +504,12 @@ cudaError_t launch_nonempty_split(const int64_t* a_ptr, const int64_t* b_ptr, in
 }
 
 cudaError_t launch_direct_scatter(const cms_hashes* h, const SparseArgsHost& in, int dt, const int32_t* dlist,
-                                  const int32_t* counts, int Kd, double* cd, cudaStream_t s) {
+                                  const int32_t* counts, int64_t n2, double* cd, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(cd, 0, static_cast<size_t>(h->d) * h->b * sizeof(double), s);
-  if (e != cudaSuccess || Kd == 0) return e;
-  const unsigned grid = static_cast<unsigned>(std::min(Kd, 65535));
+  if (e != cudaSuccess || n2 <= 0) return e;
+  // the list length is on the device: blocks stride over it and those past
+  // its end return at once
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>(n2, 4096));
   ProfScope prof_scope("k_direct_scatter", s);
   switch (dt) {
     case CMS_F32:
@@ -532,7 +540,8 @@ cudaError_t launch_add_direct(float* c, const double* cd, int64_t len, const int
 }
 
 cudaError_t launch_sketch_sparse(const SketchPlan& plan, const cms_hashes* h, const SparseArgsHost& in,
-                                 int dt, const int32_t* klist, int K, float2* partial, cudaStream_t s) {
+                                 int dt, const int32_t* klist, const int32_t* kcount, int skip_empty,
+                                 float2* partial, cudaStream_t s) {
   SparseArgs a{};
   a.ptr0 = in.a_ptr; a.ptr1 = in.b_ptr;
   a.idx0 = in.a_idx; a.idx1 = in.b_idx;
@@ -541,10 +550,10 @@ cudaError_t launch_sketch_sparse(const SketchPlan& plan, const cms_hashes* h, co
   a.nside0 = in.n1; a.nside1 = in.n3;
   a.b = plan.b;
   a.nrows = plan.nrows;
-  a.kchunk = static_cast<int>(plan.kchunk);
   a.nkc = plan.nkc;
   a.klist = klist;
-  a.K = K;
+  a.kcount = kcount;
+  a.skip_empty = skip_empty;
   a.hs = h->d_hs;
   a.tw_shift = plan.tw_shift;
   a.nhi = plan.nhi;

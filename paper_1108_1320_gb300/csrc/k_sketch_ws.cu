@@ -824,7 +824,7 @@ cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const 
   if (e != cudaSuccess) return e;
   const unsigned ntask = static_cast<unsigned>(static_cast<int64_t>(plan.d) * a.nunits * plan.nkc);
   {
-    ProfScope prof_scope("k_sketch_fused", s);
+    ProfScope prof_scope("k_sketch_ws", s);
     k_sketch_ws<<<ntask, kThreadsWs, smem, s>>>(a);
   }
   return cudaGetLastError();

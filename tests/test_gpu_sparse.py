@@ -143,8 +143,10 @@ def test_hybrid_blocks_exact(cms, limit):
     ref = O.sketch_definition_sparse(A, B, O.make_tables(7 + b, n, b, d))
     np.testing.assert_array_equal(np.rint(c), ref)
     assert O.rel_l2(c, ref) < 1e-5
-    assert ("k_sketch_sparse" in kernels) == (limit == 0)
-    assert (kernels.get("k_direct_scatter", {}).get("launches", 0) > 0) == (limit != 0)
+    # the split is made on the device (the call never waits for it): both
+    # routes' kernels launch, and the one whose list is empty returns at once
+    assert kernels["k_sketch_sparse"]["launches"] == 1
+    assert kernels["k_direct_scatter"]["launches"] == 1
     h.free()
 
 
@@ -198,7 +200,59 @@ def test_hybrid_exact_sparse_full_size(cms):
     A, B = sb.scipy()
     h = cms.make_hashes(3, n, b, d)
     c, kernels = run_hybrid(cms, to_dev(sb), n, n, h, -1)
-    assert "k_sketch_sparse" not in kernels
+    # every inner index goes direct: the FFT route's blocks return at once
+    # (its full run on this configuration takes about 18 ms)
+    assert kernels["k_sketch_sparse"]["ms"] < 1.0
     ref = O.sketch_definition_sparse(A, B, O.make_tables(3, n, b, d))
     np.testing.assert_array_equal(np.rint(c), ref)
+    h.free()
+
+
+@pytest.mark.parametrize("hybrid", [False, True])
+def test_sparse_calls_return_without_waiting_and_capture_in_a_graph(cms, hybrid):
+    # the nonempty-inner-index count stays on the device: the call returns
+    # while the stream is still busy with earlier work, and the whole call can
+    # be captured in a CUDA graph whose replay gives the same (exact) sketch
+    n, b, d = 5000, 4096, 2
+    sb = W.sparse_blocks(n, n_blocks=10, inner=8, rows=32, cols=32, seed=77)
+    A, B = sb.scipy()
+    args = to_dev(sb)
+    h = cms.make_hashes(9, n, b, d)
+    ref = O.sketch_definition_sparse(A, B, O.make_tables(9, n, b, d))
+    ws = cms.alloc_workspace(cms.sparse_workspace_size(h, n, A.shape[1], n), dev())
+    c = torch.zeros((d, b), dtype=torch.float32, device=dev())
+    dmp = -1 if hybrid else None
+    s = torch.cuda.Stream(device=dev())
+    with torch.cuda.stream(s):
+        cms.sketch_product_csr(*args, n, n, h, c=c, ws=ws, stream=s, direct_max_pairs=dmp)   # warm
+        torch.cuda._sleep(200_000_000)                 # ~0.1 s of GPU time ahead of the call
+        cms.sketch_product_csr(*args, n, n, h, c=c, ws=ws, stream=s, direct_max_pairs=dmp)
+        busy = not s.query()
+    s.synchronize()
+    assert busy, "the sparse call waited for the stream"
+    np.testing.assert_array_equal(np.rint(c.cpu().numpy()), ref)
+    c.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        cms.sketch_product_csr(*args, n, n, h, c=c, ws=ws, stream=s, direct_max_pairs=dmp)
+    for _ in range(2):
+        c.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(np.rint(c.cpu().numpy()), ref)
+    cms.check_async()
+    h.free()
+
+
+def test_hybrid_with_every_inner_index_direct_or_none(cms):
+    # the FFT route's list empty (everything direct: its kernels return at
+    # once) and the direct list empty (everything on the FFT route)
+    n, b, d = 3000, 2048, 3
+    sb = W.sparse_blocks(n, n_blocks=4, inner=8, rows=32, cols=32, seed=5)
+    A, B = sb.scipy()
+    h = cms.make_hashes(3, n, b, d)
+    ref = O.sketch_definition_sparse(A, B, O.make_tables(3, n, b, d))
+    for limit in (1 << 40, 0):
+        c = cms.sketch_product_csr(*to_dev(sb), n, n, h, direct_max_pairs=limit)
+        np.testing.assert_array_equal(np.rint(c.cpu().numpy()), ref)
     h.free()
