@@ -33,7 +33,10 @@ METRIC = "A,B GB/s as % of HBM roofline; products/s fused FP32 vs plain FP64, sa
 WORKLOAD = dict(name="covariance", m=4096, n=2048, pairs=32, rho=0.5, b=65536, d=5, seed=2)
 FLUSH_BYTES = 256 << 20            # > 129 MB L2: written between timed steps
 FP32_LANES_PER_SM = 128            # Blackwell SM: 4 partitions x 32 FP32 lanes
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_sketch_fused_covariance.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_sketch_ws_covariance.json")
+# the fused sketch kernels' profiling names: warp-specialised, lock-step,
+# shared-memory (generic)
+SKETCH_KERNEL_NAMES = ("k_sketch_ws", "k_sketch_fast", "k_sketch_fused")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1108_1320_gb300", "csrc", f)
                   for f in ("k_sketch.cu", "k_sketch_fast.cu", "k_sketch_ws.cu", "warp_fft.cuh",
                             "cms_common.cuh")]
@@ -156,60 +159,166 @@ def job_value(world: int, units_per_rank: int, max_ms: float) -> float:
     return world * units_per_rank / (max_ms / 1e3)
 
 
+def shard_ranges(total: int, world: int) -> list:
+    """The inner indices 0..total-1 cut into `world` contiguous, disjoint
+    ranges in rank order (sizes differ by at most one): rank r sketches the
+    rows X[k0:k1] of its range (eq. (1): the sketch of AB is the sum over k)."""
+    q, r = divmod(total, world)
+    out, k0 = [], 0
+    for i in range(world):
+        k1 = k0 + q + (1 if i < r else 0)
+        out.append((k0, k1))
+        k0 = k1
+    return out
+
+
+def gather_in_rank_order(part, dist) -> list:
+    """Every rank's partial sketch, in rank order (one all-gather of d b
+    floats per rank); summed in that fixed order the result is the same on
+    every rank and in every run."""
+    import torch
+    parts = [torch.empty_like(part) for _ in range(dist.get_world_size())]
+    dist.all_gather(parts, part.contiguous())
+    return parts
+
+
 # --------------------------------------------------------- CPU oracle leg --
-def oracle_sample(X: np.ndarray, w: dict, k_count: int, seed: int, rows: int = 16):
-    """Time the FP64 oracle (Route F of Fig. 1 plus DECOMPRESS) on the first
-    k_count inner indices and `rows` rows of the dense decode; returns
-    (seconds, extrapolated seconds per full product)."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_warm(_):
+    from oracle import cms_oracle  # noqa: F401
+    return os.getpid()
+
+
+def _route_f_chunk(job):
+    """Pool worker: Route F (Fig. 1) of the oracle over one contiguous range of
+    inner indices (rows of X), FP64."""
+    Xs, seed, n, b, d = job
+    from oracle import cms_oracle as O
+    X64 = np.asarray(Xs, dtype=np.float64)
+    return O.sketch_fft(X64.T, X64, O.make_tables(seed, n, b, d))
+
+
+class OraclePool:
+    """The FP64 oracle's Route F on every host core: the inner indices are cut
+    into one contiguous range per process and the partial sketches summed
+    (the sketch is linear in the sum over k, eq. (1)).  The processes are
+    started with 'spawn' (the parent holds a CUDA context) and import the
+    oracle before anything is timed."""
+
+    def __init__(self, cores: int):
+        import multiprocessing as mp
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores)
+        self.pool.map(_oracle_warm, range(cores))
+
+    def sketch(self, X: np.ndarray, seed: int, w: dict, k_count: int) -> np.ndarray:
+        ranges = [r for r in np.array_split(np.arange(k_count), self.cores) if len(r)]
+        jobs = [(X[r[0]:r[-1] + 1], seed, w["n"], w["b"], w["d"]) for r in ranges]
+        return np.sum(self.pool.map(_route_f_chunk, jobs), axis=0)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_sample(pool: OraclePool, X: np.ndarray, w: dict, k_count: int, seed: int, rows: int = 16):
+    """Time the oracle (Route F over the first k_count inner indices on all
+    host cores, then DECOMPRESS of `rows` rows of the dense decode on one);
+    returns (c of the sample, sketch seconds, decode seconds, extrapolated
+    seconds per full product)."""
     from oracle import cms_oracle as O
     n, b, d = w["n"], w["b"], w["d"]
-    Xs = X[:k_count].astype(np.float64)
-    tab = O.make_tables(seed, n, b, d)
     t0 = time.perf_counter()
-    c = O.sketch_fft(Xs.T, Xs, tab)
+    c = pool.sketch(X, seed, w, k_count)
     t1 = time.perf_counter()
-    O.decompress_dense(c, tab, rows, n)
+    O.decompress_dense(c, O.make_tables(seed, n, b, d), rows, n)
     t2 = time.perf_counter()
     per_product = (t1 - t0) * (w["m"] / k_count) + (t2 - t1) * (n / rows)
-    return t2 - t0, per_product
+    return c, t1 - t0, t2 - t1, per_product
 
 
-def cpu_baseline(X: np.ndarray, w: dict, budget_s: float = 12.0) -> dict:
-    # calibrate on a small sample, then one run sized to the budget
-    _, per = oracle_sample(X, w, 4, 1)
-    k_count = int(max(4, min(w["m"], budget_s / max(per, 1e-9) * w["m"])))
-    took, per = oracle_sample(X, w, k_count, 2)
-    return {"value": 1.0 / per, "unit": "products/s", "cores": 1, "kind": "oracle",
-            "sample": f"Route F (per-k numpy FFT, FP64) over {k_count} of {w['m']} inner "
-                      f"indices and 16 of {w['n']} decode rows, scaled to one product; "
-                      f"{took:.1f} s of CPU work, single-threaded numpy"}
+def sample_size(pool: OraclePool, X: np.ndarray, w: dict, budget_s: float) -> int:
+    """Inner indices the pool sketches (plus the decode rows) in about
+    budget_s seconds: at least one per core, at most the whole product."""
+    oracle_sample(pool, X, w, pool.cores, 1)          # first calls: FFT plans, tables
+    k = 4 * pool.cores
+    _, t_sketch, t_decode, _ = oracle_sample(pool, X, w, k, 1)
+    per_k = t_sketch / k
+    return int(max(pool.cores, min(w["m"], (budget_s - t_decode) / max(per_k, 1e-9))))
+
+
+def cpu_baseline(X: np.ndarray, w: dict, budget_s: float = 12.0, gpu_sketch=None) -> dict:
+    """The oracle as it stands on every host core, on a bounded sample of the
+    workload (the whole product when the budget allows).  With gpu_sketch
+    (seed, k_count) -> c, the library's sketch of the same sample is compared
+    with the oracle's, bucket by bucket: the rounding error of the FP32 path
+    against FP64."""
+    cores = host_cores()
+    pool = OraclePool(cores)
+    try:
+        k_count = sample_size(pool, X, w, budget_s)
+        seed = 2
+        c_ref, t_sketch, t_decode, per = oracle_sample(pool, X, w, k_count, seed)
+        took = t_sketch + t_decode
+    finally:
+        pool.close()
+    out = {"value": 1.0 / per, "unit": "products/s", "cores": cores, "kind": "oracle",
+           "sample": f"Route F (per-k numpy FFT, FP64) over {k_count} of {w['m']} inner indices on "
+                     f"{cores} processes, and 16 of {w['n']} decode rows, scaled to one product; "
+                     f"{took:.1f} s wall"}
+    if gpu_sketch is not None:
+        c_gpu = np.asarray(gpu_sketch(seed, k_count), dtype=np.float64)
+        per_rep = [float(np.linalg.norm(c_gpu[t] - c_ref[t]) / np.linalg.norm(c_ref[t]))
+                   for t in range(w["d"])]
+        out["c_rel_l2_gpu_vs_oracle"] = max(per_rep)
+        out["c_rel_l2_per_rep"] = per_rep
+        out["compared"] = f"all {w['d']} x {w['b']} buckets of the sketch of X[:{k_count}] (seed {seed})"
+        out["k_count"] = k_count
+    return out
 
 
 def reference_arm(args):
-    """--impl reference: the oracle on the host cores, rank 0 only."""
+    """--impl reference: the oracle on the host cores, rank 0 only.  Every
+    step sketches a bounded sample of the covariance workload (the first
+    k_count inner indices) on all host cores; ms_per_step is that sample's
+    wall time, value the throughput scaled to whole products."""
     if int(os.environ.get("RANK", "0")) != 0:
         return
     import workloads as W
     w = WORKLOAD
     cov = W.covariance(w["m"], w["n"], w["pairs"], w["rho"], w["seed"], dtype=np.float32)
-    k_count = 16
-    times = []
-    for i in range(args.warmup + args.steps):
-        _, per = oracle_sample(cov.X, w, k_count, 100 + i)
-        if i >= args.warmup:
-            times.append(per)
-    per = statistics.mean(times)
-    value = 1.0 / per
+    cores = host_cores()
+    pool = OraclePool(cores)
+    try:
+        per_step_s = max(0.25, min(3.0, 60.0 / max(args.steps + args.warmup, 1)))
+        k_count = sample_size(pool, cov.X, w, per_step_s)
+        walls, pers = [], []
+        for i in range(args.warmup + args.steps):
+            _, t_sketch, t_decode, per = oracle_sample(pool, cov.X, w, k_count, 100 + i)
+            took = t_sketch + t_decode
+            if i >= args.warmup:
+                walls.append(took)
+                pers.append(per)
+    finally:
+        pool.close()
+    value = 1.0 / statistics.mean(pers)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "products/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": statistics.mean(walls) * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_label(), "m": w["m"], "n": w["n"], "b": w["b"], "d": w["d"],
-                   "l2": "host run"},
-        "cpu_baseline": {"value": value, "unit": "products/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: Route F over {k_count} of {w['m']} inner indices "
-                                   f"+ 16 decode rows, scaled to one product"},
+                   "pairs": w["pairs"], "rho": w["rho"], "l2": "host run"},
+        "cpu_baseline": {"value": value, "unit": "products/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step: Route F over {k_count} of {w['m']} inner indices on "
+                                   f"{cores} processes + 16 decode rows; ms_per_step is that sample's "
+                                   f"wall time, value scaled to whole products"},
         "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -286,7 +395,10 @@ def gpu_arm(args):
     launches = int(sum(v["launches"] for v in prof.values()))
 
     # ---- roofline of the dominant kernel (the fused sketch kernel) --------
-    fused = prof.get("k_sketch_fused", {"launches": 0, "ms": float("nan")})
+    # the fused sketch kernel this plan ran (each kernel has its own record)
+    fused_name = next((k for k in SKETCH_KERNEL_NAMES if prof.get(k, {}).get("launches", 0) > 0),
+                      "k_sketch_ws")
+    fused = prof.get(fused_name, {"launches": 0, "ms": float("nan")})
     fused_ms = fused["ms"] / max(fused["launches"], 1)
     props = torch.cuda.get_device_properties(dev)
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
@@ -296,7 +408,7 @@ def gpu_arm(args):
     traffic = load_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": "k_sketch_fused", "kernel_ms": fused_ms,
+                "kernel": fused_name, "kernel_ms": fused_ms,
                 "alg_flops_per_launch": alg_flops,
                 "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
                                f"lanes x 2 flop/FMA x {max_mhz:.0f} MHz (FP32 FMA pipe, not tensor)"}
@@ -317,7 +429,7 @@ def gpu_arm(args):
         "kernel_ms": {k: v["ms"] / max(v["launches"], 1) for k, v in prof.items()},
     }
     extra["step_frac_of_roofline"] = extra["roofline_time_ms"] / ms_step
-    sketch_kernels = ("k_twiddle_table", "k_frontend_twiddles", "k_sketch_fused", "k_rows_inverse",
+    sketch_kernels = ("k_twiddle_table", "k_frontend_twiddles", *SKETCH_KERNEL_NAMES, "k_rows_inverse",
                       "k_cols_inverse")
     extra["sketch_only_ms"] = sum(prof[k]["ms"] for k in sketch_kernels if k in prof) / args.steps
 
@@ -392,7 +504,150 @@ def gpu_arm(args):
     if rank == 0 and not args.no_context:
         line["context"] = context_numbers(cms, torch, X, h, c, cov, w, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cov.X, w, budget_s=args.cpu_budget)
+        def gpu_sketch(seed, k_count):
+            Xk = X[:k_count]
+            hk = cms.make_hashes(seed, n, b, d)
+            ck = cms.sketch_product(Xk.T, Xk, hk, stream=stream).cpu().numpy()
+            hk.free()
+            return ck
+        cb = cpu_baseline(cov.X, w, budget_s=args.cpu_budget, gpu_sketch=gpu_sketch)
+        line["cpu_baseline"] = cb
+        Xk = X[: cb["k_count"]].double()
+        line["rounding_error"] = {
+            "c_rel_l2_vs_fp64_oracle": cb.get("c_rel_l2_gpu_vs_oracle"),
+            "compared": cb.get("compared"),
+            "sketch_std_of_compared": float(torch.linalg.norm(Xk.T @ Xk)) / math.sqrt(b),
+            "note": "the FP32 path's c against the oracle's Route F (FP64) over the same inner indices "
+                    "and hash draw; the sketch's own standard deviation ||AB||_F / sqrt(b) beside it"}
+        del Xk
+    if rank == 0:
+        print(json.dumps(line))
+    h.free()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def gpu_arm_kshard(args):
+    """--shard k: one product shared by all ranks (Sec. 2.2 / eq. (1): the
+    sketch is linear in the sum over k).  Rank r sketches X[k0:k1] of its
+    range with the hash draw every rank makes from the same seed; the d b
+    partial sketches are all-gathered and merged in rank order (cms_merge),
+    then decoded.  One step = one product; value = products/s over the
+    slowest rank's time (strong scaling: the work per product is fixed)."""
+    import torch
+    import torch.distributed as dist
+
+    import workloads as W
+    from paper_1108_1320_gb300 import build as B
+    B.build()
+    import paper_1108_1320_gb300 as cms
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOAD
+    m, n, b, d = w["m"], w["n"], w["b"], w["d"]
+    k0, k1 = shard_ranges(m, world)[rank]
+    cov = W.covariance(m, n, w["pairs"], w["rho"], w["seed"], dtype=np.float32)
+    X_host = torch.from_numpy(np.ascontiguousarray(cov.X[k0:k1])).pin_memory()
+    Xr = X_host.to(dev)
+    h = cms.make_hashes(w["seed"], n, b, d)
+    ws = cms.alloc_workspace(cms.workspace_size(h, n, k1 - k0, n, torch.float32), dev)
+    c_part = torch.empty((d, b), dtype=torch.float32, device=dev)
+    c = torch.empty((d, b), dtype=torch.float32, device=dev)
+    est = torch.empty((n, n), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        h.reseed(7000 + i, stream)            # the same draw on every rank
+        cms.sketch_product(Xr.T, Xr, h, c=c_part, ws=ws, stream=stream)
+        parts = gather_in_rank_order(c_part, dist) if world > 1 else [c_part]
+        cms.merge(parts, out=c, stream=stream)
+        cms.decode_dense(c, h, n, n, out=est, stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    cms.check_async()
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    sampler = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
+    sampler.start()
+    cms.profile_enable(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.mark_begin()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step(args.warmup + i)
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    sampler.mark_end()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = cms.profile_summary()
+    cms.profile_enable(False)
+    cms.check_async()
+    total_ms = reduce_max(sum(a.elapsed_time(z) for a, z in zip(starts, stops)), dist if world > 1 else None,
+                          dev)
+    value = args.steps / (total_ms / 1e3)
+    fused_name = next((k for k in SKETCH_KERNEL_NAMES if prof.get(k, {}).get("launches", 0) > 0),
+                      "k_sketch_ws")
+    fused = prof.get(fused_name, {"launches": 0, "ms": float("nan")})
+    fused_ms = fused["ms"] / max(fused["launches"], 1)
+    props = torch.cuda.get_device_properties(dev)
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    achieved = sketch_flops(d, k1 - k0, b) / (fused_ms * 1e-3) / 1e12
+    # end to end: each rank's rows of X copied from pinned host memory, the
+    # merged sketch read back, inside the timed region
+    c_host = torch.empty((d, b), dtype=torch.float32).pin_memory()
+    Xe = torch.empty_like(Xr)
+    e2e_steps = max(3, min(args.steps, 50))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        Xe.copy_(X_host, non_blocking=True)
+        h.reseed(9000 + i, stream)
+        cms.sketch_product(Xe.T, Xe, h, c=c_part, ws=ws, stream=stream)
+        parts = gather_in_rank_order(c_part, dist) if world > 1 else [c_part]
+        cms.merge(parts, out=c, stream=stream)
+        c_host.copy_(c, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1), dist if world > 1 else None, dev)
+    line = {
+        "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_label(), "m": m, "n": n, "b": b, "d": d, "pairs": w["pairs"],
+                   "rho": w["rho"],
+                   "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write, outside the step events)",
+                   "parallelism": f"one product over {world} GPUs: inner indices split in contiguous ranges, "
+                                  f"partial sketches all-gathered and merged in rank order"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": fused_name, "kernel_ms": fused_ms,
+                     "note": "this rank's share of the inner indices"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_steps / (e2e_ms / 1e3), "unit": "products/s",
+                "h2d_bytes_per_step": (k1 - k0) * n * 4, "d2h_bytes_per_step": d * b * 4, "steps": e2e_steps},
+        "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+        "rank_inner_range": [k0, k1],
+    }
     if rank == 0:
         print(json.dumps(line))
     h.free()
@@ -503,11 +758,16 @@ def sparse_context(cms, torch, dev):
     cms.sketch_product_csr(*args, n, n, h, c=c, ws=ws)
     torch.cuda.synchronize()
     reps = 5
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
+    e0.record()
     for _ in range(reps):
-        cms.sketch_product_csr(*args, n, n, h, c=c, ws=ws)   # includes one host wait (nonempty-k count)
+        cms.sketch_product_csr(*args, n, n, h, c=c, ws=ws)   # no host wait inside the call
+    e1.record()
+    host_ms = (time.perf_counter() - t0) * 1e3 / reps
     torch.cuda.synchronize()
-    ms = (time.perf_counter() - t0) * 1e3 / reps
+    ms = e0.elapsed_time(e1) / reps
     K = 256 * 8
     flops = d * K * (5.0 * b * math.log2(b) + 4.0 * b) + d * 2.5 * b * math.log2(b)
     # sparse-k hybrid (default split): every outer product here has 1024
@@ -515,17 +775,24 @@ def sparse_context(cms, torch, dev):
     ch = torch.empty_like(c)
     cms.sketch_product_csr(*args, n, n, h, c=ch, ws=ws, direct_max_pairs=-1)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e0.record()
     for _ in range(reps):
         cms.sketch_product_csr(*args, n, n, h, c=ch, ws=ws, direct_max_pairs=-1)
+    e1.record()
     torch.cuda.synchronize()
-    ms_h = (time.perf_counter() - t0) * 1e3 / reps
+    ms_h = e0.elapsed_time(e1) / reps
     same = bool(torch.equal(torch.round(c), torch.round(ch)))
+    # the direct route sums exact FP64 products of the integer values, so its
+    # c is the exact sketch: the FFT route's rounding error against it
+    err = torch.linalg.norm((c.double() - ch.double()), dim=1) / torch.linalg.norm(ch.double(), dim=1)
     h.free()
     return {"workload": "exact sparse n=2^20, 256 blocks x (8 inner, 32 rows, 32 cols), b=2^20, d=3",
             "ms_per_product": ms, "products_per_s": 1e3 / ms, "nonempty_k": K,
-            "alg_tflops": flops / (ms * 1e-3) / 1e12,
-            "note": "FFT route; host wall clock per call (the call waits once for the nonempty-k count)",
+            "alg_tflops": flops / (ms * 1e-3) / 1e12, "host_ms_per_call": host_ms,
+            "c_rel_l2_vs_exact": float(err.max()),
+            "c_max_abs_err_vs_exact": float((c.double() - ch.double()).abs().max()),
+            "note": "FFT route, CUDA events (the call does not wait for the device); error against the "
+                    "direct route's exact sketch of the integer product",
             "hybrid": {"ms_per_product": ms_h, "products_per_s": 1e3 / ms_h,
                        "direct_terms": d * K * 32 * 32, "rounded_c_equal_to_fft_route": same,
                        "note": "sparse-k hybrid, default split (all inner indices direct, FP64 scatter); "
@@ -570,8 +837,41 @@ def large_context(cms, torch, dev):
            "ms_per_product": ms, "products_per_s": 1e3 / ms, "alg_tflops": flops / (ms * 1e-3) / 1e12,
            "kernels": sorted(kernels),
            "planted_pairs": {"count": npairs, "median_estimate": float(pe.median()), "expected": rho * m}}
+    # the plain FP64 form on the first ks inner indices (cost linear in them),
+    # and the fused path's rounding error against it on the same sample
+    ks = 2048
+    Xs = Xb[:ks]
+    Xd = Xs.double()
+    c32 = cms.sketch_product(Xs.T, Xs, h)
+    wsp = cms.alloc_workspace(cms.plain_workspace_size(h, n, ks, n), dev)
+    c64 = cms.sketch_product_plain_f64(Xd.T, Xd, h, ws=wsp)
+    torch.cuda.synchronize()
+    e0.record()
+    cms.sketch_product_plain_f64(Xd.T, Xd, h, c=c64, ws=wsp)
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) * (m / ks)
+    rel = torch.linalg.norm(c32.double() - c64, dim=1) / torch.linalg.norm(c64, dim=1)
+    out["plain_f64"] = {"ms_per_product": plain_ms, "products_per_s": 1e3 / plain_ms,
+                        "note": f"timed on the first {ks} of {m} inner indices, scaled (the cost is linear in them)"}
+    out["rounding_error"] = {"c_rel_l2_vs_plain_f64": float(rel.max()),
+                             "compared": f"all {d} x {b} buckets of the sketch of X[:{ks}] (BF16 values)"}
+    del Xd, wsp, c64, c32
+    # sketch standard deviation ||AB||_F / sqrt(b) of the full product, and
+    # cuBLAS SGEMM of the same shapes for context
+    X32 = Xb.float()
+    G = torch.matmul(X32.T, X32)
+    torch.cuda.synchronize()
+    e0.record()
+    torch.matmul(X32.T, X32, out=G)
+    e1.record()
+    torch.cuda.synchronize()
+    sg = e0.elapsed_time(e1)
+    out["sketch_std"] = float(torch.linalg.norm(G)) / math.sqrt(b)
+    out["sgemm"] = {"ms": sg, "tflops": 2.0 * n * n * m / (sg * 1e-3) / 1e12,
+                    "note": "torch.matmul fp32 (cuBLAS) of X^T X, X the BF16 values widened"}
     h.free()
-    del Xb, ws, c
+    del Xb, ws, c, X32, G
     torch.cuda.empty_cache()
     return out
 
@@ -611,19 +911,23 @@ def batched_context(cms, torch, dev, n_hi: int = 8192):
     graph_ms = e0.elapsed_time(e1) / reps
     # plain FP64 form: one call per instance
     plain_ms = 0.0
-    for (A, B, h), X in zip(items, xs):
-        Xd = X.double()
+    errs = []
+    for q, ((A, B, h), X) in enumerate(zip(items, xs)):
+        # the plain form of the values the batch read (BF16 instances widened)
+        Xd = B.double()
         ws = cms.alloc_workspace(cms.plain_workspace_size(h, X.shape[1], X.shape[0], X.shape[1]), dev)
-        cms.sketch_product_plain_f64(Xd.T, Xd, h, ws=ws)
+        c64 = cms.sketch_product_plain_f64(Xd.T, Xd, h, ws=ws)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         z = torch.cuda.Event(enable_timing=True)
         a.record()
-        cms.sketch_product_plain_f64(Xd.T, Xd, h, ws=ws)
+        cms.sketch_product_plain_f64(Xd.T, Xd, h, c=c64, ws=ws)
         z.record()
         torch.cuda.synchronize()
         plain_ms += a.elapsed_time(z)
-        del Xd, ws
+        cq = batch.c[q].double()
+        errs.append(float((torch.linalg.norm(cq - c64, dim=1) / torch.linalg.norm(c64, dim=1)).max()))
+        del Xd, ws, c64
     flops = sum(3 * sp.m * (5.0 * 16 * sp.n * math.log2(16 * sp.n) + 4.0 * 16 * sp.n) for sp in specs)
     batch.free()
     for _, _, h in items:
@@ -634,7 +938,11 @@ def batched_context(cms, torch, dev, n_hi: int = 8192):
             "kernel_launches_per_run": info["launches"], "fast_kernel_instances": info["fast_instances"],
             "graph_ms_per_batch": graph_ms, "products_per_s": 64 * 1e3 / graph_ms,
             "alg_tflops": flops / (graph_ms * 1e-3) / 1e12,
-            "plain_f64_ms_per_batch": plain_ms, "plain_f64_products_per_s": 64 * 1e3 / plain_ms}
+            "plain_f64_ms_per_batch": plain_ms, "plain_f64_products_per_s": 64 * 1e3 / plain_ms,
+            "rounding_error": {"c_rel_l2_vs_plain_f64_max": max(errs), "c_rel_l2_vs_plain_f64_median":
+                               statistics.median(errs),
+                               "note": "per instance, the batch's c against the plain FP64 form of the same "
+                                       "stored values (max over the repetitions)"}}
 
 
 def main():
@@ -646,11 +954,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-context", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--shard", choices=["products", "k"], default="products",
+                    help="products: every GPU computes whole, independent products (weak scaling); "
+                         "k: the GPUs share one product, each sketching its range of inner indices, "
+                         "the partial sketches merged in rank order (strong scaling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
+    elif args.shard == "k":
+        gpu_arm_kshard(args)
     else:
         gpu_arm(args)
 

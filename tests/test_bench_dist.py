@@ -99,3 +99,69 @@ def test_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     assert bench.load_traffic() is None
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "absent.json"))
     assert bench.load_traffic() is None
+
+
+def test_shard_ranges_cover_the_inner_indices_in_order():
+    sys.path.insert(0, ROOT)
+    import bench
+    for total in (0, 1, 5, 4096, 4097):
+        for world in (1, 2, 3, 8):
+            rs = bench.shard_ranges(total, world)
+            assert len(rs) == world
+            assert rs[0][0] == 0 and rs[-1][1] == total
+            for (a0, a1), (b0, b1) in zip(rs, rs[1:]):
+                assert a1 == b0                       # contiguous, disjoint, in rank order
+            sizes = [k1 - k0 for k0, k1 in rs]
+            assert min(sizes) >= 0 and max(sizes) - min(sizes) <= 1
+
+
+def _kshard_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import numpy as np
+
+    import bench
+    import workloads as W
+    from oracle import cms_oracle as O
+    m, n, b, d = 37, 24, 64, 3
+    X = W.gaussian(m, n, 11)
+    tab = O.make_tables(5, n, b, d)
+    k0, k1 = bench.shard_ranges(m, world)[rank]
+    Xr = X[k0:k1]
+    part = torch.from_numpy(O.sketch_fft(Xr.T, Xr, tab))      # this rank's partial sketch
+    parts = bench.gather_in_rank_order(part, dist)
+    merged = parts[0].clone()
+    for p_ in parts[1:]:
+        merged += p_                                           # fixed rank order
+    q.put((rank, merged.numpy()))
+    dist.destroy_process_group()
+
+
+def test_k_split_over_two_ranks_gives_the_whole_sketch():
+    # eq. (1): the sketch of AB is the sum over k of the outer products'
+    # sketches, so two ranks sketching the two halves of the inner indices
+    # and merging their partials in rank order give the whole product's
+    # sketch, the same on both ranks
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import workloads as W
+    from oracle import cms_oracle as O
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_kshard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in range(world)), key=lambda t: t[0])
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    X = W.gaussian(37, 24, 11)
+    whole = O.sketch_fft(X.T, X, O.make_tables(5, 24, 64, 3))
+    for _, merged in res:
+        assert O.rel_l2(merged, whole) < 1e-12
+    np.testing.assert_array_equal(res[0][1], res[1][1])
