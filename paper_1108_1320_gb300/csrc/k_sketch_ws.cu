@@ -31,6 +31,7 @@
 // and stops waiting for copies (the results are then garbage and reported
 // as such) but still passes every named barrier, so no warp is left behind.
 #include <algorithm>
+#include <cstdlib>
 #include <atomic>
 
 #include "cms_internal.h"
@@ -64,6 +65,11 @@ constexpr int kBarFft = 6;               // FFT warps, 256 threads
 constexpr int kBarYFull = 7;             // 7, 8: Y buffer b written (front end arrives, FFT syncs)
 constexpr int kBarYFree = 9;             // 9, 10: Y buffer b consumed (FFT arrives, front end syncs)
 constexpr int kBarFeOvf = 11;            // front-end warps: overflow cache written
+// tensor-memory columns of a lane quarter: front-end records of the two
+// front-end warps sharing it (kFeColCap each), then two 64-column buffers
+// through which the partner FFT warps of that quarter swap half spectra
+constexpr uint32_t kFeColCap = 192;
+constexpr uint32_t kXCol = 2 * kFeColCap;   // 384
 
 __device__ uint32_t g_ws_error = 0;      // 1: a wait gave up
 
@@ -90,6 +96,7 @@ struct WsArgs {
   float2* partial;
   const float2* thi_g;  // w_b^{i 2^tw_shift}, i < nhi (k_twiddle_table, FP64)
   int ovcap;          // overflow entries whose twiddles the prologue caches
+  int force_xsmem;    // debug: swap half spectra through shared memory
 };
 
 struct WsLayout {
@@ -268,6 +275,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_err;
+  __shared__ int s_xsmem;   // 1: some front-end warp needs more than kFeColCap columns
 
   const WsLayout L = ws_layout(p.npad, p.ecap, p.alias, p.tw_shift, p.nhi, p.ovcap);
   float* stage = reinterpret_cast<float*>(sm + L.stage);
@@ -312,7 +320,10 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
     tmem_alloc(&s_tmem, 512);
     tmem_relinquish();
   }
-  if (tid == 0) s_err = 0;
+  if (tid == 0) {
+    s_err = 0;
+    s_xsmem = p.force_xsmem;
+  }
 
   // ---- prologue -------------------------------------------------------------
   for (int i = tid; i < S; i += kThreadsWs) {
@@ -432,8 +443,12 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
         }
       }
     for (; q < kItemsFe; ++q) wcol[tid * kItemsFe + q] = 0;
+    // more records than the warp's share of its quarter: this block keeps
+    // the full halves for the records and swaps spectra in shared memory
+    if (col > kFeColCap) atomicOr(&s_xsmem, 1);
   }
   __syncthreads();
+  const bool xsmem = s_xsmem != 0;
 
   // TMA copies of group g into staging buffer g & 1 (thread 0 only)
   auto issue = [&](int g) {
@@ -462,8 +477,10 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsFe));
     const int w = warp - kFftWarps;
     const int fe_tid = tid - kFftThreads;
-    // lane quarter w mod 4, column half w div 4
-    const uint32_t tq = tmem + ((32u * static_cast<uint32_t>(w & 3)) << 16) + 256u * static_cast<uint32_t>(w >> 2);
+    // lane quarter w mod 4; columns [0, kFeColCap) or [kFeColCap, kXCol)
+    // by w div 4 (halves of 256 when the block swaps spectra in shared memory)
+    const uint32_t tq = tmem + ((32u * static_cast<uint32_t>(w & 3)) << 16) +
+                        (xsmem ? 256u : kFeColCap) * static_cast<uint32_t>(w >> 2);
     // the first two groups' copies fly while the records are built
     if (fe_tid == 0) {
       if (ngroups > 0) issue(0);
@@ -607,12 +624,19 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   } else {
     // ========================== FFT warps ====================================
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsFft));
-    const int f = warp;                     // (row, side, k slot) = (f >> 2, (f >> 1) & 1, f & 1)
+    // warp f: side f >> 2, row (f >> 1) & 1, k slot f & 1; its partner (same
+    // row and k slot, other side) is warp f ^ 4, in the same tensor-memory
+    // lane quarter
+    const int f = warp;
     const int ftid = tid;
-    const int side_w = (f >> 1) & 1;
+    const int side_w = f >> 2;
+    const int row_w = (f >> 1) & 1;
     const int g_w = f & 1;
     const int own_m0 = side_w * 16;
-    const int pair_bar = kBarPair + ((f & 1) | ((f >> 2) << 1));
+    const int ri = (row_w * 2 + side_w) * kG + g_w;          // this warp's Y region
+    const int ri_partner = (row_w * 2 + (side_w ^ 1)) * kG + g_w;
+    const int pair_bar = kBarPair + (f & 3);
+    const uint32_t tx = tmem + ((32u * static_cast<uint32_t>(f & 3)) << 16) + kXCol;
     // lane twiddle anchors w_1024^{lane * 8 q}, q = 0..3, and the step w_1024^lane
     float2 anchor[4];
     float2 step;
@@ -637,8 +661,8 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       // group g + 2 (the first FFT thread issues the copies)
       if (ftid == 0 && g + 2 < ngroups && !s_err) issue(g + 2);
       float2* work = ybuf + static_cast<size_t>(b) * kFftWarps * kRegion;
-      float2* region = work + f * kRegion;
-      const float2* partner = work + (f ^ 2) * kRegion;
+      float2* region = work + ri * kRegion;
+      const float2* partner = work + ri_partner * kRegion;
       // ---- FFT of length 1024 --------------------------------------------
       float2 x[32];
 #pragma unroll
@@ -661,35 +685,78 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       for (int j = 0; j < 32; ++j) x[j] = region[lane * kPitch + j];
       dft32<false>(x);
       __syncwarp();
-      // hand the partner (same row and k slot, other side) the half of the
-      // bins it accumulates
-      if (side_w == 0) {
+      // hand the partner the half of the bins it accumulates (side 0 keeps
+      // bins 0..15 of every lane, side 1 bins 16..31): through tensor memory
+      // (the quarter's swap buffer g mod 2: side s writes its 32 columns at
+      // 32 s), or through shared memory
+      const uint32_t xb = tx + 64u * static_cast<uint32_t>(b);
+      if (!xsmem) {
+        float gv[32];
+        if (side_w == 0) {
 #pragma unroll
-        for (int m = 16; m < 32; ++m) region[lane + 32 * m] = x[m];
+          for (int m = 0; m < 16; ++m) { gv[2 * m] = x[16 + m].x; gv[2 * m + 1] = x[16 + m].y; }
+          tmem_st32(xb, gv);
+        } else {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) { gv[2 * m] = x[m].x; gv[2 * m + 1] = x[m].y; }
+          tmem_st32(xb + 32u, gv);
+        }
+        tmem_wait_st();
+        tmem_fence_before_sync();
+        named_sync(pair_bar, 64);
+        tmem_fence_after_sync();
       } else {
+        if (side_w == 0) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) region[lane + 32 * m] = x[m];
+          for (int m = 16; m < 32; ++m) region[lane + 32 * m] = x[m];
+        } else {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) region[lane + 32 * m] = x[m];
+        }
+        named_sync(pair_bar, 64);
       }
-      named_sync(pair_bar, 64);
+      // the partner's bins own_m0 + 8 h .. + 7 (its columns 16 h ..)
+      auto partner8 = [&](int h, float2 (&q)[8]) {
+        if (!xsmem) {
+          uint32_t r[32];
+          tmem_ld16_nowait(xb + 32u * static_cast<uint32_t>(side_w ^ 1) + 16u * static_cast<uint32_t>(h), r);
+          tmem_wait_ld16(r);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) q[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) q[i] = partner[lane + 32 * (own_m0 + 8 * h + i)];
+        }
+      };
       // ---- spectral products: own half of the bins ------------------------
       if (g_w < gcnt) {
         if (side_w == 0) {
 #pragma unroll
-          for (int m = 0; m < 16; ++m) {
-            const float2 q = partner[lane + 32 * m];
-            part[m].x = fmaf(x[m].x, q.x, part[m].x);
-            part[m].x = fmaf(-x[m].y, q.y, part[m].x);
-            part[m].y = fmaf(x[m].x, q.y, part[m].y);
-            part[m].y = fmaf(x[m].y, q.x, part[m].y);
+          for (int h = 0; h < 2; ++h) {
+            float2 q[8];
+            partner8(h, q);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int m = 8 * h + i;
+              part[m].x = fmaf(x[m].x, q[i].x, part[m].x);
+              part[m].x = fmaf(-x[m].y, q[i].y, part[m].x);
+              part[m].y = fmaf(x[m].x, q[i].y, part[m].y);
+              part[m].y = fmaf(x[m].y, q[i].x, part[m].y);
+            }
           }
         } else {
 #pragma unroll
-          for (int m = 0; m < 16; ++m) {
-            const float2 q = partner[lane + 32 * (16 + m)];
-            part[m].x = fmaf(x[16 + m].x, q.x, part[m].x);
-            part[m].x = fmaf(-x[16 + m].y, q.y, part[m].x);
-            part[m].y = fmaf(x[16 + m].x, q.y, part[m].y);
-            part[m].y = fmaf(x[16 + m].y, q.x, part[m].y);
+          for (int h = 0; h < 2; ++h) {
+            float2 q[8];
+            partner8(h, q);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int m = 8 * h + i;
+              part[m].x = fmaf(x[16 + m].x, q[i].x, part[m].x);
+              part[m].x = fmaf(-x[16 + m].y, q[i].y, part[m].x);
+              part[m].y = fmaf(x[16 + m].x, q[i].y, part[m].y);
+              part[m].y = fmaf(x[16 + m].y, q[i].x, part[m].y);
+            }
           }
         }
       }
@@ -818,6 +885,10 @@ cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const 
   a.partial = partial;
   a.thi_g = thi;
   a.ovcap = plan.ovcap;
+  // debug switch (environment): the partner FFT warps swap their half
+  // spectra through shared memory, the path blocks take when the front-end
+  // records leave no tensor-memory columns for the swap
+  a.force_xsmem = std::getenv("CMS_WS_SMEM_SWAP") != nullptr ? 1 : 0;
   if (!ws_kernel_usable()) return cudaErrorInvalidConfiguration;
   const int smem = static_cast<int>(plan.smem);
   cudaError_t e = cudaFuncSetAttribute(k_sketch_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -627,3 +627,26 @@ def test_lockstep_kernel_with_tensor_memory_records(cms, n1, n2, n3, b, d, dtype
         dc = (tab.s1[t][:n1] @ Ad) @ (Bd @ tab.s2[t][:n3])
         assert abs(c[t].sum() - dc) < 1e-5 * np.abs(c[t]).sum()
     h.free()
+
+
+def test_warp_specialised_kernel_both_spectrum_swaps(cms, monkeypatch):
+    # the partner FFT warps swap half spectra through tensor memory; blocks
+    # whose front-end records leave no room take the shared-memory swap
+    # (forced here by the library's debug switch); both give the oracle's
+    # sketch, at an inner dimension that crosses several Kahan folds
+    m, n, b, d = 4096, 2048, 65536, 3
+    X = W.gaussian(m, n, 17).astype(np.float32)
+    xt = torch.from_numpy(X).to(dev())
+    h = cms.make_hashes(23, n, b, d)
+    assert cms.plan_kernel(xt.T, xt, h) == "warp_specialised"
+    tab = O.make_tables(23, n, b, d)
+    Xd = X.astype(np.float64)
+    ref = O.sketch_definition(Xd.T, Xd, tab)
+    c_tm = cms.sketch_product(xt.T, xt, h).cpu().numpy()
+    monkeypatch.setenv("CMS_WS_SMEM_SWAP", "1")
+    c_sm = cms.sketch_product(xt.T, xt, h).cpu().numpy()
+    monkeypatch.delenv("CMS_WS_SMEM_SWAP")
+    cms.check_async()
+    for c in (c_tm, c_sm):
+        assert max(O.rel_l2(c[t], ref[t]) for t in range(d)) < TOL_F32
+    h.free()
