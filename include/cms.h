@@ -239,7 +239,10 @@ CMS_API cms_status cms_sketch_product_noalloc(const void* A, int64_t lda, const 
  *   b_val    : device values of B, storage type dt.
  *   Indices outside [0, n1) / [0, n3) contribute nothing.
  *   b must be a multiple of 1024 (CMS_ERR_UNSUPPORTED otherwise).
- *   The call waits once for the stream (to read the number of nonempty k).
+ *   Asynchronous: the list of nonempty k and its length stay on the device
+ *   (the FFT route runs the workspace's worst-case chunking and reads the
+ *   length there), so the call never waits for the stream and can be
+ *   captured in a CUDA graph.
  */
 CMS_API cms_status cms_sparse_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2,
                                              int64_t n3, size_t* bytes);
@@ -264,7 +267,8 @@ CMS_API cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t
  *   The FP64 additions of the direct part are atomic: their order varies
  *   between calls (results agree to FP64 rounding, exactly when the values
  *   are integers).  Workspace: cms_sparse_workspace_size.  Other arguments,
- *   errors and the one stream wait as cms_sketch_product_csr.
+ *   errors and asynchrony as cms_sketch_product_csr (the split is made on
+ *   the device; the route whose list is empty returns at once).
  */
 CMS_API cms_status cms_sketch_product_csr_hybrid(const int64_t* a_colptr, const int32_t* a_rowidx,
                                                  const void* a_val, const int64_t* b_rowptr,
@@ -298,6 +302,9 @@ typedef struct cms_batch cms_batch;
 #define CMS_BATCH_AUTOTUNE 1
 
 /*
+ * Batches: many products of uneven shapes in one persistent launch (a
+ * handle API: create once, run or replay many times, free).
+ *
  * cms_batch_create - plan a batch of `count` instances (Fig. 1 for each):
  * allocates one device workspace for all of them, computes their constant
  * twiddle tables and uploads one task descriptor per instance (synchronous
@@ -537,6 +544,12 @@ CMS_API cms_status cms_selftest_wait(void* stream);
 CMS_API cms_status cms_check_async(void* stream);
 
 /*
+ * Tracing (no counterpart in the paper).  The compute entry points (hash
+ * draws, the sketch calls, batches, decodes, post-steps, estimators,
+ * FINDSIGNIFICANTENTRIES, merge) each open an NVTX range named after the
+ * entry point, visible in a profiler's timeline; without an attached tool
+ * the ranges cost a function call.
+ *
  * cms_profile_enable - per-kernel device timing (no counterpart in the
  * paper).  While on, every kernel the library launches is bracketed by CUDA
  * events recorded on the stream it runs on.  Switching on or off clears the

@@ -169,6 +169,7 @@ const char* cms_status_string(cms_status s) {
 const char* cms_last_error(void) { return g_last_error.c_str(); }
 
 cms_status cms_make_hashes(uint64_t seed, int64_t n, int64_t b, int32_t d, cms_hashes** out) {
+  NvtxRange nvtx_range("cms_make_hashes");
   if (!out) return fail(CMS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n < 1 || n > (1LL << 24)) return fail(CMS_ERR_INVALID_ARG, "n must be in [1, 2^24]");
@@ -191,6 +192,7 @@ cms_status cms_make_hashes(uint64_t seed, int64_t n, int64_t b, int32_t d, cms_h
 }
 
 cms_status cms_reseed_hashes(cms_hashes* h, uint64_t seed, void* stream) {
+  NvtxRange nvtx_range("cms_reseed_hashes");
   if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
   if (h->from_tables) return fail(CMS_ERR_INVALID_ARG, "hashes built from tables cannot be reseeded");
   cms_status st = check_device(h);
@@ -203,6 +205,7 @@ cms_status cms_reseed_hashes(cms_hashes* h, uint64_t seed, void* stream) {
 cms_status cms_make_hashes_from_tables(int64_t n, int64_t b, int32_t d, const uint32_t* h1,
                                        const int8_t* s1, const uint32_t* h2, const int8_t* s2,
                                        cms_hashes** out) {
+  NvtxRange nvtx_range("cms_make_hashes_from_tables");
   if (!out) return fail(CMS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!h1 || !s1 || !h2 || !s2) return fail(CMS_ERR_INVALID_ARG, "table pointer is NULL");
@@ -390,6 +393,7 @@ cms_status cms_plan_kernel(const void* A, int64_t lda, const void* B, int64_t ld
 cms_status cms_sketch_product(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
                               int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h, float* c,
                               void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("cms_sketch_product");
   cms_status st = static_cast<cms_status>(cms::check_dense_call(h, A, lda, B, ldb, n1, n2, n3, dt, c));
   if (st != CMS_OK) return st;
   DeviceProps dp = device_props(h->device);
@@ -426,6 +430,7 @@ cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t* a_rowi
                                   const int64_t* b_rowptr, const int32_t* b_colidx, const void* b_val,
                                   int64_t n1, int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h,
                                   float* c, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("cms_sketch_product_csr");
   cms_status st = check_shapes(h, n1, n2, n3, std::max<int64_t>(n1, 1), std::max<int64_t>(n3, 1));
   if (st != CMS_OK) return st;
   if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
@@ -472,6 +477,7 @@ cms_status cms_sketch_product_csr_hybrid(const int64_t* a_colptr, const int32_t*
                                          int64_t n1, int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h,
                                          int64_t direct_max_pairs, float* c, void* ws, size_t ws_bytes,
                                          void* stream) {
+  NvtxRange nvtx_range("cms_sketch_product_csr_hybrid");
   cms_status st = check_shapes(h, n1, n2, n3, std::max<int64_t>(n1, 1), std::max<int64_t>(n3, 1));
   if (st != CMS_OK) return st;
   if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
@@ -540,6 +546,7 @@ cms_status cms_plain_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2,
 cms_status cms_sketch_product_plain_f64(const double* A, int64_t lda, const double* B, int64_t ldb,
                                         int64_t n1, int64_t n2, int64_t n3, const cms_hashes* h,
                                         double* c, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("cms_sketch_product_plain_f64");
   cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
   if (st != CMS_OK) return st;
   if (!c) return fail(CMS_ERR_INVALID_ARG, "c is NULL");
@@ -562,6 +569,7 @@ cms_status cms_sketch_product_plain_f64(const double* A, int64_t lda, const doub
 
 cms_status cms_decode(const float* c, const cms_hashes* h, const int64_t* ij, int64_t q, float* out,
                       void* stream) {
+  NvtxRange nvtx_range("cms_decode");
   if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
   if (q < 0) return fail(CMS_ERR_INVALID_ARG, "q < 0");
   if (q > 0 && (!c || !ij || !out)) return fail(CMS_ERR_INVALID_ARG, "NULL pointer");
@@ -574,6 +582,7 @@ cms_status cms_decode(const float* c, const cms_hashes* h, const int64_t* ij, in
 
 cms_status cms_decode_f64(const double* c, const cms_hashes* h, const int64_t* ij, int64_t q,
                           double* out, void* stream) {
+  NvtxRange nvtx_range("cms_decode_f64");
   if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
   if (q < 0) return fail(CMS_ERR_INVALID_ARG, "q < 0");
   if (q > 0 && (!c || !ij || !out)) return fail(CMS_ERR_INVALID_ARG, "NULL pointer");
@@ -586,6 +595,7 @@ cms_status cms_decode_f64(const double* c, const cms_hashes* h, const int64_t* i
 
 cms_status cms_decode_dense(const float* c, const cms_hashes* h, int64_t n1, int64_t n3, float* out,
                             int64_t ldo, void* stream) {
+  NvtxRange nvtx_range("cms_decode_dense");
   if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
   if (n1 < 0 || n3 < 0 || n1 > h->n || n3 > h->n) return fail(CMS_ERR_INVALID_ARG, "bad n1 or n3");
   if (ldo < n3) return fail(CMS_ERR_INVALID_ARG, "ldo < n3");
@@ -600,6 +610,7 @@ cms_status cms_decode_dense(const float* c, const cms_hashes* h, int64_t n1, int
 cms_status cms_sketch_remove_diagonal(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
                                       int64_t n2, int64_t n3, int32_t dt, const cms_hashes* h, float* c,
                                       void* stream) {
+  NvtxRange nvtx_range("cms_sketch_remove_diagonal");
   cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
   if (st != CMS_OK) return st;
   if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
@@ -615,6 +626,7 @@ cms_status cms_sketch_remove_diagonal(const void* A, int64_t lda, const void* B,
 cms_status cms_decode_threshold(const float* c, const cms_hashes* h, int64_t n1, int64_t n3, float tau,
                                 int32_t skip_diagonal, int64_t* ij_out, float* val_out, int64_t capacity,
                                 int64_t* count_out, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("cms_decode_threshold");
   if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
   if (n1 < 0 || n3 < 0 || n1 > h->n || n3 > h->n) return fail(CMS_ERR_INVALID_ARG, "bad n1 or n3");
   if (capacity < 0) return fail(CMS_ERR_INVALID_ARG, "capacity < 0");
@@ -642,6 +654,7 @@ cms_status cms_frobenius_workspace_size(int64_t n1, int64_t n2, int64_t n3, int3
 cms_status cms_frobenius_estimate(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2,
                                   int64_t n3, int32_t dt, uint64_t seed, int32_t d, double* est_out,
                                   double* bound_out, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("cms_frobenius_estimate");
   if (n1 < 0 || n2 < 0 || n3 < 0 || n1 >= (1LL << 31) || n3 >= (1LL << 31))
     return fail(CMS_ERR_INVALID_ARG, "bad n1, n2 or n3");
   if (d < 1 || d > kMaxD) return fail(CMS_ERR_INVALID_ARG, "d must be in [1, 64]");
@@ -669,6 +682,7 @@ cms_status cms_nnz_estimate(const int64_t* a_colptr, const int32_t* a_rowidx, co
                             const int64_t* b_rowptr, const int32_t* b_colidx, const void* b_val, int64_t n1,
                             int64_t n2, int64_t n3, int32_t dt, uint64_t seed, int32_t d, int64_t b_max,
                             int64_t* b_out, int64_t* buckets_out, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("cms_nnz_estimate");
   if (!b_out || !buckets_out) return fail(CMS_ERR_INVALID_ARG, "b_out or buckets_out is NULL");
   if (n1 < 0 || n2 < 0 || n3 < 0 || n1 >= (1LL << 31) || n3 >= (1LL << 31) || n2 >= (1LL << 31) - 1)
     return fail(CMS_ERR_INVALID_ARG, "bad n1, n2 or n3");
@@ -730,6 +744,7 @@ cms_status cms_significant_workspace_size(const cms_hashes* h, int64_t n1, int64
 cms_status cms_decode_significant(const float* sketches, const cms_hashes* h, int64_t n1, int64_t n3, float delta,
                                   int32_t rho, int64_t* ij_out, int64_t capacity, int64_t* count_out, void* ws,
                                   size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("cms_decode_significant");
   if (!h) return fail(CMS_ERR_INVALID_ARG, "hashes is NULL");
   if (n1 < 1 || n3 < 1 || n1 > h->n || n3 > h->n) return fail(CMS_ERR_INVALID_ARG, "bad n1 or n3");
   if (rho < 1 || rho > 8) return fail(CMS_ERR_INVALID_ARG, "rho must be in [1, 8]");
@@ -757,6 +772,7 @@ cms_status cms_find_significant(const void* A, int64_t lda, const void* B, int64
                                 int64_t n3, int32_t dt, const cms_hashes* h, float delta, int32_t rho,
                                 int64_t* ij_out, int64_t capacity, int64_t* count_out, void* ws, size_t ws_bytes,
                                 void* stream) {
+  NvtxRange nvtx_range("cms_find_significant");
   cms_status st = check_shapes(h, n1, n2, n3, lda, ldb);
   if (st != CMS_OK) return st;
   if (!valid_dtype(dt)) return fail(CMS_ERR_INVALID_ARG, "unknown dtype");
@@ -804,6 +820,7 @@ cms_status cms_find_significant(const void* A, int64_t lda, const void* B, int64
 
 cms_status cms_merge(const float* const* parts, int32_t count, int32_t d, int64_t b, float* c_out,
                      void* stream) {
+  NvtxRange nvtx_range("cms_merge");
   if (count < 0 || d < 1 || b < 1) return fail(CMS_ERR_INVALID_ARG, "bad count, d or b");
   if (!c_out || (count > 0 && !parts)) return fail(CMS_ERR_INVALID_ARG, "NULL pointer");
   for (int q = 0; q < count; ++q)

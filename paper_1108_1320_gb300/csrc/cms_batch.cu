@@ -191,6 +191,7 @@ int batch_chunks(const cms_instance& it, const SketchPlan& p, const cms_instance
 
 cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t flags,
                             const char* tune_cache, void* stream, cms_batch** out) {
+  NvtxRange nvtx_range("cms_batch_create");
   if (!out) return fail(CMS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (count < 1 || !items) return fail(CMS_ERR_INVALID_ARG, "need at least one instance");
@@ -340,6 +341,7 @@ cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t fl
 }
 
 cms_status cms_batch_run(cms_batch* b, void* stream) {
+  NvtxRange nvtx_range("cms_batch_run");
   if (!b) return fail(CMS_ERR_INVALID_ARG, "batch is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
@@ -360,6 +362,7 @@ cms_status cms_batch_run(cms_batch* b, void* stream) {
 }
 
 cms_status cms_batch_run_graph(cms_batch* b, void* stream) {
+  NvtxRange nvtx_range("cms_batch_run_graph");
   if (!b) return fail(CMS_ERR_INVALID_ARG, "batch is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!s) return fail(CMS_ERR_INVALID_ARG, "graph capture needs a non-default stream");

@@ -49,6 +49,18 @@ int check_dense_call(const cms_hashes* h, const void* A, int64_t lda, const void
 
 // Brackets the launches in its scope with CUDA events on stream s while
 // profiling is enabled (cms_profile_enable); a no-op otherwise.
+// NVTX range around one C entry point, named after it: visible in a
+// profiler's timeline (Nsight Systems, ncu's NVTX filters); without an
+// attached tool the push and pop return at once (NVTX 3 is header-only and
+// loads a tool library only when the profiler injects one).
+class NvtxRange {
+ public:
+  explicit NvtxRange(const char* name);
+  ~NvtxRange();
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 class ProfScope {
  public:
   ProfScope(const char* name, cudaStream_t s);

@@ -1,5 +1,6 @@
 // cms_prof.cu - per-kernel device timing: while enabled, every kernel the
-// library launches is bracketed by CUDA events recorded on its own stream.
+// library launches is bracketed by CUDA events recorded on its own stream;
+// and the NVTX ranges the C entry points open.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -7,6 +8,8 @@
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "cms_internal.h"
 
@@ -42,6 +45,10 @@ Profiler& prof() {
 }
 
 }  // namespace
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
   Profiler& p = prof();
