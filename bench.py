@@ -737,10 +737,52 @@ def context_numbers(cms, torch, X, h, c, cov, w, dev, stream):
                     "note": "torch.matmul fp32 (cuBLAS, TF32 off by default) of X^T X"}
     del Xd, wsp, c64, AB
     torch.cuda.empty_cache()
+    out["plain_method"] = plain_method_context(cms, torch, dev)
     out["sparse_exact"] = sparse_context(cms, torch, dev)
     out["batched"] = batched_context(cms, torch, dev)
     out["large"] = large_context(cms, torch, dev)
     return out
+
+
+def plain_method_context(cms, torch, dev):
+    """The plain-method shape: A, B 256 x 256 FP64 with i.i.d. N(0, 1)
+    entries, b = 1024, d = 1; the fused path (FP64 storage read as such) and
+    the plain FP64 form, per product, with a new hash draw per call."""
+    import workloads as W
+    n, b = 256, 1024
+    A = torch.from_numpy(np.ascontiguousarray(W.gaussian(n, n, 1).T)).to(dev).T
+    B = torch.from_numpy(W.gaussian(n, n, 2)).to(dev)
+    h = cms.make_hashes(1, n, b, 1)
+    ws = cms.alloc_workspace(cms.workspace_size(h, n, n, n, torch.float64), dev)
+    wsp = cms.alloc_workspace(cms.plain_workspace_size(h, n, n, n), dev)
+    c = torch.empty((1, b), dtype=torch.float32, device=dev)
+    c64 = torch.empty((1, b), dtype=torch.float64, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 50
+    res = {}
+    for name, run in (("fused", lambda i: cms.sketch_product(A, B, h, c=c, ws=ws)),
+                      ("plain_f64", lambda i: cms.sketch_product_plain_f64(A, B, h, c=c64, ws=wsp))):
+        for i in range(3):
+            h.reseed(1 + i)
+            run(i)
+        torch.cuda.synchronize()
+        e0.record()
+        for i in range(reps):
+            h.reseed(100 + i)
+            run(i)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / reps
+    h.reseed(1)
+    cms.sketch_product(A, B, h, c=c, ws=ws)
+    cms.sketch_product_plain_f64(A, B, h, c=c64, ws=wsp)
+    rel = float(torch.linalg.norm(c.double() - c64) / torch.linalg.norm(c64))
+    h.free()
+    return {"workload": "plain method A, B 256x256 FP64 N(0,1), b=1024, d=1",
+            "fused_ms_per_product": res["fused"], "plain_f64_ms_per_product": res["plain_f64"],
+            "c_rel_l2_fused_vs_plain": rel,
+            "note": "hash draw included in each call's time; launch-bound at this size"}
 
 
 def sparse_context(cms, torch, dev):
