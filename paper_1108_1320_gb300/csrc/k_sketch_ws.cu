@@ -243,7 +243,7 @@ __device__ __forceinline__ void fe_chunk(const uint16_t*& xp, uint32_t& tc, int&
         a11.x = fmaf(v1[q], w2, a11.x); a11.y = fmaf(v1[q], w3, a11.y);
       }
     }
-    float2* dp = work + wd[pos + it];
+    float2* dp = work + wd[32 * (pos + it)];
     dp[0] = a00;
     dp[kRegion] = a01;
     dp[2 * kG * kRegion] = a10;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   float2* tlo = reinterpret_cast<float2*>(sm + L.tlo);
   float2* thi = reinterpret_cast<float2*>(sm + L.thi);
   uint32_t* wmeta = reinterpret_cast<uint32_t*>(sm + L.wmeta);     // [fe warp][item]: cnt | side << 8 | ovf << 31
-  uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);       // [fe warp][lane][item]: Y slot (row 0, k 0)
+  uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);       // [fe warp][item][lane]: Y slot (row 0, k 0)
   uint32_t* ibase = reinterpret_cast<uint32_t*>(sm + L.ibase);     // [fe warp][item]: side * ecap + first record
   uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart);   // [fe warp][item]: first stream slot
   uint8_t* wcls = reinterpret_cast<uint8_t*>(sm + L.wcls);         // [fe warp][count]: items of that count
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
     ibase[tid] = static_cast<uint32_t>(side) * p.ecap + gb;
   }
   for (int i = tid; i < kFeWarps * 32 * kItemsFe; i += kThreadsWs) {
-    const int w = i / (32 * kItemsFe), l = (i / kItemsFe) % 32, j = i % kItemsFe;
+    const int w = i / (32 * kItemsFe), j = (i / 32) % kItemsFe, l = i % 32;   // [w][j][l]
     const int side = j >> 2, gi = fe_group(p, t, w, j);
     const size_t ts = static_cast<size_t>(t) * 2 + side;
     wdst[i] = static_cast<uint16_t>(side * kG * kRegion + p.dest[ts * kC + gi * 32 + l]);
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       pm_meta = wmeta[tid];
       pm_base = ibase[tid];
 #pragma unroll
-      for (int l = 0; l < 32; ++l) pm_dst[l] = wdst[(w * 32 + l) * kItemsFe + j];
+      for (int l = 0; l < 32; ++l) pm_dst[l] = wdst[(w * kItemsFe + j) * 32 + l];
     }
     __syncthreads();
     if (tid < kItems) {
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       wmeta[w * kItemsFe + rank] = pm_meta;
       ibase[w * kItemsFe + rank] = pm_base;
 #pragma unroll
-      for (int l = 0; l < 32; ++l) wdst[(w * 32 + l) * kItemsFe + rank] = pm_dst[l];
+      for (int l = 0; l < 32; ++l) wdst[(w * kItemsFe + rank) * 32 + l] = pm_dst[l];
     }
     __syncthreads();
   }
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
     }
     named_sync(kBarFeOvf, kFeThreads);
     const uint32_t* wm = wmeta + w * kItemsFe;
-    const uint16_t* wd = wdst + (w * 32 + lane) * kItemsFe;
+    const uint16_t* wd = wdst + w * kItemsFe * 32 + lane;   // item j of this lane at wd[32 j]
     const uint16_t* xbase = rec_x + istart[w * kItemsFe] * 32u + lane;
     for (int g = 0; g < ngroups; ++g) {
       const int b = g & 1;
@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       // empty bucket groups: zeros
 #pragma unroll 1
       for (; pos < kItemsFe; ++pos) {
-        float2* dp = work + wd[pos];
+        float2* dp = work + wd[32 * pos];
         const float2 z = make_float2(0.f, 0.f);
         dp[0] = z;
         dp[kRegion] = z;
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
         for (int j = 0; j < kItemsFe; ++j) {
           const uint32_t m = wm[j];
           if (!(m >> 31)) continue;
-          const uint32_t dst = wd[j];
+          const uint32_t dst = wd[32 * j];
           const int side = static_cast<int>((m >> 8) & 1u);
           const int z2 = static_cast<int>(dst) - side * kG * kRegion;
           const size_t ts = static_cast<size_t>(t) * 2 + side;
