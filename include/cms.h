@@ -323,8 +323,9 @@ CMS_API cms_status cms_batch_create(const cms_instance* items, int32_t count, in
  * cms_batch_run - compute every instance's sketch c: one persistent kernel
  * over all instances' tasks (longest first, taken from an atomic work
  * counter; each task writes only its own partial row, so results do not
- * depend on scheduling), then per instance the fixed-order reduction and
- * inverse FFT.  Asynchronous, allocates nothing.
+ * depend on scheduling), then the fixed-order reduction and inverse FFT of
+ * every instance in two launches (rows, then columns).  Asynchronous,
+ * allocates nothing.
  */
 CMS_API cms_status cms_batch_run(cms_batch* b, void* stream);
 

@@ -43,6 +43,8 @@ struct cms_batch {
   int grid = 0;
   int launches = 0;
   int use_tmem = 0;   // some instance keeps its twiddle records in tensor memory
+  void* d_inv = nullptr;            // arguments of the batched reduction + inverse
+  cms::InverseBatch inv;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -154,6 +156,8 @@ void release(cms_batch* b) {
   if (b->d_desc) cudaFree(b->d_desc);
   if (b->d_start) cudaFree(b->d_start);
   if (b->d_next) cudaFree(b->d_next);
+  if (b->d_inv) cudaFree(b->d_inv);
+  b->d_inv = nullptr;
   b->exec = nullptr;
   b->graph = nullptr;
   b->ws = nullptr;
@@ -333,8 +337,22 @@ cms_status cms_batch_create(const cms_instance* items, int32_t count, int32_t fl
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { release(b); delete b; return cuda_fail(e, "cms_batch_create (tables)"); }
-  int launches = 2;   // counter reset + persistent kernel
-  for (int i = 0; i < count; ++i) launches += (b->plans[i].fast ? 0 : 1) + 2;
+  // every instance's reduction and inverse as two launches (rows, columns)
+  {
+    std::vector<InverseSpec> specs(count);
+    for (int i = 0; i < count; ++i) {
+      const SketchPlan& p = b->plans[i];
+      char* w = b->ws + b->ws_off[i];
+      specs[i] = InverseSpec{&p, reinterpret_cast<const float2*>(w + p.off_partial),
+                             reinterpret_cast<float2*>(w + p.off_V), reinterpret_cast<const float2*>(w + p.off_twC),
+                             reinterpret_cast<const float2*>(w + p.off_twR), items[i].c};
+    }
+    e = cudaMalloc(&b->d_inv, inverse_batch_bytes(count));
+    if (e == cudaSuccess) e = build_inverse_batch(specs, b->d_inv, &b->inv, s);
+    if (e != cudaSuccess) { release(b); delete b; return cuda_fail(e, "cms_batch_create (inverse arguments)"); }
+  }
+  int launches = 2 + 2;   // counter reset + persistent kernel + batched inverse (rows, columns)
+  for (int i = 0; i < count; ++i) launches += b->plans[i].fast ? 0 : 1;
   b->launches = launches;
   *out = b;
   return CMS_OK;
@@ -350,13 +368,7 @@ cms_status cms_batch_run(cms_batch* b, void* stream) {
   if (e == cudaSuccess)
     e = launch_sketch_batched(b->d_desc, b->d_start, static_cast<int>(b->items.size()), b->total_tasks,
                               b->d_next, b->smem, b->grid, b->use_tmem, s);
-  for (size_t i = 0; i < b->items.size() && e == cudaSuccess; ++i) {
-    const SketchPlan& p = b->plans[i];
-    char* w = b->ws + b->ws_off[i];
-    e = launch_inverse(p, reinterpret_cast<const float2*>(w + p.off_partial), reinterpret_cast<float2*>(w + p.off_V),
-                       reinterpret_cast<const float2*>(w + p.off_twC), reinterpret_cast<const float2*>(w + p.off_twR),
-                       b->items[i].c, s);
-  }
+  if (e == cudaSuccess) e = launch_inverse_batched(b->inv, s);
   if (e != cudaSuccess) return cuda_fail(e, "cms_batch_run");
   return CMS_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "cms_common.cuh"
 
@@ -205,6 +206,28 @@ cudaError_t launch_inverse(const SketchPlan& plan, const float2* partial, float2
                            const float2* twR, float* c, cudaStream_t s,
                            const int32_t* skip_if_zero = nullptr);
 cudaError_t launch_twiddle_tables(float2* twC, int C, float2* twR, int R, cudaStream_t s);
+
+// Reduction + inverse of many products in two launches (a batch): each
+// instance's plan, partial rows, row spectra, twiddle tables and output.
+struct InverseSpec {
+  const SketchPlan* plan;
+  const float2* partial;
+  float2* V;
+  const float2* twC;
+  const float2* twR;
+  float* c;
+};
+struct InverseBatch {
+  void* buf = nullptr;      // device arguments (inverse_batch_bytes)
+  int count = 0, row_blocks = 0, col_blocks = 0;
+  size_t smem = 0;
+  size_t o_rows = 0, o_cols = 0, o_rs = 0, o_cs = 0;
+};
+size_t inverse_batch_bytes(int count);
+// Uploads the instances' arguments into d_buf (waits for the stream).
+cudaError_t build_inverse_batch(const std::vector<InverseSpec>& specs, void* d_buf, InverseBatch* out,
+                                cudaStream_t s);
+cudaError_t launch_inverse_batched(const InverseBatch& ib, cudaStream_t s);
 cudaError_t launch_frontend_twiddles(const SketchPlan& plan, const cms_hashes* h, char* ws, cudaStream_t s);
 
 // Batched persistent launch (descriptors built on the host, copied to the device).

@@ -23,6 +23,7 @@
 // K2b per output z = C z1 + z2: real inverse length-R DFT over f1 using the
 //     conjugate symmetry, scaled by 1/b (Fig. 1, p[t] := FFT^{-1}(p[t])).
 #include <algorithm>
+#include <vector>
 
 #include "cms_internal.h"
 #include "sketch_generic.cuh"
@@ -115,15 +116,12 @@ __device__ __forceinline__ void neumaier_add(float& s, float& e, float x) {
   s = t;
 }
 
-// K2a: one block per (t, f1).
-__global__ void __launch_bounds__(256) k_rows_inverse(InvArgs p) {
-  extern __shared__ float2 sm2[];
+// K2a body: block tr = t * nrows + f1 of one product.
+__device__ __forceinline__ void rows_inverse_block(const InvArgs& p, int tr, float2* sm2) {
   const int C = p.C;
   float2* twC = sm2;
   float2* P = twC + C;
   float2* Q = P + C;
-  if (p.skip_if_zero && *p.skip_if_zero == 0) return;
-  const int tr = blockIdx.x;   // t * nrows + f1
   const int f1 = tr % p.nrows;
   for (int i = threadIdx.x; i < C; i += blockDim.x) twC[i] = p.twC[i];
   const float2* part = p.partial + static_cast<size_t>(tr) * p.nkc * C;
@@ -150,15 +148,39 @@ __global__ void __launch_bounds__(256) k_rows_inverse(InvArgs p) {
   }
 }
 
+// K2a: one block per (t, f1).
+__global__ void __launch_bounds__(256) k_rows_inverse(InvArgs p) {
+  extern __shared__ float2 sm2[];
+  if (p.skip_if_zero && *p.skip_if_zero == 0) return;
+  rows_inverse_block(p, blockIdx.x, sm2);
+}
+
+// The instance of a batched launch that owns block `blk`: the last i with
+// start[i] <= blk (start ascending, start[0] = 0).
+__device__ __forceinline__ int batch_instance(const int* __restrict__ start, int count, int blk) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// K2a for a batch: every instance's (t, f1) blocks in one launch.
+__global__ void __launch_bounds__(256)
+k_rows_inverse_batched(const InvArgs* __restrict__ args, const int* __restrict__ start, int count) {
+  extern __shared__ float2 sm2[];
+  const int i = batch_instance(start, count, static_cast<int>(blockIdx.x));
+  const InvArgs p = args[i];
+  rows_inverse_block(p, static_cast<int>(blockIdx.x) - __ldg(start + i), sm2);
+}
+
 // K2b: c[t][C z1 + z2] = (1/b) Re sum_{f1=0}^{R-1} V[f1][z2] w_R^{-f1 z1}, rows
 // above R/2 taken as conjugates of rows below it.
-__global__ void __launch_bounds__(256)
-k_cols_inverse(const float2* __restrict__ V, const float2* __restrict__ twR, int64_t b,
-               int R, int C, int nrows, float* __restrict__ c, const int32_t* __restrict__ skip_if_zero) {
-  if (skip_if_zero && *skip_if_zero == 0) return;
-  const int t = blockIdx.y;
-  const int64_t z = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (z >= b) return;
+__device__ __forceinline__ void cols_inverse_point(const float2* __restrict__ V, const float2* __restrict__ twR,
+                                                   int64_t b, int R, int C, int nrows, float* __restrict__ c,
+                                                   int t, int64_t z) {
   const int z1 = static_cast<int>(z / C);
   const int z2 = static_cast<int>(z - static_cast<int64_t>(z1) * C);
   const float2* Vt = V + static_cast<size_t>(t) * nrows * C + z2;
@@ -174,6 +196,35 @@ k_cols_inverse(const float2* __restrict__ V, const float2* __restrict__ twR, int
     sum += (even && 2 * f1 == R) ? term : 2.f * term;
   }
   c[static_cast<size_t>(t) * b + z] = sum / static_cast<float>(b);
+}
+
+__global__ void __launch_bounds__(256)
+k_cols_inverse(const float2* __restrict__ V, const float2* __restrict__ twR, int64_t b,
+               int R, int C, int nrows, float* __restrict__ c, const int32_t* __restrict__ skip_if_zero) {
+  if (skip_if_zero && *skip_if_zero == 0) return;
+  const int64_t z = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (z >= b) return;
+  cols_inverse_point(V, twR, b, R, C, nrows, c, static_cast<int>(blockIdx.y), z);
+}
+
+struct ColsArgs {
+  const float2* V;
+  const float2* twR;
+  float* c;
+  int64_t b;
+  int R, C, nrows;
+  int nbx;   // blocks of 256 points per repetition
+};
+
+// K2b for a batch: every instance's (repetition, point block) in one launch.
+__global__ void __launch_bounds__(256)
+k_cols_inverse_batched(const ColsArgs* __restrict__ args, const int* __restrict__ start, int count) {
+  const int i = batch_instance(start, count, static_cast<int>(blockIdx.x));
+  const ColsArgs a = args[i];
+  const int local = static_cast<int>(blockIdx.x) - __ldg(start + i);
+  const int t = local / a.nbx;
+  const int64_t z = static_cast<int64_t>(local % a.nbx) * blockDim.x + threadIdx.x;
+  if (z < a.b) cols_inverse_point(a.V, a.twR, a.b, a.R, a.C, a.nrows, a.c, t, z);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -521,6 +572,87 @@ cudaError_t launch_inverse(const SketchPlan& plan, const float2* partial, float2
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_cols_inverse(plan, V, twR, c, s, skip_if_zero);
+}
+
+size_t inverse_batch_bytes(int count) {
+  const size_t n = static_cast<size_t>(std::max(count, 1));
+  return align256(n * sizeof(InvArgs)) + align256(n * sizeof(ColsArgs)) + 2 * align256((n + 1) * sizeof(int));
+}
+
+cudaError_t build_inverse_batch(const std::vector<InverseSpec>& specs, void* d_buf, InverseBatch* out,
+                                cudaStream_t s) {
+  const int count = static_cast<int>(specs.size());
+  std::vector<InvArgs> rows(count);
+  std::vector<ColsArgs> cols(count);
+  std::vector<int> rstart(count + 1), cstart(count + 1);
+  int tr = 0, tc = 0;
+  size_t smem = 0;
+  for (int i = 0; i < count; ++i) {
+    const SketchPlan& plan = *specs[i].plan;
+    InvArgs ia{};
+    ia.b = plan.b; ia.R = static_cast<int>(plan.R); ia.C = static_cast<int>(plan.C);
+    ia.nrows = plan.nrows; ia.d = plan.d; ia.nkc = plan.nkc;
+    ia.nradC = plan.nradC;
+    for (int r = 0; r < 16; ++r) ia.radC[r] = plan.radC[r];
+    ia.partial = specs[i].partial; ia.twC = specs[i].twC; ia.V = specs[i].V; ia.skip_if_zero = nullptr;
+    rows[i] = ia;
+    rstart[i] = tr;
+    tr += plan.d * plan.nrows;
+    smem = std::max(smem, static_cast<size_t>(3 * plan.C * 8));
+    ColsArgs ca{};
+    ca.V = specs[i].V; ca.twR = specs[i].twR; ca.c = specs[i].c; ca.b = plan.b;
+    ca.R = static_cast<int>(plan.R); ca.C = static_cast<int>(plan.C); ca.nrows = plan.nrows;
+    ca.nbx = static_cast<int>((plan.b + 255) / 256);
+    cols[i] = ca;
+    cstart[i] = tc;
+    tc += ca.nbx * plan.d;
+  }
+  rstart[count] = tr;
+  cstart[count] = tc;
+  char* base = static_cast<char*>(d_buf);
+  const size_t o_rows = 0;
+  const size_t o_cols = o_rows + align256(static_cast<size_t>(std::max(count, 1)) * sizeof(InvArgs));
+  const size_t o_rs = o_cols + align256(static_cast<size_t>(std::max(count, 1)) * sizeof(ColsArgs));
+  const size_t o_cs = o_rs + align256(static_cast<size_t>(count + 1) * sizeof(int));
+  cudaError_t e = cudaMemcpyAsync(base + o_rows, rows.data(), count * sizeof(InvArgs), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + o_cols, cols.data(), count * sizeof(ColsArgs), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + o_rs, rstart.data(), (count + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + o_cs, cstart.data(), (count + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host vectors go out of scope
+  out->buf = d_buf;
+  out->count = count;
+  out->row_blocks = tr;
+  out->col_blocks = tc;
+  out->smem = smem;
+  out->o_rows = o_rows; out->o_cols = o_cols; out->o_rs = o_rs; out->o_cs = o_cs;
+  return e;
+}
+
+cudaError_t launch_inverse_batched(const InverseBatch& ib, cudaStream_t s) {
+  if (ib.count == 0) return cudaSuccess;
+  const char* base = static_cast<const char*>(ib.buf);
+  cudaError_t e = cudaSuccess;
+  if (ib.smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_rows_inverse_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(ib.smem));
+    if (e != cudaSuccess) return e;
+  }
+  if (ib.row_blocks > 0) {
+    ProfScope prof_scope("k_rows_inverse_batched", s);
+    k_rows_inverse_batched<<<static_cast<unsigned>(ib.row_blocks), 256, ib.smem, s>>>(
+        reinterpret_cast<const InvArgs*>(base + ib.o_rows), reinterpret_cast<const int*>(base + ib.o_rs), ib.count);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ib.col_blocks > 0) {
+    ProfScope prof_scope("k_cols_inverse_batched", s);
+    k_cols_inverse_batched<<<static_cast<unsigned>(ib.col_blocks), 256, 0, s>>>(
+        reinterpret_cast<const ColsArgs*>(base + ib.o_cols), reinterpret_cast<const int*>(base + ib.o_cs), ib.count);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cols_inverse(const SketchPlan& plan, const float2* V, const float2* twR, float* c,

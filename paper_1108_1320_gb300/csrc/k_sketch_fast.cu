@@ -148,7 +148,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   float2* tlo = reinterpret_cast<float2*>(sm + L.tlo);
   float2* thi = reinterpret_cast<float2*>(sm + L.thi);
   uint32_t* wmeta = reinterpret_cast<uint32_t*>(sm + L.wmeta);   // [warp][item]: cnt | side << 8 | ovf << 31
-  uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);     // [warp][lane][item]: Y slot (row 0, k 0)
+  uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);     // [warp][item][lane]: Y slot (row 0, k 0)
   uint32_t* ibase = reinterpret_cast<uint32_t*>(sm + L.ibase);   // [warp][item]: side * ecap + first record
   uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart); // [warp][item]: first stream slot; [64]: total
   uint32_t* slot_src = reinterpret_cast<uint32_t*>(sm + L.slot_src);
@@ -202,7 +202,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     }
   }
   for (int i = tid; i < kWarps * 32 * kItems; i += kThreads) {
-    const int w = i / (32 * kItems), l = (i / kItems) % 32, j = i % kItems;
+    const int w = i / (32 * kItems), j = (i / 32) % kItems, l = i % 32;   // [w][j][l]: one item's lanes together
     const int slot = (j & 1) ? (kWarps - 1 - w) : w;
     const int item = j * kWarps + slot;
     const int side = item & 1, gi = item >> 1;
@@ -387,7 +387,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
 #pragma unroll 1
       for (int j = 0; j < kItems; ++j) {
         const uint32_t m = wmeta[warp * kItems + j];
-        const uint32_t dst = wdst[(warp * 32 + lane) * kItems + j];
+        const uint32_t dst = wdst[(warp * kItems + j) * 32 + lane];
         const uint32_t cnt = m & 0xFFu;
         const bool sb = (m >> 8) & 1u;
         const T* sg0 = stage + (sb ? shB0 : shA0);
@@ -440,7 +440,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         for (int j = 0; j < kItems; ++j) {
           const uint32_t m = wmeta[warp * kItems + j];
           if (!(m >> 31)) continue;
-          const uint32_t dst = wdst[(warp * 32 + lane) * kItems + j];
+          const uint32_t dst = wdst[(warp * kItems + j) * 32 + lane];
           const int side = static_cast<int>((m >> 8) & 1u);
           const int z2 = static_cast<int>(dst) - side * kG * kRegion;
           const T* st = stage + (p.alias ? 0 : side) * kG * p.npad;

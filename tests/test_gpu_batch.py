@@ -175,3 +175,26 @@ def test_batch_large_instances_keep_records_in_tensor_memory(cms):
     batch.free()
     for _, _, h in items:
         h.free()
+
+
+def test_batch_inverse_is_two_launches_for_all_instances(cms):
+    # the reduction and inverse of every instance run as one row launch and
+    # one column launch (not two per instance), with the oracle's results
+    specs = specs_small(count=6, seed=9)
+    items, refs = make_instances(cms, specs)
+    batch = cms.Batch(items)
+    info = batch.info()
+    cms.profile_enable(True)
+    batch.run()
+    torch.cuda.synchronize()
+    kernels = cms.profile_summary()
+    cms.profile_enable(False)
+    cms.check_async()
+    assert kernels["k_rows_inverse_batched"]["launches"] == 1
+    assert kernels["k_cols_inverse_batched"]["launches"] == 1
+    assert "k_rows_inverse" not in kernels and "k_cols_inverse" not in kernels
+    fast = info["fast_instances"]
+    assert info["launches"] == 4 + (len(specs) - fast)
+    for c, ref in zip(batch.c, refs):
+        check(c, ref)
+    batch.free()
