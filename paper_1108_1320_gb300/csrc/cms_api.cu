@@ -100,7 +100,8 @@ cms_status alloc_tables(cms_hashes* h) {
         (e = cudaMalloc(&h->d_fe_dest, ts * groups * 32 * 2)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_fe_ovf_off, ts * (C + 1) * 4)) != cudaSuccess ||
         (e = cudaMalloc(&h->d_fe_ovf_x, ts * h->n * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_fe_assign, ts * (kFeC / 32))) != cudaSuccess)
+        (e = cudaMalloc(&h->d_fe_assign, ts * (kFeC / 32))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_fe_ovf_hs, ts * h->n * 4)) != cudaSuccess)
       return cuda_fail(e, "cudaMalloc(front-end records)");
   }
   return CMS_OK;
@@ -112,7 +113,7 @@ void free_tables(cms_hashes* h) {
   if (h->d_off) cudaFree(h->d_off);
   h->d_hs = h->d_perm = nullptr;
   h->d_off = nullptr;
-  for (uint32_t** q : {&h->d_fe_x, &h->d_fe_hs, &h->d_fe_grp, &h->d_fe_ovf_off, &h->d_fe_ovf_x}) {
+  for (uint32_t** q : {&h->d_fe_x, &h->d_fe_hs, &h->d_fe_grp, &h->d_fe_ovf_off, &h->d_fe_ovf_x, &h->d_fe_ovf_hs}) {
     if (*q) cudaFree(*q);
     *q = nullptr;
   }
@@ -120,6 +121,7 @@ void free_tables(cms_hashes* h) {
   h->d_fe_dest = nullptr;
   if (h->d_fe_assign) cudaFree(h->d_fe_assign);
   h->d_fe_assign = nullptr;
+
   h->fe_ecap = 0;
 }
 
@@ -135,7 +137,8 @@ cms_status fill_tables(cms_hashes* h, cudaStream_t s, bool hash) {
   }
   if (h->fe_ecap > 0) {
     e = launch_frontend_tables(h->d_hs, h->d_perm, h->d_off, h->d, h->n, h->C, h->fe_ecap, h->d_fe_x, h->d_fe_hs,
-                               h->d_fe_grp, h->d_fe_dest, h->d_fe_ovf_off, h->d_fe_ovf_x, h->d_fe_assign, s);
+                               h->d_fe_grp, h->d_fe_dest, h->d_fe_ovf_off, h->d_fe_ovf_x, h->d_fe_assign,
+                               h->d_fe_ovf_hs, s);
     if (e != cudaSuccess) return cuda_fail(e, "front-end table kernel");
   }
   return CMS_OK;

@@ -31,6 +31,7 @@ struct cms_hashes {
   uint32_t* d_fe_ovf_off = nullptr;  // [d][2][C+1]
   uint32_t* d_fe_ovf_x = nullptr;    // [d][2][n]
   uint8_t* d_fe_assign = nullptr;    // [d][2][32]: bucket group of each (warp, slot), cost-balanced
+  uint32_t* d_fe_ovf_hs = nullptr;   // [d][2][n]: packed hash of each d_fe_ovf_x entry
 };
 
 namespace cms {
@@ -93,7 +94,7 @@ constexpr int kFeCap = 8;         // bucket entries kept in the padded layout
 cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, const uint32_t* off, int d,
                                    int64_t n, int64_t C, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs,
                                    uint32_t* grp, uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,
-                                   uint8_t* assign, cudaStream_t s);
+                                   uint8_t* assign, uint32_t* ovf_hs, cudaStream_t s);
 // Lengths of the in-register DFT codelets (and 32, the radix-32 DFT).
 inline bool fe_supported_L(int64_t L) {
   return L == 16 || L == 18 || L == 20 || L == 24 || L == 25 || L == 27 || L == 30 || L == 32;

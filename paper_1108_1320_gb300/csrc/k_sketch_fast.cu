@@ -63,9 +63,9 @@ struct FastArgs {
   const uint32_t* rec_hs;
   const uint32_t* grp;
   const uint16_t* dest;
-  const uint32_t* ovf_off;
-  const uint32_t* ovf_x;
-  const uint32_t* hs;
+  const uint32_t* ovf_off;   // [t][side][C + 1]: each bucket's overflow list
+  const uint32_t* ovf_x;     // [t][side][n]: overflow entries (x), bucket by bucket
+  const uint32_t* ovf_hs;    // [t][side][n]: their packed hashes
   float2* partial;
   int C, P, Q;        // FFT length C = P Q: P lanes x DFT-Q, then Q lanes x DFT-P
   int G;              // bucket groups per side, ceil(C / 32)
@@ -86,7 +86,7 @@ struct BatchDesc {
 namespace {
 
 struct SmemLayout {
-  size_t stage, rec_tw, rec_x, work, acc, tlo, thi, wmeta, wdst, ibase, istart, slot_src, ovf, wovf, bar, total;
+  size_t stage, rec_tw, rec_x, work, acc, tlo, thi, wmeta, wdst, ibase, istart, slot_src, bar, total;
 };
 
 constexpr int kWarps = kThreads / 32;
@@ -112,11 +112,20 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   L.ibase = o;    o = al16(o + static_cast<size_t>(kWarps) * kItems * 4);
   L.istart = o;   o = al16(o + static_cast<size_t>(kWarps * kItems + 1) * 4);
   L.slot_src = o; o = al16(o + (static_cast<size_t>(2) * ecap / 32 + 1) * 4);
-  L.ovf = o;      o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
-  L.wovf = o;     o = al16(o + static_cast<size_t>(kWarps) * 4);
   L.bar = o;      o = al16(o + 8);
   L.total = o;
   return L;
+}
+
+// w_b^m = exp(-2 pi i m / b) for the overflow entries, without the shared
+// twiddle tables: the phase is reduced exactly in integers to m - b in
+// (-b/2, b/2], so the angle lies in [-pi, pi], where the hardware sine and
+// cosine (__sincosf) have an absolute error of about 4e-7; w2 = 2 pi / b.
+__device__ __forceinline__ float2 wb_sfu(uint32_t m, uint32_t b, float w2) {
+  const int32_t ms = m > (b >> 1) ? static_cast<int32_t>(m) - static_cast<int32_t>(b) : static_cast<int32_t>(m);
+  float sn, cs;
+  __sincosf(static_cast<float>(ms) * w2, &sn, &cs);
+  return make_float2(cs, -sn);
 }
 
 // One task (t, row pair, k-range) of the fast kernel; `sm` is the block's
@@ -147,13 +156,11 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   float4* acc = reinterpret_cast<float4*>(sm + L.acc);
   float2* tlo = reinterpret_cast<float2*>(sm + L.tlo);
   float2* thi = reinterpret_cast<float2*>(sm + L.thi);
-  uint32_t* wmeta = reinterpret_cast<uint32_t*>(sm + L.wmeta);   // [warp][item]: cnt | side << 8 | ovf << 31
+  uint32_t* wmeta = reinterpret_cast<uint32_t*>(sm + L.wmeta);   // [warp][item]: cnt | side << 8 | overflow steps << 9
   uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);     // [warp][item][lane]: Y slot (row 0, k 0)
   uint32_t* ibase = reinterpret_cast<uint32_t*>(sm + L.ibase);   // [warp][item]: side * ecap + first record
   uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart); // [warp][item]: first stream slot; [64]: total
   uint32_t* slot_src = reinterpret_cast<uint32_t*>(sm + L.slot_src);
-  uint16_t* ovf = reinterpret_cast<uint16_t*>(sm + L.ovf);
-  uint32_t* wovf = reinterpret_cast<uint32_t*>(sm + L.wovf);   // [warp]: some item overflows
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -168,6 +175,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   const int n = p.n;
   const int S = 1 << p.tw_shift;
   const ModB modb = make_modb(p.b);
+  const float w2pi = static_cast<float>(6.283185307179586 / static_cast<double>(p.b));
   const int nstage = p.alias ? 1 : 2;
   const int k_begin = kc * p.kchunk;
   const int k_end = min(p.n2, k_begin + p.kchunk);
@@ -194,7 +202,7 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
       const size_t ts = static_cast<size_t>(t) * 2 + side;
       const uint32_t gb = p.grp[(ts * Gq + gi) * 2];
       const uint32_t gy = p.grp[(ts * Gq + gi) * 2 + 1];
-      wmeta[tid] = (gy & 0xFFu) | (static_cast<uint32_t>(side) << 8) | (gy & 0x80000000u);
+      wmeta[tid] = (gy & 0xFFu) | (static_cast<uint32_t>(side) << 8) | (((gy >> 16) & 0x7FFFu) << 9);
       ibase[tid] = static_cast<uint32_t>(side) * p.ecap + gb;
     } else {
       wmeta[tid] = kVoidItem;
@@ -208,11 +216,6 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     const int side = item & 1, gi = item >> 1;
     const size_t ts = static_cast<size_t>(t) * 2 + side;
     wdst[i] = item < 2 * Gq ? static_cast<uint16_t>(side * kG * kRegion + p.dest[(ts * Gq + gi) * 32 + l]) : 0;
-  }
-  for (int side = 0; side < 2; ++side) {
-    const size_t ts = static_cast<size_t>(t) * 2 + side;
-    for (int i = tid; i <= C; i += kThreads)
-      ovf[side * (kC + 1) + i] = static_cast<uint16_t>(p.ovf_off[ts * (C + 1) + i]);
   }
   for (int i = tid; i < kRows * kC; i += kThreads) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   // zero the staging tails [n_side, npad): entries x >= n_side read zeros.
@@ -234,11 +237,6 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     uint32_t s = 0;
     for (int i = 0; i < kWarps * kItems; ++i) { istart[i] = s; s += wmeta[i] & 0xFFu; }
     istart[kWarps * kItems] = s;
-  }
-  if (tid < kWarps) {
-    uint32_t f = 0;
-    for (int j = 0; j < kItems; ++j) f |= wmeta[tid * kItems + j] >> 31;
-    wovf[tid] = f;
   }
   __syncthreads();
   if (tid < kWarps * kItems) {
@@ -424,6 +422,50 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
             a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
           }
         }
+        // the entries of the lane's bucket past the capped count (the
+        // bucket's overflow list; the table builder groups buckets of
+        // similar totals, so the lanes' lists are of similar length), with
+        // on-the-fly twiddles (wb_sfu)
+        const uint32_t om = (m >> 9) & 0x7FFFu;
+        if (om) {
+          const size_t ts = static_cast<size_t>(t) * 2 + (sb ? 1 : 0);
+          const uint32_t z = dst - (sb ? static_cast<uint32_t>(kG * kRegion) : 0u);
+          uint32_t o = 0, o1 = 0;
+          if (z < static_cast<uint32_t>(C)) {
+            o = p.ovf_off[ts * (C + 1) + z];
+            o1 = p.ovf_off[ts * (C + 1) + z + 1];
+          }
+          const uint32_t* ox = p.ovf_x + ts * n;
+          const uint32_t* oh = p.ovf_hs + ts * n;
+          const uint32_t soff = p.alias || !sb ? 0u : static_cast<uint32_t>(kG * p.npad);
+          const uint32_t nsd = static_cast<uint32_t>(sb ? p.n3 : p.n1);
+          // the two rows are f1 and f1 + 1 (or the same row twice for the
+          // last unit of an odd count), so the second phase is the first
+          // plus h (mod b) or the first itself
+          const uint32_t bb = static_cast<uint32_t>(p.b);
+          const bool step1 = f1r[1] != f1r[0];
+          uint32_t nx = 0, nh = 0;
+          if (o < o1) { nx = ox[o]; nh = oh[o]; }
+#pragma unroll 1
+          for (; o < o1; ++o) {
+            const uint32_t x = nx, hv = nh;
+            if (o + 1 < o1) { nx = ox[o + 1]; nh = oh[o + 1]; }
+            const uint32_t hb = hv & kBucketMask;
+            const uint32_t e0 = mulmod(hb, f1r[0], modb);
+            uint32_t e1 = step1 ? e0 + hb : e0;
+            if (e1 >= bb) e1 -= bb;
+            float2 w0 = wb_sfu(e0, bb, w2pi);
+            float2 w1 = wb_sfu(e1, bb, w2pi);
+            if (hv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
+            const uint32_t xr = soff + (p.unal && x >= nsd ? static_cast<uint32_t>(p.zpos) : x);
+            const float v0 = generic::to_f32(sg0[xr]);
+            const float v1 = generic::to_f32(sg1[xr]);
+            a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
+            a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
+            a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
+            a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
+          }
+        }
         xp += 32u * cnt;
         twp += 32u * cnt;
         if (m & kVoidItem) continue;
@@ -432,43 +474,6 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         dp[kRegion] = a01;
         dp[2 * kG * kRegion] = a10;
         dp[2 * kG * kRegion + kRegion] = a11;
-      }
-      // entries past the capped count of some bucket (rare): the lane that
-      // stored the bucket's Y adds them, with on-the-fly twiddles
-      if (wovf[warp]) {
-#pragma unroll 1
-        for (int j = 0; j < kItems; ++j) {
-          const uint32_t m = wmeta[warp * kItems + j];
-          if (!(m >> 31)) continue;
-          const uint32_t dst = wdst[(warp * kItems + j) * 32 + lane];
-          const int side = static_cast<int>((m >> 8) & 1u);
-          const int z2 = static_cast<int>(dst) - side * kG * kRegion;
-          const T* st = stage + (p.alias ? 0 : side) * kG * p.npad;
-          const int sh0 = side ? shB0 : shA0, sh1 = side ? shB1 : shA1;
-          const uint32_t nsd = static_cast<uint32_t>(side ? p.n3 : p.n1);
-          const size_t ts = static_cast<size_t>(t) * 2 + side;
-          float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
-          const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
-          for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
-            const uint32_t x = p.ovf_x[ts * n + o];
-            const uint32_t wv = p.hs[ts * n + x];
-            float2 w0 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[0], modb), p.tw_shift);
-            float2 w1 = wb(tlo, thi, mulmod(wv & kBucketMask, f1r[1], modb), p.tw_shift);
-            if (wv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
-            const uint32_t xr = p.unal && x >= nsd ? static_cast<uint32_t>(p.zpos) : x;
-            const float v0 = generic::to_f32(st[sh0 + xr]);
-            const float v1 = generic::to_f32(st[p.npad + sh1 + xr]);
-            a00.x = fmaf(v0, w0.x, a00.x); a00.y = fmaf(v0, w0.y, a00.y);
-            a01.x = fmaf(v1, w0.x, a01.x); a01.y = fmaf(v1, w0.y, a01.y);
-            a10.x = fmaf(v0, w1.x, a10.x); a10.y = fmaf(v0, w1.y, a10.y);
-            a11.x = fmaf(v1, w1.x, a11.x); a11.y = fmaf(v1, w1.y, a11.y);
-          }
-          float2* dp = work + dst;
-          dp[0].x += a00.x; dp[0].y += a00.y;
-          dp[kRegion].x += a01.x; dp[kRegion].y += a01.y;
-          dp[2 * kG * kRegion].x += a10.x; dp[2 * kG * kRegion].y += a10.y;
-          dp[2 * kG * kRegion + kRegion].x += a11.x; dp[2 * kG * kRegion + kRegion].y += a11.y;
-        }
       }
     }
     __syncthreads();
@@ -712,7 +717,7 @@ void fill_batch_desc(void* dst, const SketchPlan& plan, const cms_hashes* h, con
     a.tw_shift = plan.tw_shift;
     a.nhi = plan.nhi;
     a.rec_x = h->d_fe_x; a.rec_hs = h->d_fe_hs; a.grp = h->d_fe_grp; a.dest = h->d_fe_dest;
-    a.ovf_off = h->d_fe_ovf_off; a.ovf_x = h->d_fe_ovf_x; a.hs = h->d_hs;
+    a.ovf_off = h->d_fe_ovf_off; a.ovf_x = h->d_fe_ovf_x; a.ovf_hs = h->d_fe_ovf_hs;
     a.partial = partial;
     a.C = static_cast<int>(plan.C);
     fe_pq(plan.C, &a.P, &a.Q);
@@ -787,7 +792,7 @@ cudaError_t launch_sketch_fast(const SketchPlan& plan, const cms_hashes* h, cons
   a.dest = h->d_fe_dest;
   a.ovf_off = h->d_fe_ovf_off;
   a.ovf_x = h->d_fe_ovf_x;
-  a.hs = h->d_hs;
+  a.ovf_hs = h->d_fe_ovf_hs;
   a.partial = partial;
   a.C = static_cast<int>(plan.C);
   fe_pq(plan.C, &a.P, &a.Q);

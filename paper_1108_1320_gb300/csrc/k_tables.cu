@@ -159,12 +159,15 @@ __device__ __forceinline__ uint32_t bucket_scramble(uint32_t z) {
 // Front-end tables for the C = 1024 fused kernel, one block per (t, side).
 // Buckets z2 = h mod C are ordered by capped count (<= kFeCap) descending,
 // then so that each run of 32 buckets of a class holds every residue
-// z2 mod 16 twice (scrambled order within a residue).  Consecutive runs of
+// z2 mod 16 twice (scrambled order within a residue; in the full class,
+// order of total count within a residue, so that a group's overflow lists
+// are of similar length).  Consecutive runs of
 // 32 buckets form a group whose lanes walk their buckets in lock step:
 // entry r of the bucket at group position l sits at base[group] + 32 r + l
 // (padding entries point at x = n, the fill this kernel writes).  Entries
 // past the kFeCap-th of a bucket (in x order) go to a per-bucket overflow
-// list.  This kernel writes each group's base and count, each group
+// list.  This kernel writes each group's base, count and longest overflow
+// list (count | longest << 16 | overflow flag << 31), each group
 // position's bucket, the overflow offsets (warp and block scans over the
 // bucket counts of the stable bucket sort (perm, off)) and the dealing of
 // the groups to the front-end warps; k_frontend_records then places the
@@ -185,7 +188,7 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   __shared__ uint32_t cnt[kMax];        // entries per bucket
   __shared__ uint32_t key[kMax];
   __shared__ uint32_t used[kMax];       // greedy bank counters, 32 per warp
-  __shared__ uint32_t gword[kMax / 32];  // group count | overflow flag << 31
+  __shared__ uint32_t gword[kMax / 32];  // group count | longest overflow list << 16 | overflow flag << 31
   __shared__ uint32_t wtot[32];
   __shared__ uint32_t gcost[kMax / 32];  // slots + longest overflow list of a group
   const int L = (C + 31) / 32;
@@ -212,9 +215,19 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
     const uint32_t cc = min(cnt[z], kCap);
     const uint32_t sk = used[z];
     uint32_t rank = 0;
-    for (uint32_t o = z & 15u; o < static_cast<uint32_t>(C); o += 16u) {
-      const uint32_t so = used[o];
-      if (min(cnt[o], kCap) == cc && (so < sk || (so == sk && o < z))) ++rank;
+    if (cc < kCap) {
+      for (uint32_t o = z & 15u; o < static_cast<uint32_t>(C); o += 16u) {
+        const uint32_t so = used[o];
+        if (min(cnt[o], kCap) == cc && (so < sk || (so == sk && o < z))) ++rank;
+      }
+    } else {
+      // full buckets by total count, largest first, so that the buckets of
+      // a group have overflow lists of similar length
+      const uint32_t ck = cnt[z];
+      for (uint32_t o = z & 15u; o < static_cast<uint32_t>(C); o += 16u) {
+        const uint32_t co = cnt[o], so = used[o];
+        if (co >= kCap && (co > ck || (co == ck && (so < sk || (so == sk && o < z))))) ++rank;
+      }
     }
     key[tid] = ((kCap - cc) << 20) | ((rank >> 1) << 15) | ((z & 15u) << 11) | ((rank & 1u) << 10) | z;
   } else {
@@ -276,7 +289,7 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   uint32_t om = cz > kCap ? cz - kCap : 0u;
   for (int o = 16; o > 0; o >>= 1) om = max(om, __shfl_xor_sync(0xFFFFFFFFu, om, o));
   if (lane == 0 && live) {
-    gword[warp] = cm | (any_ovf ? 0x80000000u : 0u);
+    gword[warp] = cm | (min(om, 0x7FFFu) << 16) | (any_ovf ? 0x80000000u : 0u);
     gcost[warp] = cm + om;
   }
   // overflow list offsets, by bucket index: block-wide exclusive scan
@@ -342,11 +355,12 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
   const uint32_t my_oof = wtot[warp] + incl - ov;   // bucket tid's first overflow slot
   if (tid < C) oo[tid] = my_oof;
   // the records themselves are placed by k_frontend_records
+
 }
 
 // Records of one bucket group (one warp per (t, side, group)): each lane's
 // entries (the first kFeCap of its bucket in x order) and the overflow
-// entries of its bucket.  The entries are ordered bank-aware: step r gives
+// entries of its bucket (x and its packed hash).  The entries are ordered bank-aware: step r gives
 // each lane, in order of ascending count, its remaining entry whose bank
 // (x mod 32) is least used at this step so far; padding lanes all read
 // x = n (one address).  The order is sequential over the lanes, so the
@@ -355,7 +369,8 @@ __global__ void __launch_bounds__(32)
 k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ perm,
                    const uint32_t* __restrict__ off, uint32_t n, uint32_t ecap, uint32_t* __restrict__ rec_x,
                    uint32_t* __restrict__ rec_hs, const uint32_t* __restrict__ grp, const uint16_t* __restrict__ dest,
-                   const uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x, int C) {
+                   const uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x,
+                   uint32_t* __restrict__ ovf_hs, int C) {
   constexpr uint32_t kCap = static_cast<uint32_t>(kFeCap);
   __shared__ uint32_t ub[32];
   const int L = (C + 31) / 32;
@@ -376,6 +391,7 @@ k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__
   const uint32_t o0 = of[zs];
   const uint32_t oz = ovf_off[static_cast<size_t>(ts) * (C + 1) + zs];
   uint32_t* ox = ovf_x + static_cast<size_t>(ts) * n;
+  uint32_t* oh = ovf_hs + static_cast<size_t>(ts) * n;
   uint32_t xs[kFeCap], wsv[kFeCap];
 #pragma unroll
   for (uint32_t r = 0; r < kCap; ++r)
@@ -383,7 +399,11 @@ k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__
 #pragma unroll
   for (uint32_t r = 0; r < kCap; ++r)
     if (r < c) wsv[r] = tab[xs[r]];
-  for (uint32_t r = kCap; r < cz; ++r) ox[oz + (r - kCap)] = pm[o0 + r];
+  for (uint32_t r = kCap; r < cz; ++r) {
+    const uint32_t x = pm[o0 + r];
+    ox[oz + (r - kCap)] = x;
+    oh[oz + (r - kCap)] = tab[x];
+  }
   uint32_t rank = 0;
   for (int o = 0; o < 32; ++o) {
     const uint32_t co = __shfl_sync(0xFFFFFFFFu, c, o);
@@ -437,7 +457,7 @@ k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__
 cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, const uint32_t* off, int d,
                                    int64_t n, int64_t C, uint32_t ecap, uint32_t* rec_x, uint32_t* rec_hs,
                                    uint32_t* grp, uint16_t* dest, uint32_t* ovf_off, uint32_t* ovf_x,
-                                   uint8_t* assign, cudaStream_t s) {
+                                   uint8_t* assign, uint32_t* ovf_hs, cudaStream_t s) {
   {
     ProfScope prof_scope("k_frontend_tables", s);
     k_frontend_tables<<<2 * d, kFeC, 0, s>>>(hs, perm, off, static_cast<uint32_t>(n), ecap, rec_x, rec_hs,
@@ -447,7 +467,7 @@ cudaError_t launch_frontend_tables(const uint32_t* hs, const uint32_t* perm, con
     ProfScope prof_scope("k_frontend_records", s);
     const unsigned groups = static_cast<unsigned>(2 * d * ((C + 31) / 32));
     k_frontend_records<<<groups, 32, 0, s>>>(hs, perm, off, static_cast<uint32_t>(n), ecap, rec_x, rec_hs, grp,
-                                              dest, ovf_off, ovf_x, static_cast<int>(C));
+                                              dest, ovf_off, ovf_x, ovf_hs, static_cast<int>(C));
   }
   return cudaGetLastError();
 }
