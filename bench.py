@@ -37,8 +37,11 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_sketch_ws_covariance.json")
 # the fused sketch kernels' profiling names: warp-specialised, lock-step,
 # shared-memory (generic)
 SKETCH_KERNEL_NAMES = ("k_sketch_ws", "k_sketch_fast", "k_sketch_fused")
+# the sources of the dominant kernel's code and launch: the kernel itself,
+# its helpers, the planner that shapes its launch and the table builder whose
+# records it reads (a change to any of them voids the kept DRAM counters)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1108_1320_gb300", "csrc", f)
-                  for f in ("k_sketch.cu", "k_sketch_fast.cu", "k_sketch_ws.cu", "warp_fft.cuh",
+                  for f in ("k_sketch.cu", "k_sketch_ws.cu", "k_tables.cu", "warp_fft.cuh",
                             "cms_common.cuh")]
 
 
