@@ -91,7 +91,7 @@ struct WsArgs {
   const uint16_t* dest;
   const uint32_t* ovf_off;
   const uint32_t* ovf_x;
-  const uint32_t* hs;
+  const uint32_t* ovf_hs;  // packed hash of each overflow entry
   const uint8_t* assign;   // [t][side][32]: bucket group of (front-end warp, slot)
   float2* partial;
   const float2* thi_g;  // w_b^{i 2^tw_shift}, i < nhi (k_twiddle_table, FP64)
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       const uint32_t side = i >= novf_a ? 1u : 0u;
       const size_t ts = static_cast<size_t>(t) * 2 + side;
       const uint32_t x = p.ovf_x[ts * n + (i - side * novf_a)];
-      const uint32_t hv = p.hs[ts * n + x];
+      const uint32_t hv = p.ovf_hs[ts * n + (i - side * novf_a)];
       float2 w0 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[0], modb), p.tw_shift);
       float2 w1 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[1], modb), p.tw_shift);
       if (hv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
             } else {
               // beyond the cache: twiddles on the fly
               const uint32_t x = p.ovf_x[ts * n + o];
-              const uint32_t hv = p.hs[ts * n + x];
+              const uint32_t hv = p.ovf_hs[ts * n + o];
               float2 w0 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[0], modb), p.tw_shift);
               float2 w1 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[1], modb), p.tw_shift);
               if (hv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
@@ -880,7 +880,7 @@ cudaError_t launch_sketch_ws(const SketchPlan& plan, const cms_hashes* h, const 
   a.dest = h->d_fe_dest;
   a.ovf_off = h->d_fe_ovf_off;
   a.ovf_x = h->d_fe_ovf_x;
-  a.hs = h->d_hs;
+  a.ovf_hs = h->d_fe_ovf_hs;
   a.assign = h->d_fe_assign;
   a.partial = partial;
   a.thi_g = thi;

@@ -629,6 +629,36 @@ def test_lockstep_kernel_with_tensor_memory_records(cms, n1, n2, n3, b, d, dtype
     h.free()
 
 
+def test_lockstep_kernel_long_overflow_lists(cms):
+    # 12 entries per bucket class on average at C = 1024 (a drawn hash):
+    # nearly every bucket holds more than the 8 recorded entries, so every
+    # bucket group walks overflow lists of several entries per lane, with
+    # twiddles formed on the fly; the sketch is also bit-identical across
+    # two calls
+    m, n, b, d = 12, 12288, 16384, 2
+    X = W.gaussian(m, n, 71).astype(np.float32)
+    Xr = W.bf16_round(X)[0]
+    xt = torch.from_numpy(X).to(dev(), torch.bfloat16)
+    h = cms.make_hashes(72, n, b, d)
+    assert cms.plan_kernel(xt.T, xt, h) == "lockstep_tmem"
+    tab = O.make_tables(72, n, b, d)
+    counts = np.bincount(tab.h1[0] % 1024, minlength=1024)
+    assert (counts > 8).mean() > 0.9 and counts.max() - 8 >= 4
+    c1 = cms.sketch_product(xt.T, xt, h)
+    c2 = cms.sketch_product(xt.T, xt, h)
+    cms.check_async()
+    assert torch.equal(c1, c2)
+    c = c1.cpu().numpy().astype(np.float64)
+    Xd = Xr.astype(np.float64)
+    zs = W.rng(73).choice(b, 64, replace=False)
+    for t in range(d):
+        want = O.sketch_bucket_values(Xd.T, Xd, tab, t, zs)
+        assert np.linalg.norm(c[t, zs] - want) / np.linalg.norm(want) < TOL_F32, t
+        dc = (tab.s1[t] @ Xd.T) @ (Xd @ tab.s2[t])
+        assert abs(c[t].sum() - dc) < 1e-5 * np.abs(c[t]).sum()
+    h.free()
+
+
 def test_warp_specialised_kernel_both_spectrum_swaps(cms, monkeypatch):
     # the partner FFT warps swap half spectra through tensor memory; blocks
     # whose front-end records leave no room take the shared-memory swap
