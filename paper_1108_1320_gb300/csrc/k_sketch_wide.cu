@@ -42,10 +42,7 @@ using namespace wfft;
 constexpr int kCl = 8;                 // CTAs per cluster
 constexpr int kL = 8192;               // local FFT length
 constexpr int kCw = kCl * kL;          // row length C = 65536
-#ifndef CMS_WIDE_THREADS
-#define CMS_WIDE_THREADS 256
-#endif
-constexpr int kThr = CMS_WIDE_THREADS;  // threads per CTA
+constexpr int kThr = 256;               // threads per CTA
 constexpr int kWarps = kThr / 32;
 constexpr int kQ = 1024 / kThr;         // bin groups q per thread (8 bins each)
 constexpr int kKeys = 2 * kL;           // (side, v) bucket keys per CTA
@@ -57,7 +54,6 @@ constexpr int kStageBytes = 65536;      // staging row(s) of a_k, b_k
 constexpr int kChunk = 512 / (kWarps / 4);
 constexpr int kAccCol = kChunk - 32 * kQ;
 constexpr int kCap = kAccCol / 3;       // records per thread
-static_assert(kThr == 256 || kThr == 512, "256 or 512 threads");
 static_assert(3 * kCap <= kAccCol, "record columns overlap the accumulators");
 
 __device__ uint32_t g_wide_error = 0;   // 1: a wait gave up
@@ -377,35 +373,40 @@ __global__ void __launch_bounds__(kThr, 1) k_sketch_wide(WideArgs p) {
       }
     }
     __syncthreads();
-    // ---- length-1024 FFT over m per (side, f8) block, one warp each ---------
+    // ---- length-1024 FFT over m per (side, f8) block ------------------------
+    static_assert(kWarps == 8, "warp w runs the block pair of f8 = w");
     // lane l holds B[l + 32 j]: DFT-32 over j, twiddle w_1024^{l q1}, transpose
-    // (XOR-swizzled in place), DFT-32 over l: lane q1 ends with bins q1 + 32 q2
-#pragma unroll 1
-    for (int bi = warp; bi < 16; bi += kWarps) {
-      float2* blk = Y + bi * 1024;
-      float2 x[32];
+    // (XOR-swizzled in place), DFT-32 over l: lane q1 ends with bins q1 + 32 q2.
+    // Warp w runs blocks w and w + 8 (the two sides of f8 = w) side by side,
+    // two independent streams of arithmetic for the scheduler
+    {
+      float2* blk0 = Y + warp * 1024;
+      float2* blk1 = Y + (warp + 8) * 1024;
+      float2 x0[32], x1[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) x[j] = blk[lane + 32 * j];
-      dft32<false>(x);
+      for (int j = 0; j < 32; ++j) { x0[j] = blk0[lane + 32 * j]; x1[j] = blk1[lane + 32 * j]; }
+      dft32<false>(x0);
+      dft32<false>(x1);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         float2 w = anchor[q];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-          if (q + r > 0) x[8 * q + r] = cmul(x[8 * q + r], w);
+          if (q + r > 0) { x0[8 * q + r] = cmul(x0[8 * q + r], w); x1[8 * q + r] = cmul(x1[8 * q + r], w); }
           w = cmul(w, step);
         }
       }
       __syncwarp();
 #pragma unroll
-      for (int f = 0; f < 32; ++f) blk[f * 32 + (lane ^ f)] = x[f];
+      for (int f = 0; f < 32; ++f) { blk0[f * 32 + (lane ^ f)] = x0[f]; blk1[f * 32 + (lane ^ f)] = x1[f]; }
       __syncwarp();
 #pragma unroll
-      for (int j = 0; j < 32; ++j) x[j] = blk[lane * 32 + (j ^ lane)];
-      dft32<false>(x);
+      for (int j = 0; j < 32; ++j) { x0[j] = blk0[lane * 32 + (j ^ lane)]; x1[j] = blk1[lane * 32 + (j ^ lane)]; }
+      dft32<false>(x0);
+      dft32<false>(x1);
       __syncwarp();
 #pragma unroll
-      for (int j = 0; j < 32; ++j) blk[lane + 32 * j] = x[j];
+      for (int j = 0; j < 32; ++j) { blk0[lane + 32 * j] = x0[j]; blk1[lane + 32 * j] = x1[j]; }
     }
     // ---- every CTA's L_u ready: length-8 DFT over u, products, Kahan -------
     cluster_arrive();
