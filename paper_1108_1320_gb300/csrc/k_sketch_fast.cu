@@ -117,17 +117,6 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   return L;
 }
 
-// w_b^m = exp(-2 pi i m / b) for the overflow entries, without the shared
-// twiddle tables: the phase is reduced exactly in integers to m - b in
-// (-b/2, b/2], so the angle lies in [-pi, pi], where the hardware sine and
-// cosine (__sincosf) have an absolute error of about 4e-7; w2 = 2 pi / b.
-__device__ __forceinline__ float2 wb_sfu(uint32_t m, uint32_t b, float w2) {
-  const int32_t ms = m > (b >> 1) ? static_cast<int32_t>(m) - static_cast<int32_t>(b) : static_cast<int32_t>(m);
-  float sn, cs;
-  __sincosf(static_cast<float>(ms) * w2, &sn, &cs);
-  return make_float2(cs, -sn);
-}
-
 // One task (t, row pair, k-range) of the fast kernel; `sm` is the block's
 // dynamic shared memory (fast_layout).
 //

@@ -594,11 +594,17 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
               w = ovtw[obase + o];
               xi = ovx[obase + o];
             } else {
-              // beyond the cache: twiddles on the fly
+              // beyond the cache: twiddles on the fly (rows f1 and f1 + 1,
+              // or the same row twice: one reduction, the second phase
+              // is the first plus h mod b)
               const uint32_t x = p.ovf_x[ts * n + o];
               const uint32_t hv = p.ovf_hs[ts * n + o];
-              float2 w0 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[0], modb), p.tw_shift);
-              float2 w1 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[1], modb), p.tw_shift);
+              const uint32_t hb = hv & kBucketMask, bb = static_cast<uint32_t>(p.b);
+              const uint32_t e0 = mulmod(hb, f1r[0], modb);
+              uint32_t e1 = f1r[1] != f1r[0] ? e0 + hb : e0;
+              if (e1 >= bb) e1 -= bb;
+              float2 w0 = wb(tlo, thi, e0, p.tw_shift);
+              float2 w1 = wb(tlo, thi, e1, p.tw_shift);
               if (hv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
               w = make_float4(w0.x, w0.y, w1.x, w1.y);
               xi = soff + x;

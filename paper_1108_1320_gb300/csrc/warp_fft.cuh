@@ -320,6 +320,18 @@ __device__ __forceinline__ float2 wb(const float2* tlo, const float2* thi, uint3
   return cmul(thi[m >> sh], tlo[m & ((1u << sh) - 1u)]);
 }
 
+// w_b^m = exp(-2 pi i m / b) without the shared twiddle tables (for the
+// entries past the recorded ones): the phase is reduced exactly in
+// integers to m - b in (-b/2, b/2], so the angle lies in [-pi, pi], where
+// the hardware sine and cosine (__sincosf) have an absolute error of about
+// 4e-7; w2 = 2 pi / b.
+__device__ __forceinline__ float2 wb_sfu(uint32_t m, uint32_t b, float w2) {
+  const int32_t ms = m > (b >> 1) ? static_cast<int32_t>(m) - static_cast<int32_t>(b) : static_cast<int32_t>(m);
+  float sn, cs;
+  __sincosf(static_cast<float>(ms) * w2, &sn, &cs);
+  return make_float2(cs, -sn);
+}
+
 // (h f1) mod b for h < b <= 2^31, f1 < 2^21 by a Barrett reduction with
 // m = floor((2^64 - 1) / b): the estimate q = mulhi(h f1, m) is floor(h f1 / b)
 // or one less (h f1 < 2^52), so one conditional subtraction is exact.
