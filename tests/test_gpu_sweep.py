@@ -46,6 +46,8 @@ CASES = [
     (96, 5, 80, 96, 2, "f32", False, 0),
     (1536, 8, 1536, 24576, 6, "f32", True, 0),
     (800, 25, 800, 4000, 7, "bf16", True, 0),
+    (1024, 21, 960, 32768, 3, "f32", False, 0),   # warp-specialised: two operands, odd inner dimension
+    (2048, 13, 2048, 65536, 2, "f32", True, 0),   # warp-specialised: aliased, odd inner dimension
 ]
 DT = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}
 
@@ -104,3 +106,14 @@ def test_sweep_reaches_every_kernel_family(cms):
     seen.add(cms.plan_kernel(x.T, x, h))
     h.free()
     assert seen == {"shared_memory", "lockstep", "lockstep_tmem", "warp_specialised", "cluster"}, seen
+
+
+def test_warp_specialised_cases_take_that_kernel(cms):
+    # the two odd-inner-dimension cases above run the warp-specialised
+    # kernel (its last group then holds one inner index)
+    for n1, n2, n3, b, d, dts, alias, pad in CASES[-2:]:
+        h = cms.make_hashes(1, max(n1, n3), b, d)
+        xt = torch.zeros((n2, n1), dtype=DT[dts], device=dev())
+        B = xt if alias else torch.zeros((n2, n3), dtype=DT[dts], device=dev())
+        assert cms.plan_kernel(xt.T, B, h) == "warp_specialised", (n1, n2, n3)
+        h.free()
