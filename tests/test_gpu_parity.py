@@ -479,6 +479,34 @@ def test_fast_kernel_overflow_buckets(cms):
     h.free()
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_fast_kernel_overflow_with_unaligned_rows(cms, dtype):
+    # rows not in whole 16-byte units (n1, n3 not multiples of the 16-byte
+    # element count; staged as aligned supersets) and side-a buckets of 31
+    # or 32 entries: the overflow entries are walked per lane with the
+    # staging offsets of unaligned rows, odd inner dimension
+    n1, n2, n3, b = 250, 37, 253, 1024
+    n = max(n1, n3)
+    A = W.gaussian(n1, n2, 81).astype(np.float32)
+    B = W.gaussian(n2, n3, 82).astype(np.float32)
+    Ar = W.bf16_round(A)[0] if dtype == torch.bfloat16 else A
+    Br = W.bf16_round(B)[0] if dtype == torch.bfloat16 else B
+    g = W.rng(83)
+    h1 = (np.arange(n) % 8 * 129)[None, :].astype(np.uint32)
+    h2 = g.integers(0, b, size=(1, n)).astype(np.uint32)
+    s1 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    s2 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    h = cms.Hashes.from_tables(h1, s1, h2, s2, b)
+    Ad, Bd = colmajor(A, dtype), rowmajor(B, dtype)
+    assert cms.plan_kernel(Ad, Bd, h) == "lockstep"
+    c = cms.sketch_product(Ad, Bd, h).cpu().numpy()
+    cms.check_async()
+    tab = O.Tables(h1.astype(np.int64), s1.astype(np.int64), h2.astype(np.int64), s2.astype(np.int64), b)
+    ref = O.sketch_definition(Ar.astype(np.float64), Br.astype(np.float64), tab)
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
 def test_overflow_lists_beyond_the_twiddle_cache(cms):
     # side-a hash with 2 buckets of 1024 entries each: 2032 entries go through
     # the overflow lists, more than the fused kernel caches per task (at most
