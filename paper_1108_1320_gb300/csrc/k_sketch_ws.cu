@@ -100,7 +100,7 @@ struct WsArgs {
 };
 
 struct WsLayout {
-  size_t stage, rec_x, ybuf, acc, tlo, thi, wmeta, wdst, ibase, istart, wcls, wcol, ovf, wovf, ovtw, ovx, bars, total;
+  size_t stage, rec_x, ybuf, acc, tlo, thi, wmeta, wdst, ibase, istart, wcls, wcol, wext, ovf, wovf, ovtw, ovx, bars, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
@@ -126,6 +126,7 @@ __host__ __device__ inline WsLayout ws_layout(int npad, uint32_t ecap, int alias
   L.istart = o; o = al16(o + static_cast<size_t>(kItems + 1) * 4);
   L.wcls = o;   o = al16(o + static_cast<size_t>(kFeWarps) * 16);
   L.wcol = o;   o = al16(o + static_cast<size_t>(kItems) * 2);
+  L.wext = o;   o = al16(o + static_cast<size_t>(kItems + kFeWarps) * 2);
   L.ovf = o;    o = al16(o + static_cast<size_t>(2) * (kC + 1) * 2);
   L.wovf = o;   o = al16(o + static_cast<size_t>(kFeWarps) * 4);
   L.ovtw = o;   o = al16(o + static_cast<size_t>(ovcap) * 16);
@@ -177,6 +178,16 @@ __device__ __forceinline__ void tmem_ld_part(uint32_t taddr, uint32_t* r) {
         : "r"(taddr)
         : "memory");
   }
+}
+
+// Wait for this thread's tensor-memory loads into a[0..15] and b[0..3].
+__device__ __forceinline__ void tmem_wait_ld16_4(uint32_t (&a)[32], uint32_t (&b)[4]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]),
+                 "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]),
+                 "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3])
+               :
+               : "memory");
 }
 
 // The records of a chunk: NCOL = 4, 8, 12 or 16 columns from a column that
@@ -284,12 +295,15 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
   float4* acc = reinterpret_cast<float4*>(sm + L.acc);
   float2* tlo = reinterpret_cast<float2*>(sm + L.tlo);
   float2* thi = reinterpret_cast<float2*>(sm + L.thi);
-  uint32_t* wmeta = reinterpret_cast<uint32_t*>(sm + L.wmeta);     // [fe warp][item]: cnt | side << 8 | ovf << 31
+  uint32_t* wmeta = reinterpret_cast<uint32_t*>(sm + L.wmeta);     // [fe warp][item]: cnt | side << 8 | longest overflow list << 9 | ovf << 31
   uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);       // [fe warp][item][lane]: Y slot (row 0, k 0)
   uint32_t* ibase = reinterpret_cast<uint32_t*>(sm + L.ibase);     // [fe warp][item]: side * ecap + first record
   uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart);   // [fe warp][item]: first stream slot
   uint8_t* wcls = reinterpret_cast<uint8_t*>(sm + L.wcls);         // [fe warp][count]: items of that count
   uint16_t* wcol = reinterpret_cast<uint16_t*>(sm + L.wcol);       // [fe warp][item]: first TMEM column
+  // [fe warp][item]: first TMEM column of the item's overflow records (none:
+  // 0xFFFF); then [fe warp]: end of the warp's item records
+  uint16_t* wext = reinterpret_cast<uint16_t*>(sm + L.wext);
   uint16_t* ovf = reinterpret_cast<uint16_t*>(sm + L.ovf);
   uint32_t* wovf = reinterpret_cast<uint32_t*>(sm + L.wovf);
   float4* ovtw = reinterpret_cast<float4*>(sm + L.ovtw);         // cached overflow twiddles (both rows)
@@ -338,7 +352,8 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
     const size_t ts = static_cast<size_t>(t) * 2 + side;
     const uint32_t gb = p.grp[(ts * (kC / 32) + gi) * 2];
     const uint32_t gy = p.grp[(ts * (kC / 32) + gi) * 2 + 1];
-    wmeta[tid] = (gy & 0xFFu) | (static_cast<uint32_t>(side) << 8) | (gy & 0x80000000u);
+    wmeta[tid] = (gy & 0xFFu) | (static_cast<uint32_t>(side) << 8) | (((gy >> 16) & 0x7FFFu) << 9) |
+                 (gy & 0x80000000u);
     ibase[tid] = static_cast<uint32_t>(side) * p.ecap + gb;
   }
   for (int i = tid; i < kFeWarps * 32 * kItemsFe; i += kThreadsWs) {
@@ -443,6 +458,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
         }
       }
     for (; q < kItemsFe; ++q) wcol[tid * kItemsFe + q] = 0;
+    wext[kItems + tid] = static_cast<uint16_t>(col);
     // more records than the warp's share of its quarter: this block keeps
     // the full halves for the records and swaps spectra in shared memory
     if (col > kFeColCap) atomicOr(&s_xsmem, 1);
@@ -521,6 +537,65 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
       }
       tmem_wait_st();
     }
+    // overflow records: the entries past the capped count of an item's
+    // buckets, for items whose lists fit the warp's free tensor-memory
+    // columns after its records (heavy draws leave many items empty): step r
+    // of the item (entry r of each lane's list, zero-padded to a multiple of
+    // 4 steps) has its twiddles at column e + 4 r and its staging index at
+    // column e + 4 om4 + r, e a multiple of 16
+    {
+      const uint16_t* wdx = wdst + w * kItemsFe * 32 + lane;
+      if (lane == 0) {
+        const uint32_t capw = xsmem ? 256u : kFeColCap;
+        uint32_t ec = (static_cast<uint32_t>(wext[kItems + w]) + 15u) & ~15u;
+        for (int j = 0; j < kItemsFe; ++j) {
+          const uint32_t om = (wmeta[w * kItemsFe + j] >> 9) & 0x7FFFu;
+          const uint32_t om4 = (om + 3u) & ~3u;
+          uint16_t e = 0xFFFFu;
+          if (om > 0 && ec + 5u * om4 <= capw) {
+            e = static_cast<uint16_t>(ec);
+            ec = (ec + 5u * om4 + 15u) & ~15u;
+          }
+          wext[w * kItemsFe + j] = e;
+        }
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (int j = 0; j < kItemsFe; ++j) {
+        const uint32_t e = wext[w * kItemsFe + j];
+        if (e == 0xFFFFu) continue;
+        const uint32_t m = wmeta[w * kItemsFe + j];
+        const uint32_t om4 = (((m >> 9) & 0x7FFFu) + 3u) & ~3u;
+        const uint32_t side = (m >> 8) & 1u;
+        const uint32_t z2 = static_cast<uint32_t>(wdx[32 * j]) - side * static_cast<uint32_t>(kG * kRegion);
+        const size_t ts = static_cast<size_t>(t) * 2 + side;
+        const uint32_t soff = p.alias ? 0u : side * static_cast<uint32_t>(kG * p.npad);
+        uint32_t o0 = 0, o1 = 0;
+        if (z2 < static_cast<uint32_t>(kC)) {
+          o0 = ovf[side * (kC + 1) + z2];
+          o1 = ovf[side * (kC + 1) + z2 + 1];
+        }
+#pragma unroll 1
+        for (uint32_t r = 0; r < om4; ++r) {
+          float4 tw = make_float4(0.f, 0.f, 0.f, 0.f);
+          uint32_t xs = 0;
+          if (o0 + r < o1) {
+            const uint32_t o = o0 + r;
+            const uint32_t x = p.ovf_x[ts * n + o];
+            const uint32_t hv = p.ovf_hs[ts * n + o];
+            float2 w0 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[0], modb), p.tw_shift);
+            float2 w1 = wb(tlo, thi, mulmod(hv & kBucketMask, f1r[1], modb), p.tw_shift);
+            if (hv >> 31) { w0.x = -w0.x; w0.y = -w0.y; w1.x = -w1.x; w1.y = -w1.y; }
+            tw = make_float4(w0.x, w0.y, w1.x, w1.y);
+            xs = soff + x;
+          }
+          __syncwarp();   // the tensor-memory stores are warp-collective
+          tmem_st4(tq + e + 4u * r, tw);
+          tmem_st1(tq + e + 4u * om4 + r, xs);
+        }
+      }
+      tmem_wait_st();
+    }
     // twiddles of the entries past the capped count (overflow lists of both
     // sides), cached for the whole task up to the shared-memory capacity
     const uint32_t novf_a = ovf[kC];
@@ -586,6 +661,30 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
           const uint32_t obase = side ? novf_a : 0u;
           const uint32_t soff = p.alias ? 0u : static_cast<uint32_t>(side * kG * p.npad);
           float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
+          const uint32_t e = wext[w * kItemsFe + j];
+          if (e != 0xFFFFu) {
+            // from the overflow records, 4 steps per load
+            const uint32_t om4 = (((m >> 9) & 0x7FFFu) + 3u) & ~3u;
+#pragma unroll 1
+            for (uint32_t r0 = 0; r0 < om4; r0 += 4) {
+              uint32_t tw[32], xr[4];
+              __syncwarp();
+              tmem_ld_part<16>(tq + e + 4u * r0, tw);
+              tmem_ld_part<4>(tq + e + 4u * om4 + r0, xr);
+              tmem_wait_ld16_4(tw, xr);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const float v0 = st0[xr[i]];
+                const float v1 = st1[xr[i]];
+                const float w0 = __uint_as_float(tw[4 * i]), w1 = __uint_as_float(tw[4 * i + 1]);
+                const float w2 = __uint_as_float(tw[4 * i + 2]), w3 = __uint_as_float(tw[4 * i + 3]);
+                a00.x = fmaf(v0, w0, a00.x); a00.y = fmaf(v0, w1, a00.y);
+                a01.x = fmaf(v1, w0, a01.x); a01.y = fmaf(v1, w1, a01.y);
+                a10.x = fmaf(v0, w2, a10.x); a10.y = fmaf(v0, w3, a10.y);
+                a11.x = fmaf(v1, w2, a11.x); a11.y = fmaf(v1, w3, a11.y);
+              }
+            }
+          } else {
           const uint32_t o1 = ovf[side * (kC + 1) + z2 + 1];
           for (uint32_t o = ovf[side * (kC + 1) + z2]; o < o1; ++o) {
             float4 w;
@@ -615,6 +714,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_sketch_ws(WsArgs p) {
             a01.x = fmaf(v1, w.x, a01.x); a01.y = fmaf(v1, w.y, a01.y);
             a10.x = fmaf(v0, w.z, a10.x); a10.y = fmaf(v0, w.w, a10.y);
             a11.x = fmaf(v1, w.z, a11.x); a11.y = fmaf(v1, w.w, a11.y);
+          }
           }
           float2* dp = work + dst;
           dp[0].x += a00.x; dp[0].y += a00.y;

@@ -507,6 +507,29 @@ def test_fast_kernel_overflow_with_unaligned_rows(cms, dtype):
     h.free()
 
 
+def test_warp_specialised_overflow_records_in_tensor_memory(cms):
+    # side-a hash with 128 buckets of 16 entries (8 past the records each)
+    # and the other 896 empty: the warp-specialised front end keeps those
+    # overflow entries as records in its free tensor-memory columns; odd
+    # inner dimension, X^T X (aliased operands)
+    n, m, b = 2048, 45, 65536
+    X = W.gaussian(m, n, 91).astype(np.float32)
+    g = W.rng(92)
+    h1 = ((np.arange(n) % 128) * 8 + 3 + 1024 * g.integers(0, 64, size=n))[None, :].astype(np.uint32)
+    h2 = g.integers(0, b, size=(1, n)).astype(np.uint32)
+    s1 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    s2 = g.choice([-1, 1], size=(1, n)).astype(np.int8)
+    h = cms.Hashes.from_tables(h1, s1, h2, s2, b)
+    xt = torch.from_numpy(X).to(dev())
+    assert cms.plan_kernel(xt.T, xt, h) == "warp_specialised"
+    c = cms.sketch_product(xt.T, xt, h).cpu().numpy()
+    cms.check_async()
+    tab = O.Tables(h1.astype(np.int64), s1.astype(np.int64), h2.astype(np.int64), s2.astype(np.int64), b)
+    ref = O.sketch_definition(X.T.astype(np.float64), X.astype(np.float64), tab)
+    assert O.rel_l2(c, ref) < TOL_F32
+    h.free()
+
+
 def test_overflow_lists_beyond_the_twiddle_cache(cms):
     # side-a hash with 2 buckets of 1024 entries each: 2032 entries go through
     # the overflow lists, more than the fused kernel caches per task (at most
