@@ -680,20 +680,22 @@ def test_lockstep_kernel_with_tensor_memory_records(cms, n1, n2, n3, b, d, dtype
     h.free()
 
 
-def test_lockstep_kernel_long_overflow_lists(cms):
-    # 12 entries per bucket class on average at C = 1024 (a drawn hash):
-    # nearly every bucket holds more than the 8 recorded entries, so every
-    # bucket group walks overflow lists of several entries per lane, with
-    # twiddles formed on the fly; the sketch is also bit-identical across
-    # two calls
-    m, n, b, d = 12, 12288, 16384, 2
+@pytest.mark.parametrize("n,b,C", [(12288, 16384, 1024), (10800, 13824, 864)])
+def test_lockstep_kernel_long_overflow_lists(cms, n, b, C):
+    # 12 to 12.5 entries per bucket class on average (a drawn hash): nearly
+    # every bucket holds more than the 8 recorded entries, so every bucket
+    # group walks overflow lists of several entries per lane, with twiddles
+    # formed on the fly (C = 1024, and C = 864 with items of 27 buckets);
+    # the sketch is also bit-identical across two calls
+    m, d = 12, 2
     X = W.gaussian(m, n, 71).astype(np.float32)
     Xr = W.bf16_round(X)[0]
     xt = torch.from_numpy(X).to(dev(), torch.bfloat16)
     h = cms.make_hashes(72, n, b, d)
     assert cms.plan_kernel(xt.T, xt, h) == "lockstep_tmem"
     tab = O.make_tables(72, n, b, d)
-    counts = np.bincount(tab.h1[0] % 1024, minlength=1024)
+    assert h.info()["C"] == C
+    counts = np.bincount(tab.h1[0] % C, minlength=C)
     assert (counts > 8).mean() > 0.9 and counts.max() - 8 >= 4
     c1 = cms.sketch_product(xt.T, xt, h)
     c2 = cms.sketch_product(xt.T, xt, h)
