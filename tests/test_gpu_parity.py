@@ -507,11 +507,16 @@ def test_fast_kernel_overflow_with_unaligned_rows(cms, dtype):
     h.free()
 
 
-def test_warp_specialised_overflow_records_in_tensor_memory(cms):
+@pytest.mark.parametrize("smem_swap", [False, True])
+def test_warp_specialised_overflow_records_in_tensor_memory(cms, monkeypatch, smem_swap):
     # side-a hash with 128 buckets of 16 entries (8 past the records each)
     # and the other 896 empty: the warp-specialised front end keeps those
-    # overflow entries as records in its free tensor-memory columns; odd
-    # inner dimension, X^T X (aliased operands)
+    # overflow entries as records in its free tensor-memory columns (192
+    # per warp, or 256 in blocks that swap spectra through shared memory,
+    # forced here by the library's debug switch); odd inner dimension,
+    # X^T X (aliased operands)
+    if smem_swap:
+        monkeypatch.setenv("CMS_WS_SMEM_SWAP", "1")
     n, m, b = 2048, 45, 65536
     X = W.gaussian(m, n, 91).astype(np.float32)
     g = W.rng(92)
