@@ -131,6 +131,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
 #pragma unroll
   for (int m = 0; m < 16; ++m) part[m] = make_float2(0.f, 0.f);
 
+  // one nonzero of the warp's (side, k): its contribution s(x) v w_b^{f1 h(x)}
+  // added to Y[h mod C] (lanes with distinct buckets in parallel, colliding
+  // lanes in lane order)
+  auto scatter = [&](bool valid, int32_t x, float v, uint32_t w) {
+    uint32_t z2 = 0x80000000u | static_cast<uint32_t>(lane);   // unique sentinel
+    float2 contrib = make_float2(0.f, 0.f);
+    if (valid && x >= 0 && x < nside) {
+      const uint32_t h = w & kBucketMask;
+      float2 tw = wb(tlo, thi, mulmod(h, f1, modb), p.tw_shift);
+      if (w >> 31) { tw.x = -tw.x; tw.y = -tw.y; }
+      contrib = make_float2(v * tw.x, v * tw.y);
+      z2 = h & (kC - 1);
+    }
+    // lanes sharing a bucket add in lane order: round q takes each bucket's
+    // q-th lane, so the rounds are as many as the largest multiplicity
+    const uint32_t same = __match_any_sync(0xFFFFFFFFu, z2);
+    const uint32_t rank = __popc(same & ((1u << lane) - 1u));
+    const uint32_t nrank = __reduce_max_sync(0xFFFFFFFFu, rank);
+    for (uint32_t q = 0; q <= nrank; ++q) {
+      if (rank == q && !(z2 >> 31)) {
+        float2 y = region[z2];
+        y.x += contrib.x;
+        y.y += contrib.y;
+        region[z2] = y;
+      }
+      __syncwarp();
+    }
+  };
+  // The first 32 nonzeros of each group's (side, k) are fetched during the
+  // previous group's FFT, one dependent level per FFT stage (inner index,
+  // column bounds, row index and value, hash), so the scatter finds them in
+  // registers; further nonzeros of a long column are loaded when scattered.
+  int64_t pe0 = 0, pe1 = 0;
+  int32_t px = -1;
+  float pv = 0.f;
+  uint32_t pw = 0;
+  if (l_begin + g_w < l_end) {
+    const int k = p.klist[l_begin + g_w];
+    pe0 = ptr[k];
+    pe1 = ptr[k + 1];
+    if (pe0 + lane < pe1) {
+      px = idx[pe0 + lane];
+      pv = ld_val<T>(val, pe0 + lane);
+      if (px >= 0 && px < nside) pw = __ldg(tab + px);
+    }
+  }
+
   int group = 0;
   for (int l0 = l_begin; l0 < l_end; l0 += kG, ++group) {
     const int gcnt = min(kG, l_end - l0);
@@ -140,54 +187,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     for (int i = 0; i < kC / 2 / 32; ++i) r4[lane + 32 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncwarp();
     if (g_w < gcnt) {
-      const int k = p.klist[l0 + g_w];
-      const int64_t e0 = ptr[k], e1 = ptr[k + 1];
-      for (int64_t base = e0; base < e1; base += 32) {
+      scatter(pe0 + lane < pe1, px, pv, pw);
+      for (int64_t base = pe0 + 32; base < pe1; base += 32) {
         const int64_t e = base + lane;
-        const bool valid = e < e1;
-        uint32_t z2 = 0x80000000u | static_cast<uint32_t>(lane);   // unique sentinel
-        float2 contrib = make_float2(0.f, 0.f);
+        const bool valid = e < pe1;
+        int32_t x = -1;
+        float v = 0.f;
+        uint32_t w = 0;
         if (valid) {
-          const int32_t x = idx[e];
-          const float v = ld_val<T>(val, e);
-          if (x >= 0 && x < nside) {
-            const uint32_t w = __ldg(tab + x);
-            const uint32_t h = w & kBucketMask;
-            float2 tw = wb(tlo, thi, mulmod(h, f1, modb), p.tw_shift);
-            if (w >> 31) { tw.x = -tw.x; tw.y = -tw.y; }
-            contrib = make_float2(v * tw.x, v * tw.y);
-            z2 = h & (kC - 1);
-          }
+          x = idx[e];
+          v = ld_val<T>(val, e);
+          if (x >= 0 && x < nside) w = __ldg(tab + x);
         }
-        const uint32_t same = __match_any_sync(0xFFFFFFFFu, z2);
-        const bool collide = __any_sync(0xFFFFFFFFu, __popc(same) > 1);
-        if (!collide) {
-          if (!(z2 >> 31)) {
-            float2 y = region[z2];
-            y.x += contrib.x;
-            y.y += contrib.y;
-            region[z2] = y;
-          }
-        } else {
-          for (int l = 0; l < 32; ++l) {
-            if (lane == l && !(z2 >> 31)) {
-              float2 y = region[z2];
-              y.x += contrib.x;
-              y.y += contrib.y;
-              region[z2] = y;
-            }
-            __syncwarp();
-          }
-        }
-        __syncwarp();
+        scatter(valid, x, v, w);
       }
     }
     __syncwarp();
+    // next group's inner index (first prefetch level)
+    const int ln = l0 + kG + g_w;
+    const int nk = ln < l_end ? p.klist[ln] : -1;
     // ---- FFT of length 1024 ----------------------------------------------
     float2 x[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
     dft32<false>(x);
+    // second prefetch level: the column bounds
+    int64_t ne0 = 0, ne1 = 0;
+    if (nk >= 0) {
+      ne0 = ptr[nk];
+      ne1 = ptr[nk + 1];
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float2 w = anchor[q];
@@ -203,7 +232,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 32; ++j) x[j] = region[lane * kPitch + j];
+    // third level: the lane's nonzero (row index and value)
+    int32_t nx = -1;
+    float nv = 0.f;
+    if (ne0 + lane < ne1) {
+      nx = idx[ne0 + lane];
+      nv = ld_val<T>(val, ne0 + lane);
+    }
     dft32<false>(x);
+    // fourth level: its hash
+    const uint32_t nw = (nx >= 0 && nx < nside) ? __ldg(tab + nx) : 0u;
     __syncwarp();
     if (side_w == 0) {
 #pragma unroll
@@ -234,6 +272,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
         }
       }
     }
+    pe0 = ne0;
+    pe1 = ne1;
+    px = nx;
+    pv = nv;
+    pw = nw;
     const bool last = l0 + kG >= l_end;
     if ((group % kFlush) == kFlush - 1 || last) {
       __syncthreads();
