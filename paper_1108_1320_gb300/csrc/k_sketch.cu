@@ -207,6 +207,47 @@ k_cols_inverse(const float2* __restrict__ V, const float2* __restrict__ twR, int
   cols_inverse_point(V, twR, b, R, C, nrows, c, static_cast<int>(blockIdx.y), z);
 }
 
+// K2b for long columns (large R): nv adjacent columns z2 of one repetition
+// per block; the full length-R spectrum of each is rebuilt from rows
+// 0..R/2 (row R - f1 is the conjugate of row f1) and inverted by the
+// shared-memory mixed-radix FFT (O(R log R) per column instead of the
+// direct sum's O(R^2)); c[z1 C + z2] = Re(x[z1]) / b.
+__global__ void __launch_bounds__(256)
+k_cols_inverse_fft(const float2* __restrict__ V, const float2* __restrict__ twR, int64_t b, int R, int C,
+                   int nrows, int nv, float* __restrict__ c, const int32_t* __restrict__ skip_if_zero) {
+  extern __shared__ __align__(16) float2 csm[];
+  if (skip_if_zero && *skip_if_zero == 0) return;
+  const int t = static_cast<int>(blockIdx.y);
+  const int z0 = static_cast<int>(blockIdx.x) * nv;
+  const int nvb = min(nv, C - z0);
+  const float2* Vt = V + static_cast<size_t>(t) * nrows * C;
+  float2* a = csm;
+  float2* bb = csm + static_cast<size_t>(nv) * R;
+  for (int i = threadIdx.x; i < R * nv; i += blockDim.x) {
+    const int f = i / nv, v = i - (i / nv) * nv;
+    float2 x = make_float2(0.f, 0.f);
+    if (v < nvb) {
+      if (f < nrows) {
+        x = Vt[static_cast<size_t>(f) * C + z0 + v];
+      } else {
+        const float2 y = Vt[static_cast<size_t>(R - f) * C + z0 + v];
+        x = make_float2(y.x, -y.y);
+      }
+    }
+    a[static_cast<size_t>(v) * R + f] = x;
+  }
+  __syncthreads();
+  int rad[16];
+  const int nrad = factor_radices(R, rad, 16);
+  const float2* out = fft_block<true>(a, bb, R, nv, rad, nrad, twR);
+  const float inv_b = 1.f / static_cast<float>(b);
+  float* ct = c + static_cast<size_t>(t) * b;
+  for (int i = threadIdx.x; i < R * nv; i += blockDim.x) {
+    const int z1 = i / nv, v = i - (i / nv) * nv;
+    if (v < nvb) ct[static_cast<size_t>(z1) * C + z0 + v] = out[static_cast<size_t>(v) * R + z1].x * inv_b;
+  }
+}
+
 struct ColsArgs {
   const float2* V;
   const float2* twR;
@@ -657,6 +698,22 @@ cudaError_t launch_inverse_batched(const InverseBatch& ib, cudaStream_t s) {
 
 cudaError_t launch_cols_inverse(const SketchPlan& plan, const float2* V, const float2* twR, float* c,
                                 cudaStream_t s, const int32_t* skip_if_zero) {
+  const int R = static_cast<int>(plan.R), C = static_cast<int>(plan.C);
+  int rad[16];
+  // long columns: an FFT per column (nv columns per block, 128 KB of shared
+  // memory at most) instead of the direct sum over the R/2 + 1 rows
+  if (R >= 256 && R <= 8192 && factor_radices(R, rad, 16) >= 0) {
+    const int nv = std::max(1, 8192 / R);
+    const int smem = 2 * nv * R * static_cast<int>(sizeof(float2));
+    cudaError_t e = cudaFuncSetAttribute(k_cols_inverse_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 g(static_cast<unsigned>((C + nv - 1) / nv), plan.d);
+    {
+      ProfScope prof_scope("k_cols_inverse", s);
+      k_cols_inverse_fft<<<g, 256, smem, s>>>(V, twR, plan.b, R, C, plan.nrows, nv, c, skip_if_zero);
+    }
+    return cudaGetLastError();
+  }
   dim3 g2(static_cast<unsigned>((plan.b + 255) / 256), plan.d);
   {
     ProfScope prof_scope("k_cols_inverse", s);
