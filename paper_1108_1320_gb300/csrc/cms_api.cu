@@ -423,7 +423,7 @@ cms_status cms_sparse_workspace_size(const cms_hashes* h, int64_t n1, int64_t n2
   SketchPlan plan;
   size_t off_klist = 0;
   std::string why;
-  int r = make_sparse_plan(h, n2, -1, dp.sms, &plan, &off_klist, &why);
+  int r = make_sparse_plan(h, n2, -1, dp.sms, dp.smem_optin, &plan, &off_klist, &why);
   if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
   *bytes = plan.ws_bytes;
   return CMS_OK;
@@ -446,7 +446,7 @@ cms_status cms_sketch_product_csr(const int64_t* a_colptr, const int32_t* a_rowi
   SketchPlan worst;
   size_t off_klist = 0;
   std::string why;
-  int r = make_sparse_plan(h, n2, -1, dp.sms, &worst, &off_klist, &why);
+  int r = make_sparse_plan(h, n2, -1, dp.sms, dp.smem_optin, &worst, &off_klist, &why);
   if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
   if (!ws || ws_bytes < worst.ws_bytes)
     return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_sparse_workspace_size()");
@@ -493,7 +493,7 @@ cms_status cms_sketch_product_csr_hybrid(const int64_t* a_colptr, const int32_t*
   SketchPlan worst;
   size_t off_klist = 0;
   std::string why;
-  int r = make_sparse_plan(h, n2, -1, dp.sms, &worst, &off_klist, &why);
+  int r = make_sparse_plan(h, n2, -1, dp.sms, dp.smem_optin, &worst, &off_klist, &why);
   if (r != CMS_OK) return fail(static_cast<cms_status>(r), why);
   if (!ws || ws_bytes < worst.ws_bytes)
     return fail(CMS_ERR_WORKSPACE, "workspace missing or smaller than cms_sparse_workspace_size()");

@@ -137,6 +137,7 @@ struct SketchPlan {
   int tw_shift = 0, nhi = 0;  // two-level w_b table: S = 2^tw_shift, nhi high entries
   bool wide = false;        // the cluster kernel for C = 2^16 rows (k_sketch_wide)
   bool tmem_rec = false;    // the lock-step kernel keeps its twiddle records in tensor memory
+  bool sparse_sepy = false; // the sparse kernel scatters into Y buffers of its own (kept zero)
   // workspace layout (byte offsets)
   size_t off_partial = 0, off_V = 0, off_twfe = 0, off_twC = 0, off_twR = 0;
   size_t off_thi = 0;   // warp-specialised kernel: w_b^{i 2^tw_shift}, i < nhi
@@ -245,8 +246,8 @@ struct SparseArgsHost {
   const int64_t* b_ptr; const int32_t* b_idx; const void* b_val;
   int n1, n3;
 };
-int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, SketchPlan* plan,
-                     size_t* off_klist, std::string* why);
+int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, size_t smem_optin,
+                     SketchPlan* plan, size_t* off_klist, std::string* why);
 // Ordered split of the nonempty inner indices into the FFT list (flist)
 // and the direct list (dlist; limit < 0: none); counts[0..1] their lengths;
 // scratch holds 2 x 1024 ints.

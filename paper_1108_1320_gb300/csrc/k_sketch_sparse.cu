@@ -14,6 +14,7 @@
 // product (split across the two sides' warps) and Kahan-compensated
 // accumulation, exactly as in k_sketch_fast.cu.
 #include <algorithm>
+#include <cstdlib>
 
 #include "cms_internal.h"
 #include "warp_fft.cuh"
@@ -46,6 +47,7 @@ struct SparseArgs {
   const int32_t* klist;
   const int32_t* kcount;       // device: length of klist (written by the split kernels)
   int skip_empty;              // 1: a block returns at once when the list is empty
+  int sepy;                    // 1: scatter into per-warp Y buffers kept zero between groups
   const uint32_t* hs;
   int tw_shift, nhi;
   float2* partial;
@@ -62,9 +64,10 @@ template <> __device__ __forceinline__ float ld_val<__nv_bfloat16>(const void* p
   return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[e]);
 }
 
-size_t sparse_smem_bytes(int tw_shift, int nhi) {
+size_t sparse_smem_bytes(int tw_shift, int nhi, bool sepy) {
   return static_cast<size_t>(2 * kG) * kRegion * 8 + static_cast<size_t>(kC) * 16 +
-         (static_cast<size_t>(1) << tw_shift) * 8 + static_cast<size_t>(nhi) * 8;
+         (static_cast<size_t>(1) << tw_shift) * 8 + static_cast<size_t>(nhi) * 8 +
+         (sepy ? static_cast<size_t>(2 * kG) * kC * 8 : 0);
 }
 
 template <typename T>
@@ -74,6 +77,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
   float4* acc = reinterpret_cast<float4*>(sm + static_cast<size_t>(2 * kG) * kRegion * 8);
   float2* tlo = reinterpret_cast<float2*>(acc + kC);
   float2* thi = tlo + (1 << p.tw_shift);
+  // per warp: the scatter target Y (kept zero between groups: each lane
+  // clears what it wrote once the FFT has read it)
+  float2* ysc = thi + p.nhi;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int task = blockIdx.x;
@@ -103,6 +109,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     thi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
   }
   for (int i = tid; i < kC; i += kThreads) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (p.sepy)
+    for (int i = tid; i < 2 * kG * kC; i += kThreads) ysc[i] = make_float2(0.f, 0.f);
   float2 anchor[4];
   float2 step;
   {
@@ -120,6 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
   const int side_w = warp / kG;
   const int g_w = warp % kG;
   float2* region = work + warp * kRegion;
+  float2* ybuf = p.sepy ? ysc + warp * kC : region;
   const float2* partner = work + (warp ^ kG) * kRegion;   // same k slot, other side
   const uint32_t* tab = p.hs + (static_cast<size_t>(t) * 2 + side_w) * p.n;
   const int64_t* ptr = side_w ? p.ptr1 : p.ptr0;
@@ -151,10 +160,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     const uint32_t nrank = __reduce_max_sync(0xFFFFFFFFu, rank);
     for (uint32_t q = 0; q <= nrank; ++q) {
       if (rank == q && !(z2 >> 31)) {
-        float2 y = region[z2];
+        float2 y = ybuf[z2];
         y.x += contrib.x;
         y.y += contrib.y;
-        region[z2] = y;
+        ybuf[z2] = y;
       }
       __syncwarp();
     }
@@ -181,11 +190,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
   int group = 0;
   for (int l0 = l_begin; l0 < l_end; l0 += kG, ++group) {
     const int gcnt = min(kG, l_end - l0);
-    // ---- zero this warp's Y and scatter the nonzeros of its (side, k) ----
-    float4* r4 = reinterpret_cast<float4*>(region);
+    // ---- scatter the nonzeros of this warp's (side, k) into its zero Y ---
+    // (without separate buffers the FFT region is zeroed first)
+    if (!p.sepy) {
+      float4* r4 = reinterpret_cast<float4*>(region);
 #pragma unroll
-    for (int i = 0; i < kC / 2 / 32; ++i) r4[lane + 32 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
+      for (int i = 0; i < kC / 2 / 32; ++i) r4[lane + 32 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
+    }
     if (g_w < gcnt) {
       scatter(pe0 + lane < pe1, px, pv, pw);
       for (int64_t base = pe0 + 32; base < pe1; base += 32) {
@@ -209,7 +221,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     // ---- FFT of length 1024 ----------------------------------------------
     float2 x[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = region[lane + 32 * j];
+    for (int j = 0; j < 32; ++j) x[j] = ybuf[lane + 32 * j];
+    __syncwarp();
+    // leave Y zero for the next group: each lane clears the bucket of its
+    // nonzero (a column of more than 32 nonzeros clears the whole buffer)
+    if (p.sepy && g_w < gcnt) {
+      if (pe1 - pe0 > 32) {
+        float4* y4 = reinterpret_cast<float4*>(ybuf);
+#pragma unroll
+        for (int i = 0; i < kC / 2 / 32; ++i) y4[lane + 32 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else if (pe0 + lane < pe1 && px >= 0 && px < nside) {
+        ybuf[(pw & kBucketMask) & (kC - 1)] = make_float2(0.f, 0.f);
+      }
+    }
     dft32<false>(x);
     // second prefetch level: the column bounds
     int64_t ne0 = 0, ne1 = 0;
@@ -472,8 +496,8 @@ __global__ void k_add_direct(float* __restrict__ c, const double* __restrict__ c
 
 }  // namespace
 
-int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, SketchPlan* plan,
-                     size_t* off_klist, std::string* why) {
+int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, size_t smem_optin,
+                     SketchPlan* plan, size_t* off_klist, std::string* why) {
   SketchPlan p;
   p.b = h->b;
   p.d = h->d;
@@ -489,7 +513,12 @@ int make_sparse_plan(const cms_hashes* h, int64_t n2, int64_t K, int num_sms, Sk
   while ((static_cast<int64_t>(1) << (2 * sh)) < p.b) ++sh;
   p.tw_shift = sh;
   p.nhi = static_cast<int>((p.b + (static_cast<int64_t>(1) << sh) - 1) >> sh);
-  p.smem = sparse_smem_bytes(p.tw_shift, p.nhi);
+  // separate, zero-kept scatter buffers when they fit beside the rest (a
+  // debug switch in the environment keeps the in-place form, the path of
+  // sketches too long for them)
+  p.sparse_sepy = sparse_smem_bytes(p.tw_shift, p.nhi, true) <= smem_optin &&
+                  std::getenv("CMS_SPARSE_INPLACE_Y") == nullptr;
+  p.smem = sparse_smem_bytes(p.tw_shift, p.nhi, p.sparse_sepy);
   p.G = kG;
   p.threads = kThreads;
   const int64_t units = static_cast<int64_t>(p.d) * p.nrows;
@@ -597,6 +626,7 @@ cudaError_t launch_sketch_sparse(const SketchPlan& plan, const cms_hashes* h, co
   a.klist = klist;
   a.kcount = kcount;
   a.skip_empty = skip_empty;
+  a.sepy = plan.sparse_sepy ? 1 : 0;
   a.hs = h->d_hs;
   a.tw_shift = plan.tw_shift;
   a.nhi = plan.nhi;

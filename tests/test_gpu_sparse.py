@@ -66,6 +66,36 @@ def test_sparse_real_values_match_dense_path(cms):
     h.free()
 
 
+@pytest.mark.parametrize("density", [0.02, 0.08])
+def test_sparse_scatter_buffers_in_place_and_separate(cms, monkeypatch, density):
+    # the FFT route scatters into per-warp Y buffers kept zero between groups
+    # (each lane clears its bucket after the FFT reads it; columns of more
+    # than 32 nonzeros, common at density 0.08, clear the whole buffer), or,
+    # when those do not fit (forced here by the library's debug switch),
+    # into the FFT region zeroed every group: the same sketch bit for bit,
+    # and the oracle's
+    n, n2, b, d = 900, 200, 16384, 2
+    g = W.rng(41)
+    A = np.where(g.random((n, n2)) < density, g.standard_normal((n, n2)), 0.0).astype(np.float32)
+    B = np.where(g.random((n2, n)) < density, g.standard_normal((n2, n)), 0.0).astype(np.float32)
+    import scipy.sparse as sp
+    Ac = sp.csc_matrix(A)
+    Br = sp.csr_matrix(B)
+    h = cms.make_hashes(42, n, b, d)
+    T = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev(), dt)   # noqa: E731
+    args = (T(Ac.indptr, torch.int64), T(Ac.indices, torch.int32), T(Ac.data, torch.float32),
+            T(Br.indptr, torch.int64), T(Br.indices, torch.int32), T(Br.data, torch.float32), n, n, h)
+    c_sep = cms.sketch_product_csr(*args)
+    monkeypatch.setenv("CMS_SPARSE_INPLACE_Y", "1")
+    c_inp = cms.sketch_product_csr(*args)
+    monkeypatch.delenv("CMS_SPARSE_INPLACE_Y")
+    cms.check_async()
+    assert torch.equal(c_sep, c_inp)
+    ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), O.make_tables(42, n, b, d))
+    assert O.rel_l2(c_sep.cpu().numpy(), ref) < 1e-5
+    h.free()
+
+
 def test_sparse_without_common_inner_index_is_zero(cms):
     n, b = 200, 2048
     colptr = np.zeros(11, np.int64)
