@@ -27,7 +27,7 @@ using namespace wfft;
 constexpr int kC = kFeC;       // 1024
 constexpr int kG = 4;          // nonempty inner indices per group
 constexpr int kThreads = 256;  // 8 warps = 2 sides x kG
-constexpr int kFlush = 8;      // groups between Kahan folds
+constexpr int kFlush = 16;     // groups between Kahan folds (64 products)
 constexpr int kPitch = 33;
 constexpr int kRegion = 32 * kPitch;
 constexpr int kSplitBlocks = 1024;   // chunks of the inner-index split
@@ -139,6 +139,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
   float2 part[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) part[m] = make_float2(0.f, 0.f);
+  // the only per-group exchange is between the two warps of a k slot (its
+  // two sides): they meet at a 64-thread barrier of their own (1 + k slot)
+  auto pair_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(1 + g_w) : "memory"); };
 
   // one nonzero of the warp's (side, k): its contribution s(x) v w_b^{f1 h(x)}
   // added to Y[h mod C] (lanes with distinct buckets in parallel, colliding
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     // ---- scatter the nonzeros of this warp's (side, k) into its zero Y ---
     // (without separate buffers the FFT region is zeroed first)
     if (!p.sepy) {
+      pair_sync();   // the partner has read this region's published half
       float4* r4 = reinterpret_cast<float4*>(region);
 #pragma unroll
       for (int i = 0; i < kC / 2 / 32; ++i) r4[lane + 32 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -250,7 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
         w = cmul(w, step);
       }
     }
-    __syncwarp();
+    if (p.sepy) pair_sync();   // the partner has read this region's published half
+    else __syncwarp();
 #pragma unroll
     for (int f = 0; f < 32; ++f) region[f * kPitch + lane] = x[f];
     __syncwarp();
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
 #pragma unroll
       for (int m = 0; m < 16; ++m) region[lane + 32 * m] = x[m];
     }
-    __syncthreads();
+    pair_sync();   // the partner's half is published
     if (g_w < gcnt) {
       if (side_w == 0) {
 #pragma unroll
@@ -327,8 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
         kahan_add(a.y, a.w, s.y);
         acc[f] = a;
       }
+      __syncthreads();   // every region read before any warp writes its own again
     }
-    __syncthreads();
   }
   __syncthreads();
   float2* out = p.partial + ((static_cast<size_t>(t) * p.nrows + f1) * p.nkc + kc) * kC;
