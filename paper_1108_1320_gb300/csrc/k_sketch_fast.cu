@@ -41,7 +41,7 @@ constexpr int kC = kFeC;       // 1024: the largest C = P Q
 constexpr int kG = 2;          // inner indices per group
 constexpr int kRows = 2;       // rows f1 per block
 constexpr int kThreads = 256;  // 8 warps = kRows x 2 sides x kG FFTs
-constexpr int kFlush = 16;     // groups between Kahan folds
+constexpr int kFlush = 32;     // groups between Kahan folds (64 products)
 constexpr int kPitch = 33;     // transpose row pitch (float2): conflict-free both ways
 constexpr int kRegion = 32 * kPitch;   // float2 per warp region (>= kC)
 
