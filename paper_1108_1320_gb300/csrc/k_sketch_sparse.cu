@@ -143,21 +143,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
   // two sides): they meet at a 64-thread barrier of their own (1 + k slot)
   auto pair_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(1 + g_w) : "memory"); };
 
-  // one nonzero of the warp's (side, k): its contribution s(x) v w_b^{f1 h(x)}
-  // added to Y[h mod C] (lanes with distinct buckets in parallel, colliding
-  // lanes in lane order)
-  auto scatter = [&](bool valid, int32_t x, float v, uint32_t w) {
-    uint32_t z2 = 0x80000000u | static_cast<uint32_t>(lane);   // unique sentinel
-    float2 contrib = make_float2(0.f, 0.f);
+  // one nonzero of the warp's (side, k): its bucket and contribution
+  // s(x) v w_b^{f1 h(x)} (a lane without one gets a unique sentinel bucket)
+  auto contribution = [&](bool valid, int32_t x, float v, uint32_t w, uint32_t& z2, float2& c) {
+    z2 = 0x80000000u | static_cast<uint32_t>(lane);
+    c = make_float2(0.f, 0.f);
     if (valid && x >= 0 && x < nside) {
       const uint32_t h = w & kBucketMask;
       float2 tw = wb(tlo, thi, mulmod(h, f1, modb), p.tw_shift);
       if (w >> 31) { tw.x = -tw.x; tw.y = -tw.y; }
-      contrib = make_float2(v * tw.x, v * tw.y);
+      c = make_float2(v * tw.x, v * tw.y);
       z2 = h & (kC - 1);
     }
-    // lanes sharing a bucket add in lane order: round q takes each bucket's
-    // q-th lane, so the rounds are as many as the largest multiplicity
+  };
+  // added to Y[z2]: lanes with distinct buckets in parallel, lanes sharing
+  // a bucket in lane order (round q takes each bucket's q-th lane, so the
+  // rounds are as many as the largest multiplicity)
+  auto scatter = [&](uint32_t z2, float2 contrib) {
     const uint32_t same = __match_any_sync(0xFFFFFFFFu, z2);
     const uint32_t rank = __popc(same & ((1u << lane) - 1u));
     const uint32_t nrank = __reduce_max_sync(0xFFFFFFFFu, rank);
@@ -173,21 +175,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
   };
   // The first 32 nonzeros of each group's (side, k) are fetched during the
   // previous group's FFT, one dependent level per FFT stage (inner index,
-  // column bounds, row index and value, hash), so the scatter finds them in
-  // registers; further nonzeros of a long column are loaded when scattered.
+  // column bounds, row index and value, hash), and their buckets and
+  // contributions formed at the end of that group, so the scatter finds
+  // them in registers; further nonzeros of a long column are loaded when
+  // scattered.
   int64_t pe0 = 0, pe1 = 0;
-  int32_t px = -1;
-  float pv = 0.f;
-  uint32_t pw = 0;
-  if (l_begin + g_w < l_end) {
-    const int k = p.klist[l_begin + g_w];
-    pe0 = ptr[k];
-    pe1 = ptr[k + 1];
-    if (pe0 + lane < pe1) {
-      px = idx[pe0 + lane];
-      pv = ld_val<T>(val, pe0 + lane);
-      if (px >= 0 && px < nside) pw = __ldg(tab + px);
+  uint32_t pz2;
+  float2 pc;
+  {
+    int32_t px = -1;
+    float pv = 0.f;
+    uint32_t pw = 0;
+    if (l_begin + g_w < l_end) {
+      const int k = p.klist[l_begin + g_w];
+      pe0 = ptr[k];
+      pe1 = ptr[k + 1];
+      if (pe0 + lane < pe1) {
+        px = idx[pe0 + lane];
+        pv = ld_val<T>(val, pe0 + lane);
+        if (px >= 0 && px < nside) pw = __ldg(tab + px);
+      }
     }
+    contribution(pe0 + lane < pe1, px, pv, pw, pz2, pc);
   }
 
   int group = 0;
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
       __syncwarp();
     }
     if (g_w < gcnt) {
-      scatter(pe0 + lane < pe1, px, pv, pw);
+      scatter(pz2, pc);
       for (int64_t base = pe0 + 32; base < pe1; base += 32) {
         const int64_t e = base + lane;
         const bool valid = e < pe1;
@@ -215,7 +224,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
           v = ld_val<T>(val, e);
           if (x >= 0 && x < nside) w = __ldg(tab + x);
         }
-        scatter(valid, x, v, w);
+        uint32_t z2;
+        float2 c;
+        contribution(valid, x, v, w, z2, c);
+        scatter(z2, c);
       }
     }
     __syncwarp();
@@ -234,8 +246,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
         float4* y4 = reinterpret_cast<float4*>(ybuf);
 #pragma unroll
         for (int i = 0; i < kC / 2 / 32; ++i) y4[lane + 32 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      } else if (pe0 + lane < pe1 && px >= 0 && px < nside) {
-        ybuf[(pw & kBucketMask) & (kC - 1)] = make_float2(0.f, 0.f);
+      } else if (!(pz2 >> 31)) {
+        ybuf[pz2] = make_float2(0.f, 0.f);
       }
     }
     dft32<false>(x);
@@ -303,9 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     }
     pe0 = ne0;
     pe1 = ne1;
-    px = nx;
-    pv = nv;
-    pw = nw;
+    contribution(pe0 + lane < pe1, nx, nv, nw, pz2, pc);
     const bool last = l0 + kG >= l_end;
     if ((group % kFlush) == kFlush - 1 || last) {
       __syncthreads();
