@@ -174,12 +174,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     }
   };
   // The first 32 nonzeros of each group's (side, k) are fetched during the
-  // previous group's FFT, one dependent level per FFT stage (inner index,
-  // column bounds, row index and value, hash), and their buckets and
-  // contributions formed at the end of that group, so the scatter finds
-  // them in registers; further nonzeros of a long column are loaded when
-  // scattered.
-  int64_t pe0 = 0, pe1 = 0;
+  // two previous groups' FFTs, one dependent level per FFT stage (inner
+  // index and column bounds two groups ahead, row index and value and hash
+  // one group ahead), and their buckets and contributions formed at the end
+  // of the previous group, so the scatter finds them in registers; further
+  // nonzeros of a long column are loaded when scattered.
+  int64_t pe0 = 0, pe1 = 0;     // this group's column bounds
+  int64_t ne0 = 0, ne1 = 0;     // the next group's
   uint32_t pz2;
   float2 pc;
   {
@@ -197,6 +198,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
       }
     }
     contribution(pe0 + lane < pe1, px, pv, pw, pz2, pc);
+    if (l_begin + kG + g_w < l_end) {
+      const int k1 = p.klist[l_begin + kG + g_w];
+      ne0 = ptr[k1];
+      ne1 = ptr[k1 + 1];
+    }
   }
 
   int group = 0;
@@ -231,9 +237,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
       }
     }
     __syncwarp();
-    // next group's inner index (first prefetch level)
-    const int ln = l0 + kG + g_w;
-    const int nk = ln < l_end ? p.klist[ln] : -1;
+    // first prefetch level, two groups ahead: the inner index
+    const int ln2 = l0 + 2 * kG + g_w;
+    const int nk2 = ln2 < l_end ? p.klist[ln2] : -1;
     // ---- FFT of length 1024 ----------------------------------------------
     float2 x[32];
 #pragma unroll
@@ -251,11 +257,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
       }
     }
     dft32<false>(x);
-    // second prefetch level: the column bounds
-    int64_t ne0 = 0, ne1 = 0;
-    if (nk >= 0) {
-      ne0 = ptr[nk];
-      ne1 = ptr[nk + 1];
+    // third level, next group: the lane's nonzero (row index and value)
+    int32_t nx = -1;
+    float nv = 0.f;
+    if (ne0 + lane < ne1) {
+      nx = idx[ne0 + lane];
+      nv = ld_val<T>(val, ne0 + lane);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -273,16 +280,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 32; ++j) x[j] = region[lane * kPitch + j];
-    // third level: the lane's nonzero (row index and value)
-    int32_t nx = -1;
-    float nv = 0.f;
-    if (ne0 + lane < ne1) {
-      nx = idx[ne0 + lane];
-      nv = ld_val<T>(val, ne0 + lane);
+    // fourth level, next group: its hash
+    const uint32_t nw = (nx >= 0 && nx < nside) ? __ldg(tab + nx) : 0u;
+    // second level, two groups ahead: the column bounds
+    int64_t qe0 = 0, qe1 = 0;
+    if (nk2 >= 0) {
+      qe0 = ptr[nk2];
+      qe1 = ptr[nk2 + 1];
     }
     dft32<false>(x);
-    // fourth level: its hash
-    const uint32_t nw = (nx >= 0 && nx < nside) ? __ldg(tab + nx) : 0u;
     __syncwarp();
     if (side_w == 0) {
 #pragma unroll
@@ -316,6 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sketch_sparse(SparseArgs p) {
     pe0 = ne0;
     pe1 = ne1;
     contribution(pe0 + lane < pe1, nx, nv, nw, pz2, pc);
+    ne0 = qe0;
+    ne1 = qe1;
     const bool last = l0 + kG >= l_end;
     if ((group % kFlush) == kFlush - 1 || last) {
       __syncthreads();
