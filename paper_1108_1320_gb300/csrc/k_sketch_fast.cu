@@ -86,7 +86,7 @@ struct BatchDesc {
 namespace {
 
 struct SmemLayout {
-  size_t stage, rec_tw, rec_x, work, acc, tlo, thi, wmeta, wdst, ibase, istart, slot_src, bar, total;
+  size_t stage, rec_tw, rec_x, work, acc, tlo, thi, wmeta, wdst, wovb, ibase, istart, slot_src, bar, total;
 };
 
 constexpr int kWarps = kThreads / 32;
@@ -109,6 +109,7 @@ __host__ __device__ inline SmemLayout fast_layout(int npad, uint32_t ecap, int a
   L.thi = o;      o = al16(o + static_cast<size_t>(nhi) * 8);
   L.wmeta = o;    o = al16(o + static_cast<size_t>(kWarps) * kItems * 4);
   L.wdst = o;     o = al16(o + static_cast<size_t>(kWarps) * 32 * kItems * 2);
+  L.wovb = o;     o = al16(o + static_cast<size_t>(kWarps) * 32 * kItems * 4);
   L.ibase = o;    o = al16(o + static_cast<size_t>(kWarps) * kItems * 4);
   L.istart = o;   o = al16(o + static_cast<size_t>(kWarps * kItems + 1) * 4);
   L.slot_src = o; o = al16(o + (static_cast<size_t>(2) * ecap / 32 + 1) * 4);
@@ -147,6 +148,9 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
   float2* thi = reinterpret_cast<float2*>(sm + L.thi);
   uint32_t* wmeta = reinterpret_cast<uint32_t*>(sm + L.wmeta);   // [warp][item]: cnt | side << 8 | overflow steps << 9
   uint16_t* wdst = reinterpret_cast<uint16_t*>(sm + L.wdst);     // [warp][item][lane]: Y slot (row 0, k 0)
+  // [warp][item][lane]: the lane's overflow list, start | length << 16 (both
+  // below n, which the planner keeps under 2^16 for this kernel: 3 npad <= 65535)
+  uint32_t* wovb = reinterpret_cast<uint32_t*>(sm + L.wovb);
   uint32_t* ibase = reinterpret_cast<uint32_t*>(sm + L.ibase);   // [warp][item]: side * ecap + first record
   uint32_t* istart = reinterpret_cast<uint32_t*>(sm + L.istart); // [warp][item]: first stream slot; [64]: total
   uint32_t* slot_src = reinterpret_cast<uint32_t*>(sm + L.slot_src);
@@ -204,7 +208,15 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
     const int item = j * kWarps + slot;
     const int side = item & 1, gi = item >> 1;
     const size_t ts = static_cast<size_t>(t) * 2 + side;
-    wdst[i] = item < 2 * Gq ? static_cast<uint16_t>(side * kG * kRegion + p.dest[(ts * Gq + gi) * 32 + l]) : 0;
+    const uint32_t z = item < 2 * Gq ? p.dest[(ts * Gq + gi) * 32 + l] : 0u;
+    wdst[i] = item < 2 * Gq ? static_cast<uint16_t>(side * kG * kRegion + z) : 0;
+    // the lane's overflow list (the same for every inner index)
+    uint32_t ob = 0;
+    if (item < 2 * Gq && z < static_cast<uint32_t>(C) && ((p.grp[(ts * Gq + gi) * 2 + 1] >> 16) & 0x7FFFu)) {
+      const uint32_t o = p.ovf_off[ts * (C + 1) + z];
+      ob = o | ((p.ovf_off[ts * (C + 1) + z + 1] - o) << 16);
+    }
+    wovb[i] = ob;
   }
   for (int i = tid; i < kRows * kC; i += kThreads) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   // zero the staging tails [n_side, npad): entries x >= n_side read zeros.
@@ -418,12 +430,9 @@ __device__ __forceinline__ void fast_task(const FastArgs& p, const int task, uns
         const uint32_t om = (m >> 9) & 0x7FFFu;
         if (om) {
           const size_t ts = static_cast<size_t>(t) * 2 + (sb ? 1 : 0);
-          const uint32_t z = dst - (sb ? static_cast<uint32_t>(kG * kRegion) : 0u);
-          uint32_t o = 0, o1 = 0;
-          if (z < static_cast<uint32_t>(C)) {
-            o = p.ovf_off[ts * (C + 1) + z];
-            o1 = p.ovf_off[ts * (C + 1) + z + 1];
-          }
+          const uint32_t ob = wovb[(warp * kItems + j) * 32 + lane];
+          uint32_t o = ob & 0xFFFFu;
+          const uint32_t o1 = o + (ob >> 16);
           const uint32_t* ox = p.ovf_x + ts * n;
           const uint32_t* oh = p.ovf_hs + ts * n;
           const uint32_t soff = p.alias || !sb ? 0u : static_cast<uint32_t>(kG * p.npad);

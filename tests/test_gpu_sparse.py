@@ -66,6 +66,37 @@ def test_sparse_real_values_match_dense_path(cms):
     h.free()
 
 
+@pytest.mark.parametrize("K", [1, 2, 3, 5, 7, 9, 13])
+def test_sparse_few_nonempty_inner_indices(cms, K):
+    # K nonempty inner indices (a column of A and a row of B both nonzero)
+    # among n2 = 500: partial groups of the FFT route's four inner indices,
+    # the prefetch of the next two groups running past the list's end, and
+    # chunks of the fixed launch left empty
+    n, n2, b, d = 600, 500, 4096, 3
+    g = W.rng(60 + K)
+    ks = np.sort(g.choice(n2, size=K, replace=False))
+    A = np.zeros((n, n2), np.float32)
+    B = np.zeros((n2, n), np.float32)
+    for k in ks:
+        ra = g.choice(n, size=int(g.integers(1, 40)), replace=False)
+        rb = g.choice(n, size=int(g.integers(1, 40)), replace=False)
+        A[ra, k] = g.standard_normal(ra.size)
+        B[k, rb] = g.standard_normal(rb.size)
+    # inner indices with only one side nonzero add nothing and are skipped
+    A[g.integers(0, n, 20), g.integers(0, n2, 20)] = 1.0
+    import scipy.sparse as sp
+    Ac = sp.csc_matrix(A)
+    Br = sp.csr_matrix(B)
+    h = cms.make_hashes(70 + K, n, b, d)
+    T = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev(), dt)   # noqa: E731
+    c = cms.sketch_product_csr(T(Ac.indptr, torch.int64), T(Ac.indices, torch.int32),
+                               T(Ac.data, torch.float32), T(Br.indptr, torch.int64),
+                               T(Br.indices, torch.int32), T(Br.data, torch.float32), n, n, h)
+    ref = O.sketch_definition(A.astype(np.float64), B.astype(np.float64), O.make_tables(70 + K, n, b, d))
+    assert O.rel_l2(c.cpu().numpy(), ref) < 1e-5
+    h.free()
+
+
 @pytest.mark.parametrize("density", [0.02, 0.08])
 def test_sparse_scatter_buffers_in_place_and_separate(cms, monkeypatch, density):
     # the FFT route scatters into per-warp Y buffers kept zero between groups
