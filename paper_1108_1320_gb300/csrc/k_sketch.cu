@@ -50,23 +50,41 @@ __device__ __forceinline__ float2 w_pow(uint64_t m, int64_t M) {
 // hi[i] = w_b^{i S} for i < nhi (the high half of the warp-specialised
 // kernel's split twiddle w_b^m = w_b^{m mod S} w_b^{(m div S) S}).
 __global__ void k_twiddle_table(float2* __restrict__ tw, int M, float2* __restrict__ hi, int S, int nhi,
-                                int64_t b) {
+                                int64_t b, float2* __restrict__ tw2, int M2) {
+  // blocks [0, nbt): w_M^m; then, when hi is given, nbh blocks of w_b^{i S};
+  // then, when tw2 is given, the blocks of w_M2^m (one launch for all three)
   const int nbt = (M + 255) / 256;
-  if (static_cast<int>(blockIdx.x) < nbt) {
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += nbt * blockDim.x) {
+  const int nbh = hi != nullptr ? (nhi + 255) / 256 : 0;
+  const int blk = static_cast<int>(blockIdx.x);
+  if (blk < nbt) {
+    const int m = blk * blockDim.x + threadIdx.x;
+    if (m < M) {
       double s, c;
       sincospi(2.0 * static_cast<double>(m) / static_cast<double>(M), &s, &c);
       tw[m] = make_float2(static_cast<float>(c), static_cast<float>(-s));
     }
-  } else if (hi != nullptr) {
-    const int i = (static_cast<int>(blockIdx.x) - nbt) * blockDim.x + threadIdx.x;
+  } else if (blk < nbt + nbh) {
+    const int i = (blk - nbt) * blockDim.x + threadIdx.x;
     if (i < nhi) {
       const double a = 2.0 * static_cast<double>(static_cast<int64_t>(i) * S) / static_cast<double>(b);
       double s, c;
       sincospi(a, &s, &c);
       hi[i] = make_float2(static_cast<float>(c), static_cast<float>(-s));
     }
+  } else if (tw2 != nullptr) {
+    const int m = (blk - nbt - nbh) * blockDim.x + threadIdx.x;
+    if (m < M2) {
+      double s, c;
+      sincospi(2.0 * static_cast<double>(m) / static_cast<double>(M2), &s, &c);
+      tw2[m] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+    }
   }
+}
+
+// Grid of k_twiddle_table for the three tables.
+unsigned twiddle_blocks(int M, const float2* hi, int nhi, const float2* tw2, int M2) {
+  return static_cast<unsigned>((M + 255) / 256 + (hi != nullptr ? (nhi + 255) / 256 : 0) +
+                               (tw2 != nullptr ? (M2 + 255) / 256 : 0));
 }
 
 // Front-end twiddle of sorted entry e of table (t, side) for row f1:
@@ -500,16 +518,12 @@ cudaError_t launch_sketch(const SketchPlan& plan, const cms_hashes* h, const voi
   }
   {
     ProfScope prof_scope("k_twiddle_table", s);
-    // with the warp-specialised kernel's high twiddles in extra blocks
-    const int nhb = plan.ws ? (plan.nhi + 255) / 256 : 0;
-    k_twiddle_table<<<static_cast<unsigned>((plan.C + 255) / 256 + nhb), 256, 0, s>>>(
-        twC, static_cast<int>(plan.C), plan.ws ? reinterpret_cast<float2*>(ws + plan.off_thi) : nullptr,
-        1 << plan.tw_shift, plan.nhi, plan.b);
-  }
-  {
-    ProfScope prof_scope("k_twiddle_table", s);
-    k_twiddle_table<<<static_cast<unsigned>((plan.R + 255) / 256), 256, 0, s>>>(twR, static_cast<int>(plan.R),
-                                                                                nullptr, 1, 0, plan.b);
+    // with the warp-specialised kernel's high twiddles and the length-R
+    // table in extra blocks
+    float2* hi = plan.ws ? reinterpret_cast<float2*>(ws + plan.off_thi) : nullptr;
+    const int R = static_cast<int>(plan.R);
+    k_twiddle_table<<<twiddle_blocks(static_cast<int>(plan.C), hi, plan.nhi, twR, R), 256, 0, s>>>(
+        twC, static_cast<int>(plan.C), hi, 1 << plan.tw_shift, plan.nhi, plan.b, twR, R);
   }
   if (!plan.fast) {
     dim3 grid(static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 64)), plan.nrows, 2 * plan.d);
@@ -583,11 +597,7 @@ cudaError_t launch_frontend_twiddles(const SketchPlan& plan, const cms_hashes* h
 cudaError_t launch_twiddle_tables(float2* twC, int C, float2* twR, int R, cudaStream_t s) {
   {
     ProfScope prof_scope("k_twiddle_table", s);
-    k_twiddle_table<<<static_cast<unsigned>((C + 255) / 256), 256, 0, s>>>(twC, C, nullptr, 1, 0, 1);
-  }
-  {
-    ProfScope prof_scope("k_twiddle_table", s);
-    k_twiddle_table<<<static_cast<unsigned>((R + 255) / 256), 256, 0, s>>>(twR, R, nullptr, 1, 0, 1);
+    k_twiddle_table<<<twiddle_blocks(C, nullptr, 0, twR, R), 256, 0, s>>>(twC, C, nullptr, 1, 0, 1, twR, R);
   }
   return cudaGetLastError();
 }

@@ -363,8 +363,8 @@ k_frontend_tables(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ 
 // entries of its bucket (x and its packed hash).  The entries are ordered bank-aware: step r gives
 // each lane, in order of ascending count, its remaining entry whose bank
 // (x mod 32) is least used at this step so far; padding lanes all read
-// x = n (one address).  The lanes choose four at a time, so the groups run
-// as separate warps spread over the SMs.
+// x = n (one address).  The order is sequential over the lanes, so the
+// groups run as separate warps spread over the SMs.
 __global__ void __launch_bounds__(32)
 k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__ perm,
                    const uint32_t* __restrict__ off, uint32_t n, uint32_t ecap, uint32_t* __restrict__ rec_x,
@@ -372,7 +372,6 @@ k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__
                    const uint32_t* __restrict__ ovf_off, uint32_t* __restrict__ ovf_x,
                    uint32_t* __restrict__ ovf_hs, int C) {
   constexpr uint32_t kCap = static_cast<uint32_t>(kFeCap);
-  constexpr uint32_t kTurn = 4;   // lanes choosing at once
   __shared__ uint32_t ub[32];
   const int L = (C + 31) / 32;
   const int ts = blockIdx.x / L, g = blockIdx.x % L;
@@ -421,12 +420,8 @@ k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__
     __syncwarp();
     if (lane == 0 && done) ub[n & 31u] = 1;
     __syncwarp();
-    // the lanes take their turns four at a time (in rank order): each of a
-    // round's lanes chooses from the bank counts left by the rounds before
-    // it, then all four add their choices
-    for (uint32_t k = __popc(done); k < 32; k += kTurn) {
-      const bool mine = rank >= k && rank < k + kTurn;
-      if (mine) {
+    for (uint32_t k = __popc(done); k < 32; ++k) {
+      if (rank == k) {
         uint32_t best = r, bu = ub[xs[r] & 31u];
 #pragma unroll
         for (uint32_t i = r + 1; i < kCap; ++i) {
@@ -443,9 +438,8 @@ k_frontend_records(const uint32_t* __restrict__ hs, const uint32_t* __restrict__
             xs[i] = tx; wsv[i] = tw;
           }
         }
+        ub[xs[r] & 31u] += 1;
       }
-      __syncwarp();
-      if (mine) atomicAdd(&ub[xs[r] & 31u], 1u);
       __syncwarp();
     }
   }
