@@ -25,6 +25,12 @@
  *    stream or thread) races, as does freeing it; order them on one stream or
  *    synchronise.  Workspaces and outputs follow the same rule as any device
  *    buffer: one in-flight writer at a time.
+ *  - Environment (for tests of alternative code paths; both give the same
+ *    results as the default paths): CMS_WS_SMEM_SWAP makes the warp-
+ *    specialised kernel swap half spectra through shared memory instead of
+ *    tensor memory; CMS_SPARSE_INPLACE_Y makes the sparse-input route scatter
+ *    into its FFT regions (zeroed every group) instead of per-warp buffers.
+ *    Both are read at each call.
  */
 #ifndef CMS_H
 #define CMS_H
